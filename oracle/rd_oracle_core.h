@@ -1,0 +1,139 @@
+/*
+ * Scalar-generic core of the FP64 oracle.  TEST INFRASTRUCTURE ONLY: see rd_oracle.c.
+ *
+ * Included twice by rd_oracle.c: once with SCALAR = double (the oracle proper) and once with
+ * SCALAR = double complex (complex-step differentiation: perturbing one input by i*h gives
+ * d(output)/d(input) = Im(output)/h exactly up to rounding, because every operation used here
+ * is analytic; comparisons and floor() act on real parts only).
+ *
+ * Macros expected: SCALAR, SUFFIX, S_SQRT(x), RE(x).
+ */
+#define RDO_CAT2(a, b) a##_##b
+#define RDO_CAT(a, b) RDO_CAT2(a, b)
+#define FN(name) RDO_CAT(name, SUFFIX)
+
+/* beta = u / sqrt(1 + |u|^2): Algorithm 1, velocity of a particle from its momentum p/(mc). */
+static void FN(beta_of)(const SCALAR u[3], SCALAR beta[3])
+{
+    SCALAR uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    SCALAR g = S_SQRT(1.0 + uu);
+    beta[0] = u[0] / g;
+    beta[1] = u[1] / g;
+    beta[2] = u[2] / g;
+}
+
+/*
+ * Eq. 1 (Lienard-Wiechert fields, Gaussian units with e -> q and c = 1), evaluated with the
+ * particle quantities of one trajectory sample:
+ *   E = q (n - beta) / (gamma^2 kappa^3 R^2)  +  q n x ((n - beta) x betadot) / (kappa^3 R)
+ *   B = n x E,   kappa = 1 - beta.n,   1/gamma^2 = 1 - beta^2 (Section 2 definitions)
+ * n is the unit vector from the particle to the detector cell (Section 2 text; Algorithm 1 prints
+ * the opposite sign, which would reverse the outgoing wave).
+ * flags bit 1 keeps the first (velocity, "near") term, bit 2 the second (acceleration, "far").
+ */
+static void FN(lw_field)(const SCALAR x[3], const SCALAR beta[3], const SCALAR bdot[3],
+                         const double P[3], double q, int flags, SCALAR E[3], SCALAR B[3])
+{
+    SCALAR d[3] = {P[0] - x[0], P[1] - x[1], P[2] - x[2]};
+    SCALAR R = S_SQRT(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    SCALAR n[3] = {d[0] / R, d[1] / R, d[2] / R};
+    SCALAR nb[3] = {n[0] - beta[0], n[1] - beta[1], n[2] - beta[2]};
+    SCALAR kappa = 1.0 - (beta[0] * n[0] + beta[1] * n[1] + beta[2] * n[2]);
+    SCALAR inv_gamma2 = 1.0 - (beta[0] * beta[0] + beta[1] * beta[1] + beta[2] * beta[2]);
+    SCALAR k3 = kappa * kappa * kappa;
+    for (int i = 0; i < 3; ++i) E[i] = 0.0;
+    if (flags & 1) {
+        SCALAR c = q * inv_gamma2 / (k3 * R * R);
+        for (int i = 0; i < 3; ++i) E[i] += c * nb[i];
+    }
+    if (flags & 2) {
+        /* w = (n - beta) x betadot ; far = n x w */
+        SCALAR w[3] = {nb[1] * bdot[2] - nb[2] * bdot[1],
+                       nb[2] * bdot[0] - nb[0] * bdot[2],
+                       nb[0] * bdot[1] - nb[1] * bdot[0]};
+        SCALAR f[3] = {n[1] * w[2] - n[2] * w[1],
+                       n[2] * w[0] - n[0] * w[2],
+                       n[0] * w[1] - n[1] * w[0]};
+        SCALAR c = q / (k3 * R);
+        for (int i = 0; i < 3; ++i) E[i] += c * f[i];
+    }
+    B[0] = n[1] * E[2] - n[2] * E[1];
+    B[1] = n[2] * E[0] - n[0] * E[2];
+    B[2] = n[0] * E[1] - n[1] * E[0];
+}
+
+/*
+ * Arrival time of sample k at cell P in bin units of the cell's time axis (Eq. 2, c = 1):
+ *   t_det = t_k + |x_k - P|,  t_k = t0 + k dt,   u = (t_det - T0) / dt_det
+ * evaluated in this fixed order, with no fused multiply-add:
+ *   t_k = t0 + (k*dt);  R = sqrt((dx*dx + dy*dy) + dz*dz);  u = ((t_k + R) - T0) * inv_dt_det.
+ */
+static SCALAR FN(bin_coord)(double t0, long long k, double dt, const SCALAR x[3], const double P[3],
+                            double T0, double inv_dt_det)
+{
+    double tk = t0 + (double)k * dt;
+    SCALAR dx = P[0] - x[0], dy = P[1] - x[1], dz = P[2] - x[2];
+    SCALAR R = S_SQRT((dx * dx + dy * dy) + dz * dz);
+    SCALAR tdet = tk + R;
+    return (tdet - T0) * inv_dt_det;
+}
+
+/*
+ * Integrating deposit of one interval (Section 3.2, Algorithm 2 read as the integrator
+ * detector): the field F (E then B, 6 values) is held constant over the arrival interval
+ * [a, c] (bin units) and bin b = [b, b+1) receives F * |[a, c] ∩ [b, b+1)|.
+ * Parts of the interval outside [0, n_bins) are dropped; the return value is 1 if anything
+ * was dropped, else 0.
+ */
+static int FN(deposit_interval)(SCALAR a, SCALAR c, const SCALAR F[6], int n_bins, SCALAR* row)
+{
+    double ra = RE(a), rc = RE(c);
+    int clipped = (ra < 0.0) || (rc > (double)n_bins);
+    if (rc <= 0.0 || ra >= (double)n_bins) return 1;
+    double flo = floor(ra), fhi = floor(rc);
+    long long lo = flo < 0.0 ? 0 : (long long)flo;
+    long long hi = fhi > (double)(n_bins - 1) ? (long long)(n_bins - 1) : (long long)fhi;
+    for (long long b = lo; b <= hi; ++b) {
+        SCALAR s = (ra > (double)b) ? a : (SCALAR)(double)b;
+        SCALAR e = (rc < (double)(b + 1)) ? c : (SCALAR)(double)(b + 1);
+        SCALAR w = e - s;
+        if (RE(w) > 0.0) {
+            for (int i = 0; i < 6; ++i) row[6 * b + i] += F[i] * w;
+        }
+    }
+    return clipped;
+}
+
+/*
+ * One (cell, particle) pair: Algorithm 1 inner body for every interval k = 1..S.
+ *   beta_k from u_k; betadot_k = (beta_k - beta_{k-1}) / dt (backward difference);
+ *   the field of sample k is held over [t_det,k-1, t_det,k] (the algorithm passes the current
+ *   step's field to the interpolator); sample 0 only provides the previous quantities.
+ * x, u point at this particle's samples [n_samples][3]; row is [n_bins][6] (E xyz, B xyz).
+ * Returns the number of intervals that had a part outside the window.
+ */
+static long long FN(pixel_particle)(const SCALAR* x, const SCALAR* u, int n_samples, double q,
+                                    double t0, double dt, const double P[3], double T0,
+                                    double inv_dt_det, int n_bins, int flags, SCALAR* row)
+{
+    SCALAR beta_prev[3], beta[3], bdot[3], E[3], B[3], F[6];
+    long long clipped = 0;
+    FN(beta_of)(u, beta_prev);
+    SCALAR a = FN(bin_coord)(t0, 0, dt, x, P, T0, inv_dt_det);
+    for (int k = 1; k < n_samples; ++k) {
+        const SCALAR* xk = x + 3 * (size_t)k;
+        FN(beta_of)(u + 3 * (size_t)k, beta);
+        for (int i = 0; i < 3; ++i) bdot[i] = (beta[i] - beta_prev[i]) / dt;
+        FN(lw_field)(xk, beta, bdot, P, q, flags, E, B);
+        for (int i = 0; i < 3; ++i) { F[i] = E[i]; F[3 + i] = B[i]; }
+        SCALAR c = FN(bin_coord)(t0, k, dt, xk, P, T0, inv_dt_det);
+        clipped += FN(deposit_interval)(a, c, F, n_bins, row);
+        a = c;
+        for (int i = 0; i < 3; ++i) beta_prev[i] = beta[i];
+    }
+    return clipped;
+}
+
+#undef FN
+#undef RDO_CAT
+#undef RDO_CAT2

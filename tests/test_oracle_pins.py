@@ -1,0 +1,499 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by electrodynamics.
+
+None of these compares the oracle with itself: each checks it against a worked example, a
+closed form, an independent derivation (Lienard-Wiechert potentials differentiated numerically
+in 40-digit arithmetic), a conservation law, an invariance, or brute force.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import alg2
+from paper_2302_14812_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------------------------
+# Algorithm 2: worked example, sum rule, brute force, second transcription
+# --------------------------------------------------------------------------------------------
+def _golden_cases():
+    cases = {}
+    with open(os.path.join(GOLDEN, "alg2_worked_example.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            name, dtd, nb, tp, tc, s, w = line.split()
+            c = cases.setdefault(name, dict(dt_det=float(dtd), n_bins=int(nb), t_prev=float(tp),
+                                            t_cur=float(tc), w={}))
+            c["w"][int(s)] = float(w)
+    return cases
+
+
+@pytest.mark.parametrize("case", ["cross", "same"])
+def test_worked_example_c_oracle(oracle_lib, case):
+    """Section 3.2 worked example: slots and weights of one interval (C oracle, bin units)."""
+    c = _golden_cases()[case]
+    F = np.array([1.0, -2.0, 0.5, 3.0, 0.0, -1.0])
+    row, clipped = oracle.deposit_interval(c["t_prev"] / c["dt_det"], c["t_cur"] / c["dt_det"], F,
+                                           c["n_bins"])
+    want = np.zeros((c["n_bins"], 6))
+    for s, w in c["w"].items():
+        want[s] = F * w
+    assert clipped == 0
+    np.testing.assert_allclose(row, want, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("case", ["cross", "same"])
+def test_worked_example_alg2_transcription(case):
+    """Same example through the step-by-step transcription of Algorithm 2 (absolute times)."""
+    c = _golden_cases()[case]
+    t_array = [i * c["dt_det"] for i in range(c["n_bins"] + 1)]
+    row = [[0.0] * 6 for _ in range(c["n_bins"])]
+    alg2.radiation_interpolator(row, [1.0] * 6, c["t_cur"], c["t_prev"], t_array, c["dt_det"])
+    got = np.array(row)[:, 0]
+    want = np.zeros(c["n_bins"])
+    for s, w in c["w"].items():
+        want[s] = w
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-14)
+
+
+def test_two_transcriptions_agree(oracle_lib):
+    """C oracle (cell-major, bin units) vs Algorithm 1+2 transcription (particle-major, absolute
+    times), including cells with their own time origin and intervals clipped by the window."""
+    tr = W.random_smooth(4, 60, 0.05, max_u=3.0, seed=21)
+    cells = np.array([[10.0, 1.0, 2.0], [-3.0, 9.0, 1.0], [2.0, -2.0, -11.0], [0.5, 7.0, -6.0]])
+    det = W.Detector(cells, np.array([0.0, 0.3, -0.2, 0.7]), 8.0, 0.07, 64)
+    E, B, clipped = oracle.deposit(tr, det)
+    ref = np.array(alg2.radiation_calculator(tr.x.tolist(), tr.u.tolist(), tr.q.tolist(), tr.t0,
+                                             tr.dt, cells.tolist(), det.t_min, det.dt_det,
+                                             det.n_bins, det.pix_t0.tolist()))
+    assert clipped > 0                      # the window cuts some intervals
+    scale = np.abs(E).max()
+    np.testing.assert_allclose(E, ref[..., :3], rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(B, ref[..., 3:], rtol=0, atol=1e-12 * np.abs(B).max())
+
+
+def _interval_table(tr, det, p, j):
+    """Per-interval field and bin-unit endpoints, from the oracle's single-point functions."""
+    P = det.pix_pos[j]
+    T0 = det.t_min + (0.0 if det.pix_t0 is None else det.pix_t0[j])
+    inv = 1.0 / det.dt_det
+    us = [oracle.bin_coord(tr.t0, k, tr.dt, tr.x[p, k], P, T0, inv) for k in range(tr.n_samples)]
+    F = []
+    for k in range(1, tr.n_samples):
+        b = oracle.beta(tr.u[p, k])
+        bp = oracle.beta(tr.u[p, k - 1])
+        E, B = oracle.field(tr.x[p, k], b, (b - bp) / tr.dt, P, tr.q[p], det.flags)
+        F.append(np.concatenate([E, B]))
+    return np.array(us), np.array(F)
+
+
+def test_sum_rule(oracle_lib):
+    """With every arrival inside the window, sum_b E[b] = sum_k F_k (u_k - u_{k-1}): each interval
+    deposits exactly its length (integrator detector, Section 3.2)."""
+    tr = W.random_smooth(2, 120, 0.03, max_u=4.0, seed=3)
+    cells = np.array([[20.0, 0.0, 0.0], [0.0, -15.0, 3.0]])
+    det = W.Detector(cells, None, 5.0, 0.011, 4096)
+    E, B, clipped = oracle.deposit(tr, det)
+    assert clipped == 0
+    for j in range(2):
+        want = np.zeros(6)
+        for p in range(tr.n_part):
+            us, F = _interval_table(tr, det, p, j)
+            want += (F * np.diff(us)[:, None]).sum(0)
+        got = np.concatenate([E[j].sum(0), B[j].sum(0)])
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
+
+
+def test_brute_force_sampling(oracle_lib):
+    """Each bin equals the mean of the piecewise-constant received field sampled at 40000 points
+    per bin (midpoint rule) -- an integral evaluated without interval/bin overlap logic."""
+    tr = W.random_smooth(1, 25, 0.08, max_u=2.0, seed=5)
+    cells = np.array([[6.0, 2.0, -1.0]])
+    us0, _ = _interval_table(tr, W.Detector(cells, None, 0.0, 1.0, 1), 0, 0)
+    t_lo = us0.min() - 0.3
+    dt_det = 0.05
+    n_bins = int(math.ceil((us0.max() - t_lo) / dt_det)) + 6
+    det = W.Detector(cells, None, t_lo, dt_det, n_bins)
+    E, B, clipped = oracle.deposit(tr, det)
+    assert clipped == 0
+    us, F = _interval_table(tr, det, 0, 0)
+    M = 40000
+    pts = (np.arange(n_bins)[:, None] + (np.arange(M)[None, :] + 0.5) / M).ravel()
+    idx = np.searchsorted(us, pts, side="right")          # interval k covers [us[k-1], us[k])
+    inside = (idx >= 1) & (idx < len(us))
+    vals = np.zeros((pts.size, 6))
+    vals[inside] = F[idx[inside] - 1]
+    bf = vals.reshape(n_bins, M, 6).mean(1)
+    got = np.concatenate([E[0], B[0]], axis=1)
+    assert np.abs(got - bf).max() < 2e-4 * np.abs(got).max()
+
+
+# --------------------------------------------------------------------------------------------
+# Eq. 1: closed forms and an independent derivation from the potentials
+# --------------------------------------------------------------------------------------------
+def test_static_charge_coulomb(oracle_lib):
+    """A charge at rest: every full bin holds the Coulomb field q n / R^2, and B = 0."""
+    n_s = 50
+    x = np.tile(np.array([0.3, -0.2, 0.1]), (1, n_s + 1, 1))
+    tr = W.Trajectories(x, np.zeros_like(x), np.array([-2.5]), 0.0, 0.1)
+    P = np.array([4.0, 1.0, -2.0])
+    det = W.Detector(P[None], None, 0.0, 0.25, 40)
+    E, B, _ = oracle.deposit(tr, det)
+    d = P - x[0, 0]
+    R = np.linalg.norm(d)
+    coul = -2.5 * d / R ** 3
+    first = int(math.ceil(R / 0.25)) + 1
+    last = int(math.floor((R + n_s * 0.1) / 0.25)) - 1
+    np.testing.assert_allclose(E[0, first:last], np.tile(coul, (last - first, 1)), rtol=1e-13)
+    assert np.abs(B).max() < 1e-16
+
+
+def _retarded_uniform(x0, beta, P, t_obs):
+    """Retarded time of a charge x(t) = x0 + beta t seen at (P, t_obs): closed-form root."""
+    D = P - x0
+    b2 = beta @ beta
+    a = b2 - 1.0
+    bq = 2.0 * (t_obs - D @ beta)
+    c = D @ D - t_obs ** 2
+    roots = np.roots([a, bq, c])
+    roots = roots[np.isreal(roots)].real
+    return roots[roots < t_obs].max()
+
+
+def test_uniform_motion_present_position_form(oracle_lib):
+    """Velocity field of uniform motion equals the present-position form of the boosted Coulomb
+    field, E = q (1-b^2) r / (r^3 (1 - b^2 sin^2 psi)^{3/2}), and B = beta x E (textbook closed
+    forms).  This fixes the n direction, the kappa^3 and 1/gamma^2 factors, and B = n x E."""
+    rng = np.random.default_rng(8)
+    for _ in range(20):
+        beta = rng.normal(size=3)
+        beta *= rng.uniform(0.1, 0.95) / np.linalg.norm(beta)
+        x0 = rng.normal(size=3)
+        P = rng.normal(size=3) * 10.0
+        t_obs = 3.0
+        tr_ = _retarded_uniform(x0, beta, P, t_obs)
+        xr = x0 + beta * tr_
+        E, B = oracle.field(xr, beta, np.zeros(3), P, q=1.7, flags=3)
+        r = P - (x0 + beta * t_obs)
+        rn = np.linalg.norm(r)
+        b2 = beta @ beta
+        sin2 = 1.0 - (r @ beta) ** 2 / (rn * rn * b2)
+        want = 1.7 * (1.0 - b2) * r / (rn ** 3 * (1.0 - b2 * sin2) ** 1.5)
+        np.testing.assert_allclose(E, want, rtol=1e-11, atol=1e-14 * np.abs(want).max())
+        np.testing.assert_allclose(B, np.cross(beta, want), rtol=1e-10, atol=1e-13 * np.abs(want).max())
+
+
+def test_uniform_motion_far_term_exactly_zero(oracle_lib):
+    """Constant momentum => betadot = 0 bitwise => the acceleration term deposits exact zeros."""
+    tr = W.uniform_motion(3, 80, 0.05, speed=0.9, seed=2)
+    det = W.Detector(W.spherical_cap(4, 30.0, 0.5), None, 25.0, 0.05, 256, flags=W.RD_FAR)
+    E, B, _ = oracle.deposit(tr, det)
+    assert np.all(E == 0.0) and np.all(B == 0.0)
+    det.flags = W.RD_NEAR
+    E2, _, _ = oracle.deposit(tr, det)
+    assert np.abs(E2).max() > 0.0
+
+
+def test_field_from_potentials_mpmath(oracle_lib):
+    """Eq. 1 against E = -grad(phi) - dA/dt, B = curl A of the Lienard-Wiechert potentials
+    phi = q/(kappa R), A = q beta/(kappa R) at the retarded time, differentiated numerically in
+    40-digit arithmetic, for a relativistic circular orbit (gamma = 3), near and far observers.
+    Fixes both terms of Eq. 1 with their signs and powers, the direction of n, and B = n x E."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    gam = mp.mpf(3)
+    beta0 = mp.sqrt(1 - 1 / gam ** 2)
+    rad = mp.mpf(1)
+    om = beta0 / rad
+    q = mp.mpf("-1.3")
+
+    def xt(t):
+        return mp.matrix([rad * mp.cos(om * t), rad * mp.sin(om * t), 0])
+
+    def bt(t):
+        return mp.matrix([-rad * om * mp.sin(om * t), rad * om * mp.cos(om * t), 0])
+
+    def at(t):
+        return mp.matrix([-rad * om ** 2 * mp.cos(om * t), -rad * om ** 2 * mp.sin(om * t), 0])
+
+    def retarded(P, t):
+        f = lambda tr_: t - tr_ - mp.norm(P - xt(tr_))
+        return mp.findroot(f, t - mp.norm(P))
+
+    def pot(P, t):
+        tr_ = retarded(P, t)
+        d = P - xt(tr_)
+        R = mp.norm(d)
+        n = d / R
+        b = bt(tr_)
+        kap = 1 - (b.T * n)[0]
+        return q / (kap * R), q * b / (kap * R)
+
+    rng = np.random.default_rng(4)
+    for P_np in (np.array([2.5, -1.0, 0.7]), np.array([-0.4, 3.0, -2.0]),
+                 rng.normal(size=3) * 40.0):
+        P = mp.matrix([mp.mpf(float(c)) for c in P_np])
+        t = mp.mpf("0.77")
+        e = [mp.matrix([1, 0, 0]), mp.matrix([0, 1, 0]), mp.matrix([0, 0, 1])]
+        grad_phi = [mp.diff(lambda s, i=i: pot(P + s * e[i], t)[0], 0) for i in range(3)]
+        dA_dt = [mp.diff(lambda s, i=i: pot(P, t + s)[1][i], 0) for i in range(3)]
+        dA = [[mp.diff(lambda s, i=i, j=j: pot(P + s * e[j], t)[1][i], 0) for j in range(3)]
+              for i in range(3)]
+        E_ref = np.array([float(-grad_phi[i] - dA_dt[i]) for i in range(3)])
+        B_ref = np.array([float(dA[2][1] - dA[1][2]), float(dA[0][2] - dA[2][0]),
+                          float(dA[1][0] - dA[0][1])])
+        tr_ = retarded(P, t)
+        E, B = oracle.field([float(c) for c in xt(tr_)], [float(c) for c in bt(tr_)],
+                            [float(c) for c in at(tr_)], P_np, q=float(q), flags=3)
+        np.testing.assert_allclose(E, E_ref, rtol=1e-10, atol=1e-12 * np.abs(E_ref).max())
+        np.testing.assert_allclose(B, B_ref, rtol=1e-10, atol=1e-12 * np.abs(B_ref).max())
+
+
+# --------------------------------------------------------------------------------------------
+# end-to-end: radiated energy, spectra, invariances
+# --------------------------------------------------------------------------------------------
+def _sphere_pixels(radius, n_theta, n_phi, axis_dir="z"):
+    """Gauss-Legendre nodes in cos(theta) x uniform phi on a sphere; returns positions, weights."""
+    xg, wg = np.polynomial.legendre.leggauss(n_theta)
+    ph = 2.0 * math.pi * (np.arange(n_phi) + 0.5) / n_phi
+    ct, pp = np.meshgrid(xg, ph, indexing="ij")
+    st = np.sqrt(1.0 - ct * ct)
+    pos = radius * np.stack([st * np.cos(pp), st * np.sin(pp), ct], axis=-1).reshape(-1, 3)
+    w = np.repeat(wg, n_phi) * (2.0 * math.pi / n_phi)
+    return pos, w
+
+
+def _received_energy(E, B, pos, w, dt_det):
+    """sum_pixels w R^2 sum_bins (E x B).n dt_det / (4 pi)  (Poynting flux, c = 1)."""
+    n = pos / np.linalg.norm(pos, axis=1, keepdims=True)
+    R2 = np.sum(pos * pos, axis=1)
+    S = np.einsum("pbc,pc->pb", np.cross(E, B), n)
+    return float(np.sum(w * R2 * S.sum(1)) * dt_det / (4.0 * math.pi))
+
+
+def test_larmor_dipole_energy(oracle_lib):
+    """Non-relativistic dipole x = a sin(w t) z (a w = 1e-3): received energy through a sphere
+    at 1e4 wavelengths equals the Larmor energy (2/3) q^2 int |betadot|^2 dt = q^2 a^2 w^4 T/3."""
+    q, a, w0 = 1.0, 1e-3, 1.0
+    period = 2.0 * math.pi / w0
+    n_per, n_steps = 10, 4000
+    dt = n_per * period / n_steps
+    t = dt * np.arange(n_steps + 1)
+    z = a * np.sin(w0 * t)
+    bz = a * w0 * np.cos(w0 * t)
+    uz = bz / np.sqrt(1.0 - bz * bz)
+    x = np.zeros((1, n_steps + 1, 3))
+    x[0, :, 2] = z
+    u = np.zeros_like(x)
+    u[0, :, 2] = uz
+    tr = W.Trajectories(x, u, np.array([q]), 0.0, dt)
+    Rs = 1e4 * period
+    pos, wts = _sphere_pixels(Rs, 8, 1)
+    dt_det = period / 200.0
+    n_bins = int((n_per * period + 4.0 * a) / dt_det) + 40
+    det = W.Detector(pos, None, Rs - 2.0 * a - 10 * dt_det, dt_det, n_bins)
+    E, B, clipped = oracle.deposit(tr, det)
+    assert clipped == 0
+    got = _received_energy(E, B, pos, wts, dt_det)
+    want = q * q * a * a * w0 ** 4 * n_per * period / 3.0
+    assert abs(got / want - 1.0) < 1e-3
+
+
+def test_lienard_circular_energy(oracle_lib):
+    """Relativistic circular orbit (gamma = 2): energy received over a sphere equals the Lienard
+    power (2/3) q^2 gamma^4 |betadot|^2 (beta perpendicular to betadot) times the emission time."""
+    gam, rad = 2.0, 1.0
+    n_orb, per_orb = 2, 1000
+    tr = W.circular_orbit(gamma=gam, radius=rad, n_steps=n_orb * per_orb, dt_frac=1.0 / per_orb)
+    beta = math.sqrt(1.0 - 1.0 / gam ** 2)
+    period = 2.0 * math.pi * rad / beta
+    Rs = 2e3
+    pos, wts = _sphere_pixels(Rs, 48, 4)
+    dt_det = period / 2000.0
+    n_bins = int((n_orb * period + 2.5 * rad) / dt_det) + 40
+    det = W.Detector(pos, None, Rs - rad - 10 * dt_det, dt_det, n_bins)
+    E, B, clipped = oracle.deposit(tr, det)
+    assert clipped == 0
+    got = _received_energy(E, B, pos, wts, dt_det)
+    bdot = beta * beta / rad
+    want = (2.0 / 3.0) * gam ** 4 * bdot ** 2 * n_orb * period
+    assert abs(got / want - 1.0) < 2e-3
+
+
+def _harmonic_power(sig, n_per_period, m_max):
+    """|FFT|^2 at harmonics 1..m_max of a record holding an integer number of periods."""
+    spec = np.fft.rfft(sig, axis=0)
+    n_periods = sig.shape[0] // n_per_period
+    return np.array([np.sum(np.abs(spec[m * n_periods]) ** 2) for m in range(1, m_max + 1)])
+
+
+def test_circular_orbit_schott_harmonics(oracle_lib):
+    """Observer in the orbit plane of a circular orbit (gamma = 2): the power in harmonic m of the
+    received field follows m^2 J'_m(m beta)^2 (Schott's series at theta = pi/2), after dividing
+    out the bin box filter sinc^2(m w0 dt_det / 2)."""
+    sp = pytest.importorskip("scipy.special")
+    gam, rad = 2.0, 1.0
+    beta = math.sqrt(1.0 - 1.0 / gam ** 2)
+    per_orb, n_orb = 2000, 6
+    tr = W.circular_orbit(gamma=gam, radius=rad, n_steps=n_orb * per_orb, dt_frac=1.0 / per_orb)
+    period = 2.0 * math.pi * rad / beta
+    Rs = 1e4
+    P = np.array([[Rs, 0.0, 0.0]])
+    dt_det = period / 400.0
+    # keep whole periods of steady signal: skip the first and last orbit of arrivals
+    t_min = Rs - rad + period
+    n_bins = (n_orb - 3) * 400
+    det = W.Detector(P, None, t_min, dt_det, n_bins, flags=W.RD_FAR)
+    E, _, _ = oracle.deposit(tr, det)
+    m_max = 8
+    pw = _harmonic_power(E[0], 400, m_max)
+    m = np.arange(1, m_max + 1)
+    box = np.sinc(m * dt_det / period) ** 2          # np.sinc(x) = sin(pi x)/(pi x)
+    theory = m * m * sp.jvp(m, m * beta) ** 2
+    ratio_got = (pw / box) / (pw[0] / box[0])
+    ratio_want = theory / theory[0]
+    np.testing.assert_allclose(ratio_got, ratio_want, rtol=1e-2)
+
+
+def test_undulator_on_axis_spectrum(oracle_lib):
+    """Planar undulator, observer on axis: the received field repeats with period
+    T_u (1 - beta_z), so the fundamental sits at w_u/(1 - beta_z) ~ 2 gamma^2 w_u/(1 + K^2/2);
+    even harmonics vanish on axis and the 3rd/1st energy ratio follows the textbook
+    F_n(K) = n^2 K^2/(1+K^2/2)^2 [J_(n-1)/2(Y) - J_(n+1)/2(Y)]^2, Y = n K^2 / (4 (1 + K^2/2))."""
+    sp = pytest.importorskip("scipy.special")
+    gam, K, n_per = 10.0, 1.0, 40
+    steps_per = 200
+    tr = W.undulator_ensemble(n_part=1, gamma=gam, K=K, n_periods=n_per, n_steps=n_per * steps_per,
+                              sigma_offset=0.0, seed=1)
+    tr.x[:, :, :2] -= tr.x[:, :1, :2]
+    bz_bar, w_u = W.undulator_params(gam, K)
+    T_u = 2.0 * math.pi / w_u
+    T_rad = T_u * (1.0 - bz_bar)
+    Rs = 1e5
+    P = np.array([[0.0, 0.0, Rs]])
+    n_per_T = 64
+    dt_det = T_rad / n_per_T
+    n_keep = n_per - 6
+    det = W.Detector(P, None, Rs + 3.0 * T_rad, dt_det, n_keep * n_per_T, flags=W.RD_FAR)
+    E, _, _ = oracle.deposit(tr, det)
+    sig = E[0][:, 1] - E[0][:, 1].mean()
+    spec = np.abs(np.fft.rfft(sig)) ** 2
+    peak = int(np.argmax(spec))
+    assert peak == n_keep                               # fundamental at exactly 1/T_rad
+    pw = _harmonic_power(sig[:, None], n_per_T, 3)
+    assert pw[1] < 1e-6 * pw[0]                         # no even harmonic on axis
+
+    def F(n):
+        Y = n * K * K / (4.0 * (1.0 + 0.5 * K * K))
+        return n * n * K * K / (1.0 + 0.5 * K * K) ** 2 * (sp.jv((n - 1) // 2, Y) - sp.jv((n + 1) // 2, Y)) ** 2
+
+    box = np.sinc(np.array([1.0, 3.0]) / n_per_T) ** 2
+    got = (pw[2] / box[1]) / (pw[0] / box[0])
+    # the textbook F_n assumes gamma >> 1 (terms of order 1/gamma^2 dropped)
+    assert abs(got / (F(3) / F(1)) - 1.0) < 3e-2
+
+
+def test_time_shift_invariance(oracle_lib):
+    """Shifting the emission times and the window together changes nothing; shifting the
+    emission alone by m bins moves the record by m bins (Eq. 2 is translation covariant)."""
+    tr = W.random_smooth(2, 100, 0.05, max_u=2.0, seed=9)
+    cells = W.spherical_cap(3, 25.0, 0.4)
+    det = W.Detector(cells, None, 20.0, 0.02, 700)
+    E, B, _ = oracle.deposit(tr, det)
+    shift = 37 * det.dt_det
+    tr2 = W.Trajectories(tr.x, tr.u, tr.q, tr.t0 + shift, tr.dt)
+    det2 = W.Detector(cells, None, det.t_min + shift, det.dt_det, det.n_bins)
+    E2, B2, _ = oracle.deposit(tr2, det2)
+    sc = np.abs(E).max()
+    np.testing.assert_allclose(E2, E, rtol=0, atol=1e-9 * sc)
+    E3, _, _ = oracle.deposit(tr2, det)
+    np.testing.assert_allclose(E3[:, 37 + 2:], E[:, 2:-37], rtol=0, atol=1e-9 * sc)
+
+
+def test_circular_rotation_invariance(oracle_lib):
+    """64-pixel arc in the orbit plane, pixel j at azimuth j w0 2dt: pixel j records pixel 0's
+    field rotated by that angle and delayed by exactly j bins (dt_det = 2 dt)."""
+    tr, det = W.config_circular()
+    E, B, clipped = oracle.deposit(tr, det)
+    assert clipped == 0
+    u0 = np.array([oracle.bin_coord(tr.t0, k, tr.dt, tr.x[0, k], det.pix_pos[0], det.t_min,
+                                    1.0 / det.dt_det) for k in range(tr.n_samples)])
+    sc = np.abs(E).max()
+    for j in (1, 5, 17, 63):
+        phi = math.atan2(det.pix_pos[j, 1], det.pix_pos[j, 0])
+        Rz = np.array([[math.cos(phi), -math.sin(phi), 0], [math.sin(phi), math.cos(phi), 0], [0, 0, 1]])
+        lo = int(math.ceil(u0[1])) + 1
+        hi = int(math.floor(u0[tr.n_steps - 2 * j])) - 1
+        np.testing.assert_allclose(E[j, lo + j:hi + j], E[0, lo:hi] @ Rz.T, rtol=0, atol=1e-8 * sc)
+        np.testing.assert_allclose(B[j, lo + j:hi + j], B[0, lo:hi] @ Rz.T, rtol=0, atol=1e-8 * sc)
+
+
+def test_superposition_and_charge_sign(oracle_lib):
+    """Deposits add over particles; equal and opposite charges on one trajectory cancel."""
+    tr = W.random_smooth(5, 60, 0.04, max_u=2.0, seed=12)
+    det = W.Detector(W.spherical_cap(3, 30.0, 0.5), None, 25.0, 0.03, 300)
+    E, B, _ = oracle.deposit(tr, det)
+    Ea, Ba, _ = oracle.deposit(tr.subset([0, 2]), det)
+    Eb, Bb, _ = oracle.deposit(tr.subset([1, 3, 4]), det)
+    np.testing.assert_allclose(Ea + Eb, E, rtol=0, atol=1e-13 * np.abs(E).max())
+    pair = tr.subset([1, 1])
+    pair.q = np.array([1.0, -1.0])
+    Ep, Bp, _ = oracle.deposit(pair, det)
+    E1, B1, _ = oracle.deposit(tr.subset([1]), det)
+    # per bin the two particles' sums cancel up to the rounding of the running sum
+    assert np.abs(Ep).max() <= 1e-14 * np.abs(E1).max()
+    assert np.abs(Bp).max() <= 1e-14 * np.abs(B1).max()
+
+
+def test_near_far_split(oracle_lib):
+    """The two terms of Eq. 1 deposit separately: near + far = both."""
+    tr = W.random_smooth(2, 50, 0.05, max_u=2.0, seed=13)
+    det = W.Detector(W.spherical_cap(2, 12.0, 0.5), None, 9.0, 0.04, 200)
+    E, _, _ = oracle.deposit(tr, det)
+    det.flags = W.RD_NEAR
+    En, _, _ = oracle.deposit(tr, det)
+    det.flags = W.RD_FAR
+    Ef, _, _ = oracle.deposit(tr, det)
+    np.testing.assert_allclose(En + Ef, E, rtol=0, atol=1e-13 * np.abs(E).max())
+
+
+def test_rejects_superluminal_chords(oracle_lib):
+    """A chord speed |x_k - x_(k-1)|/dt >= 1 is rejected (arrival times need not increase)."""
+    tr = W.random_smooth(1, 20, 0.05, seed=1)
+    tr.x[0, 7] = tr.x[0, 6] + np.array([0.06, 0.0, 0.0])
+    det = W.Detector(np.array([[10.0, 0, 0]]), None, 0.0, 0.1, 100)
+    with pytest.raises(oracle.OracleError):
+        oracle.deposit(tr, det)
+
+
+# --------------------------------------------------------------------------------------------
+# exact derivative (complex step) used for the adjoint: pinned by central differences
+# --------------------------------------------------------------------------------------------
+def test_complex_step_matches_central_differences(oracle_lib):
+    tr = W.random_smooth(2, 40, 0.05, max_u=2.0, seed=17)
+    det = W.Detector(W.spherical_cap(2, 15.0, 0.4), None, 12.0, 0.013, 500)
+    rng = np.random.default_rng(0)
+    for _ in range(6):
+        p = int(rng.integers(0, 2))
+        k = int(rng.integers(0, tr.n_samples))
+        which = ["x", "u"][int(rng.integers(0, 2))]
+        c = int(rng.integers(0, 3))
+        dE, dB = oracle.deposit_dir(tr, det, p, k, which, c)
+        h = 1e-6
+        arr = tr.x if which == "x" else tr.u
+        base = arr[p, k, c]
+        arr[p, k, c] = base + h
+        Ep, Bp, _ = oracle.deposit(tr, det)
+        arr[p, k, c] = base - h
+        Em, Bm, _ = oracle.deposit(tr, det)
+        arr[p, k, c] = base
+        fd = (Ep - Em) / (2 * h)
+        g = rng.normal(size=dE.shape)
+        # projected on a random cotangent (what the adjoint computes)
+        a, b = float(np.sum(g * dE)), float(np.sum(g * fd))
+        assert abs(a - b) <= 1e-5 * max(abs(a), 1e-3 * np.abs(dE).sum())
