@@ -1,0 +1,176 @@
+/*
+ * rd.h -- C ABI of a GB300 (sm_103a) library for the spatiotemporal radiation deposit of
+ * RaDiO (Pardal, Sainte-Marie, Reboul-Salze, Fonseca, Vieira: "RaDiO: an efficient
+ * spatiotemporal radiation diagnostic for particle-in-cell codes").
+ *
+ * For every (particle, trajectory interval, detector cell) triple the library
+ *   - evaluates the Lienard-Wiechert fields of Eq. 1 (velocity and acceleration terms) from the
+ *     particle's position, beta = u/sqrt(1+u^2) and betadot = (beta_k - beta_{k-1})/dt
+ *     (Algorithm 1);
+ *   - computes the arrival time t_det = t_k + |x_k - x_cell| (Eq. 2, c = 1);
+ *   - deposits E and B = n x E into the cell's time bins with the integrating interpolation of
+ *     Section 3.2 / Algorithm 2: the field of sample k is held constant between the arrival
+ *     times of samples k-1 and k, and bin b receives field * overlap / dt_det.
+ *
+ * Units: c = 1; momenta u = p/(m c) = gamma*beta; each particle carries a signed charge q (a
+ * macro-particle radiates as one point charge N*q, Section 4.2); fields are q / length^2.
+ *
+ * Conventions for every call:
+ *   - All entry points return an rd_status; nothing aborts.  rd_last_error() gives a message for
+ *     the last failing call on the calling thread.
+ *   - Work is enqueued on the caller's CUDA stream and is asynchronous unless stated otherwise.
+ *   - Errors found by kernels (invalid trajectory samples, a bounded wait that ran out, an index
+ *     outside the detector) are latched in the detector and returned by the next synchronising
+ *     call (rd_read_fields to host memory, rd_get_stats, rd_synchronize).
+ *   - A detector object may be used from one host thread at a time.
+ */
+#ifndef RD_H
+#define RD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RD_API __attribute__((visibility("default")))
+#else
+#define RD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t / CUstream).  NULL selects the legacy default stream. */
+struct CUstream_st;
+typedef struct CUstream_st* rd_stream;
+
+/* Opaque detector: geometry, time axis, field accumulators and scratch; owned by the library. */
+typedef struct rd_detector rd_detector;
+
+typedef enum {
+    RD_OK = 0,
+    RD_ERR_ARG = 1,      /* invalid argument (null pointer, bad size, bad enum value)           */
+    RD_ERR_CUDA = 2,     /* a CUDA runtime call failed                                          */
+    RD_ERR_OOM = 3,      /* device or pinned-host allocation failed                             */
+    RD_ERR_STATE = 4,    /* call not valid for this detector (e.g. wrong precision)             */
+    RD_ERR_TIMEOUT = 5,  /* a kernel's bounded wait ran out; its work was abandoned              */
+    RD_ERR_BOUNDS = 6,   /* a kernel found an index outside the detector (internal error)       */
+    RD_ERR_INPUT = 7     /* trajectory rejected: chord speed |x_k - x_{k-1}|/dt >= 1 or not finite */
+} rd_status;
+
+/* precision of a detector */
+enum { RD_FP64 = 0, RD_MIXED = 1 };
+/* terms of Eq. 1 to evaluate (bit set); the default is both */
+enum { RD_NEAR = 1, RD_FAR = 2 };
+/* where a caller buffer lives */
+enum { RD_MEM_DEVICE = 0, RD_MEM_HOST = 1 };
+/* element type of caller field / gradient-seed buffers */
+enum { RD_F32 = 0, RD_F64 = 1 };
+
+/*
+ * Virtual detector (Section 3.1): n_pix cells at positions pix_pos, each with a uniform time
+ * axis of n_bins bins; bin b of cell j covers
+ *     [t_min + pix_t0[j] + b*dt_det,  t_min + pix_t0[j] + (b+1)*dt_det).
+ * pix_t0 == NULL means 0 for every cell (one global time array as in the paper).
+ * The arrays are read during rd_create_detector only (copied); `mem` says where they live.
+ * precision: RD_MIXED -- fields and accumulation in FP32, arrival times FP64-accurate;
+ *            RD_FP64  -- everything in FP64.
+ */
+typedef struct {
+    int32_t n_pix;             /* >= 1                                                          */
+    const double* pix_pos;     /* [n_pix][3]                                                    */
+    const double* pix_t0;      /* [n_pix] or NULL                                               */
+    int32_t mem;               /* RD_MEM_DEVICE or RD_MEM_HOST for pix_pos / pix_t0             */
+    double t_min;
+    double dt_det;             /* > 0                                                           */
+    int32_t n_bins;            /* >= 1                                                          */
+    int32_t precision;         /* RD_MIXED or RD_FP64                                           */
+    int32_t flags;             /* RD_NEAR | RD_FAR (0 is read as both)                           */
+} rd_detector_desc;
+
+/*
+ * Trajectories (Algorithm 1 inputs): n_part particles, each with n_samples = S+1 samples at
+ * t_k = t0 + k*dt, k = 0..S.  Interval k (1..S) lies between samples k-1 and k; sample 0 only
+ * provides the previous position and velocity.  Layout [n_part][n_samples][3], row-major FP64.
+ * q: [n_part] charges, or NULL for q = 1.  All three arrays live where `mem` says; host arrays
+ * are copied to the device inside the call (pinned host memory copies asynchronously).
+ * The caller keeps ownership and must keep the arrays alive until the stream has passed the call.
+ */
+typedef struct {
+    int32_t n_part;            /* >= 0                                                          */
+    int32_t n_samples;         /* >= 1 (S = n_samples - 1 intervals)                            */
+    const double* x;           /* positions  [n_part][n_samples][3]                             */
+    const double* u;           /* momenta gamma*beta [n_part][n_samples][3]                     */
+    const double* q;           /* [n_part] or NULL                                              */
+    int32_t mem;               /* RD_MEM_DEVICE or RD_MEM_HOST                                  */
+    double t0;
+    double dt;                 /* > 0                                                           */
+} rd_traj;
+
+/* Counters of a detector (rd_get_stats). */
+typedef struct {
+    int64_t n_clipped;         /* (particle, interval, cell) triples whose arrival interval had
+                                  a part outside the cell's window (that part is dropped,
+                                  Algorithm 1 window test read as clipping)                    */
+    int64_t n_deposits;        /* triples processed since creation / last rd_zero_fields        */
+    uint32_t device_errors;    /* bit set of latched kernel errors (1<<RD_ERR_*)               */
+    int64_t kernel_launches;   /* deposit-kernel launches timed since the last rd_get_stats     */
+    double kernel_ms;          /* their summed duration (CUDA events on the caller's stream)    */
+} rd_stats;
+
+/*
+ * Create a detector and zero its fields.  Allocates device memory for the cell table and the
+ * accumulators ([n_pix][n_bins] E and B: 32 bytes per bin in RD_MIXED, 48 in RD_FP64).
+ * On success *out owns the detector (free with rd_destroy).  Errors: RD_ERR_ARG, RD_ERR_OOM,
+ * RD_ERR_CUDA.  The device is the one current on the calling thread.
+ */
+RD_API rd_status rd_create_detector(const rd_detector_desc* desc, rd_stream stream, rd_detector** out);
+
+/* Release every resource of the detector (synchronises its device work first).  NULL is a no-op. */
+RD_API rd_status rd_destroy(rd_detector* det);
+
+/* Set all fields and counters of the detector to zero (asynchronous). */
+RD_API rd_status rd_zero_fields(rd_detector* det, rd_stream stream);
+
+/*
+ * Deposit the radiation of the given trajectories: ACCUMULATES (+=) into the detector, so a run
+ * can be split over particle chunks or over step chunks that share one sample (the last sample
+ * of chunk i is sample 0 of chunk i+1; the run-time mode of Section 3.1).
+ * Uses Eq. 1, Eq. 2 and the integrating deposit of Section 3.2 for every (particle, interval,
+ * cell) triple.  Scratch for per-sample records is kept in the detector and grown as needed.
+ * Errors: RD_ERR_ARG (bad sizes or pointers), RD_ERR_OOM, RD_ERR_CUDA; invalid samples are
+ * reported as RD_ERR_INPUT by the next synchronising call (their deposits are undefined).
+ */
+RD_API rd_status rd_deposit_trajectories(rd_detector* det, const rd_traj* traj, rd_stream stream);
+
+/*
+ * Copy the accumulated fields out as E[n_pix][n_bins][3] and B[n_pix][n_bins][3] (either may be
+ * NULL) of type dtype (RD_F32 / RD_F64) into memory of kind mem.  To host memory the call
+ * synchronises the stream and then reports latched kernel errors; to device memory it is
+ * asynchronous.  Errors: RD_ERR_ARG, RD_ERR_CUDA, RD_ERR_OOM, latched errors.
+ */
+RD_API rd_status rd_read_fields(rd_detector* det, void* E, void* B, int32_t dtype, int32_t mem,
+                         rd_stream stream);
+
+/* Synchronise the stream and return (then clear) latched kernel errors. */
+RD_API rd_status rd_synchronize(rd_detector* det, rd_stream stream);
+
+/* Synchronise the stream and fill *out with the detector's counters (does not clear errors).
+ * kernel_launches / kernel_ms cover the deposit kernels timed since the previous call (then reset). */
+RD_API rd_status rd_get_stats(rd_detector* det, rd_stream stream, rd_stats* out);
+
+/* Enable (1) or disable (0) timing of every deposit-kernel launch with a pair of CUDA events
+ * recorded on the launch stream around it (read back through rd_get_stats). */
+RD_API rd_status rd_set_timing(rd_detector* det, int32_t enable);
+
+/* Message for the last failing call on this thread ("" if none).  Valid until the next call. */
+RD_API const char* rd_last_error(void);
+
+/* Library version string. */
+RD_API const char* rd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RD_H */

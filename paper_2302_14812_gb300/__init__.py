@@ -1,0 +1,302 @@
+"""Python binding of the radiation-deposit library (the C ABI of include/rd.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA kernels of librd.so.
+There is no fallback: if the library cannot be loaded, every call raises.
+
+Low level: functions named exactly like the C entry points (rd_create_detector, ...) taking
+ctypes structures / raw pointers and raising RDError on a non-zero status.
+High level: RadiationDetector, which accepts torch tensors (CUDA or CPU) or numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+from .build import build as build_library
+
+__all__ = [
+    "RD_OK", "RD_ERR_ARG", "RD_ERR_CUDA", "RD_ERR_OOM", "RD_ERR_STATE", "RD_ERR_TIMEOUT",
+    "RD_ERR_BOUNDS", "RD_ERR_INPUT", "RD_FP64", "RD_MIXED", "RD_NEAR", "RD_FAR", "RD_MEM_DEVICE",
+    "RD_MEM_HOST", "RD_F32", "RD_F64", "RDError", "rd_detector_desc", "rd_traj", "rd_stats",
+    "load_library", "library_path", "rd_create_detector", "rd_destroy", "rd_zero_fields",
+    "rd_deposit_trajectories", "rd_read_fields", "rd_synchronize", "rd_get_stats",
+    "rd_set_timing", "rd_last_error", "rd_version", "RadiationDetector", "build_library",
+]
+
+RD_OK, RD_ERR_ARG, RD_ERR_CUDA, RD_ERR_OOM, RD_ERR_STATE, RD_ERR_TIMEOUT, RD_ERR_BOUNDS, RD_ERR_INPUT = range(8)
+RD_FP64, RD_MIXED = 0, 1
+RD_NEAR, RD_FAR = 1, 2
+RD_MEM_DEVICE, RD_MEM_HOST = 0, 1
+RD_F32, RD_F64 = 0, 1
+
+_STATUS = {0: "RD_OK", 1: "RD_ERR_ARG", 2: "RD_ERR_CUDA", 3: "RD_ERR_OOM", 4: "RD_ERR_STATE",
+           5: "RD_ERR_TIMEOUT", 6: "RD_ERR_BOUNDS", 7: "RD_ERR_INPUT"}
+
+
+class RDError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rd_detector_desc(ctypes.Structure):
+    _fields_ = [("n_pix", ctypes.c_int32), ("pix_pos", ctypes.c_void_p), ("pix_t0", ctypes.c_void_p),
+                ("mem", ctypes.c_int32), ("t_min", ctypes.c_double), ("dt_det", ctypes.c_double),
+                ("n_bins", ctypes.c_int32), ("precision", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class rd_traj(ctypes.Structure):
+    _fields_ = [("n_part", ctypes.c_int32), ("n_samples", ctypes.c_int32), ("x", ctypes.c_void_p),
+                ("u", ctypes.c_void_p), ("q", ctypes.c_void_p), ("mem", ctypes.c_int32),
+                ("t0", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
+class rd_stats(ctypes.Structure):
+    _fields_ = [("n_clipped", ctypes.c_int64), ("n_deposits", ctypes.c_int64),
+                ("device_errors", ctypes.c_uint32), ("kernel_launches", ctypes.c_int64),
+                ("kernel_ms", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library(build_if_missing: bool = True):
+    """Load librd.so (building it first if it is missing and nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            build_library()
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"CUDA library not built: {_LIB_PATH}")
+        lib = ctypes.CDLL(_LIB_PATH)
+        P, I = ctypes.c_void_p, ctypes.c_int32
+        sig = {
+            "rd_create_detector": ([ctypes.POINTER(rd_detector_desc), P, ctypes.POINTER(P)], I),
+            "rd_destroy": ([P], I),
+            "rd_zero_fields": ([P, P], I),
+            "rd_deposit_trajectories": ([P, ctypes.POINTER(rd_traj), P], I),
+            "rd_read_fields": ([P, P, P, I, I, P], I),
+            "rd_synchronize": ([P, P], I),
+            "rd_get_stats": ([P, P, ctypes.POINTER(rd_stats)], I),
+            "rd_set_timing": ([P, I], I),
+            "rd_last_error": ([], ctypes.c_char_p),
+            "rd_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != RD_OK:
+        raise RDError(status, where, load_library().rd_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+# --------------------------------------------------------------------------------------------
+# C entry points, one to one
+# --------------------------------------------------------------------------------------------
+def rd_create_detector(desc: rd_detector_desc, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().rd_create_detector(ctypes.byref(desc), _stream_ptr(stream), ctypes.byref(h)),
+           "rd_create_detector")
+    return h.value
+
+
+def rd_destroy(det: int) -> None:
+    _check(load_library().rd_destroy(det), "rd_destroy")
+
+
+def rd_zero_fields(det: int, stream=None) -> None:
+    _check(load_library().rd_zero_fields(det, _stream_ptr(stream)), "rd_zero_fields")
+
+
+def rd_deposit_trajectories(det: int, traj: rd_traj, stream=None) -> None:
+    _check(load_library().rd_deposit_trajectories(det, ctypes.byref(traj), _stream_ptr(stream)),
+           "rd_deposit_trajectories")
+
+
+def rd_read_fields(det: int, E_ptr, B_ptr, dtype: int, mem: int, stream=None) -> None:
+    _check(load_library().rd_read_fields(det, E_ptr, B_ptr, dtype, mem, _stream_ptr(stream)),
+           "rd_read_fields")
+
+
+def rd_synchronize(det: int, stream=None) -> None:
+    _check(load_library().rd_synchronize(det, _stream_ptr(stream)), "rd_synchronize")
+
+
+def rd_get_stats(det: int, stream=None) -> rd_stats:
+    st = rd_stats()
+    _check(load_library().rd_get_stats(det, _stream_ptr(stream), ctypes.byref(st)), "rd_get_stats")
+    return st
+
+
+def rd_set_timing(det: int, enable: bool) -> None:
+    _check(load_library().rd_set_timing(det, 1 if enable else 0), "rd_set_timing")
+
+
+def rd_last_error() -> str:
+    return load_library().rd_last_error().decode(errors="replace")
+
+
+def rd_version() -> str:
+    return load_library().rd_version().decode()
+
+
+# --------------------------------------------------------------------------------------------
+# array marshalling
+# --------------------------------------------------------------------------------------------
+def _as_f64(a, keep):
+    """(pointer, mem, n_elements) of an FP64 C-contiguous view of a torch tensor or array."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            t = a.detach()
+            if t.dtype != torch.float64 or not t.is_contiguous():
+                t = t.to(torch.float64).contiguous()
+            keep.append(t)
+            return t.data_ptr(), (RD_MEM_DEVICE if t.is_cuda else RD_MEM_HOST), t.numel()
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    keep.append(arr)
+    return arr.ctypes.data, RD_MEM_HOST, arr.size
+
+
+class RadiationDetector:
+    """A virtual detector on the GPU (see include/rd.h for the semantics).
+
+    pix_pos [n_pix][3]; bin b of cell j covers [t_min + pix_t0[j] + b dt_det, ... + dt_det).
+    precision: "mixed" (FP32 fields, FP64-accurate arrival times) or "fp64".
+    """
+
+    def __init__(self, pix_pos, t_min: float, dt_det: float, n_bins: int, pix_t0=None,
+                 precision: str = "mixed", flags: int = RD_NEAR | RD_FAR, stream=None):
+        keep = []
+        pp, pmem, n = _as_f64(pix_pos, keep)
+        if n % 3:
+            raise ValueError("pix_pos must be [n_pix][3]")
+        desc = rd_detector_desc()
+        desc.n_pix = n // 3
+        desc.pix_pos = pp
+        desc.mem = pmem
+        if pix_t0 is not None:
+            tp, tmem, nt = _as_f64(pix_t0, keep)
+            if nt != n // 3 or tmem != pmem:
+                raise ValueError("pix_t0 must be [n_pix] in the same memory as pix_pos")
+            desc.pix_t0 = tp
+        desc.t_min = float(t_min)
+        desc.dt_det = float(dt_det)
+        desc.n_bins = int(n_bins)
+        desc.precision = {"mixed": RD_MIXED, "fp64": RD_FP64}[precision]
+        desc.flags = int(flags)
+        self.n_pix, self.n_bins, self.precision = n // 3, int(n_bins), precision
+        self.t_min, self.dt_det = float(t_min), float(dt_det)
+        self._h = rd_create_detector(desc, stream)
+
+    @classmethod
+    def from_workload(cls, det, precision: str = "mixed", stream=None):
+        return cls(det.pix_pos, det.t_min, det.dt_det, det.n_bins, det.pix_t0, precision, det.flags, stream)
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def traj_struct(self, x, u, q=None, t0: float = 0.0, dt: float = 1.0, keep=None):
+        keep = [] if keep is None else keep
+        xp, xmem, nx = _as_f64(x, keep)
+        up, umem, nu = _as_f64(u, keep)
+        shape = tuple(x.shape)
+        if len(shape) != 3 or shape[2] != 3 or nx != nu or xmem != umem:
+            raise ValueError("x and u must both be [n_part][n_samples][3] in the same memory")
+        t = rd_traj()
+        t.n_part, t.n_samples = shape[0], shape[1]
+        t.x, t.u, t.mem = xp, up, xmem
+        if q is not None:
+            qp, qmem, nq = _as_f64(q, keep)
+            if nq != shape[0] or qmem != xmem:
+                raise ValueError("q must be [n_part] in the same memory as x")
+            t.q = qp
+        t.t0, t.dt = float(t0), float(dt)
+        return t, keep
+
+    def deposit(self, x, u, q=None, t0: float = 0.0, dt: float = 1.0, stream=None):
+        """Accumulate the radiation of trajectories x, u ([n_part][n_samples][3])."""
+        t, keep = self.traj_struct(x, u, q, t0, dt)
+        rd_deposit_trajectories(self._h, t, stream)
+        self._keep = keep      # inputs stay referenced until the next call
+
+    def deposit_traj(self, tr, stream=None):
+        self.deposit(tr.x, tr.u, tr.q, tr.t0, tr.dt, stream)
+
+    def zero(self, stream=None):
+        rd_zero_fields(self._h, stream)
+
+    def read(self, dtype: str = "float64", device: str = "cpu", stream=None):
+        """(E, B), each [n_pix][n_bins][3]; numpy on "cpu", torch tensors on "cuda"."""
+        code = RD_F32 if dtype == "float32" else RD_F64
+        if device == "cpu":
+            E = np.empty((self.n_pix, self.n_bins, 3), dtype=np.float32 if code == RD_F32 else np.float64)
+            B = np.empty_like(E)
+            rd_read_fields(self._h, E.ctypes.data, B.ctypes.data, code, RD_MEM_HOST, stream)
+            return E, B
+        import torch
+        tdt = torch.float32 if code == RD_F32 else torch.float64
+        E = torch.empty((self.n_pix, self.n_bins, 3), dtype=tdt, device=device)
+        B = torch.empty_like(E)
+        rd_read_fields(self._h, E.data_ptr(), B.data_ptr(), code, RD_MEM_DEVICE, stream)
+        return E, B
+
+    def synchronize(self, stream=None):
+        rd_synchronize(self._h, stream)
+
+    def stats(self, stream=None) -> rd_stats:
+        return rd_get_stats(self._h, stream)
+
+    def set_timing(self, enable: bool = True):
+        rd_set_timing(self._h, enable)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            rd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,420 @@
+// Host side of the C ABI declared in include/rd.h: argument checks, device memory of the
+// detector, per-call scratch, particle chunking and kernel launches.  No entry point allocates
+// on the hot path once a detector's scratch has reached the working size.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "rd_internal.cuh"
+
+using namespace rd;
+
+struct rd_detector {
+    int device = 0;
+    int n_pix = 0;
+    int n_bins = 0;
+    int precision = RD_MIXED;
+    int flags = RD_NEAR | RD_FAR;
+    double t_min = 0.0;
+    double dt_det = 1.0;
+    D4* cells = nullptr;             // [n_pix]
+    void* fields = nullptr;          // internal accumulators
+    size_t field_bytes = 0;
+    DevCounters* counters = nullptr;
+    void* rec = nullptr;             // per-sample records
+    size_t rec_bytes = 0;
+    void* stage = nullptr;           // device copy of host trajectories
+    size_t stage_bytes = 0;
+    void* readback = nullptr;        // conversion buffer for host reads
+    size_t readback_bytes = 0;
+    long long n_deposits = 0;
+    int chunk_override = 0;          // intervals per work item (0 = automatic)
+    bool timing = false;             // record CUDA events around deposit launches
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
+    long long timed_launches = 0;
+    double timed_ms = 0.0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+rd_status fail(rd_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+rd_status cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(RD_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(RD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define RD_CUDA(call, what)                              \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Grow a scratch buffer (contents not kept).  Waits for the stream before freeing the old one.
+rd_status ensure(void** buf, size_t* have, size_t need, cudaStream_t s, const char* what)
+{
+    if (*have >= need) return RD_OK;
+    if (*buf) {
+        RD_CUDA(cudaStreamSynchronize(s), what);
+        RD_CUDA(cudaFree(*buf), what);
+        *buf = nullptr;
+        *have = 0;
+    }
+    size_t bytes = std::max(need, (size_t)(1u << 20));
+    RD_CUDA(cudaMalloc(buf, bytes), what);
+    *have = bytes;
+    return RD_OK;
+}
+
+rd_status latched(const DevCounters& c)
+{
+    if (c.errors & ERRBIT_INPUT)
+        return fail(RD_ERR_INPUT, "trajectory rejected: a chord speed |x_k - x_{k-1}|/dt >= 1 or a "
+                                  "non-finite sample");
+    if (c.errors & ERRBIT_TIMEOUT)
+        return fail(RD_ERR_TIMEOUT, "a kernel's bounded wait ran out; its work was abandoned");
+    if (c.errors & ERRBIT_BOUNDS) return fail(RD_ERR_BOUNDS, "a kernel index left the detector");
+    return RD_OK;
+}
+
+rd_status check_traj(const rd_traj* t)
+{
+    if (!t) return fail(RD_ERR_ARG, "traj is NULL");
+    if (t->n_part < 0 || t->n_samples < 1)
+        return fail(RD_ERR_ARG, "bad trajectory shape n_part=%d n_samples=%d", t->n_part, t->n_samples);
+    if (!(t->dt > 0.0) || !isfinite(t->dt) || !isfinite(t->t0))
+        return fail(RD_ERR_ARG, "dt must be finite and > 0 and t0 finite");
+    if (t->mem != RD_MEM_DEVICE && t->mem != RD_MEM_HOST) return fail(RD_ERR_ARG, "bad traj->mem");
+    if (t->n_part > 0 && (!t->x || !t->u)) return fail(RD_ERR_ARG, "traj x/u is NULL");
+    return RD_OK;
+}
+
+// Intervals per work item: the default unless the grid would leave the GPU idle.
+int choose_chunk(const rd_detector* d, int n_part, int S, int n_cell_blocks)
+{
+    if (d->chunk_override > 0) return std::min(d->chunk_override, S);
+    int chunk = std::min(kDefaultChunk, S);
+    const long long want = 152LL * 8;   // resident CTAs for a few waves
+    while (chunk > 64 && (long long)n_cell_blocks * n_part * ((S + chunk - 1) / chunk) < want)
+        chunk /= 2;
+    return std::max(1, chunk);
+}
+
+// Bracket one deposit-kernel launch with events when timing is on.
+struct LaunchTimer {
+    rd_detector* d;
+    cudaStream_t s;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    LaunchTimer(rd_detector* d_, cudaStream_t s_) : d(d_), s(s_)
+    {
+        if (!d->timing) return;
+        if (!d->ev_free.empty()) {
+            ev = d->ev_free.back();
+            d->ev_free.pop_back();
+        } else if (cudaEventCreate(&ev.first) != cudaSuccess || cudaEventCreate(&ev.second) != cudaSuccess) {
+            ev = {nullptr, nullptr};
+            return;
+        }
+        cudaEventRecord(ev.first, s);
+    }
+    ~LaunchTimer()
+    {
+        if (!ev.first) return;
+        cudaEventRecord(ev.second, s);
+        d->ev_pending.push_back(ev);
+    }
+};
+
+void collect_timings(rd_detector* d)
+{
+    for (auto& ev : d->ev_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) {
+            d->timed_ms += ms;
+            d->timed_launches += 1;
+        }
+        d->ev_free.push_back(ev);
+    }
+    d->ev_pending.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rd_last_error(void) { return g_err.c_str(); }
+
+const char* rd_version(void) { return "rd 0.1 (sm_103a)"; }
+
+rd_status rd_create_detector(const rd_detector_desc* desc, rd_stream stream, rd_detector** out)
+{
+    g_err.clear();
+    if (!desc || !out) return fail(RD_ERR_ARG, "desc/out is NULL");
+    *out = nullptr;
+    if (desc->n_pix < 1 || desc->n_bins < 1)
+        return fail(RD_ERR_ARG, "n_pix and n_bins must be >= 1 (got %d, %d)", desc->n_pix, desc->n_bins);
+    if (!desc->pix_pos) return fail(RD_ERR_ARG, "pix_pos is NULL");
+    if (!(desc->dt_det > 0.0) || !isfinite(desc->dt_det) || !isfinite(desc->t_min))
+        return fail(RD_ERR_ARG, "dt_det must be finite and > 0, t_min finite");
+    if (desc->precision != RD_MIXED && desc->precision != RD_FP64)
+        return fail(RD_ERR_ARG, "bad precision %d", desc->precision);
+    if (desc->mem != RD_MEM_DEVICE && desc->mem != RD_MEM_HOST) return fail(RD_ERR_ARG, "bad desc->mem");
+    if (desc->flags & ~(RD_NEAR | RD_FAR)) return fail(RD_ERR_ARG, "bad flags %d", desc->flags);
+    const size_t per_bin = desc->precision == RD_MIXED ? 8 * sizeof(float) : 6 * sizeof(double);
+    if ((size_t)desc->n_pix * (size_t)desc->n_bins > ((size_t)1 << 40) / per_bin)
+        return fail(RD_ERR_ARG, "detector too large");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+    // cell table on the host: (x, y, z, T0 = t_min + pix_t0)
+    std::vector<double> pos((size_t)desc->n_pix * 3), t0v;
+    if (desc->mem == RD_MEM_HOST) {
+        memcpy(pos.data(), desc->pix_pos, pos.size() * sizeof(double));
+    } else {
+        RD_CUDA(cudaMemcpy(pos.data(), desc->pix_pos, pos.size() * sizeof(double), cudaMemcpyDeviceToHost),
+                "copy pix_pos");
+    }
+    if (desc->pix_t0) {
+        t0v.resize(desc->n_pix);
+        if (desc->mem == RD_MEM_HOST)
+            memcpy(t0v.data(), desc->pix_t0, t0v.size() * sizeof(double));
+        else
+            RD_CUDA(cudaMemcpy(t0v.data(), desc->pix_t0, t0v.size() * sizeof(double), cudaMemcpyDeviceToHost),
+                    "copy pix_t0");
+    }
+    std::vector<D4> cells(desc->n_pix);
+    for (int j = 0; j < desc->n_pix; ++j) {
+        const double T0 = desc->t_min + (desc->pix_t0 ? t0v[j] : 0.0);
+        cells[j] = D4{pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], T0};
+        if (!isfinite(cells[j].x) || !isfinite(cells[j].y) || !isfinite(cells[j].z) || !isfinite(T0))
+            return fail(RD_ERR_ARG, "cell %d has a non-finite position or time origin", j);
+    }
+
+    rd_detector* d = new (std::nothrow) rd_detector();
+    if (!d) return fail(RD_ERR_OOM, "host allocation");
+    cudaGetDevice(&d->device);
+    d->n_pix = desc->n_pix;
+    d->n_bins = desc->n_bins;
+    d->precision = desc->precision;
+    d->flags = desc->flags ? desc->flags : (RD_NEAR | RD_FAR);
+    d->t_min = desc->t_min;
+    d->dt_det = desc->dt_det;
+    d->field_bytes = (size_t)desc->n_pix * desc->n_bins * per_bin;
+    cudaError_t e = cudaMalloc(&d->cells, sizeof(D4) * cells.size());
+    if (e == cudaSuccess) e = cudaMalloc(&d->fields, d->field_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&d->counters, sizeof(DevCounters));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d->cells, cells.data(), sizeof(D4) * cells.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d->fields, 0, d->field_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d->counters, 0, sizeof(DevCounters), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        rd_status st = cuda_fail(e, "rd_create_detector");
+        cudaFree(d->cells);
+        cudaFree(d->fields);
+        cudaFree(d->counters);
+        delete d;
+        return st;
+    }
+    *out = d;
+    return RD_OK;
+}
+
+rd_status rd_destroy(rd_detector* d)
+{
+    g_err.clear();
+    if (!d) return RD_OK;
+    cudaDeviceSynchronize();
+    for (auto& ev : d->ev_pending) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+    for (auto& ev : d->ev_free) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+    cudaFree(d->cells);
+    cudaFree(d->fields);
+    cudaFree(d->counters);
+    cudaFree(d->rec);
+    cudaFree(d->stage);
+    cudaFree(d->readback);
+    delete d;
+    return RD_OK;
+}
+
+rd_status rd_zero_fields(rd_detector* d, rd_stream stream)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    RD_CUDA(cudaMemsetAsync(d->fields, 0, d->field_bytes, s), "rd_zero_fields");
+    RD_CUDA(cudaMemsetAsync(&d->counters->clipped, 0, sizeof(unsigned long long), s), "rd_zero_fields");
+    d->n_deposits = 0;
+    return RD_OK;
+}
+
+rd_status rd_deposit_trajectories(rd_detector* d, const rd_traj* t, rd_stream stream)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    rd_status st = check_traj(t);
+    if (st != RD_OK) return st;
+    const int S = t->n_samples - 1;
+    if (t->n_part == 0 || S < 1) return RD_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool mixed = d->precision == RD_MIXED;
+    const size_t rec_size = mixed ? sizeof(RecF) : sizeof(RecD);
+    const size_t per_part_rec = rec_size * (size_t)t->n_samples;
+    const size_t per_part_in = 2 * 3 * sizeof(double) * (size_t)t->n_samples + sizeof(double);
+    // particle chunk: bounded scratch (records + staged input)
+    const size_t budget = (size_t)1 << 31;
+    const size_t per_part = per_part_rec + (t->mem == RD_MEM_HOST ? per_part_in : 0);
+    int pc = (int)std::max<size_t>(1, std::min<size_t>((size_t)t->n_part, budget / per_part));
+    st = ensure(&d->rec, &d->rec_bytes, per_part_rec * pc, s, "record scratch");
+    if (st != RD_OK) return st;
+    if (t->mem == RD_MEM_HOST) {
+        st = ensure(&d->stage, &d->stage_bytes, per_part_in * pc + 256, s, "staging scratch");
+        if (st != RD_OK) return st;
+    }
+    const int n_cell_blocks = (d->n_pix + kDepositThreads - 1) / kDepositThreads;
+    const int chunk = choose_chunk(d, std::min(pc, t->n_part), S, n_cell_blocks);
+
+    for (int p0 = 0; p0 < t->n_part; p0 += pc) {
+        const int np = std::min(pc, t->n_part - p0);
+        const size_t n3 = (size_t)np * t->n_samples * 3;
+        const double* x = t->x + (size_t)p0 * t->n_samples * 3;
+        const double* u = t->u + (size_t)p0 * t->n_samples * 3;
+        const double* q = t->q ? t->q + p0 : nullptr;
+        if (t->mem == RD_MEM_HOST) {
+            double* sx = static_cast<double*>(d->stage);
+            double* su = sx + n3;
+            double* sq = su + n3;
+            RD_CUDA(cudaMemcpyAsync(sx, x, n3 * sizeof(double), cudaMemcpyHostToDevice, s), "stage x");
+            RD_CUDA(cudaMemcpyAsync(su, u, n3 * sizeof(double), cudaMemcpyHostToDevice, s), "stage u");
+            if (q) RD_CUDA(cudaMemcpyAsync(sq, q, np * sizeof(double), cudaMemcpyHostToDevice, s), "stage q");
+            x = sx;
+            u = su;
+            q = q ? sq : nullptr;
+        }
+        DepositParams P;
+        P.rec = d->rec;
+        P.x = x;
+        P.q = q;
+        P.cells = d->cells;
+        P.fields = d->fields;
+        P.counters = d->counters;
+        P.n_pix = d->n_pix;
+        P.n_bins = d->n_bins;
+        P.n_samples = t->n_samples;
+        P.n_part = np;
+        P.chunk = chunk;
+        P.n_chunks = (S + chunk - 1) / chunk;
+        P.n_cell_blocks = n_cell_blocks;
+        P.t0 = t->t0;
+        P.dt = t->dt;
+        P.inv_dt_det = 1.0 / d->dt_det;
+        P.dt_f = (float)t->dt;
+        P.du_scale = (float)(t->dt / d->dt_det);
+        if (mixed) {
+            RD_CUDA(launch_precompute_mixed(x, u, np, t->n_samples, t->dt, d->flags,
+                                            static_cast<RecF*>(d->rec), d->counters, s),
+                    "precompute");
+            LaunchTimer timer(d, s);
+            RD_CUDA(launch_deposit_mixed(P, s), "deposit (mixed)");
+        } else {
+            RD_CUDA(launch_precompute_fp64(x, u, np, t->n_samples, t->dt, static_cast<RecD*>(d->rec),
+                                           d->counters, s),
+                    "precompute");
+            LaunchTimer timer(d, s);
+            RD_CUDA(launch_deposit_fp64(P, d->flags, s), "deposit (fp64)");
+        }
+    }
+    d->n_deposits += (long long)t->n_part * S * d->n_pix;
+    return RD_OK;
+}
+
+rd_status rd_read_fields(rd_detector* d, void* E, void* B, int32_t dtype, int32_t mem, rd_stream stream)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    if (dtype != RD_F32 && dtype != RD_F64) return fail(RD_ERR_ARG, "bad dtype %d", dtype);
+    if (mem != RD_MEM_DEVICE && mem != RD_MEM_HOST) return fail(RD_ERR_ARG, "bad mem %d", mem);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!E && !B) return RD_OK;
+    const size_t elem = dtype == RD_F32 ? sizeof(float) : sizeof(double);
+    const size_t one = (size_t)d->n_pix * d->n_bins * 3 * elem;
+    if (mem == RD_MEM_DEVICE) {
+        RD_CUDA(launch_read_fields(d->fields, d->precision, d->n_pix, d->n_bins, E, B, dtype, s),
+                "rd_read_fields");
+        return RD_OK;
+    }
+    rd_status st = ensure(&d->readback, &d->readback_bytes, 2 * one, s, "readback scratch");
+    if (st != RD_OK) return st;
+    char* dE = E ? static_cast<char*>(d->readback) : nullptr;
+    char* dB = B ? static_cast<char*>(d->readback) + one : nullptr;
+    RD_CUDA(launch_read_fields(d->fields, d->precision, d->n_pix, d->n_bins, dE, dB, dtype, s),
+            "rd_read_fields");
+    if (E) RD_CUDA(cudaMemcpyAsync(E, dE, one, cudaMemcpyDeviceToHost, s), "copy E to host");
+    if (B) RD_CUDA(cudaMemcpyAsync(B, dB, one, cudaMemcpyDeviceToHost, s), "copy B to host");
+    DevCounters c;
+    RD_CUDA(cudaMemcpyAsync(&c, d->counters, sizeof c, cudaMemcpyDeviceToHost, s), "read counters");
+    RD_CUDA(cudaStreamSynchronize(s), "rd_read_fields");
+    return latched(c);
+}
+
+rd_status rd_synchronize(rd_detector* d, rd_stream stream)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DevCounters c;
+    RD_CUDA(cudaMemcpyAsync(&c, d->counters, sizeof c, cudaMemcpyDeviceToHost, s), "read counters");
+    RD_CUDA(cudaStreamSynchronize(s), "rd_synchronize");
+    if (c.errors) {
+        RD_CUDA(cudaMemsetAsync(&d->counters->errors, 0, sizeof(unsigned), s), "clear errors");
+        RD_CUDA(cudaStreamSynchronize(s), "rd_synchronize");
+    }
+    return latched(c);
+}
+
+rd_status rd_get_stats(rd_detector* d, rd_stream stream, rd_stats* out)
+{
+    g_err.clear();
+    if (!d || !out) return fail(RD_ERR_ARG, "detector/out is NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DevCounters c;
+    RD_CUDA(cudaMemcpyAsync(&c, d->counters, sizeof c, cudaMemcpyDeviceToHost, s), "read counters");
+    RD_CUDA(cudaStreamSynchronize(s), "rd_get_stats");
+    out->n_clipped = (int64_t)c.clipped;
+    out->n_deposits = d->n_deposits;
+    out->device_errors = c.errors;
+    collect_timings(d);
+    out->kernel_launches = d->timed_launches;
+    out->kernel_ms = d->timed_ms;
+    d->timed_launches = 0;
+    d->timed_ms = 0.0;
+    return RD_OK;
+}
+
+rd_status rd_set_timing(rd_detector* d, int32_t enable)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    d->timing = enable != 0;
+    return RD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,622 @@
+// Deposit kernels: per-sample precompute, the mixed-precision deposit, the plain FP64 deposit
+// and the field readout.
+//
+// Work decomposition (both deposit kernels): one CTA = 256 detector cells (one per thread) x one
+// particle x one chunk of consecutive intervals.  The chunk's per-sample records are streamed
+// through shared memory in tiles of 64 samples by bulk asynchronous copies (double buffered,
+// mbarrier completion); every thread reads each record as a broadcast.  Each thread walks its
+// cell's arrival times forward in k (they increase for sub-luminal chords), keeps the bin it is
+// filling in registers and adds the bin to global memory with vector reductions only when its
+// arrival time leaves the bin.
+#include <math.h>
+
+#include "rd_internal.cuh"
+
+namespace rd {
+
+// =============================================================================================
+// Algorithm 1, per-sample part: beta, betadot (backward difference), 1/gamma^2, chord velocity.
+// =============================================================================================
+__device__ __forceinline__ void beta_of(const double* u, double& bx, double& by, double& bz,
+                                        double& ig2)
+{
+    const double ux = u[0], uy = u[1], uz = u[2];
+    const double uu = ux * ux + uy * uy + uz * uz;
+    const double g = sqrt(1.0 + uu);
+    bx = ux / g;
+    by = uy / g;
+    bz = uz / g;
+    ig2 = 1.0 / (1.0 + uu);
+}
+
+__device__ __forceinline__ bool finite3(const double* v)
+{
+    return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
+}
+
+__global__ void k_precompute_mixed(const double* __restrict__ x, const double* __restrict__ u,
+                                   int n_part, int n_samples, double dt, int flags,
+                                   RecF* __restrict__ rec, DevCounters* counters)
+{
+    const long long total = (long long)n_part * n_samples;
+    const float near_on = (flags & RD_NEAR) ? 1.f : 0.f;
+    const bool far_on = (flags & RD_FAR) != 0;
+    const double inv_dt = 1.0 / dt;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i % n_samples);
+        const double* xk = x + 3 * i;
+        const double* uk = u + 3 * i;
+        bool bad = !finite3(xk) || !finite3(uk);
+        double bx, by, bz, ig2;
+        beta_of(uk, bx, by, bz, ig2);
+        double ax = 0.0, ay = 0.0, az = 0.0, vx = 0.0, vy = 0.0, vz = 0.0, g = 1.0;
+        if (k > 0) {
+            double px, py, pz, pig2;
+            beta_of(uk - 3, px, py, pz, pig2);
+            ax = (bx - px) * inv_dt;
+            ay = (by - py) * inv_dt;
+            az = (bz - pz) * inv_dt;
+            vx = (xk[0] - xk[-3]) * inv_dt;
+            vy = (xk[1] - xk[-2]) * inv_dt;
+            vz = (xk[2] - xk[-1]) * inv_dt;
+            g = 1.0 - (vx * vx + vy * vy + vz * vz);
+            bad = bad || !(g > 0.0);
+        }
+        if (bad) atomicOr(&counters->errors, ERRBIT_INPUT);
+        RecF r;
+        r.xa = make_float4((float)xk[0], (float)xk[1], (float)xk[2], (float)(0.5 * ig2));
+        r.bb = make_float4((float)bx, (float)by, (float)bz, near_on * (float)ig2);
+        r.bd = far_on ? make_float4((float)ax, (float)ay, (float)az, (float)(dt * g))
+                      : make_float4(0.f, 0.f, 0.f, (float)(dt * g));
+        r.vb = make_float4((float)vx, (float)vy, (float)vz, (float)g);
+        rec[i] = r;
+    }
+}
+
+__global__ void k_precompute_fp64(const double* __restrict__ x, const double* __restrict__ u,
+                                  int n_part, int n_samples, double dt, RecD* __restrict__ rec,
+                                  DevCounters* counters)
+{
+    const long long total = (long long)n_part * n_samples;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i % n_samples);
+        const double* xk = x + 3 * i;
+        const double* uk = u + 3 * i;
+        bool bad = !finite3(xk) || !finite3(uk);
+        double bx, by, bz, ig2;
+        beta_of(uk, bx, by, bz, ig2);
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        if (k > 0) {
+            double px, py, pz, pig2;
+            beta_of(uk - 3, px, py, pz, pig2);
+            ax = (bx - px) / dt;
+            ay = (by - py) / dt;
+            az = (bz - pz) / dt;
+            const double vx = xk[0] - xk[-3], vy = xk[1] - xk[-2], vz = xk[2] - xk[-1];
+            bad = bad || !((vx * vx + vy * vy) + vz * vz < dt * dt);
+        }
+        if (bad) atomicOr(&counters->errors, ERRBIT_INPUT);
+        RecD r;
+        r.xa = D4{xk[0], xk[1], xk[2], 0.0};
+        r.bb = D4{bx, by, bz, ig2};
+        r.bd = D4{ax, ay, az, 0.0};
+        rec[i] = r;
+    }
+}
+
+// =============================================================================================
+// Eq. 2 in bin units, FP64, every operation separately rounded:
+//   t_k = t0 + k*dt,  R = sqrt((dx*dx + dy*dy) + dz*dz),  u = ((t_k + R) - T0) * inv_dt_det
+// =============================================================================================
+__device__ __forceinline__ double arrival_bins(double xk0, double xk1, double xk2, const D4& cell,
+                                               double t0, int k, double dt, double inv_dt_det,
+                                               double& R)
+{
+    const double dx = __dsub_rn(cell.x, xk0);
+    const double dy = __dsub_rn(cell.y, xk1);
+    const double dz = __dsub_rn(cell.z, xk2);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    R = __dsqrt_rn(r2);
+    const double tk = __dadd_rn(t0, __dmul_rn((double)k, dt));
+    return __dmul_rn(__dsub_rn(__dadd_rn(tk, R), cell.w), inv_dt_det);
+}
+
+__device__ __forceinline__ int clamp_bin(double fb)
+{
+    return (int)fmin(fmax(fb, -1073741824.0), 1073741824.0);
+}
+
+// =============================================================================================
+// Mixed-precision deposit
+// =============================================================================================
+struct MixedState {
+    int b;          // bin currently being filled (may lie outside [0, n_bins))
+    float f;        // position inside bin b, in bins
+    float Rpd;      // R_{k-1} + dt
+    float acc[6];   // running integral of the field over bin b since the thread entered it
+    int n_below;    // intervals of the chunk whose start lies before the window
+    int n_above;    // intervals whose end lies after the window
+};
+
+__device__ __forceinline__ void flush_f32(float* row, int n_bins, int b, const float* v)
+{
+    if ((unsigned)b < (unsigned)n_bins) {
+        float* p = row + (size_t)b * 8;
+        red_add_v4(p, v[0], v[1], v[2], v[3]);
+        red_add_v2(p + 4, v[4], v[5]);
+    }
+}
+
+// Field of one sample at this cell and the arrival-time increment of its interval.
+// Eq. 1 is evaluated as E = s [ (n-beta)(gamma^-2/R + n.betadot) - betadot kappa ],
+// s = q/(kappa^3 R), using n x ((n-beta) x betadot) = (n-beta)(n.betadot) - betadot (n.(n-beta))
+// and n.(n-beta) = kappa; kappa = (gamma^-2 + |n-beta|^2)/2 avoids the cancellation in 1-beta.n.
+// Interval length in arrival time (exact identity, every term positive):
+//   t'_k - t'_{k-1} = dt [dt g + R_k (g + |n_k - vbar|^2)] / (dt + R_k + R_{k-1}),
+//   vbar = (x_k - x_{k-1})/dt, g = 1 - |vbar|^2.
+__device__ __forceinline__ float mixed_field(const RecF& r, float Px, float Py, float Pz, float qf,
+                                             float dt_f, float du_scale, float& Rpd, float* F)
+{
+    const float dx = Px - r.xa.x, dy = Py - r.xa.y, dz = Pz - r.xa.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rinv = rsqrtf(r2);
+    const float R = r2 * rinv;
+    const float nx = dx * rinv, ny = dy * rinv, nz = dz * rinv;
+    // arrival-time step in bins
+    const float mx = nx - r.vb.x, my = ny - r.vb.y, mz = nz - r.vb.z;
+    const float gg = fmaf(mx, mx, fmaf(my, my, fmaf(mz, mz, r.vb.w)));
+    const float num = fmaf(R, gg, r.bd.w);
+    const float du = __fdividef(num * du_scale, R + Rpd);
+    Rpd = R + dt_f;
+    // Eq. 1
+    const float bx = nx - r.bb.x, by = ny - r.bb.y, bz = nz - r.bb.z;
+    const float nb2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+    const float kap = fmaf(nb2, 0.5f, r.xa.w);
+    const float ik = __fdividef(1.f, kap);
+    const float s = qf * rinv * (ik * ik * ik);
+    const float nbd = fmaf(nx, r.bd.x, fmaf(ny, r.bd.y, nz * r.bd.z));
+    const float c1 = fmaf(r.bb.w, rinv, nbd) * s;
+    const float ks = kap * s;
+    const float Ex = fmaf(bx, c1, -r.bd.x * ks);
+    const float Ey = fmaf(by, c1, -r.bd.y * ks);
+    const float Ez = fmaf(bz, c1, -r.bd.z * ks);
+    F[0] = Ex;
+    F[1] = Ey;
+    F[2] = Ez;
+    F[3] = fmaf(ny, Ez, -nz * Ey);
+    F[4] = fmaf(nz, Ex, -nx * Ez);
+    F[5] = fmaf(nx, Ey, -ny * Ex);
+    return du;
+}
+
+// Integrating deposit (Section 3.2) of one interval of length du (bins) starting at (b, f).
+__device__ __forceinline__ void mixed_deposit(MixedState& st, const float* F, float du, float* row,
+                                              int n_bins, int k, int k_begin, int k_end)
+{
+    const float fn = st.f + du;
+    if (fn < 1.f) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) st.acc[i] = fmaf(F[i], du, st.acc[i]);
+        st.f = fn;
+        return;
+    }
+    const float w1 = 1.f - st.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) st.acc[i] = fmaf(F[i], w1, st.acc[i]);
+    flush_f32(row, n_bins, st.b, st.acc);
+    const int b_old = st.b;
+    int b = st.b + 1;
+    float rem = fn - 1.f;
+    if (rem >= 1.f) {
+        const int nfull = (int)fminf(floorf(rem), 16777216.f);
+        const int lo = max(b, 0), hi = min(b + nfull - 1, n_bins - 1);
+        for (int j = lo; j <= hi; ++j) flush_f32(row, n_bins, j, F);
+        b += nfull;
+        rem -= (float)nfull;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) st.acc[i] = F[i] * rem;
+    st.b = b;
+    st.f = rem;
+    if (b_old < 0 && b >= 0) st.n_below = k - k_begin + 1;
+    if (b_old < n_bins && b >= n_bins) st.n_above = k_end - k + 1;
+}
+
+__global__ void __launch_bounds__(kDepositThreads, 4) k_deposit_mixed(const DepositParams P)
+{
+    __shared__ __align__(128) RecF tile[2][kTileSteps];
+    __shared__ __align__(8) uint64_t bar[2];
+
+    const int cb = (int)(blockIdx.x % (unsigned)P.n_cell_blocks);
+    const int item = (int)(blockIdx.x / (unsigned)P.n_cell_blocks);
+    const int p = item / P.n_chunks;
+    const int c = item - p * P.n_chunks;
+    const int S = P.n_samples - 1;
+    const int k_begin = 1 + c * P.chunk;
+    const int k_end = min(S, k_begin + P.chunk - 1);
+    const int n_int = k_end - k_begin + 1;
+    const int n_tiles = (n_int + kTileSteps - 1) / kTileSteps;
+    const RecF* rec = static_cast<const RecF*>(P.rec) + (size_t)p * P.n_samples;
+    const int tid = threadIdx.x;
+    const int cell = cb * kDepositThreads + tid;
+    const bool active = cell < P.n_pix;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int t = 0; t < 2 && t < n_tiles; ++t) {
+            const int k0 = k_begin + t * kTileSteps;
+            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k0 + 1) * sizeof(RecF);
+            mbar_arrive_expect_tx(&bar[t], bytes);
+            bulk_g2s(tile[t], rec + k0, bytes, &bar[t]);
+        }
+    }
+
+    // ---- per-cell anchors: exact FP64 arrival (bins) at both ends of the chunk ----
+    MixedState st;
+    float Px = 0.f, Py = 0.f, Pz = 0.f;
+    int b_end = 0;
+    float f_end = 0.f;
+    bool live = false;
+    float* row = nullptr;
+    if (active) {
+        const D4 cl = P.cells[cell];
+        const double* xp = P.x + (size_t)p * P.n_samples * 3;
+        double Ra, Re;
+        const double* xa = xp + 3 * (size_t)(k_begin - 1);
+        const double* xe = xp + 3 * (size_t)k_end;
+        const double ua = arrival_bins(xa[0], xa[1], xa[2], cl, P.t0, k_begin - 1, P.dt, P.inv_dt_det, Ra);
+        const double ue = arrival_bins(xe[0], xe[1], xe[2], cl, P.t0, k_end, P.dt, P.inv_dt_det, Re);
+        live = (ue > 0.0) && (ua < (double)P.n_bins);
+        const double fa = floor(ua), fe = floor(ue);
+        st.b = clamp_bin(fa);
+        st.f = (float)(ua - fa);
+        b_end = clamp_bin(fe);
+        f_end = (float)(ue - fe);
+        st.Rpd = (float)Ra + P.dt_f;
+        st.n_below = (ua < 0.0) ? n_int : 0;
+        st.n_above = 0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) st.acc[i] = 0.f;
+        Px = (float)cl.x;
+        Py = (float)cl.y;
+        Pz = (float)cl.z;
+        row = static_cast<float*>(P.fields) + (size_t)cell * P.n_bins * 8;
+        if (!live) {
+            unsigned long long clip = (unsigned long long)n_int;
+            atomicAdd(&P.counters->clipped, clip);
+        }
+    }
+    const float qf = P.q ? (float)P.q[p] : 1.f;
+
+    for (int t = 0; t < n_tiles; ++t) {
+        const int buf = t & 1;
+        const bool ok = mbar_wait_bounded(&bar[buf], (unsigned)(t >> 1) & 1u);
+        if (__syncthreads_or(!ok)) {
+            // a bulk copy did not complete: record it, let outstanding copies land, stop.
+            if (tid == 0) {
+                atomicOr(&P.counters->errors, ERRBIT_TIMEOUT);
+                for (int u = t; u < t + 2 && u < n_tiles; ++u)
+                    (void)mbar_wait_bounded(&bar[u & 1], (unsigned)(u >> 1) & 1u);
+            }
+            __syncthreads();
+            return;
+        }
+        const int k0 = k_begin + t * kTileSteps;
+        const int cnt = min(kTileSteps, k_end - k0 + 1);
+        const bool last_tile = (t == n_tiles - 1);
+        if (live) {
+            const int n_regular = last_tile ? cnt - 1 : cnt;
+            float F[6];
+            for (int i = 0; i < n_regular; ++i) {
+                const RecF r = tile[buf][i];
+                const float du = mixed_field(r, Px, Py, Pz, qf, P.dt_f, P.du_scale, st.Rpd, F);
+                mixed_deposit(st, F, du, row, P.n_bins, k0 + i, k_begin, k_end);
+            }
+            if (last_tile) {
+                // last interval of the chunk ends on the exact FP64 anchor
+                const RecF r = tile[buf][cnt - 1];
+                (void)mixed_field(r, Px, Py, Pz, qf, P.dt_f, P.du_scale, st.Rpd, F);
+                const float du = ((float)(b_end - st.b) + f_end) - st.f;
+                mixed_deposit(st, F, du, row, P.n_bins, k_end, k_begin, k_end);
+                flush_f32(row, P.n_bins, st.b, st.acc);
+                const int clip = min(n_int, st.n_below + st.n_above);
+                if (clip > 0) atomicAdd(&P.counters->clipped, (unsigned long long)clip);
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && t + 2 < n_tiles) {
+            fence_proxy_async();
+            const int k2 = k_begin + (t + 2) * kTileSteps;
+            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k2 + 1) * sizeof(RecF);
+            mbar_arrive_expect_tx(&bar[buf], bytes);
+            bulk_g2s(tile[buf], rec + k2, bytes, &bar[buf]);
+        }
+    }
+}
+
+// =============================================================================================
+// Plain FP64 deposit: Eq. 1 as printed, Eq. 2 evaluated directly for every sample.
+// =============================================================================================
+struct D64State {
+    int b;
+    double a;       // arrival (bins) of the previous sample
+    double acc[6];
+    int n_below;
+    int n_above;
+};
+
+__device__ __forceinline__ void flush_f64(double* row, int n_bins, int b, const double* v)
+{
+    if ((unsigned)b < (unsigned)n_bins) {
+        double* p = row + (size_t)b * 6;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) red_add_f64(p + i, v[i]);
+    }
+}
+
+__device__ __forceinline__ void fp64_field(const RecD& r, const D4& cl, double q, int flags,
+                                           double* F)
+{
+    const double dx = cl.x - r.xa.x, dy = cl.y - r.xa.y, dz = cl.z - r.xa.z;
+    const double R = sqrt(dx * dx + dy * dy + dz * dz);
+    const double rinv = 1.0 / R;
+    const double nx = dx * rinv, ny = dy * rinv, nz = dz * rinv;
+    const double bx = nx - r.bb.x, by = ny - r.bb.y, bz = nz - r.bb.z;
+    const double kap = 1.0 - (r.bb.x * nx + r.bb.y * ny + r.bb.z * nz);
+    const double ik = 1.0 / kap;
+    const double ik3 = ik * ik * ik;
+    double Ex = 0.0, Ey = 0.0, Ez = 0.0;
+    if (flags & RD_NEAR) {
+        const double cn = q * r.bb.w * ik3 * rinv * rinv;
+        Ex = cn * bx;
+        Ey = cn * by;
+        Ez = cn * bz;
+    }
+    if (flags & RD_FAR) {
+        const double wx = by * r.bd.z - bz * r.bd.y;
+        const double wy = bz * r.bd.x - bx * r.bd.z;
+        const double wz = bx * r.bd.y - by * r.bd.x;
+        const double cf = q * ik3 * rinv;
+        Ex += cf * (ny * wz - nz * wy);
+        Ey += cf * (nz * wx - nx * wz);
+        Ez += cf * (nx * wy - ny * wx);
+    }
+    F[0] = Ex;
+    F[1] = Ey;
+    F[2] = Ez;
+    F[3] = ny * Ez - nz * Ey;
+    F[4] = nz * Ex - nx * Ez;
+    F[5] = nx * Ey - ny * Ex;
+}
+
+// Deposit [st.a, c] with the bin-overlap arithmetic of the integrator detector.
+__device__ __forceinline__ void fp64_deposit(D64State& st, const double* F, double c, double* row,
+                                             int n_bins, int k, int k_begin, int k_end)
+{
+    const double fc = floor(c);
+    const int bc = clamp_bin(fc);
+    if (bc <= st.b) {
+        const double w = c - st.a;
+        if (w > 0.0) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) st.acc[i] = fma(F[i], w, st.acc[i]);
+        }
+        st.a = c;
+        return;
+    }
+    const double w1 = (double)(st.b + 1) - st.a;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) st.acc[i] = fma(F[i], w1, st.acc[i]);
+    flush_f64(row, n_bins, st.b, st.acc);
+    const int lo = max(st.b + 1, 0), hi = min(bc - 1, n_bins - 1);
+    for (int j = lo; j <= hi; ++j) flush_f64(row, n_bins, j, F);
+    const double wl = c - fc;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) st.acc[i] = F[i] * wl;
+    if (st.b < 0 && bc >= 0) st.n_below = k - k_begin + 1;
+    if (st.b < n_bins && bc >= n_bins) st.n_above = k_end - k + 1;
+    st.b = bc;
+    st.a = c;
+}
+
+__global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const DepositParams P,
+                                                                       int flags)
+{
+    __shared__ __align__(128) RecD tile[2][kTileSteps];
+    __shared__ __align__(8) uint64_t bar[2];
+
+    const int cb = (int)(blockIdx.x % (unsigned)P.n_cell_blocks);
+    const int item = (int)(blockIdx.x / (unsigned)P.n_cell_blocks);
+    const int p = item / P.n_chunks;
+    const int c = item - p * P.n_chunks;
+    const int S = P.n_samples - 1;
+    const int k_begin = 1 + c * P.chunk;
+    const int k_end = min(S, k_begin + P.chunk - 1);
+    const int n_int = k_end - k_begin + 1;
+    const int n_tiles = (n_int + kTileSteps - 1) / kTileSteps;
+    const RecD* rec = static_cast<const RecD*>(P.rec) + (size_t)p * P.n_samples;
+    const int tid = threadIdx.x;
+    const int cell = cb * kDepositThreads + tid;
+    const bool active = cell < P.n_pix;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int t = 0; t < 2 && t < n_tiles; ++t) {
+            const int k0 = k_begin + t * kTileSteps;
+            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k0 + 1) * sizeof(RecD);
+            mbar_arrive_expect_tx(&bar[t], bytes);
+            bulk_g2s(tile[t], rec + k0, bytes, &bar[t]);
+        }
+    }
+
+    D64State st;
+    D4 cl = {0.0, 0.0, 0.0, 0.0};
+    bool live = false;
+    double* row = nullptr;
+    const double* xp = P.x + (size_t)p * P.n_samples * 3;
+    if (active) {
+        cl = P.cells[cell];
+        double Ra, Re;
+        const double* xa = xp + 3 * (size_t)(k_begin - 1);
+        const double* xe = xp + 3 * (size_t)k_end;
+        const double ua = arrival_bins(xa[0], xa[1], xa[2], cl, P.t0, k_begin - 1, P.dt, P.inv_dt_det, Ra);
+        const double ue = arrival_bins(xe[0], xe[1], xe[2], cl, P.t0, k_end, P.dt, P.inv_dt_det, Re);
+        live = (ue > 0.0) && (ua < (double)P.n_bins);
+        st.a = ua;
+        st.b = clamp_bin(floor(ua));
+        st.n_below = (ua < 0.0) ? n_int : 0;
+        st.n_above = 0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) st.acc[i] = 0.0;
+        row = static_cast<double*>(P.fields) + (size_t)cell * P.n_bins * 6;
+        if (!live) atomicAdd(&P.counters->clipped, (unsigned long long)n_int);
+    }
+    const double q = P.q ? P.q[p] : 1.0;
+
+    for (int t = 0; t < n_tiles; ++t) {
+        const int buf = t & 1;
+        const bool ok = mbar_wait_bounded(&bar[buf], (unsigned)(t >> 1) & 1u);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(&P.counters->errors, ERRBIT_TIMEOUT);
+                for (int u = t; u < t + 2 && u < n_tiles; ++u)
+                    (void)mbar_wait_bounded(&bar[u & 1], (unsigned)(u >> 1) & 1u);
+            }
+            __syncthreads();
+            return;
+        }
+        const int k0 = k_begin + t * kTileSteps;
+        const int cnt = min(kTileSteps, k_end - k0 + 1);
+        if (live) {
+            double F[6];
+            for (int i = 0; i < cnt; ++i) {
+                const RecD r = tile[buf][i];
+                const int k = k0 + i;
+                fp64_field(r, cl, q, flags, F);
+                double R;
+                const double cbin = arrival_bins(r.xa.x, r.xa.y, r.xa.z, cl, P.t0, k, P.dt, P.inv_dt_det, R);
+                fp64_deposit(st, F, cbin, row, P.n_bins, k, k_begin, k_end);
+            }
+            if (t == n_tiles - 1) {
+                flush_f64(row, P.n_bins, st.b, st.acc);
+                const int clip = min(n_int, st.n_below + st.n_above);
+                if (clip > 0) atomicAdd(&P.counters->clipped, (unsigned long long)clip);
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && t + 2 < n_tiles) {
+            fence_proxy_async();
+            const int k2 = k_begin + (t + 2) * kTileSteps;
+            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k2 + 1) * sizeof(RecD);
+            mbar_arrive_expect_tx(&bar[buf], bytes);
+            bulk_g2s(tile[buf], rec + k2, bytes, &bar[buf]);
+        }
+    }
+}
+
+// =============================================================================================
+// readout: internal layout -> E[n_pix][n_bins][3], B[n_pix][n_bins][3]
+// =============================================================================================
+template <typename Tin, int STRIDE, typename Tout>
+__global__ void k_read(const Tin* __restrict__ fields, long long n, Tout* __restrict__ E,
+                       Tout* __restrict__ B)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const Tin* v = fields + i * STRIDE;
+        if (E) {
+            E[3 * i] = (Tout)v[0];
+            E[3 * i + 1] = (Tout)v[1];
+            E[3 * i + 2] = (Tout)v[2];
+        }
+        if (B) {
+            B[3 * i] = (Tout)v[3];
+            B[3 * i + 1] = (Tout)v[4];
+            B[3 * i + 2] = (Tout)v[5];
+        }
+    }
+}
+
+// =============================================================================================
+// launchers
+// =============================================================================================
+static int grid_for(long long n, int threads)
+{
+    long long g = (n + threads - 1) / threads;
+    if (g > 152LL * 16) g = 152LL * 16;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+cudaError_t launch_precompute_mixed(const double* x, const double* u, int n_part, int n_samples,
+                                    double dt, int flags, RecF* rec, DevCounters* counters,
+                                    cudaStream_t s)
+{
+    const long long n = (long long)n_part * n_samples;
+    k_precompute_mixed<<<grid_for(n, 256), 256, 0, s>>>(x, u, n_part, n_samples, dt, flags, rec,
+                                                        counters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part, int n_samples,
+                                   double dt, RecD* rec, DevCounters* counters, cudaStream_t s)
+{
+    const long long n = (long long)n_part * n_samples;
+    k_precompute_fp64<<<grid_for(n, 256), 256, 0, s>>>(x, u, n_part, n_samples, dt, rec, counters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s)
+{
+    const long long blocks = (long long)p.n_cell_blocks * p.n_part * p.n_chunks;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_deposit_mixed<<<(unsigned)blocks, kDepositThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit_fp64(const DepositParams& p, int flags, cudaStream_t s)
+{
+    const long long blocks = (long long)p.n_cell_blocks * p.n_part * p.n_chunks;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_deposit_fp64<<<(unsigned)blocks, kDepositThreads, 0, s>>>(p, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read_fields(const void* fields, int precision, int n_pix, int n_bins, void* E,
+                               void* B, int dtype, cudaStream_t s)
+{
+    const long long n = (long long)n_pix * n_bins;
+    const int g = grid_for(n, 256);
+    if (precision == RD_MIXED) {
+        if (dtype == RD_F32)
+            k_read<float, 8, float><<<g, 256, 0, s>>>(static_cast<const float*>(fields), n,
+                                                      static_cast<float*>(E), static_cast<float*>(B));
+        else
+            k_read<float, 8, double><<<g, 256, 0, s>>>(static_cast<const float*>(fields), n,
+                                                       static_cast<double*>(E), static_cast<double*>(B));
+    } else {
+        if (dtype == RD_F32)
+            k_read<double, 6, float><<<g, 256, 0, s>>>(static_cast<const double*>(fields), n,
+                                                       static_cast<float*>(E), static_cast<float*>(B));
+        else
+            k_read<double, 6, double><<<g, 256, 0, s>>>(static_cast<const double*>(fields), n,
+                                                        static_cast<double*>(E), static_cast<double*>(B));
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rd

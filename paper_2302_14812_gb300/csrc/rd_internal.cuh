@@ -1,0 +1,194 @@
+// Internal declarations of the radiation-deposit library (sm_103a).
+//
+// Data layout in device memory
+//   cell table     D4     [n_pix]              (x, y, z, T0 = t_min + pix_t0)
+//   mixed fields   float   [n_pix][n_bins][8]  (Ex Ey Ez Bx | By Bz 0 0): one 32-byte sector per bin
+//   fp64 fields    double  [n_pix][n_bins][6]  (Ex Ey Ez Bx By Bz)
+//   records        RecF / RecD [n_part][n_samples]: per-sample quantities of Algorithm 1,
+//                  computed once per call and read by every cell (staged through shared memory
+//                  with bulk asynchronous copies).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rd.h"
+
+namespace rd {
+
+// ---------------------------------------------------------------------------------------------
+// error bits latched on the device (bit i = 1 << rd_status value)
+// ---------------------------------------------------------------------------------------------
+enum : unsigned {
+    ERRBIT_TIMEOUT = 1u << RD_ERR_TIMEOUT,
+    ERRBIT_BOUNDS = 1u << RD_ERR_BOUNDS,
+    ERRBIT_INPUT = 1u << RD_ERR_INPUT,
+};
+
+struct DevCounters {
+    unsigned errors;
+    unsigned pad;
+    unsigned long long clipped;
+};
+
+// ---------------------------------------------------------------------------------------------
+// per-sample records
+// ---------------------------------------------------------------------------------------------
+// Mixed path, 64 bytes.  For interval k (between samples k-1 and k) the record of sample k holds
+//   xa = (x_k, gamma_k^-2 / 2)               geometry (FP32) and half the Lorentz factor term of kappa
+//   bb = (beta_k, near ? gamma_k^-2 : 0)     velocity; velocity-term factor
+//   bd = (far ? betadot_k : 0, dt*g_k)       acceleration (backward difference); arrival-step constant
+//   vb = (vbar_k, g_k)                       chord velocity (x_k - x_{k-1})/dt, g_k = 1 - |vbar_k|^2
+struct __align__(16) RecF {
+    float4 xa;
+    float4 bb;
+    float4 bd;
+    float4 vb;
+};
+static_assert(sizeof(RecF) == 64, "RecF must be 64 bytes");
+
+struct __align__(32) D4 {
+    double x, y, z, w;
+};
+
+// FP64 path, 96 bytes: (x_k, 0), (beta_k, gamma_k^-2), (betadot_k, 0).
+struct __align__(32) RecD {
+    D4 xa;
+    D4 bb;
+    D4 bd;
+};
+static_assert(sizeof(RecD) == 96, "RecD must be 96 bytes");
+
+// ---------------------------------------------------------------------------------------------
+// kernel parameter blocks
+// ---------------------------------------------------------------------------------------------
+struct DepositParams {
+    const void* rec;            // RecF or RecD [n_part][n_samples]
+    const double* x;            // [n_part][n_samples][3] FP64 positions (anchors of the mixed path)
+    const double* q;            // [n_part] or null
+    const D4* cells;            // [n_pix] (x, y, z, T0)
+    void* fields;               // float [n_pix][n_bins][8] or double [n_pix][n_bins][6]
+    DevCounters* counters;
+    int n_pix;
+    int n_bins;
+    int n_samples;              // S + 1
+    int n_part;
+    int chunk;                  // intervals per work item
+    int n_chunks;               // ceil(S / chunk)
+    int n_cell_blocks;          // ceil(n_pix / cells per CTA)
+    double t0;
+    double dt;
+    double inv_dt_det;
+    float dt_f;
+    float du_scale;             // dt / dt_det
+};
+
+constexpr int kDepositThreads = 256;   // one cell per thread
+constexpr int kTileSteps = 64;         // intervals per shared-memory tile
+constexpr int kDefaultChunk = 1024;    // intervals per work item (one FP64 anchor at each end)
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // give up a wait after 2 s
+
+// launchers (rd_deposit.cu)
+cudaError_t launch_precompute_mixed(const double* x, const double* u, int n_part, int n_samples,
+                                    double dt, int flags, RecF* rec, DevCounters* counters,
+                                    cudaStream_t s);
+cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part, int n_samples,
+                                   double dt, RecD* rec, DevCounters* counters, cudaStream_t s);
+cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s);
+cudaError_t launch_deposit_fp64(const DepositParams& p, int flags, cudaStream_t s);
+cudaError_t launch_read_fields(const void* fields, int precision, int n_pix, int n_bins, void* E,
+                               void* B, int dtype, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------------
+// device helpers: mbarrier, bulk async copy, vector reductions
+// ---------------------------------------------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned smem_addr(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy (TMA unit, non-tensor form); completes on the mbarrier.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for an mbarrier phase for at most kWaitLimitNs; false if it did not complete in time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    return true;
+}
+
+// Fire-and-forget vector reductions into global memory (sm_90+).
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c),
+                 "f"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void red_add_v2(float* addr, float a, float b)
+{
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
+}
+
+__device__ __forceinline__ void red_add_f64(double* addr, double v)
+{
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(addr), "d"(v) : "memory");
+}
+#endif
+
+}  // namespace rd

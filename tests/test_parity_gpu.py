@@ -1,0 +1,203 @@
+"""GPU deposit (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (relative L2 over every compared element, E and B separately):
+  FP64 path  1e-10   (both sides evaluate the arrival time with the same FP64 operations, so bin
+                      weights agree; differences come from field arithmetic order, ~1e-15)
+  mixed path 1e-4    (FP32 field and accumulation, FP64-accurate arrival time)
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2302_14812_gb300 as rd
+from paper_2302_14812_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rd.load_library()
+    oracle.build()
+
+
+def rel_l2(a, b):
+    nb = float(np.linalg.norm(b))
+    return float(np.linalg.norm(a - b)) / (nb if nb > 0 else 1.0)
+
+
+def gpu_run(tr, det, precision, where="device", calls=None):
+    import torch
+    d = rd.RadiationDetector.from_workload(det, precision)
+    parts = calls or [tr]
+    for t in parts:
+        if where == "device":
+            d.deposit(torch.from_numpy(t.x).cuda(), torch.from_numpy(t.u).cuda(),
+                      torch.from_numpy(t.q).cuda(), t.t0, t.dt)
+        else:
+            d.deposit(t.x, t.u, t.q, t.t0, t.dt)
+    E, B = d.read("float64", "cpu")
+    st = d.stats()
+    d.close()
+    return E, B, st
+
+
+def check(tr, det, precision, sel=None, where="device", Eo=None, Bo=None, clip_exact=None):
+    E, B, st = gpu_run(tr, det, precision, where)
+    if Eo is None:
+        Eo, Bo, clipped = oracle.deposit(tr, det, sel)
+    else:
+        clipped = None
+    if sel is not None:
+        E, B = E[sel], B[sel]
+    eE, eB = rel_l2(E, Eo), rel_l2(B, Bo)
+    assert np.abs(Eo).max() > 0
+    assert eE <= TOL[precision] and eB <= TOL[precision], (precision, eE, eB)
+    if clip_exact is None:
+        clip_exact = precision == "fp64" and sel is None
+    if clip_exact and clipped is not None:
+        assert st.n_clipped == clipped
+    return eE, eB
+
+
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_circular_orbit_full(precision):
+    """One electron on a circular orbit (gamma 5, 2000 steps), 64-cell arc at 1e3, 1024 bins."""
+    tr, det = W.config_circular()
+    check(tr, det, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_random_ensembles_ragged(precision, seed):
+    """Random smooth motions, 300 cells (two cell blocks, ragged), 333 intervals (several
+    64-sample tiles and chunks with a ragged tail), per-cell time origins and a window that cuts
+    some arrivals (clipped counts must match the oracle exactly in FP64)."""
+    rng = np.random.default_rng(seed)
+    tr = W.random_smooth(7, 333, 0.02, max_u=3.0, seed=seed)
+    pos = rng.normal(size=(300, 3)) * 20.0
+    pos += 25.0 * pos / np.linalg.norm(pos, axis=1, keepdims=True)
+    t0 = rng.uniform(-1.0, 1.0, 300)
+    det = W.Detector(pos, t0, 30.0, 0.013, 700)
+    check(tr, det, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_undulator_small(precision):
+    """Undulator ensemble (gamma 20, K 1, 4000 steps), 8 electrons, 32x32 cap, 2048 bins."""
+    tr, det = W.config_undulator(n_part=8, n_side=32)
+    check(tr, det, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_undulator_full_size_sampled_cells(precision):
+    """The benchmark workload at full size (1000 electrons x 4000 steps x 128x128 cells x 2048
+    bins), launched as the benchmark launches it; the oracle computes 6 sampled cells."""
+    tr, det = W.config_undulator()
+    sel = np.array([0, 127, 64 * 128 + 64, 5000, 128 * 127, 128 * 128 - 1], dtype=np.int32)
+    check(tr, det, precision, sel=sel)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_plasma_mirror_reduced(precision):
+    """Plasma-mirror-like surface (a0 5, 20 harmonics, 10000 steps), 300 electrons, 48x48 plane
+    with per-cell time origins; the oracle computes 8 cells spread over the plane."""
+    tr, det = W.config_plasma_mirror(n_part=300, n_side=48, particles=slice(0, 300))
+    sel = np.array([0, 47, 24 * 48 + 24, 1000, 1500, 2000, 48 * 47, 48 * 48 - 1], dtype=np.int32)
+    check(tr, det, precision, sel=sel)
+
+
+# --------------------------------------------------------------------------------------------
+# edge cases and API behaviour
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_host_memory_inputs(precision):
+    tr = W.random_smooth(3, 150, 0.03, seed=4)
+    det = W.Detector(W.spherical_cap(5, 20.0, 0.6), None, 16.0, 0.02, 600)
+    check(tr, det, precision, where="host")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_chunks_and_particle_chunks_accumulate(precision):
+    """Deposits accumulate: particle subsets and step chunks sharing one sample sum to the whole
+    (the run-time mode of Section 3.1)."""
+    tr = W.random_smooth(4, 200, 0.03, seed=5)
+    det = W.Detector(W.spherical_cap(4, 18.0, 0.5), None, 14.0, 0.017, 900)
+    Eo, Bo, _ = oracle.deposit(tr, det)
+    parts = [tr.subset([0, 1]).steps(0, 77), tr.subset([0, 1]).steps(77, 200), tr.subset([2, 3])]
+    E, B, _ = gpu_run(tr, det, precision, calls=parts)
+    assert rel_l2(E, Eo) <= TOL[precision] and rel_l2(B, Bo) <= TOL[precision]
+
+
+def test_empty_and_degenerate_inputs():
+    import torch
+    det = W.Detector(W.spherical_cap(2, 10.0, 0.3), None, 8.0, 0.05, 64)
+    for precision in ("fp64", "mixed"):
+        d = rd.RadiationDetector.from_workload(det, precision)
+        d.deposit(np.zeros((0, 5, 3)), np.zeros((0, 5, 3)), np.zeros(0), 0.0, 0.1)   # no particle
+        d.deposit(np.zeros((2, 1, 3)), np.zeros((2, 1, 3)), np.ones(2), 0.0, 0.1)    # no interval
+        E, B = d.read()
+        assert np.all(E == 0) and np.all(B == 0)
+        # a single interval
+        tr = W.random_smooth(1, 1, 0.05, seed=3)
+        d.deposit(torch.from_numpy(tr.x).cuda(), torch.from_numpy(tr.u).cuda(), None, tr.t0, tr.dt)
+        E, B = d.read()
+        Eo, Bo, _ = oracle.deposit(W.Trajectories(tr.x, tr.u, np.ones(1), tr.t0, tr.dt), det)
+        assert rel_l2(E, Eo) <= TOL[precision]
+        d.zero()
+        E, _ = d.read()
+        assert np.all(E == 0)
+        d.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_window_entirely_missed_counts_clipped(precision):
+    tr = W.random_smooth(2, 90, 0.03, seed=8)
+    det = W.Detector(W.spherical_cap(3, 20.0, 0.5), None, 1e4, 0.01, 100)
+    E, B, st = gpu_run(tr, det, precision)
+    assert np.all(E == 0) and np.all(B == 0)
+    assert st.n_clipped == 2 * 90 * 9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_near_and_far_terms(precision):
+    tr = W.random_smooth(2, 120, 0.03, seed=9)
+    for flags in (W.RD_NEAR, W.RD_FAR):
+        det = W.Detector(W.spherical_cap(3, 15.0, 0.5), None, 11.0, 0.02, 800, flags=flags)
+        check(tr, det, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_superluminal_chord_rejected(precision):
+    tr = W.random_smooth(1, 20, 0.05, seed=1)
+    tr.x[0, 7] = tr.x[0, 6] + np.array([0.06, 0.0, 0.0])
+    det = W.Detector(np.array([[10.0, 0, 0]]), None, 0.0, 0.1, 100)
+    d = rd.RadiationDetector.from_workload(det, precision)
+    d.deposit(tr.x, tr.u, tr.q, tr.t0, tr.dt)
+    with pytest.raises(rd.RDError) as ei:
+        d.read()
+    assert ei.value.status == rd.RD_ERR_INPUT
+    d.close()
+
+
+def test_read_fields_device_and_f32():
+    import torch
+    tr = W.random_smooth(2, 60, 0.03, seed=10)
+    det = W.Detector(W.spherical_cap(3, 12.0, 0.5), None, 9.0, 0.02, 300)
+    d = rd.RadiationDetector.from_workload(det, "mixed")
+    d.deposit_traj(tr)
+    E64, B64 = d.read("float64", "cpu")
+    E32, B32 = d.read("float32", "cpu")
+    Ed, Bd = d.read("float32", "cuda")
+    torch.cuda.synchronize()
+    assert np.array_equal(E32, E64.astype(np.float32))
+    assert np.array_equal(Ed.cpu().numpy(), E32) and np.array_equal(Bd.cpu().numpy(), B32)
+    d.close()
