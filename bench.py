@@ -34,9 +34,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle·step·pixel deposits/sec, FP32-mixed vs FP64 on one GB300 at ≤1e-4 rel L2"
 UNIT = "deposits/s"
-# FP32 operations of one deposit in the mixed kernel (FMA = 2): Eq. 1 field + B = n x E (51),
-# arrival-time increment (17), running-bin accumulation (13); plus 3 MUFU ops not counted.
-FLOPS_PER_DEPOSIT_MIXED = 81
+# FP32 operations of the mixed kernel, counted from its source (add/sub/mul = 1, fused
+# multiply-add = 2; the 3 MUFU reciprocal / reciprocal-square-root ops are not counted):
+#   per deposit: geometry and Eq. 1 with B = n x E and the arrival-time increment 60,
+#                integrating accumulation into the running bin 16
+#   per bin edge crossed: starting the next bin with the rest of the interval 9
+FLOPS_PER_DEPOSIT_MIXED = 76
+FLOPS_PER_CROSSING_MIXED = 9
 # FP32 peak derived from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "deposit_mixed_undulator_ncu.md")
@@ -335,7 +339,9 @@ def main():
                   "mixed_rel_l2_E": float(np.linalg.norm(E_mixed[sel] - Eo) / np.linalg.norm(Eo)),
                   "mixed_rel_l2_B": float(np.linalg.norm(B_mixed[sel] - Bo) / np.linalg.norm(Bo))}
 
-    achieved = FLOPS_PER_DEPOSIT_MIXED * deposits / (kernel_ms / 1e3) / 1e12
+    crossings = st.n_bin_crossings            # of the last timed step (each step starts from zero)
+    flops_step = FLOPS_PER_DEPOSIT_MIXED * deposits + FLOPS_PER_CROSSING_MIXED * crossings
+    achieved = flops_step / (kernel_ms / 1e3) / 1e12
     traffic = profile_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -351,6 +357,7 @@ def main():
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
                      "kernel_ms": kernel_ms, "flops_per_deposit": FLOPS_PER_DEPOSIT_MIXED,
+                     "flops_per_crossing": FLOPS_PER_CROSSING_MIXED, "bin_crossings_per_step": crossings,
                      "traffic": traffic},
         "clocks": clocks,
         "fp64_gpu": fp64_info,

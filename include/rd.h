@@ -113,6 +113,8 @@ typedef struct {
                                   a part outside the cell's window (that part is dropped,
                                   Algorithm 1 window test read as clipping)                    */
     int64_t n_deposits;        /* triples processed since creation / last rd_zero_fields        */
+    int64_t n_bin_crossings;   /* bin edges crossed by the arrival intervals (RD_MIXED): the
+                                  deposit touched n_deposits + n_bin_crossings (cell, bin) pairs  */
     uint32_t device_errors;    /* bit set of latched kernel errors (1<<RD_ERR_*)               */
     int64_t kernel_launches;   /* deposit-kernel launches timed since the last rd_get_stats     */
     double kernel_ms;          /* their summed duration (CUDA events on the caller's stream)    */

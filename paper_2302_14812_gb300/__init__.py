@@ -58,7 +58,7 @@ class rd_traj(ctypes.Structure):
 
 class rd_stats(ctypes.Structure):
     _fields_ = [("n_clipped", ctypes.c_int64), ("n_deposits", ctypes.c_int64),
-                ("device_errors", ctypes.c_uint32), ("kernel_launches", ctypes.c_int64),
+                ("n_bin_crossings", ctypes.c_int64), ("device_errors", ctypes.c_uint32), ("kernel_launches", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_double)]
 
 
@@ -67,7 +67,8 @@ _lib = None
 
 
 def library_path() -> str:
-    return _LIB_PATH
+    """The shared library to load: RD_LIBRARY (a build of this source elsewhere) or the in-tree build."""
+    return os.environ.get("RD_LIBRARY") or _LIB_PATH
 
 
 def load_library(build_if_missing: bool = True):
@@ -76,11 +77,12 @@ def load_library(build_if_missing: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        if build_if_missing:
+        path = library_path()
+        if build_if_missing and path == _LIB_PATH:
             build_library()
-        if not os.path.exists(_LIB_PATH):
-            raise ImportError(f"CUDA library not built: {_LIB_PATH}")
-        lib = ctypes.CDLL(_LIB_PATH)
+        if not os.path.exists(path):
+            raise ImportError(f"CUDA library not built: {path}")
+        lib = ctypes.CDLL(path)
         P, I = ctypes.c_void_p, ctypes.c_int32
         sig = {
             "rd_create_detector": ([ctypes.POINTER(rd_detector_desc), P, ctypes.POINTER(P)], I),

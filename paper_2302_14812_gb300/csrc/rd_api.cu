@@ -261,7 +261,7 @@ rd_status rd_zero_fields(rd_detector* d, rd_stream stream)
     if (!d) return fail(RD_ERR_ARG, "detector is NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     RD_CUDA(cudaMemsetAsync(d->fields, 0, d->field_bytes, s), "rd_zero_fields");
-    RD_CUDA(cudaMemsetAsync(&d->counters->clipped, 0, sizeof(unsigned long long), s), "rd_zero_fields");
+    RD_CUDA(cudaMemsetAsync(&d->counters->clipped, 0, 2 * sizeof(unsigned long long), s), "rd_zero_fields");
     d->n_deposits = 0;
     return RD_OK;
 }
@@ -276,7 +276,7 @@ rd_status rd_deposit_trajectories(rd_detector* d, const rd_traj* t, rd_stream st
     if (t->n_part == 0 || S < 1) return RD_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool mixed = d->precision == RD_MIXED;
-    const size_t rec_size = mixed ? sizeof(RecF) : sizeof(RecD);
+    const size_t rec_size = mixed ? sizeof(RecM) : sizeof(RecD);
     const size_t per_part_rec = rec_size * (size_t)t->n_samples;
     const size_t per_part_in = 2 * 3 * sizeof(double) * (size_t)t->n_samples + sizeof(double);
     // particle chunk: bounded scratch (records + staged input)
@@ -328,9 +328,11 @@ rd_status rd_deposit_trajectories(rd_detector* d, const rd_traj* t, rd_stream st
         P.inv_dt_det = 1.0 / d->dt_det;
         P.dt_f = (float)t->dt;
         P.du_scale = (float)(t->dt / d->dt_det);
+        P.W = (float)(d->dt_det / t->dt);
+        P.invW = (float)(t->dt / d->dt_det);
         if (mixed) {
             RD_CUDA(launch_precompute_mixed(x, u, np, t->n_samples, t->dt, d->flags,
-                                            static_cast<RecF*>(d->rec), d->counters, s),
+                                            static_cast<RecM*>(d->rec), d->counters, s),
                     "precompute");
             LaunchTimer timer(d, s);
             RD_CUDA(launch_deposit_mixed(P, s), "deposit (mixed)");
@@ -399,6 +401,7 @@ rd_status rd_get_stats(rd_detector* d, rd_stream stream, rd_stats* out)
     RD_CUDA(cudaMemcpyAsync(&c, d->counters, sizeof c, cudaMemcpyDeviceToHost, s), "read counters");
     RD_CUDA(cudaStreamSynchronize(s), "rd_get_stats");
     out->n_clipped = (int64_t)c.clipped;
+    out->n_bin_crossings = (int64_t)c.crossings;
     out->n_deposits = d->n_deposits;
     out->device_errors = c.errors;
     collect_timings(d);

@@ -36,10 +36,10 @@ __device__ __forceinline__ bool finite3(const double* v)
 
 __global__ void k_precompute_mixed(const double* __restrict__ x, const double* __restrict__ u,
                                    int n_part, int n_samples, double dt, int flags,
-                                   RecF* __restrict__ rec, DevCounters* counters)
+                                   RecM* __restrict__ rec, DevCounters* counters)
 {
     const long long total = (long long)n_part * n_samples;
-    const float near_on = (flags & RD_NEAR) ? 1.f : 0.f;
+    const double near_on = (flags & RD_NEAR) ? 1.0 : 0.0;
     const bool far_on = (flags & RD_FAR) != 0;
     const double inv_dt = 1.0 / dt;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -64,12 +64,30 @@ __global__ void k_precompute_mixed(const double* __restrict__ x, const double* _
             bad = bad || !(g > 0.0);
         }
         if (bad) atomicOr(&counters->errors, ERRBIT_INPUT);
-        RecF r;
-        r.xa = make_float4((float)xk[0], (float)xk[1], (float)xk[2], (float)(0.5 * ig2));
-        r.bb = make_float4((float)bx, (float)by, (float)bz, near_on * (float)ig2);
-        r.bd = far_on ? make_float4((float)ax, (float)ay, (float)az, (float)(dt * g))
-                      : make_float4(0.f, 0.f, 0.f, (float)(dt * g));
-        r.vb = make_float4((float)vx, (float)vy, (float)vz, (float)g);
+        // delta = beta_k - vbar_k (difference of end-point and chord velocities)
+        const double ex = bx - vx, ey = by - vy, ez = bz - vz;
+#if RD_PACKED
+        auto put = [](double v) { const float f = (float)v; return make_float2(f, f); };
+#else
+        auto put = [](double v) { return (float)v; };
+#endif
+        RecM r;
+        r.nx = put(-xk[0]);
+        r.ny = put(-xk[1]);
+        r.nz = put(-xk[2]);
+        r.nhig2 = put(-0.5 * ig2);
+        r.nbx = put(-bx);
+        r.nby = put(-by);
+        r.nbz = put(-bz);
+        r.ig2n = put(near_on * ig2);
+        r.bdx = put(far_on ? ax : 0.0);
+        r.bdy = put(far_on ? ay : 0.0);
+        r.bdz = put(far_on ? az : 0.0);
+        r.dtg = put(dt * g);
+        r.d2x = put(2.0 * ex);
+        r.d2y = put(2.0 * ey);
+        r.d2z = put(2.0 * ez);
+        r.gd = put(g + (ex * ex + ey * ey + ez * ez));
         rec[i] = r;
     }
 }
@@ -103,241 +121,6 @@ __global__ void k_precompute_fp64(const double* __restrict__ x, const double* __
         r.bb = D4{bx, by, bz, ig2};
         r.bd = D4{ax, ay, az, 0.0};
         rec[i] = r;
-    }
-}
-
-// =============================================================================================
-// Eq. 2 in bin units, FP64, every operation separately rounded:
-//   t_k = t0 + k*dt,  R = sqrt((dx*dx + dy*dy) + dz*dz),  u = ((t_k + R) - T0) * inv_dt_det
-// =============================================================================================
-__device__ __forceinline__ double arrival_bins(double xk0, double xk1, double xk2, const D4& cell,
-                                               double t0, int k, double dt, double inv_dt_det,
-                                               double& R)
-{
-    const double dx = __dsub_rn(cell.x, xk0);
-    const double dy = __dsub_rn(cell.y, xk1);
-    const double dz = __dsub_rn(cell.z, xk2);
-    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    R = __dsqrt_rn(r2);
-    const double tk = __dadd_rn(t0, __dmul_rn((double)k, dt));
-    return __dmul_rn(__dsub_rn(__dadd_rn(tk, R), cell.w), inv_dt_det);
-}
-
-__device__ __forceinline__ int clamp_bin(double fb)
-{
-    return (int)fmin(fmax(fb, -1073741824.0), 1073741824.0);
-}
-
-// =============================================================================================
-// Mixed-precision deposit
-// =============================================================================================
-struct MixedState {
-    int b;          // bin currently being filled (may lie outside [0, n_bins))
-    float f;        // position inside bin b, in bins
-    float Rpd;      // R_{k-1} + dt
-    float acc[6];   // running integral of the field over bin b since the thread entered it
-    int n_below;    // intervals of the chunk whose start lies before the window
-    int n_above;    // intervals whose end lies after the window
-};
-
-__device__ __forceinline__ void flush_f32(float* row, int n_bins, int b, const float* v)
-{
-    if ((unsigned)b < (unsigned)n_bins) {
-        float* p = row + (size_t)b * 8;
-        red_add_v4(p, v[0], v[1], v[2], v[3]);
-        red_add_v2(p + 4, v[4], v[5]);
-    }
-}
-
-// Field of one sample at this cell and the arrival-time increment of its interval.
-// Eq. 1 is evaluated as E = s [ (n-beta)(gamma^-2/R + n.betadot) - betadot kappa ],
-// s = q/(kappa^3 R), using n x ((n-beta) x betadot) = (n-beta)(n.betadot) - betadot (n.(n-beta))
-// and n.(n-beta) = kappa; kappa = (gamma^-2 + |n-beta|^2)/2 avoids the cancellation in 1-beta.n.
-// Interval length in arrival time (exact identity, every term positive):
-//   t'_k - t'_{k-1} = dt [dt g + R_k (g + |n_k - vbar|^2)] / (dt + R_k + R_{k-1}),
-//   vbar = (x_k - x_{k-1})/dt, g = 1 - |vbar|^2.
-__device__ __forceinline__ float mixed_field(const RecF& r, float Px, float Py, float Pz, float qf,
-                                             float dt_f, float du_scale, float& Rpd, float* F)
-{
-    const float dx = Px - r.xa.x, dy = Py - r.xa.y, dz = Pz - r.xa.z;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float rinv = rsqrtf(r2);
-    const float R = r2 * rinv;
-    const float nx = dx * rinv, ny = dy * rinv, nz = dz * rinv;
-    // arrival-time step in bins
-    const float mx = nx - r.vb.x, my = ny - r.vb.y, mz = nz - r.vb.z;
-    const float gg = fmaf(mx, mx, fmaf(my, my, fmaf(mz, mz, r.vb.w)));
-    const float num = fmaf(R, gg, r.bd.w);
-    const float du = __fdividef(num * du_scale, R + Rpd);
-    Rpd = R + dt_f;
-    // Eq. 1
-    const float bx = nx - r.bb.x, by = ny - r.bb.y, bz = nz - r.bb.z;
-    const float nb2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
-    const float kap = fmaf(nb2, 0.5f, r.xa.w);
-    const float ik = __fdividef(1.f, kap);
-    const float s = qf * rinv * (ik * ik * ik);
-    const float nbd = fmaf(nx, r.bd.x, fmaf(ny, r.bd.y, nz * r.bd.z));
-    const float c1 = fmaf(r.bb.w, rinv, nbd) * s;
-    const float ks = kap * s;
-    const float Ex = fmaf(bx, c1, -r.bd.x * ks);
-    const float Ey = fmaf(by, c1, -r.bd.y * ks);
-    const float Ez = fmaf(bz, c1, -r.bd.z * ks);
-    F[0] = Ex;
-    F[1] = Ey;
-    F[2] = Ez;
-    F[3] = fmaf(ny, Ez, -nz * Ey);
-    F[4] = fmaf(nz, Ex, -nx * Ez);
-    F[5] = fmaf(nx, Ey, -ny * Ex);
-    return du;
-}
-
-// Integrating deposit (Section 3.2) of one interval of length du (bins) starting at (b, f).
-__device__ __forceinline__ void mixed_deposit(MixedState& st, const float* F, float du, float* row,
-                                              int n_bins, int k, int k_begin, int k_end)
-{
-    const float fn = st.f + du;
-    if (fn < 1.f) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) st.acc[i] = fmaf(F[i], du, st.acc[i]);
-        st.f = fn;
-        return;
-    }
-    const float w1 = 1.f - st.f;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) st.acc[i] = fmaf(F[i], w1, st.acc[i]);
-    flush_f32(row, n_bins, st.b, st.acc);
-    const int b_old = st.b;
-    int b = st.b + 1;
-    float rem = fn - 1.f;
-    if (rem >= 1.f) {
-        const int nfull = (int)fminf(floorf(rem), 16777216.f);
-        const int lo = max(b, 0), hi = min(b + nfull - 1, n_bins - 1);
-        for (int j = lo; j <= hi; ++j) flush_f32(row, n_bins, j, F);
-        b += nfull;
-        rem -= (float)nfull;
-    }
-#pragma unroll
-    for (int i = 0; i < 6; ++i) st.acc[i] = F[i] * rem;
-    st.b = b;
-    st.f = rem;
-    if (b_old < 0 && b >= 0) st.n_below = k - k_begin + 1;
-    if (b_old < n_bins && b >= n_bins) st.n_above = k_end - k + 1;
-}
-
-__global__ void __launch_bounds__(kDepositThreads, 4) k_deposit_mixed(const DepositParams P)
-{
-    __shared__ __align__(128) RecF tile[2][kTileSteps];
-    __shared__ __align__(8) uint64_t bar[2];
-
-    const int cb = (int)(blockIdx.x % (unsigned)P.n_cell_blocks);
-    const int item = (int)(blockIdx.x / (unsigned)P.n_cell_blocks);
-    const int p = item / P.n_chunks;
-    const int c = item - p * P.n_chunks;
-    const int S = P.n_samples - 1;
-    const int k_begin = 1 + c * P.chunk;
-    const int k_end = min(S, k_begin + P.chunk - 1);
-    const int n_int = k_end - k_begin + 1;
-    const int n_tiles = (n_int + kTileSteps - 1) / kTileSteps;
-    const RecF* rec = static_cast<const RecF*>(P.rec) + (size_t)p * P.n_samples;
-    const int tid = threadIdx.x;
-    const int cell = cb * kDepositThreads + tid;
-    const bool active = cell < P.n_pix;
-
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        for (int t = 0; t < 2 && t < n_tiles; ++t) {
-            const int k0 = k_begin + t * kTileSteps;
-            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k0 + 1) * sizeof(RecF);
-            mbar_arrive_expect_tx(&bar[t], bytes);
-            bulk_g2s(tile[t], rec + k0, bytes, &bar[t]);
-        }
-    }
-
-    // ---- per-cell anchors: exact FP64 arrival (bins) at both ends of the chunk ----
-    MixedState st;
-    float Px = 0.f, Py = 0.f, Pz = 0.f;
-    int b_end = 0;
-    float f_end = 0.f;
-    bool live = false;
-    float* row = nullptr;
-    if (active) {
-        const D4 cl = P.cells[cell];
-        const double* xp = P.x + (size_t)p * P.n_samples * 3;
-        double Ra, Re;
-        const double* xa = xp + 3 * (size_t)(k_begin - 1);
-        const double* xe = xp + 3 * (size_t)k_end;
-        const double ua = arrival_bins(xa[0], xa[1], xa[2], cl, P.t0, k_begin - 1, P.dt, P.inv_dt_det, Ra);
-        const double ue = arrival_bins(xe[0], xe[1], xe[2], cl, P.t0, k_end, P.dt, P.inv_dt_det, Re);
-        live = (ue > 0.0) && (ua < (double)P.n_bins);
-        const double fa = floor(ua), fe = floor(ue);
-        st.b = clamp_bin(fa);
-        st.f = (float)(ua - fa);
-        b_end = clamp_bin(fe);
-        f_end = (float)(ue - fe);
-        st.Rpd = (float)Ra + P.dt_f;
-        st.n_below = (ua < 0.0) ? n_int : 0;
-        st.n_above = 0;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) st.acc[i] = 0.f;
-        Px = (float)cl.x;
-        Py = (float)cl.y;
-        Pz = (float)cl.z;
-        row = static_cast<float*>(P.fields) + (size_t)cell * P.n_bins * 8;
-        if (!live) {
-            unsigned long long clip = (unsigned long long)n_int;
-            atomicAdd(&P.counters->clipped, clip);
-        }
-    }
-    const float qf = P.q ? (float)P.q[p] : 1.f;
-
-    for (int t = 0; t < n_tiles; ++t) {
-        const int buf = t & 1;
-        const bool ok = mbar_wait_bounded(&bar[buf], (unsigned)(t >> 1) & 1u);
-        if (__syncthreads_or(!ok)) {
-            // a bulk copy did not complete: record it, let outstanding copies land, stop.
-            if (tid == 0) {
-                atomicOr(&P.counters->errors, ERRBIT_TIMEOUT);
-                for (int u = t; u < t + 2 && u < n_tiles; ++u)
-                    (void)mbar_wait_bounded(&bar[u & 1], (unsigned)(u >> 1) & 1u);
-            }
-            __syncthreads();
-            return;
-        }
-        const int k0 = k_begin + t * kTileSteps;
-        const int cnt = min(kTileSteps, k_end - k0 + 1);
-        const bool last_tile = (t == n_tiles - 1);
-        if (live) {
-            const int n_regular = last_tile ? cnt - 1 : cnt;
-            float F[6];
-            for (int i = 0; i < n_regular; ++i) {
-                const RecF r = tile[buf][i];
-                const float du = mixed_field(r, Px, Py, Pz, qf, P.dt_f, P.du_scale, st.Rpd, F);
-                mixed_deposit(st, F, du, row, P.n_bins, k0 + i, k_begin, k_end);
-            }
-            if (last_tile) {
-                // last interval of the chunk ends on the exact FP64 anchor
-                const RecF r = tile[buf][cnt - 1];
-                (void)mixed_field(r, Px, Py, Pz, qf, P.dt_f, P.du_scale, st.Rpd, F);
-                const float du = ((float)(b_end - st.b) + f_end) - st.f;
-                mixed_deposit(st, F, du, row, P.n_bins, k_end, k_begin, k_end);
-                flush_f32(row, P.n_bins, st.b, st.acc);
-                const int clip = min(n_int, st.n_below + st.n_above);
-                if (clip > 0) atomicAdd(&P.counters->clipped, (unsigned long long)clip);
-            }
-        }
-        __syncthreads();
-        if (tid == 0 && t + 2 < n_tiles) {
-            fence_proxy_async();
-            const int k2 = k_begin + (t + 2) * kTileSteps;
-            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k2 + 1) * sizeof(RecF);
-            mbar_arrive_expect_tx(&bar[buf], bytes);
-            bulk_g2s(tile[buf], rec + k2, bytes, &bar[buf]);
-        }
     }
 }
 
@@ -432,10 +215,11 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
     __shared__ __align__(128) RecD tile[2][kTileSteps];
     __shared__ __align__(8) uint64_t bar[2];
 
-    const int cb = (int)(blockIdx.x % (unsigned)P.n_cell_blocks);
-    const int item = (int)(blockIdx.x / (unsigned)P.n_cell_blocks);
-    const int p = item / P.n_chunks;
-    const int c = item - p * P.n_chunks;
+    const unsigned bid = blockIdx.x;
+    const int p = (int)(bid % (unsigned)P.n_part);
+    const unsigned rest = bid / (unsigned)P.n_part;
+    const int cb = (int)(rest % (unsigned)P.n_cell_blocks);
+    const int c = (int)(rest / (unsigned)P.n_cell_blocks);
     const int S = P.n_samples - 1;
     const int k_begin = 1 + c * P.chunk;
     const int k_end = min(S, k_begin + P.chunk - 1);
@@ -561,7 +345,7 @@ static int grid_for(long long n, int threads)
 }
 
 cudaError_t launch_precompute_mixed(const double* x, const double* u, int n_part, int n_samples,
-                                    double dt, int flags, RecF* rec, DevCounters* counters,
+                                    double dt, int flags, RecM* rec, DevCounters* counters,
                                     cudaStream_t s)
 {
     const long long n = (long long)n_part * n_samples;
@@ -575,15 +359,6 @@ cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part,
 {
     const long long n = (long long)n_part * n_samples;
     k_precompute_fp64<<<grid_for(n, 256), 256, 0, s>>>(x, u, n_part, n_samples, dt, rec, counters);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s)
-{
-    const long long blocks = (long long)p.n_cell_blocks * p.n_part * p.n_chunks;
-    if (blocks <= 0) return cudaSuccess;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    k_deposit_mixed<<<(unsigned)blocks, kDepositThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,7 @@
 //   cell table     D4     [n_pix]              (x, y, z, T0 = t_min + pix_t0)
 //   mixed fields   float   [n_pix][n_bins][8]  (Ex Ey Ez Bx | By Bz 0 0): one 32-byte sector per bin
 //   fp64 fields    double  [n_pix][n_bins][6]  (Ex Ey Ez Bx By Bz)
-//   records        RecF / RecD [n_part][n_samples]: per-sample quantities of Algorithm 1,
+//   records        RecM / RecD [n_part][n_samples]: per-sample quantities of Algorithm 1,
 //                  computed once per call and read by every cell (staged through shared memory
 //                  with bulk asynchronous copies).
 #pragma once
@@ -29,23 +29,43 @@ struct DevCounters {
     unsigned errors;
     unsigned pad;
     unsigned long long clipped;
+    unsigned long long crossings;   // bin edges crossed by arrival intervals (mixed path)
 };
 
 // ---------------------------------------------------------------------------------------------
 // per-sample records
 // ---------------------------------------------------------------------------------------------
-// Mixed path, 64 bytes.  For interval k (between samples k-1 and k) the record of sample k holds
-//   xa = (x_k, gamma_k^-2 / 2)               geometry (FP32) and half the Lorentz factor term of kappa
-//   bb = (beta_k, near ? gamma_k^-2 : 0)     velocity; velocity-term factor
-//   bd = (far ? betadot_k : 0, dt*g_k)       acceleration (backward difference); arrival-step constant
-//   vb = (vbar_k, g_k)                       chord velocity (x_k - x_{k-1})/dt, g_k = 1 - |vbar_k|^2
-struct __align__(16) RecF {
-    float4 xa;
-    float4 bb;
-    float4 bd;
-    float4 vb;
+// Mixed path, per-sample constants of interval k (16 values), with signs chosen so that every step
+// of the field is an add / mul / fma:
+//   nx, ny, nz = -x_k               nhig2 = -gamma_k^-2 / 2
+//   nbx..nbz   = -beta_k            ig2n  = near ? gamma_k^-2 : 0
+//   bdx..bdz   = far ? betadot_k : 0                 dtg = dt g_k,  g_k = 1 - |vbar_k|^2
+//   d2x..d2z   = 2 (beta_k - vbar_k)  gd  = g_k + |beta_k - vbar_k|^2
+// (vbar_k = (x_k - x_{k-1})/dt is the chord velocity of the interval).
+// RD_PACKED = 1: every value stored twice (RecP, 128 bytes) so that one 64-bit register pair
+// feeds a packed f32x2 operation for two cells; RD_PACKED = 0: stored once (RecS, 64 bytes).
+#ifndef RD_PACKED
+#define RD_PACKED 0
+#endif
+struct __align__(16) RecS {
+    float nx, ny, nz, nhig2;
+    float nbx, nby, nbz, ig2n;
+    float bdx, bdy, bdz, dtg;
+    float d2x, d2y, d2z, gd;
 };
-static_assert(sizeof(RecF) == 64, "RecF must be 64 bytes");
+static_assert(sizeof(RecS) == 64, "RecS must be 64 bytes");
+struct __align__(16) RecP {
+    float2 nx, ny, nz, nhig2;
+    float2 nbx, nby, nbz, ig2n;
+    float2 bdx, bdy, bdz, dtg;
+    float2 d2x, d2y, d2z, gd;
+};
+static_assert(sizeof(RecP) == 128, "RecP must be 128 bytes");
+#if RD_PACKED
+typedef RecP RecM;
+#else
+typedef RecS RecM;
+#endif
 
 struct __align__(32) D4 {
     double x, y, z, w;
@@ -63,7 +83,7 @@ static_assert(sizeof(RecD) == 96, "RecD must be 96 bytes");
 // kernel parameter blocks
 // ---------------------------------------------------------------------------------------------
 struct DepositParams {
-    const void* rec;            // RecF or RecD [n_part][n_samples]
+    const void* rec;            // RecM or RecD [n_part][n_samples]
     const double* x;            // [n_part][n_samples][3] FP64 positions (anchors of the mixed path)
     const double* q;            // [n_part] or null
     const D4* cells;            // [n_pix] (x, y, z, T0)
@@ -76,6 +96,8 @@ struct DepositParams {
     int chunk;                  // intervals per work item
     int n_chunks;               // ceil(S / chunk)
     int n_cell_blocks;          // ceil(n_pix / cells per CTA)
+    float W;                    // mixed: bin width in units of dt (dt_det / dt)
+    float invW;
     double t0;
     double dt;
     double inv_dt_det;
@@ -83,14 +105,20 @@ struct DepositParams {
     float du_scale;             // dt / dt_det
 };
 
-constexpr int kDepositThreads = 256;   // one cell per thread
+constexpr int kDepositThreads = 256;   // FP64 kernel: one cell per thread
+#ifndef RD_MIXED_MINBLOCKS
+#define RD_MIXED_MINBLOCKS 6
+#endif
+constexpr int kMixedCells = 2;                 // mixed kernel: two cells per thread, packed f32x2
+constexpr int kMixedThreads = 128;             // 256 cells per CTA
+constexpr int kMixedCellsPerCta = kMixedThreads * kMixedCells;
 constexpr int kTileSteps = 64;         // intervals per shared-memory tile
 constexpr int kDefaultChunk = 1024;    // intervals per work item (one FP64 anchor at each end)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // give up a wait after 2 s
 
 // launchers (rd_deposit.cu)
 cudaError_t launch_precompute_mixed(const double* x, const double* u, int n_part, int n_samples,
-                                    double dt, int flags, RecF* rec, DevCounters* counters,
+                                    double dt, int flags, RecM* rec, DevCounters* counters,
                                     cudaStream_t s);
 cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part, int n_samples,
                                    double dt, RecD* rec, DevCounters* counters, cudaStream_t s);
@@ -180,6 +208,25 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
                  : "memory");
 }
 
+// Predicated forms: no memory access at all when `on` is false (the address is then not used).
+__device__ __forceinline__ void red_add_v4_if(bool on, float* addr, float a, float b, float c, float d)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %5, 0;\n\t"
+        "@p red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n\t}" ::"l"(addr),
+        "f"(a), "f"(b), "f"(c), "f"(d), "r"((unsigned)on)
+        : "memory");
+}
+
+__device__ __forceinline__ void red_add_v2_if(bool on, float* addr, float a, float b)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\t"
+        "@p red.global.add.v2.f32 [%0], {%1, %2};\n\t}" ::"l"(addr),
+        "f"(a), "f"(b), "r"((unsigned)on)
+        : "memory");
+}
+
 __device__ __forceinline__ void red_add_v2(float* addr, float a, float b)
 {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
@@ -189,6 +236,44 @@ __device__ __forceinline__ void red_add_f64(double* addr, double v)
 {
     asm volatile("red.global.add.f64 [%0], %1;" ::"l"(addr), "d"(v) : "memory");
 }
+
+// Single-instruction approximations (relative error about 1 ulp, denormals flushed).
+__device__ __forceinline__ float fast_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float fast_rsqrt(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// =============================================================================================
+// Eq. 2 in bin units, FP64, every operation separately rounded:
+//   t_k = t0 + k*dt,  R = sqrt((dx*dx + dy*dy) + dz*dz),  u = ((t_k + R) - T0) * inv_dt_det
+// =============================================================================================
+__device__ __forceinline__ double arrival_bins(double xk0, double xk1, double xk2, const D4& cell,
+                                               double t0, int k, double dt, double inv_dt_det,
+                                               double& R)
+{
+    const double dx = __dsub_rn(cell.x, xk0);
+    const double dy = __dsub_rn(cell.y, xk1);
+    const double dz = __dsub_rn(cell.z, xk2);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    R = __dsqrt_rn(r2);
+    const double tk = __dadd_rn(t0, __dmul_rn((double)k, dt));
+    return __dmul_rn(__dsub_rn(__dadd_rn(tk, R), cell.w), inv_dt_det);
+}
+
+__device__ __forceinline__ int clamp_bin(double fb)
+{
+    return (int)fmin(fmax(fb, -1073741824.0), 1073741824.0);
+}
+
 #endif
 
 }  // namespace rd
