@@ -25,7 +25,7 @@ __all__ = [
     "RD_MEM_HOST", "RD_F32", "RD_F64", "RDError", "rd_detector_desc", "rd_traj", "rd_stats",
     "load_library", "library_path", "rd_create_detector", "rd_destroy", "rd_zero_fields",
     "rd_deposit_trajectories", "rd_read_fields", "rd_synchronize", "rd_get_stats",
-    "rd_set_timing", "rd_last_error", "rd_version", "RadiationDetector", "build_library",
+    "rd_set_timing", "rd_adjoint_trajectories", "rd_last_error", "rd_version", "DepositFunction", "RadiationDetector", "build_library",
 ]
 
 RD_OK, RD_ERR_ARG, RD_ERR_CUDA, RD_ERR_OOM, RD_ERR_STATE, RD_ERR_TIMEOUT, RD_ERR_BOUNDS, RD_ERR_INPUT = range(8)
@@ -93,6 +93,7 @@ def load_library(build_if_missing: bool = True):
             "rd_synchronize": ([P, P], I),
             "rd_get_stats": ([P, P, ctypes.POINTER(rd_stats)], I),
             "rd_set_timing": ([P, I], I),
+            "rd_adjoint_trajectories": ([P, ctypes.POINTER(rd_traj), P, P, I, P, P, P], I),
             "rd_last_error": ([], ctypes.c_char_p),
             "rd_version": ([], ctypes.c_char_p),
         }
@@ -159,6 +160,12 @@ def rd_get_stats(det: int, stream=None) -> rd_stats:
     st = rd_stats()
     _check(load_library().rd_get_stats(det, _stream_ptr(stream), ctypes.byref(st)), "rd_get_stats")
     return st
+
+
+def rd_adjoint_trajectories(det: int, traj: rd_traj, gE_ptr, gB_ptr, gdtype: int, gx_ptr, gu_ptr,
+                            stream=None) -> None:
+    _check(load_library().rd_adjoint_trajectories(det, ctypes.byref(traj), gE_ptr, gB_ptr, gdtype, gx_ptr,
+                                                  gu_ptr, _stream_ptr(stream)), "rd_adjoint_trajectories")
 
 
 def rd_set_timing(det: int, enable: bool) -> None:
@@ -277,6 +284,29 @@ class RadiationDetector:
         rd_read_fields(self._h, E.data_ptr(), B.data_ptr(), code, RD_MEM_DEVICE, stream)
         return E, B
 
+    def adjoint(self, x, u, q, t0, dt, gE, gB=None, stream=None):
+        """d loss / d x and d loss / d u (FP64 CUDA tensors [n_part][n_samples][3]) for upstream
+        gradients gE, gB ([n_pix][n_bins][3] CUDA tensors, float32 or float64; gB may be None)."""
+        import torch
+        t, keep = self.traj_struct(x, u, q, t0, dt)
+        if t.mem != RD_MEM_DEVICE:
+            raise ValueError("the adjoint needs CUDA trajectories")
+        gdt = gE.dtype if gE is not None else gB.dtype
+        code = RD_F32 if gdt == torch.float32 else RD_F64
+        tdt = torch.float32 if code == RD_F32 else torch.float64
+        gEc = None if gE is None else gE.detach().to(tdt).contiguous()
+        gBc = None if gB is None else gB.detach().to(tdt).contiguous()
+        for g in (gEc, gBc):
+            if g is not None and (not g.is_cuda or g.numel() != self.n_pix * self.n_bins * 3):
+                raise ValueError("seeds must be CUDA tensors of shape [n_pix][n_bins][3]")
+        gx = torch.zeros(tuple(x.shape), dtype=torch.float64, device=x.device)
+        gu = torch.zeros_like(gx)
+        rd_adjoint_trajectories(self._h, t, None if gEc is None else gEc.data_ptr(),
+                                None if gBc is None else gBc.data_ptr(), code, gx.data_ptr(), gu.data_ptr(),
+                                stream)
+        self._keep = keep + [gEc, gBc]
+        return gx, gu
+
     def synchronize(self, stream=None):
         rd_synchronize(self._h, stream)
 
@@ -302,3 +332,37 @@ class RadiationDetector:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class DepositFunction:
+    """Differentiable deposit: (x, u) -> (E, B) through a RadiationDetector (mixed precision).
+
+    forward: zero the detector, deposit, return E, B as float64 CUDA tensors [n_pix][n_bins][3];
+    backward: the adjoint kernel gives d loss / d x and d loss / d u.  q, t0 and dt are constants.
+    Usage: E, B = DepositFunction.apply(det, x, u, q, t0, dt)."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, det, x, u, q, t0, dt):
+        if cls._fn is None:
+            import torch
+
+            class _Deposit(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, x, u, det, q, t0, dt):
+                    det.zero()
+                    det.deposit(x.detach(), u.detach(), q, t0, dt)
+                    E, B = det.read("float64", x.device)
+                    ctx.det, ctx.q, ctx.t0, ctx.dt = det, q, t0, dt
+                    ctx.save_for_backward(x, u)
+                    return E, B
+
+                @staticmethod
+                def backward(ctx, gE, gB):
+                    x, u = ctx.saved_tensors
+                    gx, gu = ctx.det.adjoint(x.detach(), u.detach(), ctx.q, ctx.t0, ctx.dt, gE, gB)
+                    return gx.to(x.dtype), gu.to(u.dtype), None, None, None, None
+
+            cls._fn = _Deposit
+        return cls._fn.apply(x, u, det, q, t0, dt)

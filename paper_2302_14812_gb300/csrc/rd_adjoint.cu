@@ -1,0 +1,386 @@
+// Adjoint (gather) of the mixed-precision deposit: d loss / d x and d loss / d beta for every
+// trajectory sample, given the upstream gradient g = d loss / d (E_det, B_det).
+//
+// The deposit adds F_k * w_b(u_{k-1}, u_k) to bin b, with F_k = (E, B) of Eq. 1 at sample k and
+// w_b = |[u_{k-1}, u_k] ∩ [b, b+1)| in bin units (Section 3.2).  Its transpose, per (cell, interval):
+//   G_k = sum_b w_b g_b                      gathered seed, drives the VJP of Eq. 1
+//   d loss / d u_k     += F_k . g(bin(u_k))       (end point of interval k)
+//   d loss / d u_{k-1} -= F_k . g(bin(u_{k-1}))   (start point), with du/dR = 1/dt_det
+// and beta_k, betadot_k = (beta_k - beta_{k-1})/dt, n_k, R_k carry the chain to x_k and beta.
+// The walk over bins, arrival times and anchors is the forward walk (same records, same FP32
+// increments anchored in FP64), so the gradient is that of the computed deposit.  Field math in
+// FP32; per step the 256 cells of a CTA are summed (warp shuffles, then shared memory) and the
+// sums are added to FP64 buffers.
+#include <math.h>
+
+#include "rd_internal.cuh"
+
+namespace rd {
+
+namespace {
+
+struct ACell {
+    float Px, Py, Pz;
+    float f;            // time spent in bin b, units of dt
+    float Rpd;          // R_{k-1} + dt
+    int b;              // current bin
+    float g[6];         // seed of bin b (zero outside the window)
+    float np[3];        // n of the previous sample
+    float pend[6];      // partial gradient of the previous sample: d/dx (3), d/dbeta (3)
+    const float* row;   // seed row [n_bins][8]
+};
+
+__device__ __forceinline__ void load_seed(const float* row, int n_bins, int b, float* g)
+{
+    if ((unsigned)b < (unsigned)n_bins) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(row + (size_t)b * 8));
+        const float4 c = __ldg(reinterpret_cast<const float4*>(row + (size_t)b * 8 + 4));
+        g[0] = a.x;
+        g[1] = a.y;
+        g[2] = a.z;
+        g[3] = a.w;
+        g[4] = c.x;
+        g[5] = c.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) g[i] = 0.f;
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One interval k of one cell: forward field, gathered seed, VJP.  Returns in `out` the finished
+// gradient of sample k-1 (d/dx, d/dbeta) and keeps sample k's partial in c.pend.
+template <bool LAST>
+__device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointParams& P, float q,
+                                         float near, float far, int b_end, float f_end, float* out)
+{
+    const float W = P.W;
+    // ---- forward: geometry, arrival increment, Eq. 1 ----
+    const float dx = c.Px + r.nx, dy = c.Py + r.ny, dz = c.Pz + r.nz;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rinv = fast_rsqrt(r2);
+    const float nx = dx * rinv, ny = dy * rinv, nz = dz * rinv;
+    const float bx = nx + r.nbx, by = ny + r.nby, bz = nz + r.nbz;          // n - beta
+    const float nb2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+    const float gg = fmaf(bx, r.d2x, fmaf(by, r.d2y, fmaf(bz, r.d2z, nb2 + r.gd)));
+    const float du = fmaf(r.dtg, rinv, gg) * fast_rcp(fmaf(c.Rpd, rinv, 1.f));
+    c.Rpd = fmaf(r2, rinv, P.dt_f);
+    const float kap = fmaf(nb2, 0.5f, -r.nhig2);
+    const float ik = fast_rcp(kap);
+    const float s = q * rinv * (ik * ik * ik);
+    const float bdx = r.bdx, bdy = r.bdy, bdz = r.bdz;
+    const float dbd = fmaf(nx, bdx, fmaf(ny, bdy, nz * bdz));
+    const float c1 = fmaf(r.ig2n, rinv, dbd);                               // gamma^-2/R + n.betadot
+    const float Vx = fmaf(bx, c1, -kap * bdx), Vy = fmaf(by, c1, -kap * bdy), Vz = fmaf(bz, c1, -kap * bdz);
+    const float Ex = s * Vx, Ey = s * Vy, Ez = s * Vz;
+    const float Bx = fmaf(ny, Ez, -nz * Ey), By = fmaf(nz, Ex, -nx * Ez), Bz = fmaf(nx, Ey, -ny * Ex);
+
+    // ---- transpose of the integrating deposit: gathered seed and end-point seeds ----
+    float gs0[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) gs0[i] = c.g[i];
+    const float fn = LAST ? fmaf((float)(b_end - c.b), W, f_end) : c.f + du;
+    float G[6];
+    if (fn < W) {
+        const float w = (fn - c.f) * P.du_scale;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) G[i] = c.g[i] * w;
+        c.f = fn;
+    } else {
+        const float w1 = (W - c.f) * P.du_scale;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) G[i] = c.g[i] * w1;
+        float rem = fn - W;
+        c.b += 1;
+        if (rem >= W) {
+            // whole bins inside the interval (bounded by the window)
+            const float nf = floorf(rem * P.invW);
+            const int nfull = (int)fminf(nf, 16777216.f);
+            const int lo = max(c.b, 0), hi = min(c.b + nfull - 1, P.n_bins - 1);
+            const float wf = W * P.du_scale;
+            float tmp[6];
+            for (int j = lo; j <= hi; ++j) {
+                load_seed(c.row, P.n_bins, j, tmp);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) G[i] = fmaf(tmp[i], wf, G[i]);
+            }
+            c.b += nfull;
+            rem = fminf(fmaxf(fmaf(-nf, W, rem), 0.f), W * 0.99999994f);
+        }
+        load_seed(c.row, P.n_bins, c.b, c.g);
+        const float w2 = rem * P.du_scale;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) G[i] = fmaf(c.g[i], w2, G[i]);
+        c.f = rem;
+    }
+    // F_k . g(bin(u_k)) and F_k . g(bin(u_{k-1}))
+    const float a_end = Ex * c.g[0] + Ey * c.g[1] + Ez * c.g[2] + Bx * c.g[3] + By * c.g[4] + Bz * c.g[5];
+    const float a_beg = Ex * gs0[0] + Ey * gs0[1] + Ez * gs0[2] + Bx * gs0[3] + By * gs0[4] + Bz * gs0[5];
+
+    // ---- VJP of Eq. 1 with B = n x E, seed (GE, GB) = G ----
+    const float GEx = G[0], GEy = G[1], GEz = G[2], GBx = G[3], GBy = G[4], GBz = G[5];
+    // L = E.H + n.(E x GB),  H = GE + GB x n
+    const float Hx = GEx + (GBy * nz - GBz * ny), Hy = GEy + (GBz * nx - GBx * nz), Hz = GEz + (GBx * ny - GBy * nx);
+    float gnx = Ey * GBz - Ez * GBy, gny = Ez * GBx - Ex * GBz, gnz = Ex * GBy - Ey * GBx;
+    const float gsv = Vx * Hx + Vy * Hy + Vz * Hz;                 // d/ds
+    const float gVx = s * Hx, gVy = s * Hy, gVz = s * Hz;          // d/dV
+    const float gc1 = bx * gVx + by * gVy + bz * gVz;             // d/dc1
+    const float gk = -(bdx * gVx + bdy * gVy + bdz * gVz) - 3.f * gsv * s * ik;   // d/dkappa
+    // V = (n - beta) c1 - kappa betadot;  c1 = gamma^-2/R + n.betadot;  kappa = 1 - n.beta
+    const float betx = -r.nbx, bety = -r.nby, betz = -r.nbz;
+    gnx += c1 * gVx + gc1 * bdx - gk * betx;
+    gny += c1 * gVy + gc1 * bdy - gk * bety;
+    gnz += c1 * gVz + gc1 * bdz - gk * betz;
+    const float gig2 = gc1 * rinv * near;                          // d/d(gamma^-2), gamma^-2 = 1 - beta^2
+    const float gbetx = -c1 * gVx - gk * nx - 2.f * gig2 * betx;
+    const float gbety = -c1 * gVy - gk * ny - 2.f * gig2 * bety;
+    const float gbetz = -c1 * gVz - gk * nz - 2.f * gig2 * betz;
+    const float gbdx = (-kap * gVx + gc1 * nx) * far, gbdy = (-kap * gVy + gc1 * ny) * far,
+                gbdz = (-kap * gVz + gc1 * nz) * far;              // d/dbetadot
+    // R: s = q/(kappa^3 R), c1 contains gamma^-2/R, and the arrival time u_k contains R/dt_det
+    const float gR = -gsv * s * rinv - gc1 * r.ig2n * rinv * rinv + a_end * (float)P.inv_dt_det;
+    // d = x_cell - x:  n = d/R, dR/dd = n
+    const float ndg = nx * gnx + ny * gny + nz * gnz;
+    const float gdx = (gnx - nx * ndg) * rinv + gR * nx;
+    const float gdy = (gny - ny * ndg) * rinv + gR * ny;
+    const float gdz = (gnz - nz * ndg) * rinv + gR * nz;
+    const float inv_dt = 1.f / P.dt_f;
+
+    // sample k-1: its arrival time starts this interval; betadot_k depends on beta_{k-1}
+    const float cb = a_beg * (float)P.inv_dt_det;                    // -dL/dR_{k-1} from this interval
+    out[0] = c.pend[0] + cb * c.np[0];
+    out[1] = c.pend[1] + cb * c.np[1];
+    out[2] = c.pend[2] + cb * c.np[2];
+    out[3] = c.pend[3] - gbdx * inv_dt;
+    out[4] = c.pend[4] - gbdy * inv_dt;
+    out[5] = c.pend[5] - gbdz * inv_dt;
+    // sample k (partial until the next interval adds its terms)
+    c.pend[0] = -gdx;
+    c.pend[1] = -gdy;
+    c.pend[2] = -gdz;
+    c.pend[3] = gbetx + gbdx * inv_dt;
+    c.pend[4] = gbety + gbdy * inv_dt;
+    c.pend[5] = gbetz + gbdz * inv_dt;
+    c.np[0] = nx;
+    c.np[1] = ny;
+    c.np[2] = nz;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kAdjointThreads, 2) k_adjoint_mixed(const AdjointParams P)
+{
+    __shared__ __align__(128) RecS tile[2][kTileSteps];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float red[kAdjointThreads / 32][kTileSteps][6];
+
+    const unsigned bid = blockIdx.x;
+    const int p = (int)(bid % (unsigned)P.n_part);
+    const unsigned rest = bid / (unsigned)P.n_part;
+    const int cb = (int)(rest % (unsigned)P.n_cell_blocks);
+    const int ch = (int)(rest / (unsigned)P.n_cell_blocks);
+    const int S = P.n_samples - 1;
+    const int k_begin = 1 + ch * P.chunk;
+    const int k_end = min(S, k_begin + P.chunk - 1);
+    const int n_int = k_end - k_begin + 1;
+    const int n_tiles = (n_int + kTileSteps - 1) / kTileSteps;
+    const RecS* rec = P.rec + (size_t)p * P.n_samples;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cell = cb * kAdjointThreads + tid;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int t = 0; t < 2 && t < n_tiles; ++t) {
+            const int k0 = k_begin + t * kTileSteps;
+            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k0 + 1) * sizeof(RecS);
+            mbar_arrive_expect_tx(&bar[t], bytes);
+            bulk_g2s(tile[t], rec + k0, bytes, &bar[t]);
+        }
+    }
+
+    const float q = P.q ? (float)P.q[p] : 1.f;
+    const float near = (P.flags & RD_NEAR) ? 1.f : 0.f, far = (P.flags & RD_FAR) ? 1.f : 0.f;
+    const double* xp = P.x + (size_t)p * P.n_samples * 3;
+    ACell c;
+    bool live = false;
+    int b_end = 0;
+    float f_end = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) c.pend[i] = 0.f;
+    if (cell < P.n_pix) {
+        const D4 cl = P.cells[cell];
+        const double* xa = xp + 3 * (size_t)(k_begin - 1);
+        const double* xe = xp + 3 * (size_t)k_end;
+        double Ra, Re;
+        const double ua = arrival_bins(xa[0], xa[1], xa[2], cl, P.t0, k_begin - 1, P.dt, P.inv_dt_det, Ra);
+        const double ue = arrival_bins(xe[0], xe[1], xe[2], cl, P.t0, k_end, P.dt, P.inv_dt_det, Re);
+        live = (ue > 0.0) && (ua < (double)P.n_bins);
+        if (live) {
+            const double fa = floor(ua), fe = floor(ue);
+            c.b = clamp_bin(fa);
+            c.f = (float)(ua - fa) * P.W;
+            b_end = clamp_bin(fe);
+            f_end = (float)(ue - fe) * P.W;
+            c.Rpd = (float)Ra + P.dt_f;
+            c.Px = (float)cl.x;
+            c.Py = (float)cl.y;
+            c.Pz = (float)cl.z;
+            c.row = P.seed + (size_t)cell * P.n_bins * 8;
+            load_seed(c.row, P.n_bins, c.b, c.g);
+            c.np[0] = (float)((cl.x - xa[0]) / Ra);
+            c.np[1] = (float)((cl.y - xa[1]) / Ra);
+            c.np[2] = (float)((cl.z - xa[2]) / Ra);
+        }
+    }
+
+    for (int t = 0; t < n_tiles; ++t) {
+        const int buf = t & 1;
+        const bool ok = mbar_wait_bounded(&bar[buf], (unsigned)(t >> 1) & 1u);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(&P.counters->errors, ERRBIT_TIMEOUT);
+                for (int u = t; u < t + 2 && u < n_tiles; ++u)
+                    (void)mbar_wait_bounded(&bar[u & 1], (unsigned)(u >> 1) & 1u);
+            }
+            __syncthreads();
+            return;
+        }
+        const int k0 = k_begin + t * kTileSteps;
+        const int cnt = min(kTileSteps, k_end - k0 + 1);
+        const bool last_tile = (t == n_tiles - 1);
+        for (int i = 0; i < cnt; ++i) {
+            float out[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (live) {
+                if (last_tile && i == cnt - 1)
+                    adj_step<true>(c, tile[buf][i], P, q, near, far, b_end, f_end, out);
+                else
+                    adj_step<false>(c, tile[buf][i], P, q, near, far, 0, 0.f, out);
+            }
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                const float v = warp_sum(out[j]);
+                if (lane == 0) red[warp][i][j] = v;
+            }
+        }
+        __syncthreads();
+        // sample k0 - 1 + i gets the sum over the CTA's warps
+        for (int e = tid; e < cnt * 6; e += kAdjointThreads) {
+            const int i = e / 6, j = e - 6 * (e / 6);
+            float v = 0.f;
+#pragma unroll
+            for (int w = 0; w < kAdjointThreads / 32; ++w) v += red[w][i][j];
+            if (v != 0.f) {
+                const size_t o = ((size_t)p * P.n_samples + (size_t)(k0 - 1 + i)) * 3;
+                if (j < 3) atomicAdd(P.gx + o + j, (double)v);
+                else atomicAdd(P.gbeta + o + (j - 3), (double)v);
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && t + 2 < n_tiles) {
+            fence_proxy_async();
+            const int k2 = k_begin + (t + 2) * kTileSteps;
+            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k2 + 1) * sizeof(RecS);
+            mbar_arrive_expect_tx(&bar[buf], bytes);
+            bulk_g2s(tile[buf], rec + k2, bytes, &bar[buf]);
+        }
+    }
+    // the chunk's last sample keeps the partial of its last interval
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const float v = warp_sum(live ? c.pend[j] : 0.f);
+        if (lane == 0 && v != 0.f) {
+            const size_t o = ((size_t)p * P.n_samples + (size_t)k_end) * 3;
+            if (j < 3) atomicAdd(P.gx + o + j, (double)v);
+            else atomicAdd(P.gbeta + o + (j - 3), (double)v);
+        }
+    }
+}
+
+// upstream gradient (E, B) [n_pix][n_bins][3] of any type -> field layout [n_pix][n_bins][8] float
+template <typename T>
+__global__ void k_pack_seed(const T* __restrict__ gE, const T* __restrict__ gB, long long n, float* __restrict__ seed)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (gE) {
+            v[0] = (float)gE[3 * i];
+            v[1] = (float)gE[3 * i + 1];
+            v[2] = (float)gE[3 * i + 2];
+        }
+        if (gB) {
+            v[3] = (float)gB[3 * i];
+            v[4] = (float)gB[3 * i + 1];
+            v[5] = (float)gB[3 * i + 2];
+        }
+        float4* o = reinterpret_cast<float4*>(seed + 8 * i);
+        o[0] = make_float4(v[0], v[1], v[2], v[3]);
+        o[1] = make_float4(v[4], v[5], 0.f, 0.f);
+    }
+}
+
+// d loss / d u = (dbeta/du)^T d loss / d beta,  dbeta/du = (I - beta beta^T) / gamma
+__global__ void k_gbeta_to_gu(const double* __restrict__ u, const double* __restrict__ gbeta,
+                              double* __restrict__ gu, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double ux = u[3 * i], uy = u[3 * i + 1], uz = u[3 * i + 2];
+        const double g = sqrt(1.0 + (ux * ux + uy * uy + uz * uz));
+        const double bx = ux / g, by = uy / g, bz = uz / g;
+        const double gx = gbeta[3 * i], gy = gbeta[3 * i + 1], gz = gbeta[3 * i + 2];
+        const double bg = bx * gx + by * gy + bz * gz;
+        gu[3 * i] += (gx - bx * bg) / g;
+        gu[3 * i + 1] += (gy - by * bg) / g;
+        gu[3 * i + 2] += (gz - bz * bg) / g;
+    }
+}
+
+static int grid_for(long long n, int threads)
+{
+    long long g = (n + threads - 1) / threads;
+    if (g > 152LL * 16) g = 152LL * 16;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+cudaError_t launch_pack_seed(const void* gE, const void* gB, int dtype, int n_pix, int n_bins, float* seed,
+                             cudaStream_t s)
+{
+    const long long n = (long long)n_pix * n_bins;
+    if (dtype == RD_F32)
+        k_pack_seed<float><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const float*>(gE),
+                                                          static_cast<const float*>(gB), n, seed);
+    else
+        k_pack_seed<double><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const double*>(gE),
+                                                           static_cast<const double*>(gB), n, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_mixed(const AdjointParams& p, cudaStream_t s)
+{
+    const long long blocks = (long long)p.n_cell_blocks * p.n_part * p.n_chunks;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_adjoint_mixed<<<(unsigned)blocks, kAdjointThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gbeta_to_gu(const double* u, const double* gbeta, double* gu, long long n, cudaStream_t s)
+{
+    k_gbeta_to_gu<<<grid_for(n, 256), 256, 0, s>>>(u, gbeta, gu, n);
+    return cudaGetLastError();
+}
+
+}  // namespace rd

@@ -33,6 +33,11 @@ struct rd_detector {
     size_t stage_bytes = 0;
     void* readback = nullptr;        // conversion buffer for host reads
     size_t readback_bytes = 0;
+    void* seed = nullptr;            // adjoint: upstream gradient in field layout
+    size_t seed_bytes = 0;
+    void* gbeta = nullptr;           // adjoint: d loss / d beta (FP64)
+    size_t gbeta_bytes = 0;
+    int adjoint_chunk = 250;         // adjoint: samples between recomputed anchors
     long long n_deposits = 0;
     int chunk_override = 0;          // intervals per work item (0 = automatic)
     bool timing = false;             // record CUDA events around deposit launches
@@ -251,6 +256,8 @@ rd_status rd_destroy(rd_detector* d)
     cudaFree(d->rec);
     cudaFree(d->stage);
     cudaFree(d->readback);
+    cudaFree(d->seed);
+    cudaFree(d->gbeta);
     delete d;
     return RD_OK;
 }
@@ -409,6 +416,76 @@ rd_status rd_get_stats(rd_detector* d, rd_stream stream, rd_stats* out)
     out->kernel_ms = d->timed_ms;
     d->timed_launches = 0;
     d->timed_ms = 0.0;
+    return RD_OK;
+}
+
+rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* gE, const void* gB,
+                                  int32_t gdtype, double* gx, double* gu, rd_stream stream)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    rd_status st = check_traj(t);
+    if (st != RD_OK) return st;
+    if (d->precision != RD_MIXED) return fail(RD_ERR_STATE, "the adjoint needs an RD_MIXED detector");
+    if (t->mem != RD_MEM_DEVICE) return fail(RD_ERR_ARG, "the adjoint needs device trajectories");
+    if (!gE && !gB) return fail(RD_ERR_ARG, "gE and gB are both NULL");
+    if (gdtype != RD_F32 && gdtype != RD_F64) return fail(RD_ERR_ARG, "bad gdtype %d", gdtype);
+    if (t->n_part > 0 && (!gx || !gu)) return fail(RD_ERR_ARG, "gx/gu is NULL");
+    const int S = t->n_samples - 1;
+    if (t->n_part == 0 || S < 1) return RD_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    st = ensure(&d->seed, &d->seed_bytes, d->field_bytes, s, "seed scratch");
+    if (st != RD_OK) return st;
+    RD_CUDA(launch_pack_seed(gE, gB, gdtype, d->n_pix, d->n_bins, static_cast<float*>(d->seed), s), "pack seed");
+    const size_t per_part_rec = sizeof(RecS) * (size_t)t->n_samples;
+    const size_t per_part_gb = 3 * sizeof(double) * (size_t)t->n_samples;
+    const size_t budget = (size_t)1 << 31;
+    const int pc = (int)std::max<size_t>(1, std::min<size_t>((size_t)t->n_part, budget / (per_part_rec + per_part_gb)));
+    st = ensure(&d->rec, &d->rec_bytes, per_part_rec * pc, s, "record scratch");
+    if (st != RD_OK) return st;
+    st = ensure(&d->gbeta, &d->gbeta_bytes, per_part_gb * pc, s, "gradient scratch");
+    if (st != RD_OK) return st;
+    const int n_cell_blocks = (d->n_pix + kAdjointThreads - 1) / kAdjointThreads;
+    const int chunk = std::max(1, std::min(d->adjoint_chunk, S));
+    for (int p0 = 0; p0 < t->n_part; p0 += pc) {
+        const int np = std::min(pc, t->n_part - p0);
+        const size_t off = (size_t)p0 * t->n_samples * 3;
+        RD_CUDA(cudaMemsetAsync(d->gbeta, 0, per_part_gb * np, s), "clear gradient scratch");
+        RD_CUDA(launch_precompute_scalar(t->x + off, t->u + off, np, t->n_samples, t->dt, d->flags,
+                                         static_cast<RecS*>(d->rec), d->counters, s),
+                "precompute");
+        AdjointParams P;
+        P.rec = static_cast<const RecS*>(d->rec);
+        P.x = t->x + off;
+        P.q = t->q ? t->q + p0 : nullptr;
+        P.cells = d->cells;
+        P.seed = static_cast<const float*>(d->seed);
+        P.gx = gx + off;
+        P.gbeta = static_cast<double*>(d->gbeta);
+        P.counters = d->counters;
+        P.n_pix = d->n_pix;
+        P.n_bins = d->n_bins;
+        P.n_samples = t->n_samples;
+        P.n_part = np;
+        P.chunk = chunk;
+        P.n_chunks = (S + chunk - 1) / chunk;
+        P.n_cell_blocks = n_cell_blocks;
+        P.flags = d->flags;
+        P.t0 = t->t0;
+        P.dt = t->dt;
+        P.inv_dt_det = 1.0 / d->dt_det;
+        P.dt_f = (float)t->dt;
+        P.du_scale = (float)(t->dt / d->dt_det);
+        P.W = (float)(d->dt_det / t->dt);
+        P.invW = (float)(t->dt / d->dt_det);
+        {
+            LaunchTimer timer(d, s);
+            RD_CUDA(launch_adjoint_mixed(P, s), "adjoint");
+        }
+        RD_CUDA(launch_gbeta_to_gu(t->u + off, static_cast<const double*>(d->gbeta), gu + off,
+                                   (long long)np * t->n_samples, s),
+                "gradient to momenta");
+    }
     return RD_OK;
 }
 

@@ -34,9 +34,10 @@ __device__ __forceinline__ bool finite3(const double* v)
     return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
 }
 
+template <typename Rec, bool DUP>
 __global__ void k_precompute_mixed(const double* __restrict__ x, const double* __restrict__ u,
                                    int n_part, int n_samples, double dt, int flags,
-                                   RecM* __restrict__ rec, DevCounters* counters)
+                                   Rec* __restrict__ rec, DevCounters* counters)
 {
     const long long total = (long long)n_part * n_samples;
     const double near_on = (flags & RD_NEAR) ? 1.0 : 0.0;
@@ -66,12 +67,15 @@ __global__ void k_precompute_mixed(const double* __restrict__ x, const double* _
         if (bad) atomicOr(&counters->errors, ERRBIT_INPUT);
         // delta = beta_k - vbar_k (difference of end-point and chord velocities)
         const double ex = bx - vx, ey = by - vy, ez = bz - vz;
-#if RD_PACKED
-        auto put = [](double v) { const float f = (float)v; return make_float2(f, f); };
-#else
-        auto put = [](double v) { return (float)v; };
-#endif
-        RecM r;
+        auto put = [](double v) {
+            if constexpr (DUP) {
+                const float f = (float)v;
+                return make_float2(f, f);
+            } else {
+                return (float)v;
+            }
+        };
+        Rec r;
         r.nx = put(-xk[0]);
         r.ny = put(-xk[1]);
         r.nz = put(-xk[2]);
@@ -349,8 +353,18 @@ cudaError_t launch_precompute_mixed(const double* x, const double* u, int n_part
                                     cudaStream_t s)
 {
     const long long n = (long long)n_part * n_samples;
-    k_precompute_mixed<<<grid_for(n, 256), 256, 0, s>>>(x, u, n_part, n_samples, dt, flags, rec,
-                                                        counters);
+    k_precompute_mixed<RecM, RD_PACKED != 0><<<grid_for(n, 256), 256, 0, s>>>(x, u, n_part, n_samples, dt,
+                                                                          flags, rec, counters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_precompute_scalar(const double* x, const double* u, int n_part, int n_samples,
+                                     double dt, int flags, RecS* rec, DevCounters* counters,
+                                     cudaStream_t s)
+{
+    const long long n = (long long)n_part * n_samples;
+    k_precompute_mixed<RecS, false><<<grid_for(n, 256), 256, 0, s>>>(x, u, n_part, n_samples, dt, flags,
+                                                                     rec, counters);
     return cudaGetLastError();
 }
 

@@ -120,10 +120,35 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // give up a wait a
 cudaError_t launch_precompute_mixed(const double* x, const double* u, int n_part, int n_samples,
                                     double dt, int flags, RecM* rec, DevCounters* counters,
                                     cudaStream_t s);
+cudaError_t launch_precompute_scalar(const double* x, const double* u, int n_part, int n_samples,
+                                     double dt, int flags, RecS* rec, DevCounters* counters,
+                                     cudaStream_t s);
 cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part, int n_samples,
                                    double dt, RecD* rec, DevCounters* counters, cudaStream_t s);
 cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s);
 cudaError_t launch_deposit_fp64(const DepositParams& p, int flags, cudaStream_t s);
+// adjoint (rd_adjoint.cu)
+struct AdjointParams {
+    const RecS* rec;            // [n_part][n_samples]
+    const double* x;            // [n_part][n_samples][3] FP64 positions (anchors)
+    const double* q;            // [n_part] or null
+    const D4* cells;            // [n_pix]
+    const float* seed;          // [n_pix][n_bins][8] upstream gradient (E xyz, B xyz) in field layout
+    double* gx;                 // [n_part][n_samples][3] += d loss / d x
+    double* gbeta;              // [n_part][n_samples][3] += d loss / d beta (scratch, FP64)
+    DevCounters* counters;
+    int n_pix, n_bins, n_samples, n_part, chunk, n_chunks, n_cell_blocks;
+    int flags;
+    double t0, dt, inv_dt_det;
+    float dt_f, du_scale, W, invW;
+};
+constexpr int kAdjointThreads = 256;   // one cell per thread
+cudaError_t launch_pack_seed(const void* gE, const void* gB, int dtype, int n_pix, int n_bins, float* seed,
+                             cudaStream_t s);
+cudaError_t launch_adjoint_mixed(const AdjointParams& p, cudaStream_t s);
+cudaError_t launch_gbeta_to_gu(const double* u, const double* gbeta, double* gu, long long n_samples_total,
+                               cudaStream_t s);
+
 cudaError_t launch_read_fields(const void* fields, int precision, int n_pix, int n_bins, void* E,
                                void* B, int dtype, cudaStream_t s);
 
