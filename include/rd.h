@@ -184,6 +184,35 @@ RD_API rd_status rd_adjoint_trajectories(rd_detector* det, const rd_traj* traj, 
                                          const void* gB, int32_t gdtype, double* gx, double* gu,
                                          rd_stream stream);
 
+/*
+ * Batched form: deposit trajs[i] into dets[i] for i < n (ACCUMULATES, like n calls of
+ * rd_deposit_trajectories) with one persistent kernel launch.  The resident CTAs draw work items
+ * -- (problem, step chunk, block of 256 cells, particle) -- from one atomic counter, so problems of
+ * very different size share the GPU without a tail of idle SMs; no CTA ever waits on another.
+ * On a non-default stream the counter reset, the per-problem record precompute and the launch
+ * are recorded once into a CUDA graph that is replayed while the same detectors (by identity),
+ * trajectory pointers, shapes, time axes, chunks and flags come back; the graph reads the
+ * trajectory arrays at replay time.  Every detector must be RD_MIXED and every trajectory in
+ * device memory; the batch scratch (records of all problems) and the graph live in dets[0].
+ * Results equal the separate deposits up to FP32 summation order.
+ */
+RD_API rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* trajs,
+                                  rd_stream stream);
+
+/*
+ * Steps per work item (the step chunk between exact FP64 arrival anchors) for this detector's
+ * deposits; 0 = automatic (1024, halved while the grid would be too small to fill the GPU).
+ */
+RD_API rd_status rd_set_chunk(rd_detector* det, int32_t chunk);
+
+/*
+ * Autotuner: time rd_deposit_trajectories of `traj` with step chunks 64, 128, ..., 4096 (up to
+ * the trajectory length), keep the fastest for this detector (as rd_set_chunk) and return it in
+ * *chosen.  The trial deposits go into this detector; its fields are zeroed afterwards.
+ * Synchronises the stream.
+ */
+RD_API rd_status rd_autotune(rd_detector* det, const rd_traj* traj, rd_stream stream, int32_t* chosen);
+
 /* Message for the last failing call on this thread ("" if none).  Valid until the next call. */
 RD_API const char* rd_last_error(void);
 

@@ -25,7 +25,8 @@ __all__ = [
     "RD_MEM_HOST", "RD_F32", "RD_F64", "RDError", "rd_detector_desc", "rd_traj", "rd_stats",
     "load_library", "library_path", "rd_create_detector", "rd_destroy", "rd_zero_fields",
     "rd_deposit_trajectories", "rd_read_fields", "rd_synchronize", "rd_get_stats",
-    "rd_set_timing", "rd_adjoint_trajectories", "rd_last_error", "rd_version", "DepositFunction", "RadiationDetector", "build_library",
+    "rd_set_timing", "rd_adjoint_trajectories", "rd_deposit_batch", "rd_set_chunk", "rd_autotune",
+    "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
 ]
 
 RD_OK, RD_ERR_ARG, RD_ERR_CUDA, RD_ERR_OOM, RD_ERR_STATE, RD_ERR_TIMEOUT, RD_ERR_BOUNDS, RD_ERR_INPUT = range(8)
@@ -94,6 +95,9 @@ def load_library(build_if_missing: bool = True):
             "rd_get_stats": ([P, P, ctypes.POINTER(rd_stats)], I),
             "rd_set_timing": ([P, I], I),
             "rd_adjoint_trajectories": ([P, ctypes.POINTER(rd_traj), P, P, I, P, P, P], I),
+            "rd_deposit_batch": ([I, ctypes.POINTER(P), ctypes.POINTER(rd_traj), P], I),
+            "rd_set_chunk": ([P, I], I),
+            "rd_autotune": ([P, ctypes.POINTER(rd_traj), P, ctypes.POINTER(I)], I),
             "rd_last_error": ([], ctypes.c_char_p),
             "rd_version": ([], ctypes.c_char_p),
         }
@@ -166,6 +170,27 @@ def rd_adjoint_trajectories(det: int, traj: rd_traj, gE_ptr, gB_ptr, gdtype: int
                             stream=None) -> None:
     _check(load_library().rd_adjoint_trajectories(det, ctypes.byref(traj), gE_ptr, gB_ptr, gdtype, gx_ptr,
                                                   gu_ptr, _stream_ptr(stream)), "rd_adjoint_trajectories")
+
+
+def rd_deposit_batch(dets, trajs, stream=None) -> None:
+    """dets: sequence of detector handles; trajs: sequence of rd_traj (device memory)."""
+    n = len(dets)
+    if n != len(trajs):
+        raise ValueError("one trajectory set per detector")
+    harr = (ctypes.c_void_p * n)(*dets)
+    tarr = (rd_traj * n)(*trajs)
+    _check(load_library().rd_deposit_batch(n, harr, tarr, _stream_ptr(stream)), "rd_deposit_batch")
+
+
+def rd_set_chunk(det: int, chunk: int) -> None:
+    _check(load_library().rd_set_chunk(det, int(chunk)), "rd_set_chunk")
+
+
+def rd_autotune(det: int, traj: rd_traj, stream=None) -> int:
+    out = ctypes.c_int32(0)
+    _check(load_library().rd_autotune(det, ctypes.byref(traj), _stream_ptr(stream), ctypes.byref(out)),
+           "rd_autotune")
+    return int(out.value)
 
 
 def rd_set_timing(det: int, enable: bool) -> None:
@@ -307,6 +332,16 @@ class RadiationDetector:
         self._keep = keep + [gEc, gBc]
         return gx, gu
 
+    def set_chunk(self, chunk: int):
+        rd_set_chunk(self._h, chunk)
+
+    def autotune(self, x, u, q=None, t0: float = 0.0, dt: float = 1.0, stream=None) -> int:
+        """Pick the fastest step chunk for these trajectories (fields are zeroed afterwards)."""
+        t, keep = self.traj_struct(x, u, q, t0, dt)
+        chunk = rd_autotune(self._h, t, stream)
+        del keep
+        return chunk
+
     def synchronize(self, stream=None):
         rd_synchronize(self._h, stream)
 
@@ -332,6 +367,18 @@ class RadiationDetector:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def deposit_batch(detectors, trajectories, stream=None):
+    """One persistent launch depositing trajectories[i] = (x, u, q, t0, dt) (CUDA tensors) into
+    detectors[i] (RadiationDetector, mixed precision) for all i."""
+    keep, trajs = [], []
+    for det, (x, u, q, t0, dt) in zip(detectors, trajectories):
+        t, k = det.traj_struct(x, u, q, t0, dt)
+        keep.extend(k)
+        trajs.append(t)
+    rd_deposit_batch([d.handle for d in detectors], trajs, stream)
+    return keep
 
 
 class DepositFunction:

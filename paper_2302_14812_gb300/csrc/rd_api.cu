@@ -38,6 +38,14 @@ struct rd_detector {
     void* gbeta = nullptr;           // adjoint: d loss / d beta (FP64)
     size_t gbeta_bytes = 0;
     int adjoint_chunk = 250;         // adjoint: samples between recomputed anchors
+    unsigned long long id = 0;       // unique per created detector (keys of cached graphs)
+    // batched form (kept in the first detector of a batch)
+    void* batch_rec = nullptr;       // records of every problem
+    size_t batch_rec_bytes = 0;
+    void* batch_tab = nullptr;       // DepositParams[n] + item offsets[n+1] + counter
+    size_t batch_tab_bytes = 0;
+    std::vector<unsigned long long> graph_key;
+    cudaGraphExec_t graph_exec = nullptr;
     long long n_deposits = 0;
     int chunk_override = 0;          // intervals per work item (0 = automatic)
     bool timing = false;             // record CUDA events around deposit launches
@@ -49,6 +57,7 @@ struct rd_detector {
 namespace {
 
 thread_local std::string g_err;
+unsigned long long g_next_id = 1;   // detector ids (host side, monotonic)
 
 rd_status fail(rd_status st, const char* fmt, ...)
 {
@@ -162,6 +171,32 @@ void collect_timings(rd_detector* d)
     d->ev_pending.clear();
 }
 
+void fill_mixed_params(DepositParams& P, const rd_detector* d, const rd_traj* t, const void* rec,
+                       const double* x, const double* q, int np, int chunk)
+{
+    const int S = t->n_samples - 1;
+    P.rec = rec;
+    P.x = x;
+    P.q = q;
+    P.cells = d->cells;
+    P.fields = d->fields;
+    P.counters = d->counters;
+    P.n_pix = d->n_pix;
+    P.n_bins = d->n_bins;
+    P.n_samples = t->n_samples;
+    P.n_part = np;
+    P.chunk = chunk;
+    P.n_chunks = (S + chunk - 1) / chunk;
+    P.n_cell_blocks = (d->n_pix + kMixedCellsPerCta - 1) / kMixedCellsPerCta;
+    P.t0 = t->t0;
+    P.dt = t->dt;
+    P.inv_dt_det = 1.0 / d->dt_det;
+    P.dt_f = (float)t->dt;
+    P.du_scale = (float)(t->dt / d->dt_det);
+    P.W = (float)(d->dt_det / t->dt);
+    P.invW = (float)(t->dt / d->dt_det);
+}
+
 }  // namespace
 
 extern "C" {
@@ -216,6 +251,7 @@ rd_status rd_create_detector(const rd_detector_desc* desc, rd_stream stream, rd_
     rd_detector* d = new (std::nothrow) rd_detector();
     if (!d) return fail(RD_ERR_OOM, "host allocation");
     cudaGetDevice(&d->device);
+    d->id = __atomic_fetch_add(&g_next_id, 1ull, __ATOMIC_RELAXED);
     d->n_pix = desc->n_pix;
     d->n_bins = desc->n_bins;
     d->precision = desc->precision;
@@ -258,6 +294,9 @@ rd_status rd_destroy(rd_detector* d)
     cudaFree(d->readback);
     cudaFree(d->seed);
     cudaFree(d->gbeta);
+    cudaFree(d->batch_rec);
+    cudaFree(d->batch_tab);
+    if (d->graph_exec) cudaGraphExecDestroy(d->graph_exec);
     delete d;
     return RD_OK;
 }
@@ -297,6 +336,7 @@ rd_status rd_deposit_trajectories(rd_detector* d, const rd_traj* t, rd_stream st
         if (st != RD_OK) return st;
     }
     const int n_cell_blocks = (d->n_pix + kDepositThreads - 1) / kDepositThreads;
+    static_assert(kDepositThreads == kMixedCellsPerCta, "both deposit kernels cover 256 cells per CTA");
     const int chunk = choose_chunk(d, std::min(pc, t->n_part), S, n_cell_blocks);
 
     for (int p0 = 0; p0 < t->n_part; p0 += pc) {
@@ -486,6 +526,177 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
                                    (long long)np * t->n_samples, s),
                 "gradient to momenta");
     }
+    return RD_OK;
+}
+
+rd_status rd_set_chunk(rd_detector* d, int32_t chunk)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    if (chunk < 0) return fail(RD_ERR_ARG, "chunk must be >= 0");
+    d->chunk_override = chunk;
+    return RD_OK;
+}
+
+rd_status rd_autotune(rd_detector* d, const rd_traj* t, rd_stream stream, int32_t* chosen)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    rd_status st = check_traj(t);
+    if (st != RD_OK) return st;
+    if (d->precision != RD_MIXED) return fail(RD_ERR_STATE, "autotuning applies to RD_MIXED detectors");
+    const int S = t->n_samples - 1;
+    if (t->n_part == 0 || S < 1) {
+        if (chosen) *chosen = d->chunk_override;
+        return RD_OK;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    RD_CUDA(cudaEventCreate(&e0), "autotune");
+    RD_CUDA(cudaEventCreate(&e1), "autotune");
+    const int saved = d->chunk_override;
+    const bool timing = d->timing;
+    d->timing = false;
+    int best = 0;
+    float best_ms = 0.f;
+    for (int c = 64; c <= 4096; c *= 2) {
+        const int chunk = std::min(c, S);
+        d->chunk_override = chunk;
+        st = rd_deposit_trajectories(d, t, stream);            // warm-up (also sizes the scratch)
+        if (st == RD_OK) {
+            cudaEventRecord(e0, s);
+            st = rd_deposit_trajectories(d, t, stream);
+            cudaEventRecord(e1, s);
+        }
+        if (st != RD_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "autotune"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best == 0 || ms < best_ms) {
+            best = chunk;
+            best_ms = ms;
+        }
+        if (chunk == S) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    d->timing = timing;
+    d->chunk_override = (st == RD_OK) ? best : saved;
+    const rd_status z = rd_zero_fields(d, stream);
+    if (st != RD_OK) return st;
+    if (chosen) *chosen = best;
+    return z;
+}
+
+rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* trajs, rd_stream stream)
+{
+    g_err.clear();
+    if (n < 1 || !dets || !trajs) return fail(RD_ERR_ARG, "need n >= 1 detectors and trajectories");
+    for (int i = 0; i < n; ++i) {
+        if (!dets[i]) return fail(RD_ERR_ARG, "detector %d is NULL", i);
+        if (dets[i]->precision != RD_MIXED) return fail(RD_ERR_STATE, "detector %d is not RD_MIXED", i);
+        rd_status st = check_traj(&trajs[i]);
+        if (st != RD_OK) return st;
+        if (trajs[i].mem != RD_MEM_DEVICE) return fail(RD_ERR_ARG, "batch trajectories must be in device memory");
+        if (dets[i]->device != dets[0]->device) return fail(RD_ERR_ARG, "all detectors must be on one device");
+    }
+    rd_detector* d0 = dets[0];
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // layout of the records of every problem, work items per problem
+    std::vector<size_t> rec_off(n + 1, 0);
+    std::vector<long long> item_off(n + 1, 0);
+    std::vector<int> chunks(n);
+    for (int i = 0; i < n; ++i) {
+        const rd_traj& t = trajs[i];
+        const int S = t.n_samples - 1;
+        const bool empty = t.n_part == 0 || S < 1;
+        rec_off[i + 1] = rec_off[i] + (empty ? 0 : sizeof(RecM) * (size_t)t.n_part * t.n_samples);
+        const int ncb = (dets[i]->n_pix + kMixedCellsPerCta - 1) / kMixedCellsPerCta;
+        chunks[i] = empty ? 1 : choose_chunk(dets[i], t.n_part, S, ncb);
+        const long long items = empty ? 0 : (long long)ncb * t.n_part * ((S + chunks[i] - 1) / chunks[i]);
+        item_off[i + 1] = item_off[i] + items;
+    }
+    const size_t tab_bytes = sizeof(DepositParams) * n + sizeof(long long) * (n + 1) + 64;
+    rd_status st = ensure(&d0->batch_rec, &d0->batch_rec_bytes, std::max<size_t>(rec_off[n], 256), s, "batch records");
+    if (st != RD_OK) return st;
+    st = ensure(&d0->batch_tab, &d0->batch_tab_bytes, tab_bytes, s, "batch table");
+    if (st != RD_OK) return st;
+    char* tab = static_cast<char*>(d0->batch_tab);
+    DepositParams* d_probs = reinterpret_cast<DepositParams*>(tab);
+    long long* d_off = reinterpret_cast<long long*>(tab + sizeof(DepositParams) * n);
+    unsigned long long* d_counter =
+        reinterpret_cast<unsigned long long*>(tab + ((sizeof(DepositParams) * n + sizeof(long long) * (n + 1) + 15) & ~size_t(15)));
+    // graph key: everything a replay depends on
+    std::vector<unsigned long long> key;
+    key.push_back((unsigned long long)n);
+    key.push_back((unsigned long long)(uintptr_t)d0->batch_rec);
+    key.push_back((unsigned long long)(uintptr_t)d0->batch_tab);
+    key.push_back((unsigned long long)(uintptr_t)s);
+    for (int i = 0; i < n; ++i) {
+        const rd_traj& t = trajs[i];
+        unsigned long long t0b, dtb;
+        memcpy(&t0b, &t.t0, 8);
+        memcpy(&dtb, &t.dt, 8);
+        key.insert(key.end(), {dets[i]->id, (unsigned long long)(uintptr_t)t.x, (unsigned long long)(uintptr_t)t.u,
+                               (unsigned long long)(uintptr_t)t.q, (unsigned long long)t.n_part,
+                               (unsigned long long)t.n_samples, t0b, dtb, (unsigned long long)chunks[i],
+                               (unsigned long long)dets[i]->flags});
+    }
+    const bool reuse = d0->graph_exec && key == d0->graph_key;
+    if (!reuse) {
+        // problem table (stays in device memory for replays)
+        std::vector<DepositParams> probs(n);
+        for (int i = 0; i < n; ++i)
+            fill_mixed_params(probs[i], dets[i], &trajs[i], static_cast<char*>(d0->batch_rec) + rec_off[i],
+                              trajs[i].x, trajs[i].q, trajs[i].n_part, chunks[i]);
+        RD_CUDA(cudaMemcpyAsync(d_probs, probs.data(), sizeof(DepositParams) * n, cudaMemcpyHostToDevice, s),
+                "batch table");
+        RD_CUDA(cudaMemcpyAsync(d_off, item_off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, s),
+                "batch table");
+        RD_CUDA(cudaStreamSynchronize(s), "batch table");     // host vectors go out of scope
+        if (d0->graph_exec) {
+            cudaGraphExecDestroy(d0->graph_exec);
+            d0->graph_exec = nullptr;
+        }
+    }
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s);
+        for (int i = 0; i < n && e == cudaSuccess; ++i) {
+            const rd_traj& t = trajs[i];
+            if (rec_off[i + 1] == rec_off[i]) continue;
+            e = launch_precompute_mixed(t.x, t.u, t.n_part, t.n_samples, t.dt, dets[i]->flags,
+                                        reinterpret_cast<RecM*>(static_cast<char*>(d0->batch_rec) + rec_off[i]),
+                                        dets[i]->counters, s);
+        }
+        if (e == cudaSuccess && item_off[n] > 0) e = launch_deposit_batch(d_probs, d_off, n, d_counter, batch_grid(), s);
+        return e;
+    };
+    if (s == nullptr) {
+        // the legacy default stream cannot be captured: launch directly
+        RD_CUDA(enqueue(), "rd_deposit_batch");
+    } else {
+        if (!reuse) {
+            cudaGraph_t graph = nullptr;
+            RD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture batch");
+            const cudaError_t e = enqueue();
+            const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return cuda_fail(e != cudaSuccess ? e : e2, "capture batch");
+            }
+            const cudaError_t e3 = cudaGraphInstantiate(&d0->graph_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e3 != cudaSuccess) {
+                d0->graph_exec = nullptr;
+                return cuda_fail(e3, "instantiate batch graph");
+            }
+            d0->graph_key = key;
+        }
+        LaunchTimer timer(d0, s);
+        RD_CUDA(cudaGraphLaunch(d0->graph_exec, s), "launch batch graph");
+    }
+    for (int i = 0; i < n; ++i)
+        dets[i]->n_deposits += (long long)trajs[i].n_part * std::max(0, trajs[i].n_samples - 1) * dets[i]->n_pix;
     return RD_OK;
 }
 

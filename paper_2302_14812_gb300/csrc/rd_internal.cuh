@@ -126,6 +126,9 @@ cudaError_t launch_precompute_scalar(const double* x, const double* u, int n_par
 cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part, int n_samples,
                                    double dt, RecD* rec, DevCounters* counters, cudaStream_t s);
 cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s);
+cudaError_t launch_deposit_batch(const DepositParams* probs, const long long* item_off, int n_probs,
+                                 unsigned long long* next_item, int grid, cudaStream_t s);
+int batch_grid();   // resident CTAs of the persistent batch kernel on the current device
 cudaError_t launch_deposit_fp64(const DepositParams& p, int flags, cudaStream_t s);
 // adjoint (rd_adjoint.cu)
 struct AdjointParams {

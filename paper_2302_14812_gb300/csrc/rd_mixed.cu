@@ -19,6 +19,8 @@
 // time leaves the bin, the bin is added to global memory with two vector reductions.
 #include <math.h>
 
+#include <algorithm>
+
 #include "rd_internal.cuh"
 
 namespace rd {
@@ -284,16 +286,13 @@ __device__ __forceinline__ void walk_tile(Pair& c, const RecM* tile, int cnt, bo
 
 }  // namespace
 
-__global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_mixed(const DepositParams P)
+// One work item -- particle p, cell block cb, step chunk ch of one problem -- run by the whole
+// CTA.  tile / bar: the CTA's shared staging buffers; g_base counts the tiles the CTA staged
+// before this item (it selects buffer and mbarrier phase, so the buffers carry over between items).
+// Returns false if a bounded wait ran out (the error is recorded; the CTA must stop).
+__device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int cb, int ch,
+                                             RecM (*tile)[kTileSteps], uint64_t* bar, unsigned& g_base)
 {
-    __shared__ __align__(128) RecM tile[2][kTileSteps];
-    __shared__ __align__(8) uint64_t bar[2];
-
-    const unsigned bid = blockIdx.x;
-    const int p = (int)(bid % (unsigned)P.n_part);
-    const unsigned rest = bid / (unsigned)P.n_part;
-    const int cb = (int)(rest % (unsigned)P.n_cell_blocks);
-    const int ch = (int)(rest / (unsigned)P.n_cell_blocks);
     const int S = P.n_samples - 1;
     const int k_begin = 1 + ch * P.chunk;
     const int k_end = min(S, k_begin + P.chunk - 1);
@@ -303,17 +302,13 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_m
     const int tid = threadIdx.x;
 
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
+        fence_proxy_async();
         for (int t = 0; t < 2 && t < n_tiles; ++t) {
             const int k0 = k_begin + t * kTileSteps;
+            const unsigned g = g_base + t;
             const unsigned bytes = (unsigned)min(kTileSteps, k_end - k0 + 1) * sizeof(RecM);
-            mbar_arrive_expect_tx(&bar[t], bytes);
-            bulk_g2s(tile[t], rec + k0, bytes, &bar[t]);
+            mbar_arrive_expect_tx(&bar[g & 1], bytes);
+            bulk_g2s(tile[g & 1], rec + k0, bytes, &bar[g & 1]);
         }
     }
 
@@ -387,17 +382,18 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_m
     const bool track = __syncthreads_or(partial) != 0;
 
     for (int t = 0; t < n_tiles; ++t) {
-        const int buf = t & 1;
-        const bool ok = mbar_wait_bounded(&bar[buf], (unsigned)(t >> 1) & 1u);
+        const unsigned g = g_base + t;
+        const int buf = g & 1;
+        const bool ok = mbar_wait_bounded(&bar[buf], (g >> 1) & 1u);
         if (__syncthreads_or(!ok)) {
             // a bulk copy did not complete: record it, let outstanding copies land, stop.
             if (tid == 0) {
                 atomicOr(&P.counters->errors, ERRBIT_TIMEOUT);
                 for (int u = t; u < t + 2 && u < n_tiles; ++u)
-                    (void)mbar_wait_bounded(&bar[u & 1], (unsigned)(u >> 1) & 1u);
+                    (void)mbar_wait_bounded(&bar[(g_base + u) & 1], ((g_base + u) >> 1) & 1u);
             }
             __syncthreads();
-            return;
+            return false;
         }
         const int k0 = k_begin + t * kTileSteps;
         const int cnt = min(kTileSteps, k_end - k0 + 1);
@@ -415,6 +411,7 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_m
             bulk_g2s(tile[buf], rec + k2, bytes, &bar[buf]);
         }
     }
+    g_base += (unsigned)n_tiles;
     // close the last bin; count clipped intervals and crossed bin edges
     if (c.live[0]) {
         flush(c.row[0], C.n_bins, c.b[0], c.acc[0].x, c.acc[1].x, c.acc[2].x, c.acc[3].x, c.acc[4].x, c.acc[5].x);
@@ -429,6 +426,82 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_m
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) crossed += __shfl_xor_sync(0xffffffffu, crossed, o);
     if ((tid & 31) == 0 && crossed) atomicAdd(&P.counters->crossings, crossed);
+    return true;
+}
+
+__device__ __forceinline__ void init_staging(uint64_t* bar)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_mixed(const DepositParams P)
+{
+    __shared__ __align__(128) RecM tile[2][kTileSteps];
+    __shared__ __align__(8) uint64_t bar[2];
+    init_staging(bar);
+    const unsigned bid = blockIdx.x;
+    const int p = (int)(bid % (unsigned)P.n_part);
+    const unsigned rest = bid / (unsigned)P.n_part;
+    const int cb = (int)(rest % (unsigned)P.n_cell_blocks);
+    const int ch = (int)(rest / (unsigned)P.n_cell_blocks);
+    unsigned g = 0;
+    (void)deposit_item(P, p, cb, ch, tile, bar, g);
+}
+
+// Persistent form: the resident CTAs draw work items of all problems from one counter.
+// Items of problem i are [item_off[i], item_off[i+1]), ordered particle-fastest within a
+// (chunk, cell block) like the single-problem grid.  The counter only grows (atomicAdd): no CTA
+// ever waits on another.
+__global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS)
+    k_deposit_batch(const DepositParams* __restrict__ probs, const long long* __restrict__ item_off, int n_probs,
+                    unsigned long long* next_item)
+{
+    __shared__ __align__(128) RecM tile[2][kTileSteps];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ long long s_item;
+    init_staging(bar);
+    const long long total = item_off[n_probs];
+    unsigned g = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(next_item, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = n_probs - 1;
+        while (lo < hi) {                       // last problem whose first item <= item
+            const int mid = (lo + hi + 1) >> 1;
+            if (item_off[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const DepositParams P = probs[lo];
+        const long long local = item - item_off[lo];
+        const int p = (int)(local % P.n_part);
+        const long long rest = local / P.n_part;
+        const int cb = (int)(rest % P.n_cell_blocks);
+        const int ch = (int)(rest / P.n_cell_blocks);
+        if (!deposit_item(P, p, cb, ch, tile, bar, g)) break;
+    }
+}
+
+cudaError_t launch_deposit_batch(const DepositParams* probs, const long long* item_off, int n_probs,
+                                 unsigned long long* next_item, int grid, cudaStream_t s)
+{
+    k_deposit_batch<<<grid, kMixedThreads, 0, s>>>(probs, item_off, n_probs, next_item);
+    return cudaGetLastError();
+}
+
+int batch_grid()
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deposit_batch, kMixedThreads, 0);
+    return std::max(1, sms) * std::max(1, per_sm);
 }
 
 cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s)

@@ -331,7 +331,10 @@ def spherical_cap(n_side: int, radius: float, half_angle: float, axis: int = 2) 
     """
     th = -half_angle + (np.arange(n_side) + 0.5) * (2.0 * half_angle / n_side)
     a, b = np.meshgrid(np.sin(th), np.sin(th), indexing="ij")
-    c = np.sqrt(1.0 - a * a - b * b)
+    c2 = 1.0 - a * a - b * b
+    if np.any(c2 <= 0.0):
+        raise ValueError("half_angle too large: corner cells would leave the sphere")
+    c = np.sqrt(c2)
     dirs = np.zeros((n_side, n_side, 3))
     others = [i for i in range(3) if i != axis]
     dirs[..., others[0]] = a
@@ -441,7 +444,7 @@ def batch_problems(n_problems: int = 64, seed: int = 4, scale: float = 1.0):
                            RD_NEAR | RD_FAR, (side, side))
         else:
             tr = oscillator_ensemble(n_part=n_p, n_steps=n_s, seed=sub)
-            pos = spherical_cap(side, 1e3, 0.8, axis=1)
+            pos = spherical_cap(side, 1e3, 0.6, axis=1)
             reach = 3.0
             span = n_s * tr.dt + 2.0 * reach
             det = Detector(pos, None, 1e3 - reach - 0.02 * span, 1.04 * span / n_b, n_b,
