@@ -44,7 +44,7 @@ FLOPS_PER_CROSSING_MIXED = 9
 # FP32 peak derived from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "deposit_mixed_undulator_ncu.md")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_2302_14812_gb300", "csrc", "rd_deposit.cu")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2302_14812_gb300", "csrc", "rd_mixed.cu")
 
 
 def parse():
@@ -59,12 +59,37 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["undulator", "batch", "adjoint"], default="undulator",
+                    help="undulator: the headline deposit; batch: 64 uneven problems, one persistent "
+                         "launch vs separate launches; adjoint: gradient kernel")
+    ap.add_argument("--batch-scale", type=float, default=0.1,
+                    help="particle-count scale of the 64-problem set (memory: every problem resident)")
     return ap.parse_args()
 
 
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def rank_seed(rank: int) -> int:
+    """Seed of rank r's independent ensemble (weak scaling: same shape, different particles)."""
+    return 2 + 1000 * rank
+
+
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The slowest rank's time (host-side timing reduction, not a data-path collective)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(deposits_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job deposits/s: every rank processes deposits_per_rank per step."""
+    return deposits_per_rank * world / (ms_per_step / 1e3)
 
 
 # ----------------------------------------------------------------------------------------------
@@ -208,11 +233,119 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------------------------
+def run_batch_workload(args):
+    """64 uneven problems: one rd_deposit_batch (persistent kernel, graph replay) against 64
+    separate rd_deposit_trajectories calls on the same stream."""
+    import torch
+    import paper_2302_14812_gb300 as rd
+    from paper_2302_14812_gb300 import workloads as W
+    rd.load_library()
+    probs = W.batch_problems(64, seed=4, scale=args.batch_scale)
+    stream = torch.cuda.Stream()
+    dets, trajs, deposits = [], [], 0
+    for _, tr, det in probs:
+        dets.append(rd.RadiationDetector.from_workload(det, "mixed", stream))
+        trajs.append((torch.from_numpy(tr.x).cuda(), torch.from_numpy(tr.u).cuda(),
+                      torch.from_numpy(tr.q).cuda(), tr.t0, tr.dt))
+        deposits += W.deposits(tr, det)
+    torch.cuda.synchronize()
+
+    def separate():
+        for d, t in zip(dets, trajs):
+            d.deposit(*t, stream=stream)
+
+    def batched():
+        rd.deposit_batch(dets, trajs, stream)
+
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, fn in (("separate", separate), ("batch", batched)):
+            for _ in range(args.warmup):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stream.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            out[name] = {"ms_per_step": ms, "value": deposits / (ms / 1e3)}
+    for d in dets:
+        d.close()
+    line = {"metric": "deposits/sec, 64 uneven problems in one persistent launch (CUDA graph)",
+            "value": out["batch"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out["batch"]["ms_per_step"], "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"64 problems (undulator/circular/oscillator, particles log-uniform "
+                                   f"[100,5e4] x {args.batch_scale}, steps 500-8000, 32^2..128^2 cells x "
+                                   f"16*side bins)", "deposits_per_step": deposits},
+            "separate_launches": out["separate"],
+            "speedup_batch_vs_separate": out["separate"]["ms_per_step"] / out["batch"]["ms_per_step"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint_workload(args):
+    """Forward and adjoint of 1e4 undulator electrons (gamma 10) x 2000 steps on 64x64 x 1024."""
+    import torch
+    import paper_2302_14812_gb300 as rd
+    from paper_2302_14812_gb300 import workloads as W
+    rd.load_library()
+    tr, det = W.config_undulator(n_part=10_000, n_steps=2000, n_side=64, n_bins=1024, gamma=10.0, K=1.0,
+                                 n_periods=10.0, distance=1e4, seed=5)
+    deposits = W.deposits(tr, det)
+    x = torch.from_numpy(tr.x).cuda()
+    u = torch.from_numpy(tr.u).cuda()
+    q = torch.from_numpy(tr.q).cuda()
+    d = rd.RadiationDetector.from_workload(det, "mixed")
+    d.set_timing(True)
+    rng = np.random.default_rng(5)
+    gE = torch.from_numpy(rng.normal(size=(det.n_pix, det.n_bins, 3)).astype(np.float32)).cuda()
+    res = {}
+    for name in ("forward", "adjoint"):
+        def step():
+            if name == "forward":
+                d.zero()
+                d.deposit(x, u, q, tr.t0, tr.dt)
+            else:
+                d.adjoint(x, u, q, tr.t0, tr.dt, gE)
+        for _ in range(args.warmup):
+            step()
+        d.stats()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        st = d.stats()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[name] = {"ms_per_step": ms, "value": deposits / (ms / 1e3),
+                     "kernel_ms": st.kernel_ms / max(1, st.kernel_launches)}
+    d.close()
+    line = {"metric": "deposits/sec of the adjoint (gather) kernel, gradient wrt positions and momenta",
+            "value": res["adjoint"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["adjoint"]["ms_per_step"], "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "1e4 undulator e- (gamma 10, K 1) x 2000 steps, 64x64 cap x 1024 bins, "
+                                   "anchors recomputed every 250 samples", "deposits_per_step": deposits},
+            "forward": res["forward"], "adjoint": res["adjoint"],
+            "adjoint_over_forward_time": res["adjoint"]["ms_per_step"] / res["forward"]["ms_per_step"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, local_rank, world = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch":
+        run_batch_workload(args)
+        return
+    if args.workload == "adjoint":
+        run_adjoint_workload(args)
         return
 
     import torch
@@ -230,7 +363,7 @@ def main():
     rd.load_library()
 
     # every rank: its own independent ensemble of the same shape (weak scaling)
-    tr, det = W.config_undulator(n_part=args.particles, seed=2 + 1000 * rank)
+    tr, det = W.config_undulator(n_part=args.particles, seed=rank_seed(rank))
     deposits = W.deposits(tr, det)
     xd = torch.from_numpy(tr.x).to(dev)
     ud = torch.from_numpy(tr.u).to(dev)
@@ -241,12 +374,8 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(v: float) -> float:
+        return max_over_ranks(v, dist, dev)
 
     # ---------------- mixed path, inputs resident in HBM ----------------
     mixed = rd.RadiationDetector.from_workload(det, "mixed")
@@ -264,13 +393,13 @@ def main():
             mixed.deposit(xd, ud, qd, tr.t0, tr.dt)
         ev1.record(stream)
         barrier()
-    ms_total = max_over_ranks(ev0.elapsed_time(ev1))
+    ms_total = slowest(ev0.elapsed_time(ev1))
     st = mixed.stats()
     clocks = clk.summary()
     ms_step = ms_total / args.steps
     kernel_ms = st.kernel_ms / max(1, st.kernel_launches)
     launches = 2 * args.steps          # per step: precompute + deposit kernel
-    value = deposits * world / (ms_step / 1e3)
+    value = job_throughput(deposits, world, ms_step)
 
     E_mixed, B_mixed = mixed.read("float64", "cpu")
 
@@ -289,7 +418,7 @@ def main():
             f64.deposit(xd, ud, qd, tr.t0, tr.dt)
         e1.record(stream)
         barrier()
-        ms64 = max_over_ranks(e0.elapsed_time(e1)) / args.fp64_steps
+        ms64 = slowest(e0.elapsed_time(e1)) / args.fp64_steps
         E64, B64 = f64.read("float64", "cpu")
         rel_e = float(np.linalg.norm(E_mixed - E64) / np.linalg.norm(E64))
         rel_b = float(np.linalg.norm(B_mixed - B64) / np.linalg.norm(B64))
@@ -321,7 +450,7 @@ def main():
         for _ in range(args.steps):
             e2e_step()
         barrier()
-        secs = max_over_ranks(time.perf_counter() - t)
+        secs = slowest(time.perf_counter() - t)
         e2e = {"value": deposits * world * args.steps / secs, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * secs / args.steps}
