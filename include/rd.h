@@ -213,6 +213,35 @@ RD_API rd_status rd_set_chunk(rd_detector* det, int32_t chunk);
  */
 RD_API rd_status rd_autotune(rd_detector* det, const rd_traj* traj, rd_stream stream, int32_t* chosen);
 
+/*
+ * Allocation-free deposit.  The paper has no counterpart: this entry point exists for callers
+ * that cannot call cudaMalloc -- a particle-in-cell code that reserves all device memory in its
+ * own pool at start-up and allows no allocation inside its time-step loop, a host framework whose
+ * allocator owns the device memory, or a latency-bound loop that must not pay the device-wide
+ * synchronisation cudaMalloc / cudaFree can cause.  It performs the same computation as
+ * rd_deposit_trajectories on an RD_MIXED detector (Eq. 1, Eq. 2, integrating deposit; FP32 fields
+ * and accumulation, FP64-anchored arrival times) without a detector object and without any
+ * allocation: it calls no cudaMalloc, cudaFree or allocating library routine.
+ *   pix_pos [n_pix][3], pix_t0 [n_pix] or NULL: cell positions and time origins (device memory);
+ *     bin b of cell j covers [t_min + pix_t0[j] + b*dt_det, ... + dt_det); flags as RD_NEAR/RD_FAR.
+ *   traj: trajectories in device memory (RD_MEM_DEVICE), as for rd_deposit_trajectories.
+ *   fields: caller-allocated device accumulators float[n_pix][n_bins][8], per bin
+ *     (Ex, Ey, Ez, Bx, By, Bz, unused, unused); the call ACCUMULATES (+=) into them.
+ *   errors: NULL, or a host pointer that receives this call's latched kernel error bits
+ *     (1 << RD_ERR_INPUT for a rejected sample); given, the call synchronises the stream.
+ * Scratch: one 64 MiB array inside the library, held by every GPU that loads it until the process
+ * exits.  Limits: n_pix <= 262144, and one particle's samples must fit the 56 MiB record area
+ * (n_samples <= 917504); larger requests return RD_ERR_ARG.  Particles are processed in chunks
+ * that fit.  The first call on a device looks up the array's device address (once per device);
+ * make that first call before any stream capture.  Every call shares the array, which keeps the
+ * last call's contents: calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  Asynchronous on `stream` unless `errors` is given.
+ */
+RD_API rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix_t0, int32_t n_pix,
+                                    double t_min, double dt_det, int32_t n_bins, int32_t flags,
+                                    const rd_traj* traj, float* fields, uint32_t* errors,
+                                    rd_stream stream);
+
 /* Message for the last failing call on this thread ("" if none).  Valid until the next call. */
 RD_API const char* rd_last_error(void);
 

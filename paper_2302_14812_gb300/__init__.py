@@ -26,7 +26,7 @@ __all__ = [
     "load_library", "library_path", "rd_create_detector", "rd_destroy", "rd_zero_fields",
     "rd_deposit_trajectories", "rd_read_fields", "rd_synchronize", "rd_get_stats",
     "rd_set_timing", "rd_adjoint_trajectories", "rd_deposit_batch", "rd_set_chunk", "rd_autotune",
-    "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
+    "rd_deposit_noalloc", "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
 ]
 
 RD_OK, RD_ERR_ARG, RD_ERR_CUDA, RD_ERR_OOM, RD_ERR_STATE, RD_ERR_TIMEOUT, RD_ERR_BOUNDS, RD_ERR_INPUT = range(8)
@@ -98,6 +98,8 @@ def load_library(build_if_missing: bool = True):
             "rd_deposit_batch": ([I, ctypes.POINTER(P), ctypes.POINTER(rd_traj), P], I),
             "rd_set_chunk": ([P, I], I),
             "rd_autotune": ([P, ctypes.POINTER(rd_traj), P, ctypes.POINTER(I)], I),
+            "rd_deposit_noalloc": ([P, P, I, ctypes.c_double, ctypes.c_double, I, I, ctypes.POINTER(rd_traj), P,
+                                    ctypes.POINTER(ctypes.c_uint32), P], I),
             "rd_last_error": ([], ctypes.c_char_p),
             "rd_version": ([], ctypes.c_char_p),
         }
@@ -191,6 +193,18 @@ def rd_autotune(det: int, traj: rd_traj, stream=None) -> int:
     _check(load_library().rd_autotune(det, ctypes.byref(traj), _stream_ptr(stream), ctypes.byref(out)),
            "rd_autotune")
     return int(out.value)
+
+
+def rd_deposit_noalloc(pix_pos_ptr, pix_t0_ptr, n_pix: int, t_min: float, dt_det: float, n_bins: int,
+                       flags: int, traj: rd_traj, fields_ptr, want_errors: bool = True, stream=None):
+    """Allocation-free deposit into caller-owned float[n_pix][n_bins][8] accumulators (device
+    pointers throughout).  Returns the call's latched error bits when want_errors (synchronising)."""
+    err = ctypes.c_uint32(0)
+    _check(load_library().rd_deposit_noalloc(pix_pos_ptr, pix_t0_ptr, int(n_pix), float(t_min), float(dt_det),
+                                             int(n_bins), int(flags), ctypes.byref(traj), fields_ptr,
+                                             ctypes.byref(err) if want_errors else None, _stream_ptr(stream)),
+           "rd_deposit_noalloc")
+    return int(err.value) if want_errors else None
 
 
 def rd_set_timing(det: int, enable: bool) -> None:

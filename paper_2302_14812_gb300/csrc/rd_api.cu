@@ -199,6 +199,15 @@ void fill_mixed_params(DepositParams& P, const rd_detector* d, const rd_traj* t,
 
 }  // namespace
 
+namespace rd {
+// Last-error message for entry points defined in other translation units.
+rd_status set_last_error(rd_status st, const char* msg)
+{
+    g_err = msg ? msg : "";
+    return st;
+}
+}  // namespace rd
+
 extern "C" {
 
 const char* rd_last_error(void) { return g_err.c_str(); }
