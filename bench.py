@@ -36,10 +36,10 @@ METRIC = "particle·step·pixel deposits/sec, FP32-mixed vs FP64 on one GB300 at
 UNIT = "deposits/s"
 # FP32 operations of the mixed kernel, counted from its source (add/sub/mul = 1, fused
 # multiply-add = 2; the 3 MUFU reciprocal / reciprocal-square-root ops are not counted):
-#   per deposit: geometry and Eq. 1 with B = n x E and the arrival-time increment 60,
-#                integrating accumulation into the running bin 16
+#   per deposit: geometry and Eq. 1 with B = n x E and the arrival-time increment 58,
+#                integrating accumulation into the running bin 17
 #   per bin edge crossed: starting the next bin with the rest of the interval 9
-FLOPS_PER_DEPOSIT_MIXED = 76
+FLOPS_PER_DEPOSIT_MIXED = 75
 FLOPS_PER_CROSSING_MIXED = 9
 # FP32 peak derived from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12

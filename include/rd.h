@@ -83,7 +83,7 @@ typedef struct {
     int32_t mem;               /* RD_MEM_DEVICE or RD_MEM_HOST for pix_pos / pix_t0             */
     double t_min;
     double dt_det;             /* > 0                                                           */
-    int32_t n_bins;            /* >= 1                                                          */
+    int32_t n_bins;            /* >= 1; <= 4194304 (2^22) for RD_MIXED                          */
     int32_t precision;         /* RD_MIXED or RD_FP64                                           */
     int32_t flags;             /* RD_NEAR | RD_FAR (0 is read as both)                           */
 } rd_detector_desc;
@@ -230,7 +230,7 @@ RD_API rd_status rd_autotune(rd_detector* det, const rd_traj* traj, rd_stream st
  *   errors: NULL, or a host pointer that receives this call's latched kernel error bits
  *     (1 << RD_ERR_INPUT for a rejected sample); given, the call synchronises the stream.
  * Scratch: one 64 MiB array inside the library, held by every GPU that loads it until the process
- * exits.  Limits: n_pix <= 262144, and one particle's samples must fit the 56 MiB record area
+ * exits.  Limits: n_pix <= 262144, n_bins <= 4194304, and one particle's samples must fit the 56 MiB record area
  * (n_samples <= 917504); larger requests return RD_ERR_ARG.  Particles are processed in chunks
  * that fit.  The first call on a device looks up the array's device address (once per device);
  * make that first call before any stream capture.  Every call shares the array, which keeps the

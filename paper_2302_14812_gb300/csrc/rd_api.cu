@@ -228,6 +228,9 @@ rd_status rd_create_detector(const rd_detector_desc* desc, rd_stream stream, rd_
         return fail(RD_ERR_ARG, "bad precision %d", desc->precision);
     if (desc->mem != RD_MEM_DEVICE && desc->mem != RD_MEM_HOST) return fail(RD_ERR_ARG, "bad desc->mem");
     if (desc->flags & ~(RD_NEAR | RD_FAR)) return fail(RD_ERR_ARG, "bad flags %d", desc->flags);
+    if (desc->precision == RD_MIXED && desc->n_bins > kMixedMaxBins)
+        return fail(RD_ERR_ARG, "an RD_MIXED detector holds at most %d bins per cell (got %d)", kMixedMaxBins,
+                    desc->n_bins);
     const size_t per_bin = desc->precision == RD_MIXED ? 8 * sizeof(float) : 6 * sizeof(double);
     if ((size_t)desc->n_pix * (size_t)desc->n_bins > ((size_t)1 << 40) / per_bin)
         return fail(RD_ERR_ARG, "detector too large");
@@ -331,7 +334,7 @@ rd_status rd_deposit_trajectories(rd_detector* d, const rd_traj* t, rd_stream st
     if (t->n_part == 0 || S < 1) return RD_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool mixed = d->precision == RD_MIXED;
-    const size_t rec_size = mixed ? sizeof(RecM) : sizeof(RecD);
+    const size_t rec_size = mixed ? sizeof(RecS) : sizeof(RecD);
     const size_t per_part_rec = rec_size * (size_t)t->n_samples;
     const size_t per_part_in = 2 * 3 * sizeof(double) * (size_t)t->n_samples + sizeof(double);
     // particle chunk: bounded scratch (records + staged input)
@@ -387,8 +390,8 @@ rd_status rd_deposit_trajectories(rd_detector* d, const rd_traj* t, rd_stream st
         P.W = (float)(d->dt_det / t->dt);
         P.invW = (float)(t->dt / d->dt_det);
         if (mixed) {
-            RD_CUDA(launch_precompute_mixed(x, u, np, t->n_samples, t->dt, d->flags,
-                                            static_cast<RecM*>(d->rec), d->counters, s),
+            RD_CUDA(launch_precompute_mixed(x, u, q, t->dt / d->dt_det, np, t->n_samples, t->dt, d->flags,
+                                            static_cast<RecS*>(d->rec), d->counters, s),
                     "precompute");
             LaunchTimer timer(d, s);
             RD_CUDA(launch_deposit_mixed(P, s), "deposit (mixed)");
@@ -500,8 +503,8 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
         const int np = std::min(pc, t->n_part - p0);
         const size_t off = (size_t)p0 * t->n_samples * 3;
         RD_CUDA(cudaMemsetAsync(d->gbeta, 0, per_part_gb * np, s), "clear gradient scratch");
-        RD_CUDA(launch_precompute_scalar(t->x + off, t->u + off, np, t->n_samples, t->dt, d->flags,
-                                         static_cast<RecS*>(d->rec), d->counters, s),
+        RD_CUDA(launch_precompute_mixed(t->x + off, t->u + off, nullptr, 0.0, np, t->n_samples, t->dt, d->flags,
+                                        static_cast<RecS*>(d->rec), d->counters, s),
                 "precompute");
         AdjointParams P;
         P.rec = static_cast<const RecS*>(d->rec);
@@ -619,7 +622,7 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
         const rd_traj& t = trajs[i];
         const int S = t.n_samples - 1;
         const bool empty = t.n_part == 0 || S < 1;
-        rec_off[i + 1] = rec_off[i] + (empty ? 0 : sizeof(RecM) * (size_t)t.n_part * t.n_samples);
+        rec_off[i + 1] = rec_off[i] + (empty ? 0 : sizeof(RecS) * (size_t)t.n_part * t.n_samples);
         const int ncb = (dets[i]->n_pix + kMixedCellsPerCta - 1) / kMixedCellsPerCta;
         chunks[i] = empty ? 1 : choose_chunk(dets[i], t.n_part, S, ncb);
         const long long items = empty ? 0 : (long long)ncb * t.n_part * ((S + chunks[i] - 1) / chunks[i]);
@@ -673,8 +676,9 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
         for (int i = 0; i < n && e == cudaSuccess; ++i) {
             const rd_traj& t = trajs[i];
             if (rec_off[i + 1] == rec_off[i]) continue;
-            e = launch_precompute_mixed(t.x, t.u, t.n_part, t.n_samples, t.dt, dets[i]->flags,
-                                        reinterpret_cast<RecM*>(static_cast<char*>(d0->batch_rec) + rec_off[i]),
+            e = launch_precompute_mixed(t.x, t.u, t.q, t.dt / dets[i]->dt_det, t.n_part, t.n_samples, t.dt,
+                                        dets[i]->flags,
+                                        reinterpret_cast<RecS*>(static_cast<char*>(d0->batch_rec) + rec_off[i]),
                                         dets[i]->counters, s);
         }
         if (e == cudaSuccess && item_off[n] > 0) e = launch_deposit_batch(d_probs, d_off, n, d_counter, batch_grid(), s);

@@ -34,10 +34,9 @@ __device__ __forceinline__ bool finite3(const double* v)
     return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
 }
 
-template <typename Rec, bool DUP>
 __global__ void k_precompute_mixed(const double* __restrict__ x, const double* __restrict__ u,
-                                   int n_part, int n_samples, double dt, int flags,
-                                   Rec* __restrict__ rec, DevCounters* counters)
+                                   const double* __restrict__ q, double qscale, int n_part, int n_samples,
+                                   double dt, int flags, RecS* __restrict__ rec, DevCounters* counters)
 {
     const long long total = (long long)n_part * n_samples;
     const double near_on = (flags & RD_NEAR) ? 1.0 : 0.0;
@@ -46,6 +45,8 @@ __global__ void k_precompute_mixed(const double* __restrict__ x, const double* _
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(i % n_samples);
+        // charge factor folded into the betadot and gamma^-2 terms of Eq. 1 (deposit records)
+        const double qf = qscale != 0.0 ? -(q ? q[i / n_samples] : 1.0) * qscale : 1.0;
         const double* xk = x + 3 * i;
         const double* uk = u + 3 * i;
         bool bad = !finite3(xk) || !finite3(uk);
@@ -67,15 +68,8 @@ __global__ void k_precompute_mixed(const double* __restrict__ x, const double* _
         if (bad) atomicOr(&counters->errors, ERRBIT_INPUT);
         // delta = beta_k - vbar_k (difference of end-point and chord velocities)
         const double ex = bx - vx, ey = by - vy, ez = bz - vz;
-        auto put = [](double v) {
-            if constexpr (DUP) {
-                const float f = (float)v;
-                return make_float2(f, f);
-            } else {
-                return (float)v;
-            }
-        };
-        Rec r;
+        auto put = [](double v) { return (float)v; };
+        RecS r;
         r.nx = put(-xk[0]);
         r.ny = put(-xk[1]);
         r.nz = put(-xk[2]);
@@ -83,10 +77,10 @@ __global__ void k_precompute_mixed(const double* __restrict__ x, const double* _
         r.nbx = put(-bx);
         r.nby = put(-by);
         r.nbz = put(-bz);
-        r.ig2n = put(near_on * ig2);
-        r.bdx = put(far_on ? ax : 0.0);
-        r.bdy = put(far_on ? ay : 0.0);
-        r.bdz = put(far_on ? az : 0.0);
+        r.ig2n = put(qf * (near_on * ig2));
+        r.bdx = put(far_on ? qf * ax : 0.0);
+        r.bdy = put(far_on ? qf * ay : 0.0);
+        r.bdz = put(far_on ? qf * az : 0.0);
         r.dtg = put(dt * g);
         r.d2x = put(2.0 * ex);
         r.d2y = put(2.0 * ey);
@@ -348,23 +342,13 @@ static int grid_for(long long n, int threads)
     return (int)g;
 }
 
-cudaError_t launch_precompute_mixed(const double* x, const double* u, int n_part, int n_samples,
-                                    double dt, int flags, RecM* rec, DevCounters* counters,
+cudaError_t launch_precompute_mixed(const double* x, const double* u, const double* q, double qscale, int n_part,
+                                    int n_samples, double dt, int flags, RecS* rec, DevCounters* counters,
                                     cudaStream_t s)
 {
     const long long n = (long long)n_part * n_samples;
-    k_precompute_mixed<RecM, RD_PACKED != 0><<<grid_for(n, 256), 256, 0, s>>>(x, u, n_part, n_samples, dt,
-                                                                          flags, rec, counters);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_precompute_scalar(const double* x, const double* u, int n_part, int n_samples,
-                                     double dt, int flags, RecS* rec, DevCounters* counters,
-                                     cudaStream_t s)
-{
-    const long long n = (long long)n_part * n_samples;
-    k_precompute_mixed<RecS, false><<<grid_for(n, 256), 256, 0, s>>>(x, u, n_part, n_samples, dt, flags,
-                                                                     rec, counters);
+    k_precompute_mixed<<<grid_for(n, 256), 256, 0, s>>>(x, u, q, qscale, n_part, n_samples, dt, flags, rec,
+                                                        counters);
     return cudaGetLastError();
 }
 

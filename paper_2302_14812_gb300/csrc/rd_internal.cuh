@@ -4,7 +4,7 @@
 //   cell table     D4     [n_pix]              (x, y, z, T0 = t_min + pix_t0)
 //   mixed fields   float   [n_pix][n_bins][8]  (Ex Ey Ez Bx | By Bz 0 0): one 32-byte sector per bin
 //   fp64 fields    double  [n_pix][n_bins][6]  (Ex Ey Ez Bx By Bz)
-//   records        RecM / RecD [n_part][n_samples]: per-sample quantities of Algorithm 1,
+//   records        RecS / RecD [n_part][n_samples]: per-sample quantities of Algorithm 1,
 //                  computed once per call and read by every cell (staged through shared memory
 //                  with bulk asynchronous copies).
 #pragma once
@@ -38,15 +38,12 @@ struct DevCounters {
 // Mixed path, per-sample constants of interval k (16 values), with signs chosen so that every step
 // of the field is an add / mul / fma:
 //   nx, ny, nz = -x_k               nhig2 = -gamma_k^-2 / 2
-//   nbx..nbz   = -beta_k            ig2n  = near ? gamma_k^-2 : 0
-//   bdx..bdz   = far ? betadot_k : 0                 dtg = dt g_k,  g_k = 1 - |vbar_k|^2
+//   nbx..nbz   = -beta_k            ig2n  = Q (near ? gamma_k^-2 : 0)
+//   bdx..bdz   = Q (far ? betadot_k : 0)             dtg = dt g_k,  g_k = 1 - |vbar_k|^2
 //   d2x..d2z   = 2 (beta_k - vbar_k)  gd  = g_k + |beta_k - vbar_k|^2
-// (vbar_k = (x_k - x_{k-1})/dt is the chord velocity of the interval).
-// RD_PACKED = 1: every value stored twice (RecP, 128 bytes) so that one 64-bit register pair
-// feeds a packed f32x2 operation for two cells; RD_PACKED = 0: stored once (RecS, 64 bytes).
-#ifndef RD_PACKED
-#define RD_PACKED 0
-#endif
+// (vbar_k = (x_k - x_{k-1})/dt is the chord velocity of the interval).  Q = -q_p dt/dt_det in the
+// records of a deposit (charge and bin-weight scale folded in: E' and d x E' come out scaled by
+// Q), Q = 1 in the records of the adjoint.
 struct __align__(16) RecS {
     float nx, ny, nz, nhig2;
     float nbx, nby, nbz, ig2n;
@@ -54,18 +51,6 @@ struct __align__(16) RecS {
     float d2x, d2y, d2z, gd;
 };
 static_assert(sizeof(RecS) == 64, "RecS must be 64 bytes");
-struct __align__(16) RecP {
-    float2 nx, ny, nz, nhig2;
-    float2 nbx, nby, nbz, ig2n;
-    float2 bdx, bdy, bdz, dtg;
-    float2 d2x, d2y, d2z, gd;
-};
-static_assert(sizeof(RecP) == 128, "RecP must be 128 bytes");
-#if RD_PACKED
-typedef RecP RecM;
-#else
-typedef RecS RecM;
-#endif
 
 struct __align__(32) D4 {
     double x, y, z, w;
@@ -83,7 +68,7 @@ static_assert(sizeof(RecD) == 96, "RecD must be 96 bytes");
 // kernel parameter blocks
 // ---------------------------------------------------------------------------------------------
 struct DepositParams {
-    const void* rec;            // RecM or RecD [n_part][n_samples]
+    const void* rec;            // RecS or RecD [n_part][n_samples]
     const double* x;            // [n_part][n_samples][3] FP64 positions (anchors of the mixed path)
     const double* q;            // [n_part] or null
     const D4* cells;            // [n_pix] (x, y, z, T0)
@@ -107,22 +92,25 @@ struct DepositParams {
 
 constexpr int kDepositThreads = 256;   // FP64 kernel: one cell per thread
 #ifndef RD_MIXED_MINBLOCKS
-#define RD_MIXED_MINBLOCKS 6
+#define RD_MIXED_MINBLOCKS (RD_MIXED_CELLS >= 4 ? 6 : 5)
 #endif
-constexpr int kMixedCells = 2;                 // mixed kernel: two cells per thread, packed f32x2
-constexpr int kMixedThreads = 128;             // 256 cells per CTA
-constexpr int kMixedCellsPerCta = kMixedThreads * kMixedCells;
+#ifndef RD_MIXED_CELLS
+#define RD_MIXED_CELLS 2
+#endif
+constexpr int kMixedCells = RD_MIXED_CELLS;    // mixed kernel: cells walked by one thread
+constexpr int kMixedCellsPerCta = 256;
+constexpr int kMixedThreads = kMixedCellsPerCta / kMixedCells;
+constexpr int kMixedMaxBins = 1 << 22;         // bins per cell of an RD_MIXED detector
 constexpr int kTileSteps = 64;         // intervals per shared-memory tile
 constexpr int kDefaultChunk = 1024;    // intervals per work item (one FP64 anchor at each end)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // give up a wait after 2 s
 
 // launchers (rd_deposit.cu)
-cudaError_t launch_precompute_mixed(const double* x, const double* u, int n_part, int n_samples,
-                                    double dt, int flags, RecM* rec, DevCounters* counters,
+// qscale != 0: deposit records, betadot and gamma^-2 terms multiplied by -q_p * qscale (q null:
+// unit charges); qscale == 0: plain records (adjoint).
+cudaError_t launch_precompute_mixed(const double* x, const double* u, const double* q, double qscale, int n_part,
+                                    int n_samples, double dt, int flags, RecS* rec, DevCounters* counters,
                                     cudaStream_t s);
-cudaError_t launch_precompute_scalar(const double* x, const double* u, int n_part, int n_samples,
-                                     double dt, int flags, RecS* rec, DevCounters* counters,
-                                     cudaStream_t s);
 cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part, int n_samples,
                                    double dt, RecD* rec, DevCounters* counters, cudaStream_t s);
 cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s);

@@ -5,11 +5,10 @@
 // particles of the same chunk and cell block, so the CTAs resident at one time all reduce into
 // the same ~(256 cells x chunk span) slice of the detector, which stays in L2.
 //
-// Each thread walks two cells through the chunk as one pair: every per-cell quantity is a float2
-// (cell A, cell B) and the field arithmetic runs as packed f32x2 add / mul / fma, one instruction
-// for both cells; the per-sample constants arrive duplicated and sign-folded (RecM) so no packed
-// operation needs a separate negation.  Per cell the walk carries the bin b it is filling and the
-// time f already spent in that bin, in units of dt; a step adds the arrival-time increment
+// Each thread walks kMixedCells cells through the chunk; the per-sample constants (RecS) are read
+// once per sample from shared memory and serve all of them.  Per cell the walk carries the bin it
+// is filling (as an offset from the CTA's first field row) and the time f already spent in that
+// bin, in units of dt; a step adds the arrival-time increment
 //     t'_k - t'_{k-1} = dt [dt g + R_k (g + |n_k - vbar|^2)] / (dt + R_k + R_{k-1})
 // (vbar = (x_k - x_{k-1})/dt, g = 1 - |vbar|^2), an exact identity with only positive terms, so
 // FP32 keeps its relative precision; the chunk's first and last arrival times are computed in
@@ -27,260 +26,284 @@ namespace rd {
 
 namespace {
 
-#ifndef RD_PIPELINE
-#define RD_PIPELINE 0
-#endif
+constexpr int NC = kMixedCells;
+// Bin indices of the walk are clamped to +-2^29 so that offsets (row * n_bins + bin, with
+// n_bins <= kMixedMaxBins) and differences of two of them stay inside int32.
+constexpr double kWalkClamp = 536870912.0;
 
-__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ int walk_bin(double fb) { return (int)fmin(fmax(fb, -kWalkClamp), kWalkClamp); }
 
-// Two-cell arithmetic: packed f32x2 instructions, or the same operations on each half.
-#if RD_PACKED
-__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-#define RV(r, f) ((r).f)
-#else
-__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
-__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c)
-{
-    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
-}
-#define RV(r, f) f2((r).f)
-#endif
-
-// a*b - c*d per half (scalar form: the negation folds into the fused multiply-add)
-__device__ __forceinline__ float2 vfms(float2 a, float2 b, float2 c, float2 d)
-{
-#if RD_PACKED
-    return __ffma2_rn(a, b, __fmul2_rn(__fmul2_rn(c, f2(-1.f)), d));
-#else
-    return make_float2(fmaf(a.x, b.x, -(c.x * d.x)), fmaf(a.y, b.y, -(c.y * d.y)));
-#endif
-}
-
-struct Pair {
-    float2 Px, Py, Pz;   // cell positions
-    float2 f;            // time spent in the current bin, units of dt (0 <= f < W)
-    float2 Rpd;          // R_{k-1} + dt
-    float2 acc[6];       // E xyz, B xyz of the current bin so far (weights in bins)
-    int b[2];            // bin being filled (may lie outside [0, n_bins))
-    float* row[2];       // [n_bins][8] accumulators of each cell
-    bool live[2];        // some arrival of the chunk falls inside the window
-    int below[2];        // intervals whose start lies before the window (clip tracking only)
-    int above[2];        // intervals whose end lies after the window (clip tracking only)
+// Walk state of the thread's cells.
+struct Cells {
+    float px[NC], py[NC], pz[NC];   // cell positions
+    float f[NC];                    // time spent in the current bin, units of dt (0 <= f < W)
+    float rpd[NC];                  // R_{k-1} + dt
+    float acc[6][NC];               // E xyz, B xyz of the current bin so far (weights in bins)
+    int bo[NC];                     // row * n_bins + bin being filled (bin may lie outside the window)
+    int rb[NC];                     // row * n_bins (row = the cell's index inside the CTA's block)
+    bool live[NC];                  // some arrival of the chunk falls inside the window
+    int below[NC];                  // intervals whose start lies before the window (clip tracking only)
+    int above[NC];                  // intervals whose end lies after the window (clip tracking only)
 };
 
 struct Consts {
-    float W;             // bin width / dt
+    float W;                        // bin width / dt
     float invW;
-    float2 Q;            // -(charge * dt / dt_det): weights in dt units -> bins, sign of E' folded in
-    float2 DT;
+    float DT;
     int n_bins;
+    float* base;                    // field row 0 of the CTA's cell block
 };
 
-// Packed field of one sample at both cells (E = S E', B = (S/R) d x E').
-struct Sample {
-    float2 E[3];         // E' = (n - beta)(-c1/kappa) + betadot
-    float2 B[3];         // d x E'
-    float2 S;            // -q' / (kappa^2 R)
-    float2 rinv;         // 1 / R
-    float2 du;           // t'_k - t'_{k-1} in units of dt
+// Field of one sample at one cell, scaled to the bin weights (E = S E', B = (S/R) d x E').
+struct Field {
+    float E[3];                     // E' = Q [(n - beta)(-c1/kappa) + betadot],  Q = -q dt/dt_det
+    float B[3];                     // d x E'
+    float S;                        // 1 / (kappa^2 R)
+    float rinv;                     // 1 / R
+    float num, rden;                // t'_k - t'_{k-1} = num * rden in units of dt
 };
 
-// Add one bin to global memory; bins outside the window are dropped.
-__device__ __forceinline__ void flush(float* row, int n_bins, int b, float e0, float e1, float e2,
-                                      float b0, float b1, float b2)
+__device__ __forceinline__ float* bin_addr(const Consts& C, int bo)
 {
-    if ((unsigned)b < (unsigned)n_bins) {
-        float* p = row + (size_t)b * 8;
+    return reinterpret_cast<float*>(reinterpret_cast<char*>(C.base) + (size_t)(unsigned)bo * 32u);
+}
+
+// Add one bin (b = bin index, bo = its offset) to global memory; bins outside the window are dropped.
+__device__ __forceinline__ void flush(const Consts& C, int b, int bo, float e0, float e1, float e2, float b0,
+                                      float b1, float b2)
+{
+    if ((unsigned)b < (unsigned)C.n_bins) {
+        float* p = bin_addr(C, bo);
         red_add_v4(p, e0, e1, e2, b0);
         red_add_v2(p + 4, b1, b2);
     }
 }
 
-// Eq. 1 with B = n x E, for both cells:
+// Eq. 1 with B = n x E at one cell:
 //   E = q/(kappa^3 R) [ (n - beta)(gamma^-2/R + n.betadot) - betadot kappa ]
-//     = S E',  E' = (n - beta)(-c1/kappa) + betadot,  c1 = gamma^-2/R + n.betadot,  S = -q/(kappa^2 R)
+//     = S E',  S = 1/(kappa^2 R),  E' = -q [(n - beta)(-c1/kappa) + betadot],  c1 = gamma^-2/R + n.betadot
 //   B = n x E = (S/R) d x E'
-// and kappa = (gamma^-2 + |n - beta|^2)/2 avoids the cancellation in 1 - beta.n.
-__device__ __forceinline__ void sample_field(Pair& c, const RecM& r, const Consts& C, Sample& o)
+// E' also carries the bin weight per unit dt (the records hold Q = -q dt/dt_det times betadot and
+// gamma^-2), and kappa = (gamma^-2 + |n - beta|^2)/2 avoids the cancellation in 1 - beta.n.
+__device__ __forceinline__ void field_at(const RecS& r, float px, float py, float pz, float& rpd, const Consts& C,
+                                         Field& o)
 {
-    const float2 one = f2(1.f), mhalf = f2(-0.5f);
     // geometry: d = x_cell - x_k, R = |d|
-    const float2 dx = vadd(c.Px, RV(r, nx)), dy = vadd(c.Py, RV(r, ny)), dz = vadd(c.Pz, RV(r, nz));
-    const float2 r2 = vfma(dx, dx, vfma(dy, dy, vmul(dz, dz)));
-    float2 rinv;
-    rinv.x = fast_rsqrt(r2.x);
-    rinv.y = fast_rsqrt(r2.y);
-    const float2 bx = vfma(dx, rinv, RV(r, nbx)), by = vfma(dy, rinv, RV(r, nby)),
-                 bz = vfma(dz, rinv, RV(r, nbz));                       // n - beta
-    const float2 nb2 = vfma(bx, bx, vfma(by, by, vmul(bz, bz)));
+    const float dx = px + r.nx, dy = py + r.ny, dz = pz + r.nz;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rinv = fast_rsqrt(r2);
+    const float bx = fmaf(dx, rinv, r.nbx), by = fmaf(dy, rinv, r.nby), bz = fmaf(dz, rinv, r.nbz);   // n - beta
+    const float nb2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
     // arrival-time increment in units of dt, numerator and denominator divided by R:
     //   [dt g / R + (g + |n - vbar|^2)] / [1 + (R_{k-1} + dt) / R],
     //   g + |n - vbar|^2 = |n - beta|^2 + 2 (n - beta).(beta - vbar) + (g + |beta - vbar|^2)
-    const float2 gg = vfma(bx, RV(r, d2x), vfma(by, RV(r, d2y), vfma(bz, RV(r, d2z), vadd(nb2, RV(r, gd)))));
-    const float2 num = vfma(RV(r, dtg), rinv, gg);
-    const float2 den = vfma(c.Rpd, rinv, one);
-    float2 rden;
-    rden.x = fast_rcp(den.x);
-    rden.y = fast_rcp(den.y);
-    o.du = vmul(num, rden);
-    c.Rpd = vfma(r2, rinv, C.DT);
+    const float gg = fmaf(bx, r.d2x, fmaf(by, r.d2y, fmaf(bz, r.d2z, nb2 + r.gd)));
+    const float num = fmaf(r.dtg, rinv, gg);
+    const float den = fmaf(rpd, rinv, 1.f);
+    o.num = num;
+    o.rden = fast_rcp(den);
+    rpd = fmaf(r2, rinv, C.DT);
     // Eq. 1
-    const float2 kn = vfma(nb2, mhalf, RV(r, nhig2));                  // -kappa
-    float2 ikn;
-    ikn.x = fast_rcp(kn.x);
-    ikn.y = fast_rcp(kn.y);                                            // -1/kappa
-    const float2 nrik = vmul(rinv, ikn);                               // -1/(kappa R)
-    o.S = vmul(vmul(C.Q, nrik), ikn);                                  // Q/(kappa^2 R) = -q'/(kappa^2 R)
-    const float2 dbd = vfma(dx, RV(r, bdx), vfma(dy, RV(r, bdy), vmul(dz, RV(r, bdz))));
-    const float2 c1n = vmul(vadd(RV(r, ig2n), dbd), nrik);            // -c1/kappa
-    o.E[0] = vfma(bx, c1n, RV(r, bdx));
-    o.E[1] = vfma(by, c1n, RV(r, bdy));
-    o.E[2] = vfma(bz, c1n, RV(r, bdz));
-    o.B[0] = vfms(dy, o.E[2], dz, o.E[1]);
-    o.B[1] = vfms(dz, o.E[0], dx, o.E[2]);
-    o.B[2] = vfms(dx, o.E[1], dy, o.E[0]);
+    const float kn = fmaf(nb2, -0.5f, r.nhig2);                         // -kappa
+    const float ikn = fast_rcp(kn);                                     // -1/kappa
+    const float nrik = rinv * ikn;                                      // -1/(kappa R)
+    o.S = nrik * ikn;                                                   // 1/(kappa^2 R)
+    // with the record's charge factor Q: Q (gamma^-2 + d.betadot) (-1/(kappa R)) = -Q c1/kappa
+    const float c1n = fmaf(dx, r.bdx, fmaf(dy, r.bdy, fmaf(dz, r.bdz, r.ig2n))) * nrik;
+    o.E[0] = fmaf(bx, c1n, r.bdx);
+    o.E[1] = fmaf(by, c1n, r.bdy);
+    o.E[2] = fmaf(bz, c1n, r.bdz);
+    o.B[0] = fmaf(dy, o.E[2], -(dz * o.E[1]));
+    o.B[1] = fmaf(dz, o.E[0], -(dx * o.E[2]));
+    o.B[2] = fmaf(dx, o.E[1], -(dy * o.E[0]));
     o.rinv = rinv;
 }
 
-// Interval of cell H (0 = .x, 1 = .y) that passes two or more bin edges (rare): flush the bin
-// being filled and the whole bins inside the interval, leaving the state one edge short so that
-// the common path below finishes the step (it flushes the last whole bin and starts the next).
-template <int H, bool TRACK>
-__device__ __forceinline__ void multi_edges(Pair& c, const Sample& o, const Consts& C, float2& fn, int k,
-                                         int k_begin, int k_end)
+// Interval of cell j that passes two or more bin edges (rare): flush the bin being filled and the
+// whole bins inside the interval, leaving the state one edge short so that the common path below
+// finishes the step (it flushes the last whole bin and starts the next).
+template <bool TRACK>
+__device__ __forceinline__ void multi_edges(Cells& c, int j, const Field& o, const Consts& C, float& fn, int k,
+                                            int k_begin, int k_end)
 {
-    auto h = [](const float2& v) -> float { return H == 0 ? v.x : v.y; };
-    auto set = [](float2& v, float x) {
-        if (H == 0) v.x = x;
-        else v.y = x;
-    };
-    const float f = h(fn);
+    const float f = fn;
     if (!(f >= 2.f * C.W)) return;
-    const int b0 = c.b[H];
+    const int b0 = c.bo[j] - c.rb[j];
     const int m = (int)fminf(floorf(f * C.invW), 16777216.f);      // edges passed, >= 2
-    flush(c.row[H], C.n_bins, b0, h(c.acc[0]), h(c.acc[1]), h(c.acc[2]), h(c.acc[3]), h(c.acc[4]),
-          h(c.acc[5]));
-    const float S = h(o.S), rinv = h(o.rinv);
-    const float fs = C.W * S, fb = fs * rinv;
+    flush(C, b0, c.bo[j], c.acc[0][j], c.acc[1][j], c.acc[2][j], c.acc[3][j], c.acc[4][j], c.acc[5][j]);
+    const float fs = C.W * o.S, fb = fs * o.rinv;
     // whole bins b0+1 .. b0+m-2 now; bin b0+m-1 is left in the accumulator for the common path
     const int lo = max(b0 + 1, 0), hi = min(b0 + m - 2, C.n_bins - 1);
-    for (int j = lo; j <= hi; ++j)
-        flush(c.row[H], C.n_bins, j, h(o.E[0]) * fs, h(o.E[1]) * fs, h(o.E[2]) * fs, h(o.B[0]) * fb,
-              h(o.B[1]) * fb, h(o.B[2]) * fb);
-    set(c.acc[0], h(o.E[0]) * fs);
-    set(c.acc[1], h(o.E[1]) * fs);
-    set(c.acc[2], h(o.E[2]) * fs);
-    set(c.acc[3], h(o.B[0]) * fb);
-    set(c.acc[4], h(o.B[1]) * fb);
-    set(c.acc[5], h(o.B[2]) * fb);
-    c.b[H] = b0 + m - 1;
-    set(fn, fminf(fmaxf(fmaf(-(float)(m - 1), C.W, f), C.W), C.W * 1.99999988f));
+    for (int b = lo; b <= hi; ++b)
+        flush(C, b, c.rb[j] + b, o.E[0] * fs, o.E[1] * fs, o.E[2] * fs, o.B[0] * fb, o.B[1] * fb, o.B[2] * fb);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        c.acc[i][j] = o.E[i] * fs;
+        c.acc[3 + i][j] = o.B[i] * fb;
+    }
+    c.bo[j] += m - 1;
+    fn = fminf(fmaxf(fmaf(-(float)(m - 1), C.W, f), C.W), C.W * 1.99999988f);
     if (TRACK) {
-        if (b0 < 0 && b0 + m - 1 >= 0) c.below[H] = k - k_begin + 1;
-        if (b0 < C.n_bins && b0 + m - 1 >= C.n_bins) c.above[H] = k_end - k + 1;
+        if (b0 < 0 && b0 + m - 1 >= 0) c.below[j] = k - k_begin + 1;
+        if (b0 < C.n_bins && b0 + m - 1 >= C.n_bins) c.above[j] = k_end - k + 1;
     }
 }
 
-// Integrating deposit of one interval for both cells: the part of [f, f + du] inside the current
-// bin goes to the running bin; a cell whose arrival time passes the bin edge flushes the bin and
-// starts the next one with the rest of the interval.  Branch free apart from the rare case of an
-// interval spanning several bins.  LAST: the interval ends on the exact FP64 anchors.
-// TRACK: bins may lie outside the window (checked, clipped intervals counted).
-template <bool LAST, bool TRACK>
-__device__ __forceinline__ void deposit(Pair& c, const Sample& o, const Consts& C, const int* b_end,
-                                        const float* f_end, int k, int k_begin, int k_end)
+// Walk modes.  kFast: the common step, with no code for an interval that passes two or more bin
+// edges; such an interval sets the cell's time to -inf, after which the cell crosses no edge and
+// flushes nothing for the rest of the tile.  kExact: the same arithmetic plus the multi-edge case;
+// used to walk a tile again (from its saved start) for a warp in which some cell stopped, flushing
+// only from the interval that stopped it onwards (earlier bins were flushed by the fast walk).
+// Both walks evaluate every value with the same operations in the same order (no implicit
+// contraction), so they agree bit for bit up to that interval.
+enum { kFast = 0, kExact = 1 };
+
+// One interval for all cells of the thread: field of the sample (Eq. 1), the part of [f, f + du]
+// inside the current bin added to the running bin; a cell whose arrival time passes the bin edge
+// flushes the bin and starts the next one with the rest of the interval.  LAST: the interval ends
+// on the exact FP64 anchors.  TRACK: bins may lie outside the window (checked, clipped intervals
+// counted).  ok: kExact only, false from the interval that stopped the fast walk onwards.
+template <int MODE, bool LAST, bool TRACK>
+__device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, const int* bo_end,
+                                     const float* f_end, int k, int k_begin, int k_end, bool* ok)
 {
-    float2 fn;
-    if (LAST) {
-        fn.x = fmaf((float)(b_end[0] - c.b[0]), C.W, f_end[0]);
-        fn.y = fmaf((float)(b_end[1] - c.b[1]), C.W, f_end[1]);
-    } else {
-        fn = vadd(c.f, o.du);
+    Field o[NC];
+    float fn[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        field_at(r, c.px[j], c.py[j], c.pz[j], c.rpd[j], C, o[j]);
+        float t;
+        if (LAST) {
+            t = fmaf((float)(bo_end[j] - c.bo[j]), C.W, f_end[j]);
+            if (MODE == kFast) t = c.f[j] == -INFINITY ? -INFINITY : t;
+        } else {
+            t = fmaf(o[j].num, o[j].rden, c.f[j]);
+        }
+        const float ws = (fminf(t, C.W) - c.f[j]) * o[j].S;
+        const float wb = ws * o[j].rinv;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            c.acc[i][j] = fmaf(o[j].E[i], ws, c.acc[i][j]);
+            c.acc[3 + i][j] = fmaf(o[j].B[i], wb, c.acc[3 + i][j]);
+        }
+        if (MODE == kFast)
+            t = t < 2.f * C.W ? t : -INFINITY;
+        else
+            ok[j] = ok[j] && (t < 2.f * C.W);
+        fn[j] = t;
     }
-    float2 mn;
-    mn.x = fminf(fn.x, C.W);
-    mn.y = fminf(fn.y, C.W);
-    const float2 ws = vmul(vfma(c.f, f2(-1.f), mn), o.S);
-    const float2 wb = vmul(ws, o.rinv);
-    c.acc[0] = vfma(o.E[0], ws, c.acc[0]);
-    c.acc[1] = vfma(o.E[1], ws, c.acc[1]);
-    c.acc[2] = vfma(o.E[2], ws, c.acc[2]);
-    c.acc[3] = vfma(o.B[0], wb, c.acc[3]);
-    c.acc[4] = vfma(o.B[1], wb, c.acc[4]);
-    c.acc[5] = vfma(o.B[2], wb, c.acc[5]);
-    if (__any_sync(0xffffffffu, fmaxf(fn.x, fn.y) >= 2.f * C.W)) {
-        multi_edges<0, TRACK>(c, o, C, fn, k, k_begin, k_end);
-        multi_edges<1, TRACK>(c, o, C, fn, k, k_begin, k_end);
+    if (MODE == kExact) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) multi_edges<TRACK>(c, j, o[j], C, fn[j], k, k_begin, k_end);
     }
-    const bool cx = fn.x >= C.W, cy = fn.y >= C.W;
-    // flush the finished bins (predicated, per cell)
-    const bool px = TRACK ? (cx && (unsigned)c.b[0] < (unsigned)C.n_bins) : cx;
-    const bool py = TRACK ? (cy && (unsigned)c.b[1] < (unsigned)C.n_bins) : cy;
-    float* ax = c.row[0] + (ptrdiff_t)c.b[0] * 8;
-    float* ay = c.row[1] + (ptrdiff_t)c.b[1] * 8;
-    red_add_v4_if(px, ax, c.acc[0].x, c.acc[1].x, c.acc[2].x, c.acc[3].x);
-    red_add_v2_if(px, ax + 4, c.acc[4].x, c.acc[5].x);
-    red_add_v4_if(py, ay, c.acc[0].y, c.acc[1].y, c.acc[2].y, c.acc[3].y);
-    red_add_v2_if(py, ay + 4, c.acc[4].y, c.acc[5].y);
-    // start the next bin with the rest of the interval
-    const float2 rem = vadd(fn, f2(-C.W));
-    const float2 rs = vmul(rem, o.S);
-    const float2 rb = vmul(rs, o.rinv);
-    const float2 t0 = vmul(o.E[0], rs), t1 = vmul(o.E[1], rs), t2 = vmul(o.E[2], rs);
-    const float2 t3 = vmul(o.B[0], rb), t4 = vmul(o.B[1], rb), t5 = vmul(o.B[2], rb);
-    c.acc[0] = make_float2(cx ? t0.x : c.acc[0].x, cy ? t0.y : c.acc[0].y);
-    c.acc[1] = make_float2(cx ? t1.x : c.acc[1].x, cy ? t1.y : c.acc[1].y);
-    c.acc[2] = make_float2(cx ? t2.x : c.acc[2].x, cy ? t2.y : c.acc[2].y);
-    c.acc[3] = make_float2(cx ? t3.x : c.acc[3].x, cy ? t3.y : c.acc[3].y);
-    c.acc[4] = make_float2(cx ? t4.x : c.acc[4].x, cy ? t4.y : c.acc[4].y);
-    c.acc[5] = make_float2(cx ? t5.x : c.acc[5].x, cy ? t5.y : c.acc[5].y);
-    c.f = make_float2(cx ? rem.x : fn.x, cy ? rem.y : fn.y);
-    if (TRACK) {
-        if (cx && c.b[0] == -1) c.below[0] = k - k_begin + 1;
-        if (cx && c.b[0] == C.n_bins - 1) c.above[0] = k_end - k + 1;
-        if (cy && c.b[1] == -1) c.below[1] = k - k_begin + 1;
-        if (cy && c.b[1] == C.n_bins - 1) c.above[1] = k_end - k + 1;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        // the arrival time passed the bin edge (a time exactly on the edge belongs to the upper bin)
+        const bool cr = fn[j] >= C.W;
+        if (MODE == kFast && !TRACK) {
+            if (cr) {
+                float* a = bin_addr(C, c.bo[j]);
+                red_add_v4(a, c.acc[0][j], c.acc[1][j], c.acc[2][j], c.acc[3][j]);
+                red_add_v2(a + 4, c.acc[4][j], c.acc[5][j]);
+                const float rem = fn[j] - C.W;
+                const float rs = rem * o[j].S;
+                const float rbw = rs * o[j].rinv;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    c.acc[i][j] = o[j].E[i] * rs;
+                    c.acc[3 + i][j] = o[j].B[i] * rbw;
+                }
+                c.f[j] = rem;
+                c.bo[j] += 1;
+            } else {
+                c.f[j] = fn[j];
+            }
+        } else {
+            const int b = c.bo[j] - c.rb[j];
+            const bool go = MODE == kFast || !ok[j];
+            const bool pr = cr && go && (!TRACK || (unsigned)b < (unsigned)C.n_bins);
+            float* a = bin_addr(C, c.bo[j]);
+            red_add_v4_if(pr, a, c.acc[0][j], c.acc[1][j], c.acc[2][j], c.acc[3][j]);
+            red_add_v2_if(pr, a + 4, c.acc[4][j], c.acc[5][j]);
+            const float rem = fn[j] - C.W;
+            const float rs = rem * o[j].S;
+            const float rbw = rs * o[j].rinv;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                c.acc[i][j] = cr ? o[j].E[i] * rs : c.acc[i][j];
+                c.acc[3 + i][j] = cr ? o[j].B[i] * rbw : c.acc[3 + i][j];
+            }
+            c.f[j] = cr ? rem : fn[j];
+            if (TRACK) {
+                if (cr && b == -1) c.below[j] = k - k_begin + 1;
+                if (cr && b == C.n_bins - 1) c.above[j] = k_end - k + 1;
+            }
+            c.bo[j] += cr ? 1 : 0;
+        }
     }
-    c.b[0] += cx ? 1 : 0;
-    c.b[1] += cy ? 1 : 0;
+}
+
+#ifndef RD_UNROLL
+#define RD_UNROLL 0
+#endif
+constexpr int kUnroll = RD_UNROLL > 0 ? RD_UNROLL : 1;   // samples per loop iteration
+
+// Per-thread copy of the walk state at the start of a tile, in shared memory ([word][thread]).
+constexpr int kSaveWords = NC * 11;
+
+__device__ __forceinline__ void save_state(const Cells& c, float (*sv)[kMixedThreads], int tid)
+{
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        sv[j * 11 + 0][tid] = c.f[j];
+        sv[j * 11 + 1][tid] = c.rpd[j];
+        sv[j * 11 + 2][tid] = __int_as_float(c.bo[j]);
+        sv[j * 11 + 3][tid] = __int_as_float(c.below[j]);
+        sv[j * 11 + 4][tid] = __int_as_float(c.above[j]);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) sv[j * 11 + 5 + i][tid] = c.acc[i][j];
+    }
+}
+
+__device__ __forceinline__ void restore_state(Cells& c, float (*sv)[kMixedThreads], int tid)
+{
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        c.f[j] = sv[j * 11 + 0][tid];
+        c.rpd[j] = sv[j * 11 + 1][tid];
+        c.bo[j] = __float_as_int(sv[j * 11 + 2][tid]);
+        c.below[j] = __float_as_int(sv[j * 11 + 3][tid]);
+        c.above[j] = __float_as_int(sv[j * 11 + 4][tid]);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) c.acc[i][j] = sv[j * 11 + 5 + i][tid];
+    }
 }
 
 template <bool TRACK>
-__device__ __forceinline__ void walk_tile(Pair& c, const RecM* tile, int cnt, bool last_tile,
-                                          const Consts& C, const int* b_end, const float* f_end, int k0,
-                                          int k_begin, int k_end)
+__device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, bool last_tile, const Consts& C,
+                                          const int* bo_end, const float* f_end, int k0, int k_begin, int k_end,
+                                          float (*sv)[kMixedThreads])
 {
+    const int tid = threadIdx.x;
     const int n_regular = last_tile ? cnt - 1 : cnt;
-#if RD_PIPELINE
-    // the field of sample i+1 is evaluated while sample i is deposited (independent work)
-    if (n_regular > 0) {
-        Sample cur;
-        sample_field(c, tile[0], C, cur);
-        for (int i = 0; i < n_regular; ++i) {
-            Sample nxt;
-            const bool more = i + 1 < cnt;
-            if (more) sample_field(c, tile[i + 1], C, nxt);
-            deposit<false, TRACK>(c, cur, C, b_end, f_end, k0 + i, k_begin, k_end);
-            cur = nxt;
-        }
-        if (last_tile) deposit<true, TRACK>(c, cur, C, b_end, f_end, k_end, k_begin, k_end);
-        return;
-    }
-#else
-#pragma unroll 2
-    for (int i = 0; i < n_regular; ++i) {
-        Sample o;
-        sample_field(c, tile[i], C, o);
-        deposit<false, TRACK>(c, o, C, b_end, f_end, k0 + i, k_begin, k_end);
-    }
-#endif
-    if (last_tile) {
-        Sample o;
-        sample_field(c, tile[cnt - 1], C, o);
-        deposit<true, TRACK>(c, o, C, b_end, f_end, k_end, k_begin, k_end);
+    save_state(c, sv, tid);
+    bool ok[NC];
+#pragma unroll kUnroll
+    for (int i = 0; i < n_regular; ++i)
+        step<kFast, false, TRACK>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok);
+    if (last_tile) step<kFast, true, TRACK>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok);
+    bool stopped = false;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) stopped = stopped || c.f[j] == -INFINITY;
+    if (__any_sync(0xffffffffu, stopped)) {
+        // some interval of a cell of this warp passed two or more bin edges: walk the tile again
+        restore_state(c, sv, tid);
+#pragma unroll
+        for (int j = 0; j < NC; ++j) ok[j] = true;
+#pragma unroll 1
+        for (int i = 0; i < n_regular; ++i)
+            step<kExact, false, TRACK>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok);
+        if (last_tile) step<kExact, true, TRACK>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok);
     }
 }
 
@@ -291,14 +314,15 @@ __device__ __forceinline__ void walk_tile(Pair& c, const RecM* tile, int cnt, bo
 // before this item (it selects buffer and mbarrier phase, so the buffers carry over between items).
 // Returns false if a bounded wait ran out (the error is recorded; the CTA must stop).
 __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int cb, int ch,
-                                             RecM (*tile)[kTileSteps], uint64_t* bar, unsigned& g_base)
+                                             RecS (*tile)[kTileSteps], uint64_t* bar, float (*sv)[kMixedThreads],
+                                             unsigned& g_base)
 {
     const int S = P.n_samples - 1;
     const int k_begin = 1 + ch * P.chunk;
     const int k_end = min(S, k_begin + P.chunk - 1);
     const int n_int = k_end - k_begin + 1;
     const int n_tiles = (n_int + kTileSteps - 1) / kTileSteps;
-    const RecM* rec = static_cast<const RecM*>(P.rec) + (size_t)p * P.n_samples;
+    const RecS* rec = static_cast<const RecS*>(P.rec) + (size_t)p * P.n_samples;
     const int tid = threadIdx.x;
 
     if (tid == 0) {
@@ -306,7 +330,7 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
         for (int t = 0; t < 2 && t < n_tiles; ++t) {
             const int k0 = k_begin + t * kTileSteps;
             const unsigned g = g_base + t;
-            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k0 + 1) * sizeof(RecM);
+            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k0 + 1) * sizeof(RecS);
             mbar_arrive_expect_tx(&bar[g & 1], bytes);
             bulk_g2s(tile[g & 1], rec + k0, bytes, &bar[g & 1]);
         }
@@ -315,33 +339,35 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
     Consts C;
     C.W = P.W;
     C.invW = P.invW;
-    C.Q = f2(-(P.q ? (float)P.q[p] : 1.f) * P.du_scale);
-    C.DT = f2(P.dt_f);
+    C.DT = P.dt_f;
     C.n_bins = P.n_bins;
+    C.base = static_cast<float*>(P.fields) + (size_t)cb * kMixedCellsPerCta * P.n_bins * 8;
 
     // anchors: exact FP64 arrival (bins) at both ends of the chunk, per cell
-    Pair c;
-    int b_end[2];
-    float f_end[2];
+    Cells c;
+    int bo_end[NC];
+    float f_end[NC];
     bool partial = false;
     unsigned long long clip = 0, crossed = 0;
     const double* xp = P.x + (size_t)p * P.n_samples * 3;
-    float px[2], py[2], pz[2], fa[2], rpd[2];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const int cell = cb * kMixedCellsPerCta + j * kMixedThreads + tid;
+    for (int j = 0; j < NC; ++j) {
+        const int row = j * kMixedThreads + tid;
+        const int cell = cb * kMixedCellsPerCta + row;
         // a cell without arrivals in the window still walks (no per-cell branch in the step) but
         // from a time that never reaches a bin edge: nothing is flushed
+        c.rb[j] = row * P.n_bins;
+        c.bo[j] = c.rb[j];
         c.live[j] = false;
-        c.b[j] = -1073741824;
-        c.row[j] = static_cast<float*>(P.fields);
         c.below[j] = c.above[j] = 0;
-        fa[j] = -1e30f;
-        rpd[j] = 1e6f;
-        px[j] = 1e6f;
-        py[j] = pz[j] = 0.f;
-        b_end[j] = c.b[j];
+        c.f[j] = -1e30f;
+        c.rpd[j] = 1e6f;
+        c.px[j] = 1e6f;
+        c.py[j] = c.pz[j] = 0.f;
+        bo_end[j] = c.bo[j];
         f_end[j] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) c.acc[i][j] = 0.f;
         if (cell < P.n_pix) {
             const D4 cl = P.cells[cell];
             const double* xa = xp + 3 * (size_t)(k_begin - 1);
@@ -354,30 +380,22 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
                 clip += (unsigned long long)n_int;
             } else {
                 const double fla = floor(ua), fle = floor(ue);
-                c.b[j] = clamp_bin(fla);
-                fa[j] = (float)(ua - fla) * P.W;
-                b_end[j] = clamp_bin(fle);
+                c.bo[j] = c.rb[j] + walk_bin(fla);
+                c.f[j] = (float)(ua - fla) * P.W;
+                bo_end[j] = c.rb[j] + walk_bin(fle);
                 f_end[j] = (float)(ue - fle) * P.W;
-                rpd[j] = (float)Ra + P.dt_f;
-                px[j] = (float)cl.x;
-                py[j] = (float)cl.y;
-                pz[j] = (float)cl.z;
-                c.row[j] = static_cast<float*>(P.fields) + (size_t)cell * P.n_bins * 8;
+                c.rpd[j] = (float)Ra + P.dt_f;
+                c.px[j] = (float)cl.x;
+                c.py[j] = (float)cl.y;
+                c.pz[j] = (float)cl.z;
                 c.below[j] = (ua < 0.0) ? n_int : 0;
                 // unchecked bins need a margin of one bin to each window edge (the FP32 walk may
                 // drift by far less than a bin before the end anchor corrects it)
                 partial = partial || (ua < 1.0) || (ue > (double)P.n_bins - 1.0);
-                crossed += (unsigned long long)max(0, b_end[j] - c.b[j]);
+                crossed += (unsigned long long)max(0, bo_end[j] - c.bo[j]);
             }
         }
     }
-    c.Px = make_float2(px[0], px[1]);
-    c.Py = make_float2(py[0], py[1]);
-    c.Pz = make_float2(pz[0], pz[1]);
-    c.f = make_float2(fa[0], fa[1]);
-    c.Rpd = make_float2(rpd[0], rpd[1]);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) c.acc[i] = f2(0.f);
     // clip tracking costs instructions in the bin-crossing path: only CTAs that need it use it
     const bool track = __syncthreads_or(partial) != 0;
 
@@ -399,27 +417,27 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
         const int cnt = min(kTileSteps, k_end - k0 + 1);
         const bool last_tile = (t == n_tiles - 1);
         if (track)
-            walk_tile<true>(c, tile[buf], cnt, last_tile, C, b_end, f_end, k0, k_begin, k_end);
+            walk_tile<true>(c, tile[buf], cnt, last_tile, C, bo_end, f_end, k0, k_begin, k_end, sv);
         else
-            walk_tile<false>(c, tile[buf], cnt, last_tile, C, b_end, f_end, k0, k_begin, k_end);
+            walk_tile<false>(c, tile[buf], cnt, last_tile, C, bo_end, f_end, k0, k_begin, k_end, sv);
         __syncthreads();
         if (tid == 0 && t + 2 < n_tiles) {
             fence_proxy_async();
             const int k2 = k_begin + (t + 2) * kTileSteps;
-            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k2 + 1) * sizeof(RecM);
+            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k2 + 1) * sizeof(RecS);
             mbar_arrive_expect_tx(&bar[buf], bytes);
             bulk_g2s(tile[buf], rec + k2, bytes, &bar[buf]);
         }
     }
     g_base += (unsigned)n_tiles;
     // close the last bin; count clipped intervals and crossed bin edges
-    if (c.live[0]) {
-        flush(c.row[0], C.n_bins, c.b[0], c.acc[0].x, c.acc[1].x, c.acc[2].x, c.acc[3].x, c.acc[4].x, c.acc[5].x);
-        clip += (unsigned long long)min(n_int, c.below[0] + c.above[0]);
-    }
-    if (c.live[1]) {
-        flush(c.row[1], C.n_bins, c.b[1], c.acc[0].y, c.acc[1].y, c.acc[2].y, c.acc[3].y, c.acc[4].y, c.acc[5].y);
-        clip += (unsigned long long)min(n_int, c.below[1] + c.above[1]);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        if (c.live[j]) {
+            flush(C, c.bo[j] - c.rb[j], c.bo[j], c.acc[0][j], c.acc[1][j], c.acc[2][j], c.acc[3][j], c.acc[4][j],
+                  c.acc[5][j]);
+            clip += (unsigned long long)min(n_int, c.below[j] + c.above[j]);
+        }
     }
     if (clip) atomicAdd(&P.counters->clipped, clip);
     // warp-aggregated count of bin edges crossed (bins touched = intervals + crossings)
@@ -441,8 +459,9 @@ __device__ __forceinline__ void init_staging(uint64_t* bar)
 
 __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_mixed(const DepositParams P)
 {
-    __shared__ __align__(128) RecM tile[2][kTileSteps];
+    __shared__ __align__(128) RecS tile[2][kTileSteps];
     __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float sv[kSaveWords][kMixedThreads];
     init_staging(bar);
     const unsigned bid = blockIdx.x;
     const int p = (int)(bid % (unsigned)P.n_part);
@@ -450,7 +469,7 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_m
     const int cb = (int)(rest % (unsigned)P.n_cell_blocks);
     const int ch = (int)(rest / (unsigned)P.n_cell_blocks);
     unsigned g = 0;
-    (void)deposit_item(P, p, cb, ch, tile, bar, g);
+    (void)deposit_item(P, p, cb, ch, tile, bar, sv, g);
 }
 
 // Persistent form: the resident CTAs draw work items of all problems from one counter.
@@ -461,9 +480,10 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS)
     k_deposit_batch(const DepositParams* __restrict__ probs, const long long* __restrict__ item_off, int n_probs,
                     unsigned long long* next_item)
 {
-    __shared__ __align__(128) RecM tile[2][kTileSteps];
+    __shared__ __align__(128) RecS tile[2][kTileSteps];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ long long s_item;
+    __shared__ float sv[kSaveWords][kMixedThreads];
     init_staging(bar);
     const long long total = item_off[n_probs];
     unsigned g = 0;
@@ -484,7 +504,7 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS)
         const long long rest = local / P.n_part;
         const int cb = (int)(rest % P.n_cell_blocks);
         const int ch = (int)(rest / P.n_cell_blocks);
-        if (!deposit_item(P, p, cb, ch, tile, bar, g)) break;
+        if (!deposit_item(P, p, cb, ch, tile, bar, sv, g)) break;
     }
 }
 

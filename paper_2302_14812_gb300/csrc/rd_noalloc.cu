@@ -77,6 +77,7 @@ extern "C" rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix
     set_last_error(RD_OK, "");
     if (!pix_pos || !fields || !t) return set_last_error(RD_ERR_ARG, "pix_pos, fields and traj must be given");
     if (n_pix < 1 || n_bins < 1) return set_last_error(RD_ERR_ARG, "n_pix and n_bins must be >= 1");
+    if (n_bins > kMixedMaxBins) return set_last_error(RD_ERR_ARG, "n_bins must be <= 4194304");
     if (n_pix > kNoallocMaxCells)
         return set_last_error(RD_ERR_ARG, "rd_deposit_noalloc: n_pix exceeds its maximum of 262144 cells");
     if (!(dt_det > 0.0) || !isfinite(dt_det) || !isfinite(t_min))
@@ -86,7 +87,7 @@ extern "C" rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix
         return set_last_error(RD_ERR_ARG, "bad trajectory shape or time axis");
     if (t->mem != RD_MEM_DEVICE) return set_last_error(RD_ERR_ARG, "rd_deposit_noalloc needs device trajectories");
     if (t->n_part > 0 && (!t->x || !t->u)) return set_last_error(RD_ERR_ARG, "traj x/u is NULL");
-    const size_t per_part = sizeof(RecM) * (size_t)t->n_samples;
+    const size_t per_part = sizeof(RecS) * (size_t)t->n_samples;
     if (per_part > kRecordBytes)
         return set_last_error(RD_ERR_ARG, "rd_deposit_noalloc: one particle's samples exceed the 56 MiB record scratch "
                                           "(at most 917500 samples per particle)");
@@ -96,7 +97,7 @@ extern "C" rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     DevCounters* counters = reinterpret_cast<DevCounters*>(base);
     D4* cells = reinterpret_cast<D4*>(base + kCounterBytes);
-    RecM* records = reinterpret_cast<RecM*>(base + kCounterBytes + kCellBytes);
+    RecS* records = reinterpret_cast<RecS*>(base + kCounterBytes + kCellBytes);
     const int fl = flags ? flags : (RD_NEAR | RD_FAR);
 
     // the array keeps the previous call's contents: counters must start at zero
@@ -115,7 +116,8 @@ extern "C" rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix
         for (int p0 = 0; p0 < t->n_part && e == cudaSuccess; p0 += pc) {
             const int np = std::min(pc, t->n_part - p0);
             const size_t off = (size_t)p0 * t->n_samples * 3;
-            e = launch_precompute_mixed(t->x + off, t->u + off, np, t->n_samples, t->dt, fl, records, counters, s);
+            e = launch_precompute_mixed(t->x + off, t->u + off, t->q ? t->q + p0 : nullptr, t->dt / dt_det, np,
+                                        t->n_samples, t->dt, fl, records, counters, s);
             if (e != cudaSuccess) break;
             DepositParams P;
             P.rec = records;
