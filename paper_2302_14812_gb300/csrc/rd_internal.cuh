@@ -101,7 +101,10 @@ constexpr int kMixedCells = RD_MIXED_CELLS;    // mixed kernel: cells walked by 
 constexpr int kMixedCellsPerCta = 256;
 constexpr int kMixedThreads = kMixedCellsPerCta / kMixedCells;
 constexpr int kMixedMaxBins = 1 << 22;         // bins per cell of an RD_MIXED detector
-constexpr int kTileSteps = 64;         // intervals per shared-memory tile
+#ifndef RD_TILE_STEPS
+#define RD_TILE_STEPS 64
+#endif
+constexpr int kTileSteps = RD_TILE_STEPS;   // intervals per shared-memory tile
 constexpr int kDefaultChunk = 1024;    // intervals per work item (one FP64 anchor at each end)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // give up a wait after 2 s
 

@@ -90,6 +90,44 @@ def test_random_ensembles_ragged(precision, seed):
     check(tr, det, precision)
 
 
+def _multi_edge_case():
+    """Relativistic oscillators along x seen from +-x at distance 50 with bins 1.2 dt wide: about 8 %
+    of the (cell, interval) pairs pass two or more bin edges, mixed with single crossings in every
+    64-interval tile.  Cells 0-255 see every arrival inside the window with a margin (no clip
+    tracking); cells 256-511 have time origins shifted by +-20 so the window cuts their arrivals at
+    one end or the other (clip tracking)."""
+    tr = W.oscillator_ensemble(6, 900, amp_range=(0.5, 1.0), seed=11)
+    rng = np.random.default_rng(11)
+    n = 512
+    sgn = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    pos = np.stack([50.0 * sgn, rng.uniform(-5, 5, n), rng.uniform(-5, 5, n)], axis=1)
+    shift = np.where(np.arange(n) < 256, 0.0, np.where(np.arange(n) % 4 < 2, 20.0, -20.0))
+    return tr, W.Detector(pos, shift, 30.0, 1.2 * tr.dt, 1161)
+
+
+def _bin_coords(tr, det):
+    k = np.arange(tr.n_samples)
+    tt = tr.t0 + k * tr.dt
+    T0 = det.t_min + (0.0 if det.pix_t0 is None else det.pix_t0)
+    return np.array([(tt[None] + np.linalg.norm(det.pix_pos[:, None, :] - tr.x[p][None], axis=-1)
+                      - np.asarray(T0).reshape(-1, 1)) / det.dt_det for p in range(tr.n_part)])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_intervals_spanning_several_bins(precision):
+    """Intervals that pass two or more bin edges (the mixed kernel's fast walk stops such a cell
+    and walks its tile again with the exact step) among ordinary ones, in tracked and untracked
+    cell blocks; every cell against the oracle."""
+    tr, det = _multi_edge_case()
+    u = _bin_coords(tr, det)
+    edges = np.diff(np.floor(u), axis=-1)
+    frac = float(np.mean(edges >= 2))
+    assert 0.02 < frac < 0.5, frac
+    assert u[:, :256].min() >= 1.0 and u[:, :256].max() <= det.n_bins - 1.0     # untracked block
+    assert u[:, 256:].min() < 0.0 and u[:, 256:].max() > det.n_bins              # window cuts block 2
+    check(tr, det, precision)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_undulator_small(precision):
     """Undulator ensemble (gamma 20, K 1, 4000 steps), 8 electrons, 32x32 cap, 2048 bins."""
