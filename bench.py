@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--workload", choices=["undulator", "batch", "adjoint"], default="undulator",
                     help="undulator: the headline deposit; batch: 64 uneven problems, one persistent "
                          "launch vs separate launches; adjoint: gradient kernel")
+    ap.add_argument("--adjoint-particles", type=int, default=10_000,
+                    help="electrons of the adjoint workload (1e4 = the full configuration)")
     ap.add_argument("--batch-scale", type=float, default=0.1,
                     help="particle-count scale of the 64-problem set (memory: every problem resident)")
     return ap.parse_args()
@@ -291,8 +293,8 @@ def run_adjoint_workload(args):
     import paper_2302_14812_gb300 as rd
     from paper_2302_14812_gb300 import workloads as W
     rd.load_library()
-    tr, det = W.config_undulator(n_part=10_000, n_steps=2000, n_side=64, n_bins=1024, gamma=10.0, K=1.0,
-                                 n_periods=10.0, distance=1e4, seed=5)
+    tr, det = W.config_undulator(n_part=args.adjoint_particles, n_steps=2000, n_side=64, n_bins=1024, gamma=10.0,
+                                 K=1.0, n_periods=10.0, distance=1e4, seed=5)
     deposits = W.deposits(tr, det)
     x = torch.from_numpy(tr.x).cuda()
     u = torch.from_numpy(tr.u).cuda()
@@ -328,8 +330,8 @@ def run_adjoint_workload(args):
             "value": res["adjoint"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["adjoint"]["ms_per_step"], "higher_is_better": True,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "1e4 undulator e- (gamma 10, K 1) x 2000 steps, 64x64 cap x 1024 bins, "
-                                   "anchors recomputed every 250 samples", "deposits_per_step": deposits},
+            "config": {"workload": f"{tr.n_part} undulator e- (gamma 10, K 1) x 2000 steps, 64x64 cap x 1024 "
+                                   "bins, anchors recomputed every 250 samples", "deposits_per_step": deposits},
             "forward": res["forward"], "adjoint": res["adjoint"],
             "adjoint_over_forward_time": res["adjoint"]["ms_per_step"] / res["forward"]["ms_per_step"]}
     print(json.dumps(line), flush=True)

@@ -9,8 +9,8 @@
 // and beta_k, betadot_k = (beta_k - beta_{k-1})/dt, n_k, R_k carry the chain to x_k and beta.
 // The walk over bins, arrival times and anchors is the forward walk (same records, same FP32
 // increments anchored in FP64), so the gradient is that of the computed deposit.  Field math in
-// FP32; per step the 256 cells of a CTA are summed (warp shuffles, then shared memory) and the
-// sums are added to FP64 buffers.
+// FP32; per step the cells of a CTA (one per thread) are summed (a reduce-scatter over each warp,
+// then shared memory) and the sums are added to FP64 buffers once per 64-step tile.
 #include <math.h>
 
 #include "rd_internal.cuh"
@@ -52,6 +52,32 @@ __device__ __forceinline__ float warp_sum(float v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Sums of six per-lane values over the warp by reduce-scatter (values padded to eight): at each
+// of the first three butterfly stages a lane keeps half of its values and sends the other half,
+// so 7 + 2 shuffles replace 6 x 5.  Returns, on every lane, the warp sum of value (lane >> 2) & 7
+// (values 6 and 7 are zero).
+__device__ __forceinline__ float warp_sum6(const float* v, int lane)
+{
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+    float a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float lo = v[i], hi = i + 4 < 6 ? v[i + 4] : 0.f;
+        const float keep = h4 ? hi : lo, send = h4 ? lo : hi;
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float b[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float keep = h3 ? a[i + 2] : a[i], send = h3 ? a[i] : a[i + 2];
+        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float c = (h2 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h2 ? b[0] : b[1], 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
 }
 
 // One interval k of one cell: forward field, gathered seed, VJP.  Returns in `out` the finished
@@ -174,7 +200,7 @@ __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointP
 
 }  // namespace
 
-__global__ void __launch_bounds__(kAdjointThreads, 2) k_adjoint_mixed(const AdjointParams P)
+__global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_mixed(const AdjointParams P)
 {
     __shared__ __align__(128) RecS tile[2][kTileSteps];
     __shared__ __align__(8) uint64_t bar[2];
@@ -267,11 +293,9 @@ __global__ void __launch_bounds__(kAdjointThreads, 2) k_adjoint_mixed(const Adjo
                 else
                     adj_step<false>(c, tile[buf][i], P, q, near, far, 0, 0.f, out);
             }
-#pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                const float v = warp_sum(out[j]);
-                if (lane == 0) red[warp][i][j] = v;
-            }
+            const float v = warp_sum6(out, lane);
+            const int j = lane >> 2;
+            if ((lane & 3) == 0 && j < 6) red[warp][i][j] = v;
         }
         __syncthreads();
         // sample k0 - 1 + i gets the sum over the CTA's warps

@@ -136,7 +136,13 @@ struct AdjointParams {
     double t0, dt, inv_dt_det;
     float dt_f, du_scale, W, invW;
 };
-constexpr int kAdjointThreads = 256;   // one cell per thread
+#ifndef RD_ADJ_THREADS
+#define RD_ADJ_THREADS 128
+#endif
+#ifndef RD_ADJ_MINBLOCKS
+#define RD_ADJ_MINBLOCKS 6
+#endif
+constexpr int kAdjointThreads = RD_ADJ_THREADS;   // one cell per thread
 cudaError_t launch_pack_seed(const void* gE, const void* gB, int dtype, int n_pix, int n_bins, float* seed,
                              cudaStream_t s);
 cudaError_t launch_adjoint_mixed(const AdjointParams& p, cudaStream_t s);
