@@ -193,11 +193,22 @@ RD_API rd_status rd_adjoint_trajectories(rd_detector* det, const rd_traj* traj, 
  * are recorded once into a CUDA graph that is replayed while the same detectors (by identity),
  * trajectory pointers, shapes, time axes, chunks and flags come back; the graph reads the
  * trajectory arrays at replay time.  Every detector must be RD_MIXED and every trajectory in
- * device memory; the batch scratch (records of all problems) and the graph live in dets[0].
- * Results equal the separate deposits up to FP32 summation order.
+ * device memory; the batch scratch and the graph live in dets[0].  Memory: the per-sample records
+ * (64 bytes per particle and sample) are computed for a group of problems -- a problem's particles
+ * may be split across groups -- whose records fit dets[0]'s batch budget (rd_set_batch_budget,
+ * default 4 GiB); the groups run one after another, each as record precomputes plus one
+ * persistent launch, reusing one record buffer.  Results equal the separate deposits up to FP32
+ * summation order.
  */
 RD_API rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* trajs,
                                   rd_stream stream);
+
+/*
+ * Bytes of per-sample records per launch group of rd_deposit_batch calls whose first detector is
+ * `det` (0 = the default, 4 GiB; a group always holds at least one particle).  No counterpart in
+ * the paper: it bounds the batch scratch.  RD_ERR_ARG for a negative value.
+ */
+RD_API rd_status rd_set_batch_budget(rd_detector* det, long long bytes);
 
 /*
  * Steps per work item (the step chunk between exact FP64 arrival anchors) for this detector's

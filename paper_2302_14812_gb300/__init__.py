@@ -26,6 +26,7 @@ __all__ = [
     "load_library", "library_path", "rd_create_detector", "rd_destroy", "rd_zero_fields",
     "rd_deposit_trajectories", "rd_read_fields", "rd_synchronize", "rd_get_stats",
     "rd_set_timing", "rd_adjoint_trajectories", "rd_deposit_batch", "rd_set_chunk", "rd_autotune",
+    "rd_set_batch_budget",
     "rd_deposit_noalloc", "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
 ]
 
@@ -97,6 +98,7 @@ def load_library(build_if_missing: bool = True):
             "rd_adjoint_trajectories": ([P, ctypes.POINTER(rd_traj), P, P, I, P, P, P], I),
             "rd_deposit_batch": ([I, ctypes.POINTER(P), ctypes.POINTER(rd_traj), P], I),
             "rd_set_chunk": ([P, I], I),
+            "rd_set_batch_budget": ([P, ctypes.c_longlong], I),
             "rd_autotune": ([P, ctypes.POINTER(rd_traj), P, ctypes.POINTER(I)], I),
             "rd_deposit_noalloc": ([P, P, I, ctypes.c_double, ctypes.c_double, I, I, ctypes.POINTER(rd_traj), P,
                                     ctypes.POINTER(ctypes.c_uint32), P], I),
@@ -186,6 +188,10 @@ def rd_deposit_batch(dets, trajs, stream=None) -> None:
 
 def rd_set_chunk(det: int, chunk: int) -> None:
     _check(load_library().rd_set_chunk(det, int(chunk)), "rd_set_chunk")
+
+
+def rd_set_batch_budget(det: int, nbytes: int) -> None:
+    _check(load_library().rd_set_batch_budget(det, int(nbytes)), "rd_set_batch_budget")
 
 
 def rd_autotune(det: int, traj: rd_traj, stream=None) -> int:
@@ -348,6 +354,10 @@ class RadiationDetector:
 
     def set_chunk(self, chunk: int):
         rd_set_chunk(self._h, chunk)
+
+    def set_batch_budget(self, nbytes: int):
+        """Bytes of per-sample records per launch group of batches led by this detector (0 = 4 GiB)."""
+        rd_set_batch_budget(self._h, nbytes)
 
     def autotune(self, x, u, q=None, t0: float = 0.0, dt: float = 1.0, stream=None) -> int:
         """Pick the fastest step chunk for these trajectories (fields are zeroed afterwards)."""

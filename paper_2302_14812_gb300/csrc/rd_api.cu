@@ -15,6 +15,8 @@
 
 using namespace rd;
 
+static constexpr size_t kBatchBudgetDefault = (size_t)4 << 30;   // records per batch launch group
+
 struct rd_detector {
     int device = 0;
     int n_pix = 0;
@@ -42,8 +44,9 @@ struct rd_detector {
     // batched form (kept in the first detector of a batch)
     void* batch_rec = nullptr;       // records of every problem
     size_t batch_rec_bytes = 0;
-    void* batch_tab = nullptr;       // DepositParams[n] + item offsets[n+1] + counter
+    void* batch_tab = nullptr;       // DepositParams per segment + item offsets + a counter per group
     size_t batch_tab_bytes = 0;
+    size_t batch_budget = kBatchBudgetDefault;   // bytes of records per launch group
     std::vector<unsigned long long> graph_key;
     cudaGraphExec_t graph_exec = nullptr;
     long long n_deposits = 0;
@@ -614,36 +617,60 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
     }
     rd_detector* d0 = dets[0];
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    // layout of the records of every problem, work items per problem
-    std::vector<size_t> rec_off(n + 1, 0);
-    std::vector<long long> item_off(n + 1, 0);
-    std::vector<int> chunks(n);
+    // Segments (a problem's particles [p0, p0 + np)) in groups whose records fit the budget; each
+    // group is one record precompute per segment and one persistent launch over its segments.
+    struct Seg {
+        int prob, p0, np, chunk;
+        size_t rec_off;
+    };
+    std::vector<Seg> segs;
+    std::vector<int> group_first{0};          // group g = segs[group_first[g], group_first[g + 1])
+    std::vector<long long> item_off{0};       // per segment, restarting at 0 in every group
+    size_t used = 0, rec_need = 256;
     for (int i = 0; i < n; ++i) {
         const rd_traj& t = trajs[i];
         const int S = t.n_samples - 1;
-        const bool empty = t.n_part == 0 || S < 1;
-        rec_off[i + 1] = rec_off[i] + (empty ? 0 : sizeof(RecS) * (size_t)t.n_part * t.n_samples);
+        if (t.n_part == 0 || S < 1) continue;
+        const size_t per_part = sizeof(RecS) * (size_t)t.n_samples;
+        const size_t budget = std::max(d0->batch_budget, per_part);
         const int ncb = (dets[i]->n_pix + kMixedCellsPerCta - 1) / kMixedCellsPerCta;
-        chunks[i] = empty ? 1 : choose_chunk(dets[i], t.n_part, S, ncb);
-        const long long items = empty ? 0 : (long long)ncb * t.n_part * ((S + chunks[i] - 1) / chunks[i]);
-        item_off[i + 1] = item_off[i] + items;
+        const int chunk = choose_chunk(dets[i], t.n_part, S, ncb);
+        for (int p0 = 0; p0 < t.n_part;) {
+            if (budget - std::min(used, budget) < per_part) {      // close the group
+                group_first.push_back((int)segs.size());
+                item_off.push_back(0);
+                used = 0;
+            }
+            const int np = (int)std::min<size_t>((size_t)(t.n_part - p0), (budget - used) / per_part);
+            segs.push_back({i, p0, np, chunk, used});
+            item_off.push_back(item_off.back() + (long long)ncb * np * ((S + chunk - 1) / chunk));
+            used += per_part * np;
+            rec_need = std::max(rec_need, used);
+            p0 += np;
+        }
     }
-    const size_t tab_bytes = sizeof(DepositParams) * n + sizeof(long long) * (n + 1) + 64;
-    rd_status st = ensure(&d0->batch_rec, &d0->batch_rec_bytes, std::max<size_t>(rec_off[n], 256), s, "batch records");
+    const int n_seg = (int)segs.size();
+    const int n_groups = n_seg ? (int)group_first.size() : 0;
+    group_first.push_back(n_seg);
+    // device tables: DepositParams[n_seg], item offsets (n_seg + n_groups), one counter per group
+    const size_t off_bytes = sizeof(long long) * item_off.size();
+    const size_t cnt_at = (sizeof(DepositParams) * n_seg + off_bytes + 15) & ~size_t(15);
+    const size_t tab_bytes = cnt_at + sizeof(unsigned long long) * std::max(1, n_groups);
+    rd_status st = ensure(&d0->batch_rec, &d0->batch_rec_bytes, rec_need, s, "batch records");
     if (st != RD_OK) return st;
     st = ensure(&d0->batch_tab, &d0->batch_tab_bytes, tab_bytes, s, "batch table");
     if (st != RD_OK) return st;
     char* tab = static_cast<char*>(d0->batch_tab);
     DepositParams* d_probs = reinterpret_cast<DepositParams*>(tab);
-    long long* d_off = reinterpret_cast<long long*>(tab + sizeof(DepositParams) * n);
-    unsigned long long* d_counter =
-        reinterpret_cast<unsigned long long*>(tab + ((sizeof(DepositParams) * n + sizeof(long long) * (n + 1) + 15) & ~size_t(15)));
+    long long* d_off = reinterpret_cast<long long*>(tab + sizeof(DepositParams) * n_seg);
+    unsigned long long* d_counter = reinterpret_cast<unsigned long long*>(tab + cnt_at);
     // graph key: everything a replay depends on
     std::vector<unsigned long long> key;
     key.push_back((unsigned long long)n);
     key.push_back((unsigned long long)(uintptr_t)d0->batch_rec);
     key.push_back((unsigned long long)(uintptr_t)d0->batch_tab);
     key.push_back((unsigned long long)(uintptr_t)s);
+    key.push_back((unsigned long long)d0->batch_budget);
     for (int i = 0; i < n; ++i) {
         const rd_traj& t = trajs[i];
         unsigned long long t0b, dtb;
@@ -651,43 +678,53 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
         memcpy(&dtb, &t.dt, 8);
         key.insert(key.end(), {dets[i]->id, (unsigned long long)(uintptr_t)t.x, (unsigned long long)(uintptr_t)t.u,
                                (unsigned long long)(uintptr_t)t.q, (unsigned long long)t.n_part,
-                               (unsigned long long)t.n_samples, t0b, dtb, (unsigned long long)chunks[i],
-                               (unsigned long long)dets[i]->flags});
+                               (unsigned long long)t.n_samples, t0b, dtb, (unsigned long long)dets[i]->flags,
+                               (unsigned long long)dets[i]->chunk_override});
     }
     const bool reuse = d0->graph_exec && key == d0->graph_key;
-    if (!reuse) {
-        // problem table (stays in device memory for replays)
-        std::vector<DepositParams> probs(n);
-        for (int i = 0; i < n; ++i)
-            fill_mixed_params(probs[i], dets[i], &trajs[i], static_cast<char*>(d0->batch_rec) + rec_off[i],
-                              trajs[i].x, trajs[i].q, trajs[i].n_part, chunks[i]);
-        RD_CUDA(cudaMemcpyAsync(d_probs, probs.data(), sizeof(DepositParams) * n, cudaMemcpyHostToDevice, s),
-                "batch table");
-        RD_CUDA(cudaMemcpyAsync(d_off, item_off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, s),
-                "batch table");
-        RD_CUDA(cudaStreamSynchronize(s), "batch table");     // host vectors go out of scope
-        if (d0->graph_exec) {
-            cudaGraphExecDestroy(d0->graph_exec);
-            d0->graph_exec = nullptr;
+    if (!reuse && n_seg > 0) {
+        // segment table (stays in device memory for replays)
+        std::vector<DepositParams> probs(n_seg);
+        for (int k = 0; k < n_seg; ++k) {
+            const Seg& g = segs[k];
+            const rd_traj& t = trajs[g.prob];
+            const size_t off = (size_t)g.p0 * t.n_samples * 3;
+            fill_mixed_params(probs[k], dets[g.prob], &t, static_cast<char*>(d0->batch_rec) + g.rec_off, t.x + off,
+                              t.q ? t.q + g.p0 : nullptr, g.np, g.chunk);
         }
+        RD_CUDA(cudaMemcpyAsync(d_probs, probs.data(), sizeof(DepositParams) * n_seg, cudaMemcpyHostToDevice, s),
+                "batch table");
+        RD_CUDA(cudaMemcpyAsync(d_off, item_off.data(), off_bytes, cudaMemcpyHostToDevice, s), "batch table");
+        RD_CUDA(cudaStreamSynchronize(s), "batch table");     // host vectors go out of scope
+    }
+    if (!reuse && d0->graph_exec) {
+        cudaGraphExecDestroy(d0->graph_exec);
+        d0->graph_exec = nullptr;
     }
     auto enqueue = [&]() -> cudaError_t {
-        cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s);
-        for (int i = 0; i < n && e == cudaSuccess; ++i) {
-            const rd_traj& t = trajs[i];
-            if (rec_off[i + 1] == rec_off[i]) continue;
-            e = launch_precompute_mixed(t.x, t.u, t.q, t.dt / dets[i]->dt_det, t.n_part, t.n_samples, t.dt,
-                                        dets[i]->flags,
-                                        reinterpret_cast<RecS*>(static_cast<char*>(d0->batch_rec) + rec_off[i]),
-                                        dets[i]->counters, s);
+        if (n_seg == 0) return cudaSuccess;
+        cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long) * n_groups, s);
+        for (int gi = 0; gi < n_groups && e == cudaSuccess; ++gi) {
+            const int a = group_first[gi], b = group_first[gi + 1];
+            for (int k = a; k < b && e == cudaSuccess; ++k) {
+                const Seg& g = segs[k];
+                const rd_traj& t = trajs[g.prob];
+                const size_t off = (size_t)g.p0 * t.n_samples * 3;
+                e = launch_precompute_mixed(t.x + off, t.u + off, t.q ? t.q + g.p0 : nullptr, t.dt / dets[g.prob]->dt_det,
+                                            g.np, t.n_samples, t.dt, dets[g.prob]->flags,
+                                            reinterpret_cast<RecS*>(static_cast<char*>(d0->batch_rec) + g.rec_off),
+                                            dets[g.prob]->counters, s);
+            }
+            // segment k's items are d_off[k + gi], relative to the group's first item
+            if (e == cudaSuccess)
+                e = launch_deposit_batch(d_probs + a, d_off + a + gi, b - a, d_counter + gi, batch_grid(), s);
         }
-        if (e == cudaSuccess && item_off[n] > 0) e = launch_deposit_batch(d_probs, d_off, n, d_counter, batch_grid(), s);
         return e;
     };
     if (s == nullptr) {
         // the legacy default stream cannot be captured: launch directly
         RD_CUDA(enqueue(), "rd_deposit_batch");
-    } else {
+    } else if (n_seg > 0) {
         if (!reuse) {
             cudaGraph_t graph = nullptr;
             RD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture batch");
@@ -710,6 +747,15 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
     }
     for (int i = 0; i < n; ++i)
         dets[i]->n_deposits += (long long)trajs[i].n_part * std::max(0, trajs[i].n_samples - 1) * dets[i]->n_pix;
+    return RD_OK;
+}
+
+rd_status rd_set_batch_budget(rd_detector* d, long long bytes)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    if (bytes < 0) return fail(RD_ERR_ARG, "budget must be >= 0 (got %lld)", bytes);
+    d->batch_budget = bytes > 0 ? (size_t)bytes : kBatchBudgetDefault;
     return RD_OK;
 }
 

@@ -67,3 +67,9 @@ def test_argument_errors_without_gpu():
     with pytest.raises(rd.RDError) as ei:
         rd.rd_create_detector(d)
     assert ei.value.status == rd.RD_ERR_ARG
+    # an RD_MIXED detector holds at most 2^22 bins per cell (walk offsets stay in int32)
+    d.precision, d.n_bins = rd.RD_MIXED, (1 << 22) + 1
+    assert lib.rd_create_detector(ctypes.byref(d), None, ctypes.byref(h)) == rd.RD_ERR_ARG
+    assert "4194304" in rd.rd_last_error()
+    assert lib.rd_set_batch_budget(None, 0) == rd.RD_ERR_ARG
+    assert lib.rd_set_chunk(None, 0) == rd.RD_ERR_ARG

@@ -176,3 +176,36 @@ def test_uneven_64_problem_set_reduced_particles():
     del keep
     for d in dets:
         d.close()
+
+
+def test_batch_record_budget_splits_into_groups():
+    """A 150 KB record budget splits the six problems into particle segments and ~20 launch groups
+    (each records + one persistent launch); results equal separate deposits, on first capture and
+    on replay (accumulating)."""
+    import torch
+    probs = small_problems()
+    sep = run_separate(probs)
+    stream = torch.cuda.Stream()
+    dets = [rd.RadiationDetector.from_workload(det, "mixed") for _, det in probs]
+    dets[0].set_batch_budget(150_000)
+    trajs = [_dev(tr) for tr, _ in probs]
+    with torch.cuda.stream(stream):
+        keep = rd.deposit_batch(dets, trajs, stream)
+        once = [d.read(stream=stream) for d in dets]
+        keep2 = rd.deposit_batch(dets, trajs, stream)          # replayed graph, accumulates
+        twice = [d.read(stream=stream) for d in dets]
+    del keep, keep2
+    for (E, B), (E2, B2), (Es, Bs) in zip(once, twice, sep):
+        assert rel_l2(E, Es) <= 2e-6 and rel_l2(B, Bs) <= 2e-6
+        assert rel_l2(E2, 2 * Es) <= 2e-6 and rel_l2(B2, 2 * Bs) <= 2e-6
+    dets[0].set_batch_budget(0)                                   # back to the default: one group
+    for d in dets:
+        d.zero(stream)
+    with torch.cuda.stream(stream):
+        keep = rd.deposit_batch(dets, trajs, stream)
+        again = [d.read(stream=stream) for d in dets]
+    del keep
+    for (E, B), (Es, Bs) in zip(again, sep):
+        assert rel_l2(E, Es) <= 2e-6 and rel_l2(B, Bs) <= 2e-6
+    for d in dets:
+        d.close()
