@@ -59,9 +59,12 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["undulator", "batch", "adjoint"], default="undulator",
+    ap.add_argument("--workload", choices=["undulator", "batch", "adjoint", "plasma_mirror"], default="undulator",
                     help="undulator: the headline deposit; batch: 64 uneven problems, one persistent "
                          "launch vs separate launches; adjoint: gradient kernel")
+    ap.add_argument("--pm-particles", type=int, default=100_000,
+                    help="electrons of the plasma-mirror workload (1e5 = the full configuration)")
+    ap.add_argument("--pm-chunk", type=int, default=10_000, help="electrons generated and deposited per chunk")
     ap.add_argument("--adjoint-particles", type=int, default=10_000,
                     help="electrons of the adjoint workload (1e4 = the full configuration)")
     ap.add_argument("--batch-scale", type=float, default=0.1,
@@ -337,6 +340,80 @@ def run_adjoint_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_plasma_mirror_workload(args):
+    """The plasma-mirror configuration at full size: 1e5 electrons x 10000 steps onto 256x256 cells
+    x 4096 bins (6.55e13 deposits), generated on the device in particle chunks and deposited
+    (accumulating) into one mixed detector; the FP64 GPU path on 64 random cells of the same
+    detector and the CPU oracle on 2 of them give the parity of the full-size result."""
+    import torch
+    import oracle
+    import paper_2302_14812_gb300 as rd
+    from paper_2302_14812_gb300 import workloads as W
+    rd.load_library()
+    oracle.build()
+    n_part, n_steps = args.pm_particles, 10_000
+    dt = 12.0 * 2.0 * math.pi / n_steps
+    det = W.plasma_mirror_detector(dt)
+    rng = np.random.default_rng(3)
+    cells64 = np.sort(rng.choice(det.n_pix, 64, replace=False))
+    sel2 = np.sort(rng.choice(64, 2, replace=False)).astype(np.int32)
+    sub = det.subset(cells64)
+    dm = rd.RadiationDetector.from_workload(det, "mixed")
+    d64 = rd.RadiationDetector.from_workload(sub, "fp64")
+    Eo = np.zeros((2, det.n_bins, 3))
+    Bo = np.zeros((2, det.n_bins, 3))
+    t_mixed = t_fp64 = t_oracle = 0.0
+    for p0 in range(0, n_part, args.pm_chunk):
+        x, u, q, (t0, dtc) = W.plasma_mirror_surface_torch(slice(p0, min(n_part, p0 + args.pm_chunk)),
+                                                           n_part=n_part, n_steps=n_steps)
+        torch.cuda.synchronize()
+        for d, which in ((dm, "mixed"), (d64, "fp64")):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            d.deposit(x, u, q, t0, dtc)
+            e1.record()
+            e1.synchronize()
+            if which == "mixed":
+                t_mixed += e0.elapsed_time(e1) / 1e3
+            else:
+                t_fp64 += e0.elapsed_time(e1) / 1e3
+        tr = W.Trajectories(x.cpu().numpy(), u.cpu().numpy(), q.cpu().numpy(), t0, dtc)
+        c0 = time.perf_counter()
+        e_o, b_o, _ = oracle.deposit(tr, sub, sel2)
+        t_oracle += time.perf_counter() - c0
+        Eo += e_o
+        Bo += b_o
+        del x, u, q, tr
+    E, B = dm.read("float32", "cuda")
+    idx = torch.from_numpy(cells64).cuda()
+    Em, Bm = E[idx].double().cpu().numpy(), B[idx].double().cpu().numpy()
+    del E, B
+    E64, B64 = d64.read()
+    st = dm.stats()
+    dm.close()
+    d64.close()
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    deposits = n_part * n_steps * det.n_pix
+    line = {"metric": "particle·step·pixel deposits/sec, plasma-mirror configuration at full size",
+            "value": deposits / t_mixed, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (generated on the device in particle chunks)",
+            "config": {"workload": f"plasma-mirror surface: {n_part} e- (a0 5, 20 harmonics n^-2, 12 periods) x "
+                                   f"{n_steps} steps, 256x256-cell plane x 4096 bins", "deposits": deposits,
+                       "particle_chunk": args.pm_chunk},
+            "seconds_mixed": t_mixed, "bin_crossings": st.n_bin_crossings, "clipped": st.n_clipped,
+            "fp64_gpu_64_cells": {"value": n_part * n_steps * 64 / t_fp64, "seconds": t_fp64},
+            "parity": {"mixed_vs_fp64_gpu_64_cells_E": rel(Em, E64), "mixed_vs_fp64_gpu_64_cells_B": rel(Bm, B64),
+                       "mixed_vs_oracle_2_cells_E": rel(Em[sel2], Eo), "mixed_vs_oracle_2_cells_B": rel(Bm[sel2], Bo),
+                       "fp64_gpu_vs_oracle_2_cells_E": rel(E64[sel2], Eo),
+                       "fp64_gpu_vs_oracle_2_cells_B": rel(B64[sel2], Bo)},
+            "oracle_2_cells": {"value": n_part * n_steps * 2 / t_oracle, "seconds": t_oracle,
+                               "cores": oracle.default_threads()}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, local_rank, world = dist_env()
@@ -348,6 +425,9 @@ def main():
         return
     if args.workload == "adjoint":
         run_adjoint_workload(args)
+        return
+    if args.workload == "plasma_mirror":
+        run_plasma_mirror_workload(args)
         return
 
     import torch

@@ -246,6 +246,60 @@ def plasma_mirror_surface(n_part: int = 100_000, n_steps: int = 10_000, n_period
     return Trajectories(x, u, np.full(n_sel, q), 0.0, dt)
 
 
+def plasma_mirror_surface_torch(particles: slice, n_part: int = 100_000, n_steps: int = 10_000,
+                                n_periods: float = 12.0, a0: float = 5.0, n_harm: int = 20, jitter: float = 0.01,
+                                half_width_lambda: float = 3.0, phase_slope: float = 0.5, seed: int = 3,
+                                q: float = -1.0, device="cuda", sub: int = 1000):
+    """plasma_mirror_surface(..., particles=particles) evaluated with PyTorch in FP64 on `device`:
+    the same seeded particle parameters and formulas, positions by the same 8-node Gauss-Legendre
+    quadrature (summed on the device, so values agree with the numpy generator to rounding).
+    For ensembles too large to generate on the host.  Returns (x, u, q) tensors and (t0, dt)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    lam0 = 2.0 * math.pi
+    yz = rng.uniform(-half_width_lambda * lam0, half_width_lambda * lam0, (n_part, 2))[particles]
+    xs = rng.uniform(0.0, 0.05 * lam0, n_part)[particles]
+    amp = (a0 * (1.0 + jitter * rng.standard_normal(n_part)))[particles]
+    n_sel = yz.shape[0]
+    f64 = dict(dtype=torch.float64, device=device)
+    s_max = 1.0 + float(np.sum(np.arange(2, n_harm + 1, dtype=np.float64) ** -2.0))
+    t_total = n_periods * 2.0 * math.pi
+    dt = t_total / n_steps
+    t = dt * torch.arange(n_steps + 1, **f64)
+    k = torch.arange(n_steps, **f64)
+    tn = (dt * (k[:, None] + 0.5 * (1.0 + torch.tensor(_GL_X, **f64)[None, :]))).reshape(-1)   # [S*8]
+    glw = torch.tensor(_GL_W, **f64)
+
+    def s_fn(th):
+        acc = torch.cos(th)
+        for n in range(2, n_harm + 1):
+            acc = acc + torch.cos(n * th) / float(n * n)
+        return acc
+
+    def mom(tt, ph, a):
+        env = torch.sin(math.pi * torch.clamp(tt / t_total, 0.0, 1.0)) ** 2
+        th = tt[None, :] + ph[:, None]
+        ux = a[:, None] * env[None, :] * s_fn(th) / s_max
+        uz = 0.5 * a[:, None] * env[None, :] * torch.sin(th)
+        return torch.stack([ux, torch.zeros_like(ux), uz], dim=-1)
+
+    x = torch.empty((n_sel, n_steps + 1, 3), **f64)
+    u = torch.empty((n_sel, n_steps + 1, 3), **f64)
+    for p0 in range(0, n_sel, sub):
+        p1 = min(n_sel, p0 + sub)
+        ph = torch.tensor(phase_slope * yz[p0:p1, 0], **f64)
+        a = torch.tensor(amp[p0:p1], **f64)
+        u[p0:p1] = mom(t, ph, a)
+        un = mom(tn, ph, a)
+        b = un / torch.sqrt(1.0 + torch.sum(un * un, dim=-1, keepdim=True))
+        inc = 0.5 * dt * torch.einsum("psnc,n->psc", b.reshape(p1 - p0, n_steps, 8, 3), glw)
+        x0 = torch.tensor(np.stack([xs[p0:p1], yz[p0:p1, 0], yz[p0:p1, 1]], axis=-1), **f64)
+        x[p0:p1, 0] = x0
+        x[p0:p1, 1:] = x0[:, None, :] + torch.cumsum(inc, dim=1)
+        del un, b, inc
+    return x, u, torch.full((n_sel,), q, **f64), (0.0, dt)
+
+
 def oscillator_ensemble(n_part: int, n_steps: int, amp_range=(0.1, 2.0), omega: float = 1.0,
                         n_periods: float = 6.0, seed: int = 4, q: float = -1.0) -> Trajectories:
     """Linear relativistic oscillators along x: u_x = a_i sin(w t + phi_i), random a_i, phi_i."""
@@ -402,17 +456,22 @@ def config_undulator(n_part: int = 1000, n_steps: int = 4000, n_side: int = 128,
     return tr, det
 
 
-def config_plasma_mirror(n_part: int = 100_000, n_steps: int = 10_000, n_side: int = 256,
-                         n_bins: int = 4096, particles: Optional[slice] = None, seed: int = 3):
-    """Plasma-mirror-like surface (a0 5, 20 harmonics, 12 periods), cartesian plane at
-    x = -6.4 lambda0 spanning +-6.4 lambda0, pix_t0 = |x_pix| - reach, dt_det = 5 dt."""
-    tr = plasma_mirror_surface(n_part=n_part, n_steps=n_steps, particles=particles, seed=seed)
+def plasma_mirror_detector(dt: float, n_side: int = 256, n_bins: int = 4096) -> Detector:
+    """Cartesian plane at x = -6.4 lambda0 spanning +-6.4 lambda0 (reflected direction of the
+    plasma-mirror surface), pix_t0 = |x_pix| - reach, dt_det = 5 dt."""
     lam0 = 2.0 * math.pi
     pos = cartesian_plane(n_side, -6.4 * lam0, 6.4 * lam0)
     reach = math.sqrt(2.0) * 3.0 * lam0 + 0.1 * lam0 + 5.0    # slab half-diagonal + depth + margin
     pix_t0 = np.linalg.norm(pos, axis=1) - reach
-    det = Detector(pos, pix_t0, 0.0, 5.0 * tr.dt, n_bins, RD_NEAR | RD_FAR, (n_side, n_side))
-    return tr, det
+    return Detector(pos, pix_t0, 0.0, 5.0 * dt, n_bins, RD_NEAR | RD_FAR, (n_side, n_side))
+
+
+def config_plasma_mirror(n_part: int = 100_000, n_steps: int = 10_000, n_side: int = 256,
+                         n_bins: int = 4096, particles: Optional[slice] = None, seed: int = 3):
+    """Plasma-mirror-like surface (a0 5, 20 harmonics, 12 periods) and its detector
+    (plasma_mirror_detector)."""
+    tr = plasma_mirror_surface(n_part=n_part, n_steps=n_steps, particles=particles, seed=seed)
+    return tr, plasma_mirror_detector(tr.dt, n_side, n_bins)
 
 
 def batch_problems(n_problems: int = 64, seed: int = 4, scale: float = 1.0):

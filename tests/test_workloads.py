@@ -1,0 +1,42 @@
+"""Input generators (no method arithmetic): shapes, seeding, and the device-side generator of the
+plasma-mirror ensemble against the host one."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2302_14812_gb300 import workloads as W
+
+
+def test_plasma_mirror_device_generator_matches_host_generator():
+    """The PyTorch generator (used for ensembles too large to build on the host) gives the host
+    generator's trajectories for the same particle slice, to rounding."""
+    torch = pytest.importorskip("torch")
+    sl = slice(100, 130)
+    tr = W.plasma_mirror_surface(n_steps=1000, particles=sl)
+    x, u, q, (t0, dt) = W.plasma_mirror_surface_torch(sl, n_steps=1000, device="cpu", sub=7)
+    assert x.dtype == torch.float64 and tuple(x.shape) == tr.x.shape
+    assert np.abs(x.numpy() - tr.x).max() <= 1e-13 * np.abs(tr.x).max()
+    assert np.abs(u.numpy() - tr.u).max() <= 1e-13 * np.abs(tr.u).max()
+    assert t0 == tr.t0 and dt == tr.dt and np.array_equal(q.numpy(), tr.q)
+
+
+def test_plasma_mirror_ensemble_is_subluminal_and_seeded():
+    tr = W.plasma_mirror_surface(n_part=2000, n_steps=400, particles=slice(0, 40))
+    v = np.linalg.norm(np.diff(tr.x, axis=1), axis=-1) / tr.dt
+    assert v.max() < 1.0
+    tr2 = W.plasma_mirror_surface(n_part=2000, n_steps=400, particles=slice(20, 40))
+    assert np.array_equal(tr.x[20:], tr2.x)          # a slice is the same particles
+
+
+def test_plasma_mirror_detector_window_covers_arrivals():
+    """pix_t0 = |x_pix| - reach and 4096 bins of 5 dt: every arrival of the surface electrons
+    lies inside the window of every cell (on a sample of cells and particles)."""
+    tr = W.plasma_mirror_surface(n_part=100_000, n_steps=10_000, particles=slice(0, 3))
+    det = W.plasma_mirror_detector(tr.dt, n_side=16)
+    k = np.arange(tr.n_samples)
+    for p in range(tr.n_part):
+        R = np.linalg.norm(det.pix_pos[:, None, :] - tr.x[p][None], axis=-1)
+        ub = (tr.t0 + k[None] * tr.dt + R - (det.t_min + det.pix_t0[:, None])) / det.dt_det
+        assert ub.min() > 0.0 and ub.max() < det.n_bins
+    assert math.isclose(det.dt_det, 5.0 * tr.dt)
