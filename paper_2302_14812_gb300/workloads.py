@@ -456,6 +456,28 @@ def config_undulator(n_part: int = 1000, n_steps: int = 4000, n_side: int = 128,
     return tr, det
 
 
+def config_sinusoidal_benchmark(n_cells: int = 512, n_periods: float = 5.0, n_bins: int = 131072,
+                                gamma: float = 50.0, K: float = 10.0, k_beta: float = 0.1, dt: float = 0.01,
+                                distance: float = 1e5, aperture: float = 0.1):
+    """Section 4 benchmark: one electron (gamma 50) on a sinusoidal trajectory with K = 10
+    (r_beta = K/(gamma k_beta) = 2, k_beta = 0.1) stepped with dt = 0.01, moving along +z and
+    oscillating in y; a line of a spherical detector at 1e5 in the x-z plane (the plane normal to
+    the motion plane through the axis), `aperture` rad wide around +z, n_cells cells, n_bins bins
+    of 2.98e-5.  Each cell's time origin is its earliest arrival minus 0.01."""
+    lam = 2.0 * math.pi / k_beta
+    bz, _ = undulator_params(gamma, K, lam)
+    n_steps = int(round(n_periods * lam / bz / dt))
+    tr = undulator_ensemble(n_part=1, gamma=gamma, K=K, n_periods=n_periods, n_steps=n_steps, lambda_u=lam,
+                            sigma_offset=0.0, seed=1)
+    tr.x[:, :, :2] -= tr.x[:, :1, :2]
+    th = np.linspace(-0.5 * aperture, 0.5 * aperture, n_cells)
+    pos = np.stack([distance * np.sin(th), np.zeros_like(th), distance * np.cos(th)], axis=1)
+    k = np.arange(tr.n_samples)
+    first = np.array([np.min(tr.t0 + k * tr.dt + np.linalg.norm(p - tr.x[0], axis=1)) for p in pos])
+    det = Detector(pos, first - 0.01 - distance, distance, 2.98e-5, n_bins, RD_NEAR | RD_FAR, (n_cells,))
+    return tr, det, th
+
+
 def plasma_mirror_detector(dt: float, n_side: int = 256, n_bins: int = 4096) -> Detector:
     """Cartesian plane at x = -6.4 lambda0 spanning +-6.4 lambda0 (reflected direction of the
     plasma-mirror surface), pix_t0 = |x_pix| - reach, dt_det = 5 dt."""

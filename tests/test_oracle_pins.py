@@ -497,3 +497,87 @@ def test_complex_step_matches_central_differences(oracle_lib):
         # projected on a random cotangent (what the adjoint computes)
         a, b = float(np.sum(g * dE)), float(np.sum(g * fd))
         assert abs(a - b) <= 1e-5 * max(abs(a), 1e-3 * np.abs(dE).sum())
+
+
+# ---------------------------------------------------------------------------------------------
+# Section 4 benchmark: K = 10 sinusoidal trajectory against Eq. 8 and Eq. 9
+# ---------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def sinusoidal_spectra(oracle_lib):
+    """Oracle fields of the Section 4 benchmark (gamma 50, K 10, k_beta 0.1, dt 0.01, 5 periods)
+    on 33 cells of the detector line (theta in [-0.05, 0.05] out of the motion plane, R = 1e5,
+    131072 bins of 2.98e-5), as power spectra |E(w)|^2 (box filter of the bins divided out),
+    averaged over 24 log-spaced frequency bands in [0.02, 3] w_c."""
+    gam, K = 50.0, 10.0
+    tr, det, th = W.config_sinusoidal_benchmark(n_cells=33)
+    E, _, clipped = oracle.deposit(tr, det)
+    assert clipped == 0
+    bz, wb = W.undulator_params(gam, K, 2.0 * math.pi / 0.1)
+    wc = 1.5 * K * gam ** 2 * wb
+    spec = np.sum(np.abs(np.fft.rfft(E, axis=1)) ** 2, axis=2)
+    w = 2.0 * math.pi * np.fft.rfftfreq(det.n_bins, det.dt_det)
+    spec /= np.sinc(w * det.dt_det / (2.0 * math.pi))[None, :] ** 2
+    edges = np.geomspace(0.02, 3.0, 25) * wc
+    band = np.array([[spec[c, (w >= a) & (w < b)].mean() for a, b in zip(edges[:-1], edges[1:])]
+                     for c in range(len(th))])
+    return dict(gam=gam, K=K, wb=wb, wc=wc, th=th, edges=edges, band=band)
+
+
+def _eq8_shape(w, th, gam, K, wb, swapped=False):
+    """Angular-spectral shape of Eq. 8: w^2 (g^-2 + th^2)^2 [K_2/3^2(Y) + th^2/(g^-2 + th^2) K_1/3^2(Y)],
+    Y = w gam / (3 wb K) (g^-2 + th^2)^(3/2) (textbook order of the Bessel functions); swapped: the
+    orders as printed in the paper."""
+    sp = pytest.importorskip("scipy.special")
+    a = gam ** -2 + th * th
+    ups = w * gam / (3.0 * wb * K) * a ** 1.5
+    k23, k13 = sp.kv(2.0 / 3.0, ups) ** 2, sp.kv(1.0 / 3.0, ups) ** 2
+    pol = th * th / a * k23 + k13 if swapped else k23 + th * th / a * k13
+    return w * w * a * a * pol
+
+
+def test_sinusoidal_benchmark_angular_spectrum_eq8(sinusoidal_spectra):
+    """Band-averaged spectra on axis (w/w_c in [0.1, 2.2]) and at theta = 0.94/gamma (w/w_c in
+    [0.1, 1.5]) follow Eq. 8 within 8 % (normalised to the on-axis peak band: the formula's
+    prefactor is asymptotic; five periods leave a few harmonics per low-frequency band, whose
+    placement moves a band mean by a few per cent).  Eq. 8 as printed, with the Bessel orders
+    exchanged, misses the on-axis shape by more than 50 % near w = 0.1 w_c: the textbook order is
+    the one the fields follow."""
+    s = sinusoidal_spectra
+    th, edges, band = s["th"], s["edges"], s["band"]
+    mid = np.sqrt(edges[1:] * edges[:-1])
+    use = (mid >= 0.1 * s["wc"]) & (mid <= 2.2 * s["wc"])
+    c0 = int(np.argmin(np.abs(th)))
+    ref = int(np.argmax(band[c0]))
+
+    def theory(c, swapped=False):
+        return np.array([np.mean(_eq8_shape(np.linspace(a, b, 16), th[c], s["gam"], s["K"], s["wb"], swapped))
+                         for a, b in zip(edges[:-1], edges[1:])])
+    t0 = theory(c0)
+    c1 = int(np.argmin(np.abs(th - 1.0 / s["gam"])))
+    for c, hi in ((c0, 2.2), (c1, 1.5)):
+        ratio = (band[c] / band[c0, ref]) / (theory(c) / t0[ref])
+        sel = (mid >= 0.1 * s["wc"]) & (mid <= hi * s["wc"])
+        assert np.all(np.abs(ratio[sel] - 1.0) < 0.08), (th[c], ratio[sel])
+    sw = theory(c0, swapped=True)
+    ratio_sw = (band[c0] / band[c0, ref]) / (sw / sw[ref])
+    assert np.max(np.abs(ratio_sw[use] - 1.0)) > 0.5
+
+
+def test_sinusoidal_benchmark_angle_integrated_eq9(sinusoidal_spectra):
+    """Summed over the detector line (theta integral), the band-averaged spectrum follows Eq. 9,
+    dI/dw ~ (w/w_c) int_{w/w_c}^inf K_5/3(x) dx, within 3 % for w/w_c in [0.15, 2.2] (at lower
+    frequencies the emission cone is wider than the 0.1 rad line)."""
+    sp = pytest.importorskip("scipy.special")
+    si = pytest.importorskip("scipy.integrate")
+    s = sinusoidal_spectra
+    edges, wc = s["edges"], s["wc"]
+    mid = np.sqrt(edges[1:] * edges[:-1])
+    tint = s["band"].sum(axis=0)
+
+    def F(x):
+        return x * si.quad(lambda v: sp.kv(5.0 / 3.0, v), x, np.inf)[0]
+    eq9 = np.array([np.mean([F(x / wc) for x in np.linspace(a, b, 8)]) for a, b in zip(edges[:-1], edges[1:])])
+    ref = int(np.argmax(tint))
+    ratio = (tint / tint[ref]) / (eq9 / eq9[ref])
+    use = (mid >= 0.15 * wc) & (mid <= 2.2 * wc)
+    assert np.all(np.abs(ratio[use] - 1.0) < 0.03), ratio[use]
