@@ -66,6 +66,8 @@ enum { RD_NEAR = 1, RD_FAR = 2 };
 enum { RD_MEM_DEVICE = 0, RD_MEM_HOST = 1 };
 /* element type of caller field / gradient-seed buffers */
 enum { RD_F32 = 0, RD_F64 = 1 };
+/* field whose power spectrum rd_power_spectrum computes */
+enum { RD_SPEC_E = 0, RD_SPEC_B = 1 };
 
 /*
  * Virtual detector (Section 3.1): n_pix cells at positions pix_pos, each with a uniform time
@@ -153,6 +155,19 @@ RD_API rd_status rd_deposit_trajectories(rd_detector* det, const rd_traj* traj, 
  */
 RD_API rd_status rd_read_fields(rd_detector* det, void* E, void* B, int32_t dtype, int32_t mem,
                          rd_stream stream);
+
+/*
+ * Power spectrum of every cell's time series (Section 4: the detector data Fourier transformed in
+ * time, the spectra compared with Eq. 8 and Eq. 9).  With N = n_bins, F = E (which = RD_SPEC_E) or
+ * B (RD_SPEC_B) and F_c[j][b] the bin values:
+ *     out[j][k] = dt_det^2 * sum_{c=x,y,z} | sum_{b<N} F_c[j][b] exp(-2 pi i k b / N) |^2,
+ * k = 0..N/2, angular frequency w_k = 2 pi k / (N dt_det).  The bins are averages over dt_det,
+ * so the spectrum of the underlying field is out / sinc^2(w dt_det / 2) below the Nyquist
+ * frequency.  out: caller-owned device memory, float[n_pix][N/2 + 1].  FP32 FFT (relative error
+ * ~1e-6 of the spectrum's norm).  Requires N a power of two (else RD_ERR_ARG); scratch of
+ * 32 * n_pix * N bytes held by the detector.  Asynchronous on `stream`.
+ */
+RD_API rd_status rd_power_spectrum(rd_detector* det, int32_t which, float* out, rd_stream stream);
 
 /* Synchronise the stream and return (then clear) latched kernel errors. */
 RD_API rd_status rd_synchronize(rd_detector* det, rd_stream stream);

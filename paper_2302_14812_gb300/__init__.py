@@ -26,7 +26,7 @@ __all__ = [
     "load_library", "library_path", "rd_create_detector", "rd_destroy", "rd_zero_fields",
     "rd_deposit_trajectories", "rd_read_fields", "rd_synchronize", "rd_get_stats",
     "rd_set_timing", "rd_adjoint_trajectories", "rd_deposit_batch", "rd_set_chunk", "rd_autotune",
-    "rd_set_batch_budget",
+    "rd_set_batch_budget", "rd_power_spectrum",
     "rd_deposit_noalloc", "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
 ]
 
@@ -35,6 +35,7 @@ RD_FP64, RD_MIXED = 0, 1
 RD_NEAR, RD_FAR = 1, 2
 RD_MEM_DEVICE, RD_MEM_HOST = 0, 1
 RD_F32, RD_F64 = 0, 1
+RD_SPEC_E, RD_SPEC_B = 0, 1
 
 _STATUS = {0: "RD_OK", 1: "RD_ERR_ARG", 2: "RD_ERR_CUDA", 3: "RD_ERR_OOM", 4: "RD_ERR_STATE",
            5: "RD_ERR_TIMEOUT", 6: "RD_ERR_BOUNDS", 7: "RD_ERR_INPUT"}
@@ -99,6 +100,7 @@ def load_library(build_if_missing: bool = True):
             "rd_deposit_batch": ([I, ctypes.POINTER(P), ctypes.POINTER(rd_traj), P], I),
             "rd_set_chunk": ([P, I], I),
             "rd_set_batch_budget": ([P, ctypes.c_longlong], I),
+            "rd_power_spectrum": ([P, I, P, P], I),
             "rd_autotune": ([P, ctypes.POINTER(rd_traj), P, ctypes.POINTER(I)], I),
             "rd_deposit_noalloc": ([P, P, I, ctypes.c_double, ctypes.c_double, I, I, ctypes.POINTER(rd_traj), P,
                                     ctypes.POINTER(ctypes.c_uint32), P], I),
@@ -192,6 +194,10 @@ def rd_set_chunk(det: int, chunk: int) -> None:
 
 def rd_set_batch_budget(det: int, nbytes: int) -> None:
     _check(load_library().rd_set_batch_budget(det, int(nbytes)), "rd_set_batch_budget")
+
+
+def rd_power_spectrum(det: int, which: int, out_ptr: int, stream=None) -> None:
+    _check(load_library().rd_power_spectrum(det, int(which), out_ptr, _stream_ptr(stream)), "rd_power_spectrum")
 
 
 def rd_autotune(det: int, traj: rd_traj, stream=None) -> int:
@@ -328,6 +334,14 @@ class RadiationDetector:
         B = torch.empty_like(E)
         rd_read_fields(self._h, E.data_ptr(), B.data_ptr(), code, RD_MEM_DEVICE, stream)
         return E, B
+
+    def power_spectrum(self, field: str = "E", stream=None):
+        """dt_det^2 sum_c |FFT_b F_c[j][b]|^2 for k = 0..n_bins/2 (F = E or B): a float32 CUDA
+        tensor [n_pix][n_bins/2 + 1]; angular frequency of column k is 2 pi k / (n_bins dt_det)."""
+        import torch
+        out = torch.empty((self.n_pix, self.n_bins // 2 + 1), dtype=torch.float32, device="cuda")
+        rd_power_spectrum(self._h, RD_SPEC_B if field == "B" else RD_SPEC_E, out.data_ptr(), stream)
+        return out
 
     def adjoint(self, x, u, q, t0, dt, gE, gB=None, stream=None):
         """d loss / d x and d loss / d u (FP64 CUDA tensors [n_part][n_samples][3]) for upstream

@@ -47,6 +47,12 @@ struct rd_detector {
     void* batch_tab = nullptr;       // DepositParams per segment + item offsets + a counter per group
     size_t batch_tab_bytes = 0;
     size_t batch_budget = kBatchBudgetDefault;   // bytes of records per launch group
+    void* spec = nullptr;            // power spectra: two complex work arrays
+    size_t spec_bytes = 0;
+    void* spec_tw = nullptr;         // twiddles of length spec_n
+    size_t spec_tw_bytes = 0;
+    int spec_n = 0;
+    std::vector<float2> spec_tw_host;
     std::vector<unsigned long long> graph_key;
     cudaGraphExec_t graph_exec = nullptr;
     long long n_deposits = 0;
@@ -311,6 +317,8 @@ rd_status rd_destroy(rd_detector* d)
     cudaFree(d->gbeta);
     cudaFree(d->batch_rec);
     cudaFree(d->batch_tab);
+    cudaFree(d->spec);
+    cudaFree(d->spec_tw);
     if (d->graph_exec) cudaGraphExecDestroy(d->graph_exec);
     delete d;
     return RD_OK;
@@ -747,6 +755,36 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
     }
     for (int i = 0; i < n; ++i)
         dets[i]->n_deposits += (long long)trajs[i].n_part * std::max(0, trajs[i].n_samples - 1) * dets[i]->n_pix;
+    return RD_OK;
+}
+
+rd_status rd_power_spectrum(rd_detector* d, int32_t which, float* out, rd_stream stream)
+{
+    g_err.clear();
+    if (!d || !out) return fail(RD_ERR_ARG, "detector/out is NULL");
+    if (which != RD_SPEC_E && which != RD_SPEC_B) return fail(RD_ERR_ARG, "bad field selector %d", which);
+    const int N = d->n_bins;
+    if (N < 2 || (N & (N - 1)) != 0) return fail(RD_ERR_ARG, "n_bins must be a power of two >= 2 (got %d)", N);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t work = sizeof(float2) * 2 * (size_t)d->n_pix * N;
+    rd_status st = ensure(&d->spec, &d->spec_bytes, 2 * work, s, "spectrum scratch");
+    if (st != RD_OK) return st;
+    if (d->spec_n != N) {
+        st = ensure(&d->spec_tw, &d->spec_tw_bytes, sizeof(float2) * (N / 2), s, "twiddles");
+        if (st != RD_OK) return st;
+        RD_CUDA(cudaStreamSynchronize(s), "twiddles");          // the host table may be in flight
+        d->spec_tw_host.resize(N / 2);
+        fill_twiddles(d->spec_tw_host.data(), N);
+        RD_CUDA(cudaMemcpyAsync(d->spec_tw, d->spec_tw_host.data(), sizeof(float2) * (N / 2), cudaMemcpyHostToDevice,
+                                s),
+                "twiddles");
+        d->spec_n = N;
+    }
+    float2* z = static_cast<float2*>(d->spec);
+    float2* y = reinterpret_cast<float2*>(static_cast<char*>(d->spec) + work);
+    RD_CUDA(launch_power_spectrum(d->fields, d->precision, d->n_pix, N, which == RD_SPEC_B ? 3 : 0, z, y,
+                                  static_cast<const float2*>(d->spec_tw), (float)(d->dt_det * d->dt_det), out, s),
+            "power spectrum");
     return RD_OK;
 }
 

@@ -151,6 +151,10 @@ cudaError_t launch_gbeta_to_gu(const double* u, const double* gbeta, double* gu,
 
 cudaError_t launch_read_fields(const void* fields, int precision, int n_pix, int n_bins, void* E,
                                void* B, int dtype, cudaStream_t s);
+// power spectra (rd_spectrum.cu): twiddles exp(-2 pi i j / N), j < N/2, computed on the host
+void fill_twiddles(float2* host, int N);
+cudaError_t launch_power_spectrum(const void* fields, int precision, int n_pix, int N, int c0, float2* z,
+                                  float2* y, const float2* tw, float scale, float* P, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------------
 // device helpers: mbarrier, bulk async copy, vector reductions
