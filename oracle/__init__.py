@@ -57,7 +57,7 @@ def _load():
             lib.rdo_arrival_time.argtypes = [ctypes.c_double, D, D]
             lib.rdo_arrival_time.restype = ctypes.c_double
             lib.rdo_bin_coord.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.c_double, D, D,
-                                          ctypes.c_double, ctypes.c_double]
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int32]
             lib.rdo_bin_coord.restype = ctypes.c_double
             lib.rdo_deposit_interval.argtypes = [ctypes.c_double, ctypes.c_double, D, ctypes.c_int32, D]
             lib.rdo_deposit_interval.restype = ctypes.c_int32
@@ -114,10 +114,11 @@ def arrival_time(t, x, P) -> float:
     return float(lib.rdo_arrival_time(float(t), _dp(_vec(x)), _dp(_vec(P))))
 
 
-def bin_coord(t0, k, dt, x, P, T0, inv_dt_det) -> float:
+def bin_coord(t0, k, dt, x, P, T0, inv_dt_det, flags=3) -> float:
+    """Arrival time of sample k at cell P in bin units: Eq. 2, or Eq. 3 when flags has bit 4."""
     lib = _load()
     return float(lib.rdo_bin_coord(float(t0), int(k), float(dt), _dp(_vec(x)), _dp(_vec(P)),
-                                   float(T0), float(inv_dt_det)))
+                                   float(T0), float(inv_dt_det), int(flags)))
 
 
 def deposit_interval(a, c, F, n_bins, row=None):

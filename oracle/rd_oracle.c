@@ -10,6 +10,8 @@
  * selected cell j, particle p and interval k = 1..S between trajectory samples k-1 and k:
  *     F_pk   = Eq. 1 at sample k (beta_k = u_k/sqrt(1+u_k^2), betadot_k = (beta_k-beta_{k-1})/dt)
  *     t'_pk  = t_k + |x_k - P_j|                                       (Eq. 2)
+ *              (flags bit 4: the far-field limit, Eq. 3 and Eq. 1 with n, R of the cell seen
+ *              from the origin; see rd_oracle_core.h)
  *     E_det[j][b] += F_pk * |[t'_p,k-1, t'_pk] ∩ [T_b, T_b+1)| / dt_det, T_b = t_min + pix_t0[j] + b dt_det
  * with times taken in bin units of the cell's axis so that bin edges are exact integers.
  * Loop order: cell -> particle -> interval -> bin (Algorithm 1 with Algorithm 2 inside).
@@ -76,7 +78,10 @@ typedef struct {
 void rdo_field(const double x[3], const double beta[3], const double bdot[3], const double P[3],
                double q, int32_t flags, double E[3], double B[3])
 {
-    lw_field_r(x, beta, bdot, P, q, flags, E, B);
+    if (flags & 4)
+        ff_field_r(beta, bdot, P, q, flags, E, B);
+    else
+        lw_field_r(x, beta, bdot, P, q, flags, E, B);
 }
 
 double rdo_arrival_time(double t, const double x[3], const double P[3])
@@ -86,9 +91,9 @@ double rdo_arrival_time(double t, const double x[3], const double P[3])
 }
 
 double rdo_bin_coord(double t0, int64_t k, double dt, const double x[3], const double P[3],
-                     double T0, double inv_dt_det)
+                     double T0, double inv_dt_det, int32_t flags)
 {
-    return bin_coord_r(t0, (long long)k, dt, x, P, T0, inv_dt_det);
+    return bin_coord_r(t0, (long long)k, dt, x, P, T0, inv_dt_det, flags);
 }
 
 /* Deposit one interval [a, c] (bin units) of the constant field F[6] into row[n_bins][6]. */

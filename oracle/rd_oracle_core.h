@@ -63,15 +63,55 @@ static void FN(lw_field)(const SCALAR x[3], const SCALAR beta[3], const SCALAR b
 }
 
 /*
+ * Far-field (Fraunhofer) limit, flags bit 4.  A cell at P is seen from the origin along
+ * n_c = P/|P| at distance R_c = |P| (computed as R_c = sqrt((P0*P0 + P1*P1) + P2*P2), n_c = P/R_c).
+ * The radiation term of Eq. 1 is taken with n = n_c and R = R_c:
+ *   E = q n_c x ((n_c - beta) x betadot) / (kappa^3 R_c),  kappa = 1 - beta.n_c,  B = n_c x E;
+ * the velocity term, of order 1/R^2, is not part of this limit (bit 1 is ignored).
+ */
+static void FN(ff_dir)(const double P[3], double nc[3], double* Rc)
+{
+    double R = sqrt((P[0] * P[0] + P[1] * P[1]) + P[2] * P[2]);
+    *Rc = R;
+    for (int i = 0; i < 3; ++i) nc[i] = P[i] / R;
+}
+
+static void FN(ff_field)(const SCALAR beta[3], const SCALAR bdot[3], const double P[3], double q, int flags,
+                         SCALAR E[3], SCALAR B[3])
+{
+    double nc[3], Rc;
+    FN(ff_dir)(P, nc, &Rc);
+    SCALAR m[3] = {nc[0] - beta[0], nc[1] - beta[1], nc[2] - beta[2]};
+    SCALAR kap = 1.0 - (beta[0] * nc[0] + beta[1] * nc[1] + beta[2] * nc[2]);
+    SCALAR v[3] = {m[1] * bdot[2] - m[2] * bdot[1], m[2] * bdot[0] - m[0] * bdot[2], m[0] * bdot[1] - m[1] * bdot[0]};
+    SCALAR s = (flags & 2) ? q / (kap * kap * kap * Rc) : 0.0;
+    E[0] = s * (nc[1] * v[2] - nc[2] * v[1]);
+    E[1] = s * (nc[2] * v[0] - nc[0] * v[2]);
+    E[2] = s * (nc[0] * v[1] - nc[1] * v[0]);
+    B[0] = nc[1] * E[2] - nc[2] * E[1];
+    B[1] = nc[2] * E[0] - nc[0] * E[2];
+    B[2] = nc[0] * E[1] - nc[1] * E[0];
+}
+
+/*
  * Arrival time of sample k at cell P in bin units of the cell's time axis (Eq. 2, c = 1):
  *   t_det = t_k + |x_k - P|,  t_k = t0 + k dt,   u = (t_det - T0) / dt_det
  * evaluated in this fixed order, with no fused multiply-add:
  *   t_k = t0 + (k*dt);  R = sqrt((dx*dx + dy*dy) + dz*dz);  u = ((t_k + R) - T0) * inv_dt_det.
+ * flags bit 4: Eq. 3 in place of Eq. 2 (far-field limit above).
  */
 static SCALAR FN(bin_coord)(double t0, long long k, double dt, const SCALAR x[3], const double P[3],
-                            double T0, double inv_dt_det)
+                            double T0, double inv_dt_det, int flags)
 {
     double tk = t0 + (double)k * dt;
+    if (flags & 4) {
+        /* Eq. 3: t_det = t + R_c - x.n_c, as ((t_k + R_c) - ((x0*n0 + x1*n1) + x2*n2)) */
+        double nc[3], Rc;
+        FN(ff_dir)(P, nc, &Rc);
+        SCALAR xn = (x[0] * nc[0] + x[1] * nc[1]) + x[2] * nc[2];
+        SCALAR t_ff = (tk + Rc) - xn;
+        return (t_ff - T0) * inv_dt_det;
+    }
     SCALAR dx = P[0] - x[0], dy = P[1] - x[1], dz = P[2] - x[2];
     SCALAR R = S_SQRT((dx * dx + dy * dy) + dz * dz);
     SCALAR tdet = tk + R;
@@ -119,14 +159,17 @@ static long long FN(pixel_particle)(const SCALAR* x, const SCALAR* u, int n_samp
     SCALAR beta_prev[3], beta[3], bdot[3], E[3], B[3], F[6];
     long long clipped = 0;
     FN(beta_of)(u, beta_prev);
-    SCALAR a = FN(bin_coord)(t0, 0, dt, x, P, T0, inv_dt_det);
+    SCALAR a = FN(bin_coord)(t0, 0, dt, x, P, T0, inv_dt_det, flags);
     for (int k = 1; k < n_samples; ++k) {
         const SCALAR* xk = x + 3 * (size_t)k;
         FN(beta_of)(u + 3 * (size_t)k, beta);
         for (int i = 0; i < 3; ++i) bdot[i] = (beta[i] - beta_prev[i]) / dt;
-        FN(lw_field)(xk, beta, bdot, P, q, flags, E, B);
+        if (flags & 4)
+            FN(ff_field)(beta, bdot, P, q, flags, E, B);
+        else
+            FN(lw_field)(xk, beta, bdot, P, q, flags, E, B);
         for (int i = 0; i < 3; ++i) { F[i] = E[i]; F[3 + i] = B[i]; }
-        SCALAR c = FN(bin_coord)(t0, k, dt, xk, P, T0, inv_dt_det);
+        SCALAR c = FN(bin_coord)(t0, k, dt, xk, P, T0, inv_dt_det, flags);
         clipped += FN(deposit_interval)(a, c, F, n_bins, row);
         a = c;
         for (int i = 0; i < 3; ++i) beta_prev[i] = beta[i];

@@ -35,6 +35,10 @@ MUTATIONS = {
                        "SCALAR inv_gamma2 = 1.0 - (beta[0] * beta[0] + beta[1] * beta[1]);"),
     "overlap_from_bin_start": ("SCALAR s = (ra > (double)b) ? a : (SCALAR)(double)b;",
                                "SCALAR s = (SCALAR)(double)b;"),
+    # far-field limit: Eq. 3 with the projection added instead of subtracted; kappa^2
+    "farfield_time_sign": ("SCALAR t_ff = (tk + Rc) - xn;", "SCALAR t_ff = (tk + Rc) + xn;"),
+    "farfield_kappa_squared": ("SCALAR s = (flags & 2) ? q / (kap * kap * kap * Rc) : 0.0;",
+                               "SCALAR s = (flags & 2) ? q / (kap * kap * Rc) : 0.0;"),
 }
 
 

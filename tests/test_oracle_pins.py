@@ -276,9 +276,11 @@ def _received_energy(E, B, pos, w, dt_det):
     return float(np.sum(w * R2 * S.sum(1)) * dt_det / (4.0 * math.pi))
 
 
-def test_larmor_dipole_energy(oracle_lib):
+@pytest.mark.parametrize("flags", [W.RD_NEAR | W.RD_FAR, W.RD_FAR | W.RD_FARFIELD])
+def test_larmor_dipole_energy(oracle_lib, flags):
     """Non-relativistic dipole x = a sin(w t) z (a w = 1e-3): received energy through a sphere
-    at 1e4 wavelengths equals the Larmor energy (2/3) q^2 int |betadot|^2 dt = q^2 a^2 w^4 T/3."""
+    at 1e4 wavelengths equals the Larmor energy (2/3) q^2 int |betadot|^2 dt = q^2 a^2 w^4 T/3,
+    with the exact fields and in the far-field limit."""
     q, a, w0 = 1.0, 1e-3, 1.0
     period = 2.0 * math.pi / w0
     n_per, n_steps = 10, 4000
@@ -296,7 +298,7 @@ def test_larmor_dipole_energy(oracle_lib):
     pos, wts = _sphere_pixels(Rs, 8, 1)
     dt_det = period / 200.0
     n_bins = int((n_per * period + 4.0 * a) / dt_det) + 40
-    det = W.Detector(pos, None, Rs - 2.0 * a - 10 * dt_det, dt_det, n_bins)
+    det = W.Detector(pos, None, Rs - 2.0 * a - 10 * dt_det, dt_det, n_bins, flags=flags)
     E, B, clipped = oracle.deposit(tr, det)
     assert clipped == 0
     got = _received_energy(E, B, pos, wts, dt_det)
@@ -581,3 +583,37 @@ def test_sinusoidal_benchmark_angle_integrated_eq9(sinusoidal_spectra):
     ratio = (tint / tint[ref]) / (eq9 / eq9[ref])
     use = (mid >= 0.15 * wc) & (mid <= 2.2 * wc)
     assert np.all(np.abs(ratio[use] - 1.0) < 0.03), ratio[use]
+
+
+# ---------------------------------------------------------------------------------------------
+# far-field limit (Eq. 3 with Eq. 1's radiation term at the cell's direction and distance)
+# ---------------------------------------------------------------------------------------------
+def test_farfield_limit_converges_to_exact_deposit(oracle_lib):
+    """One undulator electron (gamma 10, K 1, 10 periods) seen by cells within 0.1 rad of its axis
+    at R = 1e3, 1e4, 1e5: the far-field deposit differs from the exact one (Eq. 2 and the exact
+    radiation term) by terms of order |x|/R and |x_perp|^2/(2R), so the relative difference falls
+    tenfold per decade of R."""
+    tr = W.undulator_ensemble(n_part=1, gamma=10.0, K=1.0, n_periods=10, n_steps=2000, sigma_offset=0.0, seed=1)
+    dirs = W.spherical_cap(3, 1.0, 0.1)
+    k = np.arange(tr.n_samples)
+    diffs = []
+    for R in (1e3, 1e4, 1e5):
+        pos = R * dirs
+        first = np.array([np.min(tr.t0 + k * tr.dt + np.linalg.norm(p - tr.x[0], axis=1)) for p in pos])
+        dt_det = 2e-3
+        det = W.Detector(pos, first - R - 0.05, R, dt_det, 1024, flags=W.RD_FAR)
+        Ee, Be, ce = oracle.deposit(tr, det)
+        det.flags = W.RD_FAR | W.RD_FARFIELD
+        Ef, Bf, cf = oracle.deposit(tr, det)
+        assert ce == 0 and cf == 0
+        diffs.append(np.linalg.norm(Ef - Ee) / np.linalg.norm(Ee))
+    r1, r2 = diffs[1] / diffs[0], diffs[2] / diffs[1]
+    assert 0.05 < r1 < 0.2 and 0.05 < r2 < 0.2, diffs
+    assert diffs[2] < 1e-2
+
+
+def test_farfield_uniform_motion_exactly_zero(oracle_lib):
+    tr = W.uniform_motion(3, 80, 0.05, speed=0.9, seed=2)
+    det = W.Detector(W.spherical_cap(4, 30.0, 0.5), None, 25.0, 0.05, 256, flags=W.RD_FAR | W.RD_FARFIELD)
+    E, B, _ = oracle.deposit(tr, det)
+    assert np.all(E == 0.0) and np.all(B == 0.0)
