@@ -59,6 +59,7 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-farfield", action="store_true", help="skip the far-field-limit leg")
     ap.add_argument("--workload", choices=["undulator", "batch", "adjoint", "plasma_mirror"], default="undulator",
                     help="undulator: the headline deposit; batch: 64 uneven problems, one persistent "
                          "launch vs separate launches; adjoint: gradient kernel")
@@ -510,6 +511,28 @@ def main():
         f64.close()
         del E64, B64
 
+    # ---------------- far-field limit (RD_FARFIELD) on the same workload ----------------
+    ff_info = None
+    if not args.no_farfield:
+        det_ff = W.Detector(det.pix_pos, det.pix_t0, det.t_min, det.dt_det, det.n_bins, W.RD_FAR | W.RD_FARFIELD)
+        ffd = rd.RadiationDetector.from_workload(det_ff, "mixed")
+        for _ in range(max(1, args.warmup)):
+            ffd.zero()
+            ffd.deposit(xd, ud, qd, tr.t0, tr.dt)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ffd.zero()
+            ffd.deposit(xd, ud, qd, tr.t0, tr.dt)
+        e1.record(stream)
+        barrier()
+        ms_ff = slowest(e0.elapsed_time(e1)) / args.steps
+        ffd.close()
+        ff_info = {"value": deposits * world / (ms_ff / 1e3), "ms_per_step": ms_ff,
+                   "speedup_vs_exact": ms_step / ms_ff,
+                   "mode": "far-field limit: Eq. 3 arrival times, radiation term at the cell direction"}
+
     # ---------------- end to end through the C ABI with host buffers ----------------
     e2e = None
     if not args.no_e2e:
@@ -572,6 +595,7 @@ def main():
                      "traffic": traffic},
         "clocks": clocks,
         "fp64_gpu": fp64_info,
+        "farfield": ff_info,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "parity_vs_oracle": parity,

@@ -60,8 +60,13 @@ typedef enum {
 
 /* precision of a detector */
 enum { RD_FP64 = 0, RD_MIXED = 1 };
-/* terms of Eq. 1 to evaluate (bit set); the default is both */
-enum { RD_NEAR = 1, RD_FAR = 2 };
+/*
+ * terms of Eq. 1 to evaluate (bit set); the default is both.  RD_FARFIELD (with RD_FAR, without
+ * RD_NEAR) selects the far-field limit: arrival times by Eq. 3, t + R_c - x.n_c, and the radiation
+ * term of Eq. 1 with the direction n_c and distance R_c of the cell seen from the origin
+ * (R_c n_c = pix_pos) in place of the particle-to-cell n and R.
+ */
+enum { RD_NEAR = 1, RD_FAR = 2, RD_FARFIELD = 4 };
 /* where a caller buffer lives */
 enum { RD_MEM_DEVICE = 0, RD_MEM_HOST = 1 };
 /* element type of caller field / gradient-seed buffers */
@@ -87,7 +92,7 @@ typedef struct {
     double dt_det;             /* > 0                                                           */
     int32_t n_bins;            /* >= 1; <= 4194304 (2^22) for RD_MIXED                          */
     int32_t precision;         /* RD_MIXED or RD_FP64                                           */
-    int32_t flags;             /* RD_NEAR | RD_FAR (0 is read as both)                           */
+    int32_t flags;             /* RD_NEAR | RD_FAR (0 is read as both), or RD_FAR | RD_FARFIELD  */
 } rd_detector_desc;
 
 /*

@@ -177,6 +177,26 @@ __device__ __forceinline__ void fp64_field(const RecD& r, const D4& cl, double q
     F[5] = nx * Ey - ny * Ex;
 }
 
+// Far-field limit of the radiation term: E = q n_c x ((n_c - beta) x betadot) / (kappa^3 R_c),
+// kappa = 1 - beta.n_c, B = n_c x E.
+__device__ __forceinline__ void fp64_field_ff(const RecD& r, double nx, double ny, double nz, double Rc, double q,
+                                              int flags, double* F)
+{
+    const double mx = nx - r.bb.x, my = ny - r.bb.y, mz = nz - r.bb.z;
+    const double kap = 1.0 - (r.bb.x * nx + r.bb.y * ny + r.bb.z * nz);
+    const double s = (flags & RD_FAR) ? q / (kap * kap * kap * Rc) : 0.0;
+    const double wx = my * r.bd.z - mz * r.bd.y;
+    const double wy = mz * r.bd.x - mx * r.bd.z;
+    const double wz = mx * r.bd.y - my * r.bd.x;
+    const double Ex = s * (ny * wz - nz * wy), Ey = s * (nz * wx - nx * wz), Ez = s * (nx * wy - ny * wx);
+    F[0] = Ex;
+    F[1] = Ey;
+    F[2] = Ez;
+    F[3] = ny * Ez - nz * Ey;
+    F[4] = nz * Ex - nx * Ez;
+    F[5] = nx * Ey - ny * Ex;
+}
+
 // Deposit [st.a, c] with the bin-overlap arithmetic of the integrator detector.
 __device__ __forceinline__ void fp64_deposit(D64State& st, const double* F, double c, double* row,
                                              int n_bins, int k, int k_begin, int k_end)
@@ -245,6 +265,8 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
 
     D64State st;
     D4 cl = {0.0, 0.0, 0.0, 0.0};
+    double ncx = 0.0, ncy = 0.0, ncz = 1.0, Rc = 1.0;       // far-field limit: cell direction, distance
+    const bool ff = P.ff != 0;
     bool live = false;
     double* row = nullptr;
     const double* xp = P.x + (size_t)p * P.n_samples * 3;
@@ -253,8 +275,15 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
         double Ra, Re;
         const double* xa = xp + 3 * (size_t)(k_begin - 1);
         const double* xe = xp + 3 * (size_t)k_end;
-        const double ua = arrival_bins(xa[0], xa[1], xa[2], cl, P.t0, k_begin - 1, P.dt, P.inv_dt_det, Ra);
-        const double ue = arrival_bins(xe[0], xe[1], xe[2], cl, P.t0, k_end, P.dt, P.inv_dt_det, Re);
+        double ua, ue;
+        if (ff) {
+            farfield_cell(cl, ncx, ncy, ncz, Rc);
+            ua = arrival_bins_ff(xa[0], xa[1], xa[2], ncx, ncy, ncz, Rc, cl.w, P.t0, k_begin - 1, P.dt, P.inv_dt_det);
+            ue = arrival_bins_ff(xe[0], xe[1], xe[2], ncx, ncy, ncz, Rc, cl.w, P.t0, k_end, P.dt, P.inv_dt_det);
+        } else {
+            ua = arrival_bins(xa[0], xa[1], xa[2], cl, P.t0, k_begin - 1, P.dt, P.inv_dt_det, Ra);
+            ue = arrival_bins(xe[0], xe[1], xe[2], cl, P.t0, k_end, P.dt, P.inv_dt_det, Re);
+        }
         live = (ue > 0.0) && (ua < (double)P.n_bins);
         st.a = ua;
         st.b = clamp_bin(floor(ua));
@@ -286,9 +315,15 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
             for (int i = 0; i < cnt; ++i) {
                 const RecD r = tile[buf][i];
                 const int k = k0 + i;
-                fp64_field(r, cl, q, flags, F);
-                double R;
-                const double cbin = arrival_bins(r.xa.x, r.xa.y, r.xa.z, cl, P.t0, k, P.dt, P.inv_dt_det, R);
+                double cbin;
+                if (ff) {
+                    fp64_field_ff(r, ncx, ncy, ncz, Rc, q, flags, F);
+                    cbin = arrival_bins_ff(r.xa.x, r.xa.y, r.xa.z, ncx, ncy, ncz, Rc, cl.w, P.t0, k, P.dt, P.inv_dt_det);
+                } else {
+                    fp64_field(r, cl, q, flags, F);
+                    double R;
+                    cbin = arrival_bins(r.xa.x, r.xa.y, r.xa.z, cl, P.t0, k, P.dt, P.inv_dt_det, R);
+                }
                 fp64_deposit(st, F, cbin, row, P.n_bins, k, k_begin, k_end);
             }
             if (t == n_tiles - 1) {

@@ -88,6 +88,7 @@ struct DepositParams {
     double inv_dt_det;
     float dt_f;
     float du_scale;             // dt / dt_det
+    int ff;                     // far-field limit (RD_FARFIELD): Eq. 3, radiation term at (n_c, R_c)
 };
 
 constexpr int kDepositThreads = 256;   // FP64 kernel: one cell per thread
@@ -296,6 +297,28 @@ __device__ __forceinline__ double arrival_bins(double xk0, double xk1, double xk
     R = __dsqrt_rn(r2);
     const double tk = __dadd_rn(t0, __dmul_rn((double)k, dt));
     return __dmul_rn(__dsub_rn(__dadd_rn(tk, R), cell.w), inv_dt_det);
+}
+
+// Far-field limit: the cell seen from the origin along n_c = P/R_c at R_c = |P|, computed as
+// R_c = sqrt((x*x + y*y) + z*z), n_c = P / R_c (separately rounded).
+__device__ __forceinline__ void farfield_cell(const D4& cell, double& nx, double& ny, double& nz, double& Rc)
+{
+    Rc = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(cell.x, cell.x), __dmul_rn(cell.y, cell.y)),
+                              __dmul_rn(cell.z, cell.z)));
+    nx = __ddiv_rn(cell.x, Rc);
+    ny = __ddiv_rn(cell.y, Rc);
+    nz = __ddiv_rn(cell.z, Rc);
+}
+
+// Eq. 3 in bin units, FP64, every operation separately rounded:
+//   u = (((t0 + k*dt) + R_c) - ((x*nx + y*ny) + z*nz) - T0) * inv_dt_det
+__device__ __forceinline__ double arrival_bins_ff(double xk0, double xk1, double xk2, double nx, double ny,
+                                                  double nz, double Rc, double T0, double t0, int k, double dt,
+                                                  double inv_dt_det)
+{
+    const double tk = __dadd_rn(t0, __dmul_rn((double)k, dt));
+    const double xn = __dadd_rn(__dadd_rn(__dmul_rn(xk0, nx), __dmul_rn(xk1, ny)), __dmul_rn(xk2, nz));
+    return __dmul_rn(__dsub_rn(__dsub_rn(__dadd_rn(tk, Rc), xn), T0), inv_dt_det);
 }
 
 __device__ __forceinline__ int clamp_bin(double fb)

@@ -37,7 +37,8 @@ __device__ __forceinline__ int walk_bin(double fb) { return (int)fmin(fmax(fb, -
 struct Cells {
     float px[NC], py[NC], pz[NC];   // cell positions
     float f[NC];                    // time spent in the current bin, units of dt (0 <= f < W)
-    float rpd[NC];                  // R_{k-1} + dt
+    float rpd[NC];                  // R_{k-1} + dt (far-field limit: 1/R_c)
+    float ec[NC];                   // far-field limit: |n_c|^2 - 1 of the rounded direction
     float acc[6][NC];               // E xyz, B xyz of the current bin so far (weights in bins)
     int bo[NC];                     // row * n_bins + bin being filled (bin may lie outside the window)
     int rb[NC];                     // row * n_bins (row = the cell's index inside the CTA's block)
@@ -119,6 +120,33 @@ __device__ __forceinline__ void field_at(const RecS& r, float px, float py, floa
     o.rinv = rinv;
 }
 
+// Far-field limit (RD_FARFIELD) at one cell, seen from the origin along n_c at R_c (n_c and
+// 1/R_c fixed per cell):
+//   t'_k - t'_{k-1} = dt (1 - n_c.vbar) = dt [g + |n_c - vbar|^2 - (|n_c|^2 - 1)] / 2   (Eq. 3)
+//   E = S E',  S = 1/(kappa^2 R_c),  E' = Q [(n_c - beta)(-n_c.betadot/kappa) + betadot],  B = S n_c x E'
+// with kappa = 1 - beta.n_c = (gamma^-2 + |n_c - beta|^2 - (|n_c|^2 - 1))/2: the rounded direction is
+// not exactly of unit length, and its error ec = |n_c|^2 - 1 (~1e-7, fixed per cell) is taken out
+// of |n_c - beta|^2 so that kappa carries no per-cell bias.
+__device__ __forceinline__ void field_at_ff(const RecS& r, float nx, float ny, float nz, float invR, float ec,
+                                            Field& o)
+{
+    const float bx = nx + r.nbx, by = ny + r.nby, bz = nz + r.nbz;      // n_c - beta
+    const float nb2 = fmaf(bx, bx, fmaf(by, by, fmaf(bz, bz, -ec)));
+    o.num = fmaf(bx, r.d2x, fmaf(by, r.d2y, fmaf(bz, r.d2z, nb2 + r.gd)));
+    o.rden = 0.5f;
+    const float kn = fmaf(nb2, -0.5f, r.nhig2);                         // -kappa
+    const float ikn = fast_rcp(kn);
+    o.S = (ikn * ikn) * invR;
+    const float c1n = fmaf(nx, r.bdx, fmaf(ny, r.bdy, nz * r.bdz)) * ikn; // -Q n_c.betadot / kappa
+    o.E[0] = fmaf(bx, c1n, r.bdx);
+    o.E[1] = fmaf(by, c1n, r.bdy);
+    o.E[2] = fmaf(bz, c1n, r.bdz);
+    o.B[0] = fmaf(ny, o.E[2], -(nz * o.E[1]));
+    o.B[1] = fmaf(nz, o.E[0], -(nx * o.E[2]));
+    o.B[2] = fmaf(nx, o.E[1], -(ny * o.E[0]));
+    o.rinv = 1.f;
+}
+
 // Interval of cell j that passes two or more bin edges (rare): flush the bin being filled and the
 // whole bins inside the interval, leaving the state one edge short so that the common path below
 // finishes the step (it flushes the last whole bin and starts the next).
@@ -163,7 +191,7 @@ enum { kFast = 0, kExact = 1 };
 // flushes the bin and starts the next one with the rest of the interval.  LAST: the interval ends
 // on the exact FP64 anchors.  TRACK: bins may lie outside the window (checked, clipped intervals
 // counted).  ok: kExact only, false from the interval that stopped the fast walk onwards.
-template <int MODE, bool LAST, bool TRACK>
+template <int MODE, bool LAST, bool TRACK, bool FF>
 __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, const int* bo_end,
                                      const float* f_end, int k, int k_begin, int k_end, bool* ok)
 {
@@ -171,7 +199,10 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
     float fn[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        field_at(r, c.px[j], c.py[j], c.pz[j], c.rpd[j], C, o[j]);
+        if (FF)
+            field_at_ff(r, c.px[j], c.py[j], c.pz[j], c.rpd[j], c.ec[j], o[j]);
+        else
+            field_at(r, c.px[j], c.py[j], c.pz[j], c.rpd[j], C, o[j]);
         float t;
         if (LAST) {
             t = fmaf((float)(bo_end[j] - c.bo[j]), C.W, f_end[j]);
@@ -279,7 +310,7 @@ __device__ __forceinline__ void restore_state(Cells& c, float (*sv)[kMixedThread
     }
 }
 
-template <bool TRACK>
+template <bool TRACK, bool FF>
 __device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, bool last_tile, const Consts& C,
                                           const int* bo_end, const float* f_end, int k0, int k_begin, int k_end,
                                           float (*sv)[kMixedThreads])
@@ -290,8 +321,8 @@ __device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, b
     bool ok[NC];
 #pragma unroll kUnroll
     for (int i = 0; i < n_regular; ++i)
-        step<kFast, false, TRACK>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok);
-    if (last_tile) step<kFast, true, TRACK>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok);
+        step<kFast, false, TRACK, FF>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok);
+    if (last_tile) step<kFast, true, TRACK, FF>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok);
     bool stopped = false;
 #pragma unroll
     for (int j = 0; j < NC; ++j) stopped = stopped || c.f[j] == -INFINITY;
@@ -302,8 +333,9 @@ __device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, b
         for (int j = 0; j < NC; ++j) ok[j] = true;
 #pragma unroll 1
         for (int i = 0; i < n_regular; ++i)
-            step<kExact, false, TRACK>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok);
-        if (last_tile) step<kExact, true, TRACK>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok);
+            step<kExact, false, TRACK, FF>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok);
+        if (last_tile)
+            step<kExact, true, TRACK, FF>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok);
     }
 }
 
@@ -313,6 +345,7 @@ __device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, b
 // CTA.  tile / bar: the CTA's shared staging buffers; g_base counts the tiles the CTA staged
 // before this item (it selects buffer and mbarrier phase, so the buffers carry over between items).
 // Returns false if a bounded wait ran out (the error is recorded; the CTA must stop).
+template <bool FF>
 __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int cb, int ch,
                                              RecS (*tile)[kTileSteps], uint64_t* bar, float (*sv)[kMixedThreads],
                                              unsigned& g_base)
@@ -364,6 +397,7 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
         c.rpd[j] = 1e6f;
         c.px[j] = 1e6f;
         c.py[j] = c.pz[j] = 0.f;
+        c.ec[j] = 0.f;
         bo_end[j] = c.bo[j];
         f_end[j] = 0.f;
 #pragma unroll
@@ -372,9 +406,15 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
             const D4 cl = P.cells[cell];
             const double* xa = xp + 3 * (size_t)(k_begin - 1);
             const double* xe = xp + 3 * (size_t)k_end;
-            double Ra, Re;
-            const double ua = arrival_bins(xa[0], xa[1], xa[2], cl, P.t0, k_begin - 1, P.dt, P.inv_dt_det, Ra);
-            const double ue = arrival_bins(xe[0], xe[1], xe[2], cl, P.t0, k_end, P.dt, P.inv_dt_det, Re);
+            double Ra = 0.0, Re, ua, ue, ncx = 0.0, ncy = 0.0, ncz = 0.0, Rc = 1.0;
+            if (FF) {
+                farfield_cell(cl, ncx, ncy, ncz, Rc);
+                ua = arrival_bins_ff(xa[0], xa[1], xa[2], ncx, ncy, ncz, Rc, cl.w, P.t0, k_begin - 1, P.dt, P.inv_dt_det);
+                ue = arrival_bins_ff(xe[0], xe[1], xe[2], ncx, ncy, ncz, Rc, cl.w, P.t0, k_end, P.dt, P.inv_dt_det);
+            } else {
+                ua = arrival_bins(xa[0], xa[1], xa[2], cl, P.t0, k_begin - 1, P.dt, P.inv_dt_det, Ra);
+                ue = arrival_bins(xe[0], xe[1], xe[2], cl, P.t0, k_end, P.dt, P.inv_dt_det, Re);
+            }
             c.live[j] = (ue > 0.0) && (ua < (double)P.n_bins);
             if (!c.live[j]) {
                 clip += (unsigned long long)n_int;
@@ -384,10 +424,19 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
                 c.f[j] = (float)(ua - fla) * P.W;
                 bo_end[j] = c.rb[j] + walk_bin(fle);
                 f_end[j] = (float)(ue - fle) * P.W;
-                c.rpd[j] = (float)Ra + P.dt_f;
-                c.px[j] = (float)cl.x;
-                c.py[j] = (float)cl.y;
-                c.pz[j] = (float)cl.z;
+                if (FF) {
+                    c.px[j] = (float)ncx;
+                    c.py[j] = (float)ncy;
+                    c.pz[j] = (float)ncz;
+                    c.rpd[j] = (float)(1.0 / Rc);
+                    const double ex = c.px[j], ey = c.py[j], ez = c.pz[j];
+                    c.ec[j] = (float)(((ex * ex + ey * ey) + ez * ez) - 1.0);
+                } else {
+                    c.rpd[j] = (float)Ra + P.dt_f;
+                    c.px[j] = (float)cl.x;
+                    c.py[j] = (float)cl.y;
+                    c.pz[j] = (float)cl.z;
+                }
                 c.below[j] = (ua < 0.0) ? n_int : 0;
                 // unchecked bins need a margin of one bin to each window edge (the FP32 walk may
                 // drift by far less than a bin before the end anchor corrects it)
@@ -417,9 +466,9 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
         const int cnt = min(kTileSteps, k_end - k0 + 1);
         const bool last_tile = (t == n_tiles - 1);
         if (track)
-            walk_tile<true>(c, tile[buf], cnt, last_tile, C, bo_end, f_end, k0, k_begin, k_end, sv);
+            walk_tile<true, FF>(c, tile[buf], cnt, last_tile, C, bo_end, f_end, k0, k_begin, k_end, sv);
         else
-            walk_tile<false>(c, tile[buf], cnt, last_tile, C, bo_end, f_end, k0, k_begin, k_end, sv);
+            walk_tile<false, FF>(c, tile[buf], cnt, last_tile, C, bo_end, f_end, k0, k_begin, k_end, sv);
         __syncthreads();
         if (tid == 0 && t + 2 < n_tiles) {
             fence_proxy_async();
@@ -457,6 +506,7 @@ __device__ __forceinline__ void init_staging(uint64_t* bar)
     __syncthreads();
 }
 
+template <bool FF>
 __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_mixed(const DepositParams P)
 {
     __shared__ __align__(128) RecS tile[2][kTileSteps];
@@ -469,7 +519,7 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_m
     const int cb = (int)(rest % (unsigned)P.n_cell_blocks);
     const int ch = (int)(rest / (unsigned)P.n_cell_blocks);
     unsigned g = 0;
-    (void)deposit_item(P, p, cb, ch, tile, bar, sv, g);
+    (void)deposit_item<FF>(P, p, cb, ch, tile, bar, sv, g);
 }
 
 // Persistent form: the resident CTAs draw work items of all problems from one counter.
@@ -504,7 +554,9 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS)
         const long long rest = local / P.n_part;
         const int cb = (int)(rest % P.n_cell_blocks);
         const int ch = (int)(rest / P.n_cell_blocks);
-        if (!deposit_item(P, p, cb, ch, tile, bar, sv, g)) break;
+        const bool ok = P.ff ? deposit_item<true>(P, p, cb, ch, tile, bar, sv, g)
+                             : deposit_item<false>(P, p, cb, ch, tile, bar, sv, g);
+        if (!ok) break;
     }
 }
 
@@ -529,7 +581,10 @@ cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s)
     const long long blocks = (long long)p.n_cell_blocks * p.n_part * p.n_chunks;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    k_deposit_mixed<<<(unsigned)blocks, kMixedThreads, 0, s>>>(p);
+    if (p.ff)
+        k_deposit_mixed<true><<<(unsigned)blocks, kMixedThreads, 0, s>>>(p);
+    else
+        k_deposit_mixed<false><<<(unsigned)blocks, kMixedThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

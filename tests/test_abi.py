@@ -71,5 +71,11 @@ def test_argument_errors_without_gpu():
     d.precision, d.n_bins = rd.RD_MIXED, (1 << 22) + 1
     assert lib.rd_create_detector(ctypes.byref(d), None, ctypes.byref(h)) == rd.RD_ERR_ARG
     assert "4194304" in rd.rd_last_error()
+    # the far-field limit keeps only the radiation term
+    d.n_bins, d.flags = 8, rd.RD_NEAR | rd.RD_FARFIELD
+    assert lib.rd_create_detector(ctypes.byref(d), None, ctypes.byref(h)) == rd.RD_ERR_ARG
+    assert "RD_FARFIELD" in rd.rd_last_error()
+    d.flags = 8
+    assert lib.rd_create_detector(ctypes.byref(d), None, ctypes.byref(h)) == rd.RD_ERR_ARG
     assert lib.rd_set_batch_budget(None, 0) == rd.RD_ERR_ARG
     assert lib.rd_set_chunk(None, 0) == rd.RD_ERR_ARG

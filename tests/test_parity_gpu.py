@@ -239,3 +239,45 @@ def test_read_fields_device_and_f32():
     assert np.array_equal(E32, E64.astype(np.float32))
     assert np.array_equal(Ed.cpu().numpy(), E32) and np.array_equal(Bd.cpu().numpy(), B32)
     d.close()
+
+
+# --------------------------------------------------------------------------------------------
+# far-field limit (RD_FARFIELD): Eq. 3 arrival times, radiation term at the cell's (n_c, R_c)
+# --------------------------------------------------------------------------------------------
+def _farfield_cases():
+    rng = np.random.default_rng(8)
+    tr1 = W.random_smooth(5, 333, 0.02, max_u=3.0, seed=8)
+    pos = rng.normal(size=(300, 3)) * 20.0
+    pos += 25.0 * pos / np.linalg.norm(pos, axis=1, keepdims=True)
+    det1 = W.Detector(pos, rng.uniform(-1.0, 1.0, 300), 30.0, 0.013, 700, flags=W.RD_FAR | W.RD_FARFIELD)
+    tr2, det2 = W.config_undulator(n_part=6, n_side=24, n_bins=1024, seed=4)
+    det2.flags = W.RD_FAR | W.RD_FARFIELD
+    tr3, det3 = _multi_edge_case()
+    det3.flags = W.RD_FAR | W.RD_FARFIELD
+    return [(tr1, det1), (tr2, det2), (tr3, det3)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", [0, 1, 2])
+def test_farfield_limit(precision, case):
+    """Random motions with per-cell origins and window cuts; the undulator ensemble on a cap at
+    1e4; intervals spanning several bins in tracked and untracked blocks: every cell against
+    the oracle's far-field limit (clipped counts exact in FP64)."""
+    tr, det = _farfield_cases()[case]
+    check(tr, det, precision)
+
+
+def test_farfield_flag_checks():
+    import torch
+    det = W.Detector(np.array([[10.0, 0.0, 0.0]]), None, 0.0, 0.1, 64, flags=W.RD_NEAR | W.RD_FARFIELD)
+    with pytest.raises(rd.RDError) as ei:
+        rd.RadiationDetector.from_workload(det, "mixed")
+    assert ei.value.status == rd.RD_ERR_ARG
+    det.flags = W.RD_FAR | W.RD_FARFIELD
+    d = rd.RadiationDetector.from_workload(det, "mixed")
+    tr = W.random_smooth(1, 20, 0.05, seed=1)
+    x, u = torch.from_numpy(tr.x).cuda(), torch.from_numpy(tr.u).cuda()
+    with pytest.raises(rd.RDError) as ei:
+        d.adjoint(x, u, None, tr.t0, tr.dt, torch.zeros((1, 64, 3), dtype=torch.float32, device="cuda"))
+    assert ei.value.status == rd.RD_ERR_STATE
+    d.close()
