@@ -162,6 +162,26 @@ RD_API rd_status rd_read_fields(rd_detector* det, void* E, void* B, int32_t dtyp
                          rd_stream stream);
 
 /*
+ * Streamed deposit (Section 3: run-time use inside a particle code, which hands over each new
+ * stretch of the trajectories as it computes them).  traj holds the NEW samples only, at
+ * t0 + k*dt, k < n_samples; the detector keeps every particle's last sample from the previous
+ * streamed call and deposits the interval from it to the first new sample, so that consecutive
+ * calls on consecutive, non-overlapping stretches deposit exactly what one call on the whole
+ * trajectory would (up to FP32 summation order and, in RD_MIXED, the placement of the FP64
+ * arrival-time anchors).  The first call after creation or rd_stream_reset has nothing in front
+ * of its first sample (as in rd_deposit_trajectories).  A continuing call must have the same
+ * n_part and dt, and t0 equal to the stored last time + dt; otherwise RD_ERR_STATE.  Memory: the
+ * new samples are copied (host or device) behind the stored ones into detector-held scratch,
+ * 48 bytes per particle and sample.  Each call pays a record precompute, a launch and FP64 arrival
+ * anchors at both ends of its stretch: hand over several steps per call where the caller can.
+ * Asynchronous on `stream`; calls of one stream must come in order on one CUDA stream.
+ */
+RD_API rd_status rd_deposit_stream(rd_detector* det, const rd_traj* traj, rd_stream stream);
+
+/* Forget the stored last samples: the next rd_deposit_stream call starts a new stream. */
+RD_API rd_status rd_stream_reset(rd_detector* det);
+
+/*
  * Power spectrum of every cell's time series (Section 4: the detector data Fourier transformed in
  * time, the spectra compared with Eq. 8 and Eq. 9).  With N = n_bins, F = E (which = RD_SPEC_E) or
  * B (RD_SPEC_B) and F_c[j][b] the bin values:

@@ -26,7 +26,7 @@ __all__ = [
     "load_library", "library_path", "rd_create_detector", "rd_destroy", "rd_zero_fields",
     "rd_deposit_trajectories", "rd_read_fields", "rd_synchronize", "rd_get_stats",
     "rd_set_timing", "rd_adjoint_trajectories", "rd_deposit_batch", "rd_set_chunk", "rd_autotune",
-    "rd_set_batch_budget", "rd_power_spectrum",
+    "rd_set_batch_budget", "rd_power_spectrum", "rd_deposit_stream", "rd_stream_reset",
     "rd_deposit_noalloc", "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
 ]
 
@@ -101,6 +101,8 @@ def load_library(build_if_missing: bool = True):
             "rd_set_chunk": ([P, I], I),
             "rd_set_batch_budget": ([P, ctypes.c_longlong], I),
             "rd_power_spectrum": ([P, I, P, P], I),
+            "rd_deposit_stream": ([P, ctypes.POINTER(rd_traj), P], I),
+            "rd_stream_reset": ([P], I),
             "rd_autotune": ([P, ctypes.POINTER(rd_traj), P, ctypes.POINTER(I)], I),
             "rd_deposit_noalloc": ([P, P, I, ctypes.c_double, ctypes.c_double, I, I, ctypes.POINTER(rd_traj), P,
                                     ctypes.POINTER(ctypes.c_uint32), P], I),
@@ -194,6 +196,14 @@ def rd_set_chunk(det: int, chunk: int) -> None:
 
 def rd_set_batch_budget(det: int, nbytes: int) -> None:
     _check(load_library().rd_set_batch_budget(det, int(nbytes)), "rd_set_batch_budget")
+
+
+def rd_deposit_stream(det: int, traj: rd_traj, stream=None) -> None:
+    _check(load_library().rd_deposit_stream(det, ctypes.byref(traj), _stream_ptr(stream)), "rd_deposit_stream")
+
+
+def rd_stream_reset(det: int) -> None:
+    _check(load_library().rd_stream_reset(det), "rd_stream_reset")
 
 
 def rd_power_spectrum(det: int, which: int, out_ptr: int, stream=None) -> None:
@@ -334,6 +344,15 @@ class RadiationDetector:
         B = torch.empty_like(E)
         rd_read_fields(self._h, E.data_ptr(), B.data_ptr(), code, RD_MEM_DEVICE, stream)
         return E, B
+
+    def deposit_stream(self, x, u, q=None, t0: float = 0.0, dt: float = 1.0, stream=None):
+        """Deposit the next stretch of a streamed trajectory (new samples only, at t0 + k dt)."""
+        t, keep = self.traj_struct(x, u, q, t0, dt)
+        rd_deposit_stream(self._h, t, stream)
+        self._keep = keep      # inputs stay referenced until the next call
+
+    def stream_reset(self):
+        rd_stream_reset(self._h)
 
     def power_spectrum(self, field: str = "E", stream=None):
         """dt_det^2 sum_c |FFT_b F_c[j][b]|^2 for k = 0..n_bins/2 (F = E or B): a float32 CUDA

@@ -53,6 +53,14 @@ struct rd_detector {
     size_t spec_tw_bytes = 0;
     int spec_n = 0;
     std::vector<float2> spec_tw_host;
+    // streamed deposits: the last sample (x, u) of every particle from the previous call
+    void* strm_last = nullptr;       // [2][n_part][3] doubles
+    size_t strm_last_bytes = 0;
+    void* strm_stage = nullptr;      // this call's samples with the stored one in front, and q
+    size_t strm_stage_bytes = 0;
+    int strm_n_part = -1;            // -1: no stream in progress
+    double strm_t_last = 0.0;
+    double strm_dt = 0.0;
     std::vector<unsigned long long> graph_key;
     cudaGraphExec_t graph_exec = nullptr;
     long long n_deposits = 0;
@@ -320,6 +328,8 @@ rd_status rd_destroy(rd_detector* d)
     cudaFree(d->gbeta);
     cudaFree(d->batch_rec);
     cudaFree(d->batch_tab);
+    cudaFree(d->strm_last);
+    cudaFree(d->strm_stage);
     cudaFree(d->spec);
     cudaFree(d->spec_tw);
     if (d->graph_exec) cudaGraphExecDestroy(d->graph_exec);
@@ -790,6 +800,75 @@ rd_status rd_power_spectrum(rd_detector* d, int32_t which, float* out, rd_stream
     RD_CUDA(launch_power_spectrum(d->fields, d->precision, d->n_pix, N, which == RD_SPEC_B ? 3 : 0, z, y,
                                   static_cast<const float2*>(d->spec_tw), (float)(d->dt_det * d->dt_det), out, s),
             "power spectrum");
+    return RD_OK;
+}
+
+rd_status rd_deposit_stream(rd_detector* d, const rd_traj* t, rd_stream stream)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    rd_status st = check_traj(t);
+    if (st != RD_OK) return st;
+    if (t->n_part < 1) return fail(RD_ERR_ARG, "a streamed call needs n_part >= 1");
+    const bool cont = d->strm_n_part >= 0;
+    if (cont) {
+        if (t->n_part != d->strm_n_part)
+            return fail(RD_ERR_STATE, "streamed call has %d particles, the stream %d (rd_stream_reset starts a new one)",
+                        t->n_part, d->strm_n_part);
+        if (fabs(t->dt - d->strm_dt) > 1e-12 * d->strm_dt)
+            return fail(RD_ERR_STATE, "streamed call has dt = %.17g, the stream %.17g", t->dt, d->strm_dt);
+        const double expect = d->strm_t_last + d->strm_dt;
+        if (fabs(t->t0 - expect) > 1e-6 * t->dt + 1e-12 * fabs(expect))
+            return fail(RD_ERR_STATE, "streamed call starts at t0 = %.17g, the stream continues at %.17g", t->t0,
+                        expect);
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int np = t->n_part, m = t->n_samples, ns = m + (cont ? 1 : 0);
+    const size_t row = sizeof(double) * 3 * (size_t)ns, mrow = sizeof(double) * 3 * (size_t)m, one = 3 * sizeof(double);
+    st = ensure(&d->strm_stage, &d->strm_stage_bytes, 2 * row * np + sizeof(double) * np, s, "stream staging");
+    if (st != RD_OK) return st;
+    if (!cont) {
+        st = ensure(&d->strm_last, &d->strm_last_bytes, 2 * one * np, s, "stream state");
+        if (st != RD_OK) return st;
+    }
+    double* xs = static_cast<double*>(d->strm_stage);
+    double* us = xs + (size_t)np * ns * 3;
+    double* qs = us + (size_t)np * ns * 3;
+    double* lx = static_cast<double*>(d->strm_last);
+    double* lu = lx + (size_t)np * 3;
+    const cudaMemcpyKind kind = t->mem == RD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const size_t off = cont ? 3 : 0;
+    RD_CUDA(cudaMemcpy2DAsync(xs + off, row, t->x, mrow, mrow, np, kind, s), "stream x");
+    RD_CUDA(cudaMemcpy2DAsync(us + off, row, t->u, mrow, mrow, np, kind, s), "stream u");
+    if (cont) {
+        RD_CUDA(cudaMemcpy2DAsync(xs, row, lx, one, one, np, cudaMemcpyDeviceToDevice, s), "stream x");
+        RD_CUDA(cudaMemcpy2DAsync(us, row, lu, one, one, np, cudaMemcpyDeviceToDevice, s), "stream u");
+    }
+    if (t->q) RD_CUDA(cudaMemcpyAsync(qs, t->q, sizeof(double) * np, kind, s), "stream q");
+    rd_traj staged = *t;
+    staged.n_samples = ns;
+    staged.x = xs;
+    staged.u = us;
+    staged.q = t->q ? qs : nullptr;
+    staged.mem = RD_MEM_DEVICE;
+    staged.t0 = cont ? t->t0 - t->dt : t->t0;
+    st = rd_deposit_trajectories(d, &staged, stream);
+    if (st != RD_OK) return st;
+    RD_CUDA(cudaMemcpy2DAsync(lx, one, xs + 3 * (size_t)(ns - 1), row, one, np, cudaMemcpyDeviceToDevice, s),
+            "stream state");
+    RD_CUDA(cudaMemcpy2DAsync(lu, one, us + 3 * (size_t)(ns - 1), row, one, np, cudaMemcpyDeviceToDevice, s),
+            "stream state");
+    d->strm_n_part = np;
+    d->strm_t_last = t->t0 + (double)(m - 1) * t->dt;
+    d->strm_dt = t->dt;
+    return RD_OK;
+}
+
+rd_status rd_stream_reset(rd_detector* d)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    d->strm_n_part = -1;
     return RD_OK;
 }
 

@@ -78,4 +78,6 @@ def test_argument_errors_without_gpu():
     d.flags = 8
     assert lib.rd_create_detector(ctypes.byref(d), None, ctypes.byref(h)) == rd.RD_ERR_ARG
     assert lib.rd_set_batch_budget(None, 0) == rd.RD_ERR_ARG
+    assert lib.rd_deposit_stream(None, None, None) == rd.RD_ERR_ARG
+    assert lib.rd_stream_reset(None) == rd.RD_ERR_ARG
     assert lib.rd_set_chunk(None, 0) == rd.RD_ERR_ARG

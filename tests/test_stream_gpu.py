@@ -1,0 +1,104 @@
+"""Streamed deposits (rd_deposit_stream): a trajectory handed over in consecutive stretches of
+new samples deposits what one call on the whole trajectory deposits.
+
+FP64 detectors evaluate every arrival time and field from its own sample, so stretches change
+only the order of the FP64 reductions (bar 1e-12).  RD_MIXED detectors restart their FP32
+arrival-time walk from an exact FP64 anchor at the ends of every stretch, which moves values by
+rounding only (bar 2e-6, the suite's same-arithmetic bar), and stay within the mixed path's 1e-4
+of the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2302_14812_gb300 as rd
+from paper_2302_14812_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rd.load_library()
+    oracle.build()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _case():
+    rng = np.random.default_rng(6)
+    tr = W.random_smooth(5, 400, 0.02, max_u=2.5, seed=6)
+    pos = rng.normal(size=(300, 3)) * 20.0
+    pos += 25.0 * pos / np.linalg.norm(pos, axis=1, keepdims=True)
+    det = W.Detector(pos, rng.uniform(-1.0, 1.0, 300), 30.0, 0.013, 800)
+    return tr, det
+
+
+def _stretches(n, sizes):
+    out, k = [], 0
+    for m in sizes:
+        if k >= n:
+            break
+        out.append((k, min(n, k + m)))
+        k += m
+    if k < n:
+        out.append((k, n))
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-6)])
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_stream_equals_single_call(precision, tol, where):
+    import torch
+    tr, det = _case()
+    ref = rd.RadiationDetector.from_workload(det, precision)
+    ref.deposit(torch.from_numpy(tr.x).cuda(), torch.from_numpy(tr.u).cuda(), torch.from_numpy(tr.q).cuda(),
+                tr.t0, tr.dt)
+    Er, Br = ref.read()
+    ref.close()
+    d = rd.RadiationDetector.from_workload(det, precision)
+    for a, b in _stretches(tr.n_samples, [1, 1, 7, 64, 1, 150, 3]):
+        x, u = np.ascontiguousarray(tr.x[:, a:b]), np.ascontiguousarray(tr.u[:, a:b])
+        q = tr.q
+        if where == "device":
+            x, u, q = torch.from_numpy(x).cuda(), torch.from_numpy(u).cuda(), torch.from_numpy(q).cuda()
+        d.deposit_stream(x, u, q, tr.t0 + a * tr.dt, tr.dt)
+    E, B = d.read()
+    assert rel_l2(E, Er) <= tol and rel_l2(B, Br) <= tol
+    if precision == "mixed":
+        sel = np.array([0, 77, 150, 299], dtype=np.int32)
+        Eo, Bo, _ = oracle.deposit(tr, det, sel)
+        assert rel_l2(E[sel], Eo) <= 1e-4 and rel_l2(B[sel], Bo) <= 1e-4
+    d.close()
+
+
+def test_stream_continuity_checks_and_reset():
+    import torch
+    tr, det = _case()
+    d = rd.RadiationDetector.from_workload(det, "mixed")
+    x, u = torch.from_numpy(tr.x).cuda(), torch.from_numpy(tr.u).cuda()
+    d.deposit_stream(x[:, :10], u[:, :10], None, tr.t0, tr.dt)
+    for bad in (dict(t0=tr.t0 + 12 * tr.dt), dict(dt=1.5 * tr.dt), dict(n_part=3)):
+        n = bad.get("n_part", tr.n_part)
+        with pytest.raises(rd.RDError) as ei:
+            d.deposit_stream(x[:n, 10:20].contiguous(), u[:n, 10:20].contiguous(), None,
+                             bad.get("t0", tr.t0 + 10 * tr.dt), bad.get("dt", tr.dt))
+        assert ei.value.status == rd.RD_ERR_STATE
+    d.deposit_stream(x[:, 10:20].contiguous(), u[:, 10:20].contiguous(), None, tr.t0 + 10 * tr.dt, tr.dt)
+    E1, _ = d.read()
+    # after a reset the next call starts a new stream: its first sample emits nothing
+    d.stream_reset()
+    d.zero()
+    d.deposit_stream(x[:3, 40:60].contiguous(), u[:3, 40:60].contiguous(), None, tr.t0 + 40 * tr.dt, tr.dt)
+    E2, _ = d.read()
+    one = rd.RadiationDetector.from_workload(det, "mixed")
+    one.deposit(x[:3, 40:60].contiguous(), u[:3, 40:60].contiguous(), None, tr.t0 + 40 * tr.dt, tr.dt)
+    E3, _ = one.read()
+    assert rel_l2(E2, E3) <= 2e-6 and np.abs(E1).max() > 0
+    one.close()
+    d.close()
