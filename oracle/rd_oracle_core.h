@@ -145,10 +145,39 @@ static int FN(deposit_interval)(SCALAR a, SCALAR c, const SCALAR F[6], int n_bin
 }
 
 /*
+ * Linear-in-time variant (flags bit 8; an interpolation of higher order than the held field, of
+ * the kind the paper's outlook names): over the arrival interval [a, c] the field varies linearly
+ * in arrival time from F0 (sample k-1) at a to F1 (sample k) at c, and bin b receives the integral
+ * of that line over [a, c] ∩ [b, b+1):
+ *     F0 (e - s) + (F1 - F0) ((e - a)^2 - (s - a)^2) / (2 (c - a)),   [s, e] the overlap.
+ */
+static int FN(deposit_interval_lin)(SCALAR a, SCALAR c, const SCALAR F0[6], const SCALAR F1[6], int n_bins,
+                                    SCALAR* row)
+{
+    double ra = RE(a), rc = RE(c);
+    int clipped = (ra < 0.0) || (rc > (double)n_bins);
+    if (rc <= 0.0 || ra >= (double)n_bins) return 1;
+    long long first = floor(ra) < 0.0 ? 0 : (long long)floor(ra);
+    long long last = floor(rc) > (double)(n_bins - 1) ? (long long)(n_bins - 1) : (long long)floor(rc);
+    for (long long b = first; b <= last; ++b) {
+        SCALAR u0 = (ra > (double)b) ? a : (SCALAR)(double)b;
+        SCALAR u1 = (rc < (double)(b + 1)) ? c : (SCALAR)(double)(b + 1);
+        SCALAR len = u1 - u0;
+        if (RE(len) > 0.0) {
+            SCALAR ramp = ((u1 - a) * (u1 - a) - (u0 - a) * (u0 - a)) / (2.0 * (c - a));
+            for (int i = 0; i < 6; ++i) row[6 * b + i] += F0[i] * len + (F1[i] - F0[i]) * ramp;
+        }
+    }
+    return clipped;
+}
+
+/*
  * One (cell, particle) pair: Algorithm 1 inner body for every interval k = 1..S.
  *   beta_k from u_k; betadot_k = (beta_k - beta_{k-1}) / dt (backward difference);
  *   the field of sample k is held over [t_det,k-1, t_det,k] (the algorithm passes the current
  *   step's field to the interpolator); sample 0 only provides the previous quantities.
+ * flags bit 8: from interval 2 on, the field varies linearly from F_{k-1} to F_k over the
+ * interval (deposit_interval_lin); interval 1 holds F_1 (sample 0 has no field: no betadot).
  * x, u point at this particle's samples [n_samples][3]; row is [n_bins][6] (E xyz, B xyz).
  * Returns the number of intervals that had a part outside the window.
  */
@@ -156,7 +185,7 @@ static long long FN(pixel_particle)(const SCALAR* x, const SCALAR* u, int n_samp
                                     double t0, double dt, const double P[3], double T0,
                                     double inv_dt_det, int n_bins, int flags, SCALAR* row)
 {
-    SCALAR beta_prev[3], beta[3], bdot[3], E[3], B[3], F[6];
+    SCALAR beta_prev[3], beta[3], bdot[3], E[3], B[3], F[6], Fprev[6];
     long long clipped = 0;
     FN(beta_of)(u, beta_prev);
     SCALAR a = FN(bin_coord)(t0, 0, dt, x, P, T0, inv_dt_det, flags);
@@ -170,7 +199,11 @@ static long long FN(pixel_particle)(const SCALAR* x, const SCALAR* u, int n_samp
             FN(lw_field)(xk, beta, bdot, P, q, flags, E, B);
         for (int i = 0; i < 3; ++i) { F[i] = E[i]; F[3 + i] = B[i]; }
         SCALAR c = FN(bin_coord)(t0, k, dt, xk, P, T0, inv_dt_det, flags);
-        clipped += FN(deposit_interval)(a, c, F, n_bins, row);
+        if ((flags & 8) && k > 1)
+            clipped += FN(deposit_interval_lin)(a, c, Fprev, F, n_bins, row);
+        else
+            clipped += FN(deposit_interval)(a, c, F, n_bins, row);
+        for (int i = 0; i < 6; ++i) Fprev[i] = F[i];
         a = c;
         for (int i = 0; i < 3; ++i) beta_prev[i] = beta[i];
     }

@@ -29,6 +29,7 @@ import numpy as np
 RD_NEAR = 1
 RD_FAR = 2
 RD_FARFIELD = 4
+RD_LINEAR = 8
 
 
 @dataclasses.dataclass

@@ -39,6 +39,11 @@ MUTATIONS = {
     "farfield_time_sign": ("SCALAR t_ff = (tk + Rc) - xn;", "SCALAR t_ff = (tk + Rc) + xn;"),
     "farfield_kappa_squared": ("SCALAR s = (flags & 2) ? q / (kap * kap * kap * Rc) : 0.0;",
                                "SCALAR s = (flags & 2) ? q / (kap * kap * Rc) : 0.0;"),
+    # linear-in-time interpolation: ramp weight doubled; the two end fields exchanged
+    "linear_ramp_doubled": ("SCALAR ramp = ((u1 - a) * (u1 - a) - (u0 - a) * (u0 - a)) / (2.0 * (c - a));",
+                            "SCALAR ramp = ((u1 - a) * (u1 - a) - (u0 - a) * (u0 - a)) / (c - a);"),
+    "linear_ends_exchanged": ("row[6 * b + i] += F0[i] * len + (F1[i] - F0[i]) * ramp;",
+                              "row[6 * b + i] += F1[i] * len + (F0[i] - F1[i]) * ramp;"),
 }
 
 

@@ -617,3 +617,82 @@ def test_farfield_uniform_motion_exactly_zero(oracle_lib):
     det = W.Detector(W.spherical_cap(4, 30.0, 0.5), None, 25.0, 0.05, 256, flags=W.RD_FAR | W.RD_FARFIELD)
     E, B, _ = oracle.deposit(tr, det)
     assert np.all(E == 0.0) and np.all(B == 0.0)
+
+
+# ---------------------------------------------------------------------------------------------
+# linear-in-time interpolation of the field over each interval (flags bit 8)
+# ---------------------------------------------------------------------------------------------
+def _sample_fields(tr, p, P, flags):
+    """Per-sample fields F_k (k >= 1) of particle p at cell P and the arrival coordinates u_k (bins
+    of width 1 from T0 = 0)."""
+    betas = [oracle.beta(tr.u[p, k]) for k in range(tr.n_samples)]
+    F = [None]
+    for k in range(1, tr.n_samples):
+        bd = (betas[k] - betas[k - 1]) / tr.dt
+        E, B = oracle.field(tr.x[p, k], betas[k], bd, P, tr.q[p], flags)
+        F.append(np.concatenate([E, B]))
+    u = np.array([oracle.bin_coord(tr.t0, k, tr.dt, tr.x[p, k], P, 0.0, 1.0 / 0.05, flags) for k in range(tr.n_samples)])
+    return F, u
+
+
+def test_linear_interpolation_sum_rule(oracle_lib):
+    """With every arrival inside the window, the bins of a cell add up to the trapezoid rule over the
+    arrival intervals: F_1 (u_1 - u_0) + sum_{k>=2} (F_{k-1} + F_k)/2 (u_k - u_{k-1})."""
+    tr = W.random_smooth(2, 60, 0.02, max_u=2.0, seed=3)
+    P = np.array([[12.0, -5.0, 3.0]])
+    det = W.Detector(P, None, 0.0, 0.05, 2000, flags=W.RD_NEAR | W.RD_FAR | W.RD_LINEAR)
+    E, B, clipped = oracle.deposit(tr, det)
+    assert clipped == 0
+    want = np.zeros(6)
+    for p in range(tr.n_part):
+        F, u = _sample_fields(tr, p, P[0], W.RD_NEAR | W.RD_FAR)
+        want += F[1] * (u[1] - u[0])
+        for k in range(2, tr.n_samples):
+            want += 0.5 * (F[k - 1] + F[k]) * (u[k] - u[k - 1])
+    got = np.concatenate([E[0].sum(axis=0), B[0].sum(axis=0)])
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+
+
+def test_linear_interpolation_brute_force(oracle_lib):
+    """One particle, 12 samples, bins about as long as the intervals: each bin equals a fine
+    midpoint-rule integral of the piecewise-linear emission (held F_1 on the first interval)."""
+    tr = W.random_smooth(1, 11, 0.05, max_u=1.5, seed=9)
+    P = np.array([[3.0, 1.0, -2.0]])
+    F, u = _sample_fields(tr, 0, P[0], W.RD_NEAR | W.RD_FAR)
+    lo = int(np.floor(u[0])) - 1
+    det = W.Detector(P, None, lo * 0.05, 0.05, int(np.ceil(u[-1])) - lo + 2,
+                     flags=W.RD_NEAR | W.RD_FAR | W.RD_LINEAR)
+    E, B, clipped = oracle.deposit(tr, det)
+    assert clipped == 0
+    uu = u - lo
+    got = np.concatenate([E[0], B[0]], axis=1)
+    n_sub = 20000
+    for b in range(det.n_bins):
+        s = b + (np.arange(n_sub) + 0.5) / n_sub
+        val = np.zeros((n_sub, 6))
+        first = (s >= uu[0]) & (s < uu[1])
+        val[first] = F[1]
+        for k in range(2, tr.n_samples):
+            m = (s >= uu[k - 1]) & (s < uu[k])
+            if np.any(m):
+                w = ((s[m] - uu[k - 1]) / (uu[k] - uu[k - 1]))[:, None]
+                val[m] = (1.0 - w) * F[k - 1] + w * F[k]
+        np.testing.assert_allclose(got[b], val.mean(axis=0), rtol=2e-5, atol=2e-6 * np.abs(got).max())
+
+
+def test_linear_interpolation_is_second_order(oracle_lib):
+    """Velocity field of a circular orbit (gamma 2) at a cell 6.4 orbit radii away: halving dt cuts
+    the change of the deposit fourfold with the linear interpolation and twofold with the held
+    field (samples are exact, so only the interpolation changes with dt)."""
+    P = np.array([[6.0, 2.0, 1.0]])
+    period = 2.0 * math.pi / math.sqrt(0.75)
+    ratios = {}
+    for fl in (W.RD_NEAR, W.RD_NEAR | W.RD_LINEAR):
+        Ds = []
+        for m in (1, 2, 4):
+            tr = W.circular_orbit(gamma=2.0, radius=1.0, n_steps=200 * m, dt_frac=0.01 / m)
+            det = W.Detector(P, None, 7.0, period / 50.0, 80, flags=fl)
+            Ds.append(oracle.deposit(tr, det)[0][0])
+        ratios[fl] = np.linalg.norm(Ds[0] - Ds[1]) / np.linalg.norm(Ds[1] - Ds[2])
+    assert 1.8 < ratios[W.RD_NEAR] < 2.2, ratios
+    assert 3.5 < ratios[W.RD_NEAR | W.RD_LINEAR] < 4.5, ratios
