@@ -170,16 +170,16 @@ __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointP
     const float gbdx = (-kap * gVx + gc1 * nx) * far, gbdy = (-kap * gVy + gc1 * ny) * far,
                 gbdz = (-kap * gVz + gc1 * nz) * far;              // d/dbetadot
     // R: s = q/(kappa^3 R), c1 contains gamma^-2/R, and the arrival time u_k contains R/dt_det
-    const float gR = -gsv * s * rinv - gc1 * r.ig2n * rinv * rinv + a_end * (float)P.inv_dt_det;
+    const float gR = -gsv * s * rinv - gc1 * r.ig2n * rinv * rinv + a_end * P.inv_dt_det_f;
     // d = x_cell - x:  n = d/R, dR/dd = n
     const float ndg = nx * gnx + ny * gny + nz * gnz;
     const float gdx = (gnx - nx * ndg) * rinv + gR * nx;
     const float gdy = (gny - ny * ndg) * rinv + gR * ny;
     const float gdz = (gnz - nz * ndg) * rinv + gR * nz;
-    const float inv_dt = 1.f / P.dt_f;
+    const float inv_dt = P.inv_dt_f;
 
     // sample k-1: its arrival time starts this interval; betadot_k depends on beta_{k-1}
-    const float cb = a_beg * (float)P.inv_dt_det;                    // -dL/dR_{k-1} from this interval
+    const float cb = a_beg * P.inv_dt_det_f;                        // -dL/dR_{k-1} from this interval
     out[0] = c.pend[0] + cb * c.np[0];
     out[1] = c.pend[1] + cb * c.np[1];
     out[2] = c.pend[2] + cb * c.np[2];

@@ -556,6 +556,8 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
         P.du_scale = (float)(t->dt / d->dt_det);
         P.W = (float)(d->dt_det / t->dt);
         P.invW = (float)(t->dt / d->dt_det);
+        P.inv_dt_det_f = (float)(1.0 / d->dt_det);
+        P.inv_dt_f = (float)(1.0 / t->dt);
         {
             LaunchTimer timer(d, s);
             RD_CUDA(launch_adjoint_mixed(P, s), "adjoint");

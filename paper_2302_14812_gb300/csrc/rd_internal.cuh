@@ -136,6 +136,7 @@ struct AdjointParams {
     int flags;
     double t0, dt, inv_dt_det;
     float dt_f, du_scale, W, invW;
+    float inv_dt_det_f, inv_dt_f;   // 1/dt_det and 1/dt in FP32 (no conversion or division per step)
 };
 #ifndef RD_ADJ_THREADS
 #define RD_ADJ_THREADS 128
