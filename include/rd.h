@@ -65,8 +65,13 @@ enum { RD_FP64 = 0, RD_MIXED = 1 };
  * RD_NEAR) selects the far-field limit: arrival times by Eq. 3, t + R_c - x.n_c, and the radiation
  * term of Eq. 1 with the direction n_c and distance R_c of the cell seen from the origin
  * (R_c n_c = pix_pos) in place of the particle-to-cell n and R.
+ *
+ * RD_LINEAR (with any of the above) replaces the held field of the integrating deposit by a field
+ * that varies linearly in arrival time over each interval, from the field of sample k-1 to that
+ * of sample k (second order in dt where the held field is first order; the first interval of a
+ * trajectory still holds the field of sample 1).  Not supported by rd_adjoint_trajectories.
  */
-enum { RD_NEAR = 1, RD_FAR = 2, RD_FARFIELD = 4 };
+enum { RD_NEAR = 1, RD_FAR = 2, RD_FARFIELD = 4, RD_LINEAR = 8 };
 /* where a caller buffer lives */
 enum { RD_MEM_DEVICE = 0, RD_MEM_HOST = 1 };
 /* element type of caller field / gradient-seed buffers */
@@ -92,7 +97,7 @@ typedef struct {
     double dt_det;             /* > 0                                                           */
     int32_t n_bins;            /* >= 1; <= 4194304 (2^22) for RD_MIXED                          */
     int32_t precision;         /* RD_MIXED or RD_FP64                                           */
-    int32_t flags;             /* RD_NEAR | RD_FAR (0 is read as both), or RD_FAR | RD_FARFIELD  */
+    int32_t flags;             /* RD_NEAR | RD_FAR (0 = both), or RD_FAR | RD_FARFIELD; | RD_LINEAR */
 } rd_detector_desc;
 
 /*

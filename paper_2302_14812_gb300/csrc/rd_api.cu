@@ -211,6 +211,7 @@ void fill_mixed_params(DepositParams& P, const rd_detector* d, const rd_traj* t,
     P.dt_f = (float)t->dt;
     P.du_scale = (float)(t->dt / d->dt_det);
     P.ff = (d->flags & RD_FARFIELD) != 0;
+    P.lin = (d->flags & RD_LINEAR) != 0;
     P.W = (float)(d->dt_det / t->dt);
     P.invW = (float)(t->dt / d->dt_det);
 }
@@ -245,7 +246,10 @@ rd_status rd_create_detector(const rd_detector_desc* desc, rd_stream stream, rd_
     if (desc->precision != RD_MIXED && desc->precision != RD_FP64)
         return fail(RD_ERR_ARG, "bad precision %d", desc->precision);
     if (desc->mem != RD_MEM_DEVICE && desc->mem != RD_MEM_HOST) return fail(RD_ERR_ARG, "bad desc->mem");
-    if (desc->flags & ~(RD_NEAR | RD_FAR | RD_FARFIELD)) return fail(RD_ERR_ARG, "bad flags %d", desc->flags);
+    if (desc->flags & ~(RD_NEAR | RD_FAR | RD_FARFIELD | RD_LINEAR))
+        return fail(RD_ERR_ARG, "bad flags %d", desc->flags);
+    if ((desc->flags & (RD_NEAR | RD_FAR)) == 0 && desc->flags != 0)
+        return fail(RD_ERR_ARG, "flags %d select no term of Eq. 1 (RD_NEAR and/or RD_FAR)", desc->flags);
     if ((desc->flags & RD_FARFIELD) && (desc->flags & RD_NEAR))
         return fail(RD_ERR_ARG, "RD_FARFIELD keeps only the radiation term: RD_NEAR cannot be combined with it");
     if (desc->precision == RD_MIXED && desc->n_bins > kMixedMaxBins)
@@ -414,6 +418,7 @@ rd_status rd_deposit_trajectories(rd_detector* d, const rd_traj* t, rd_stream st
         P.W = (float)(d->dt_det / t->dt);
         P.invW = (float)(t->dt / d->dt_det);
         P.ff = (d->flags & RD_FARFIELD) != 0;
+        P.lin = (d->flags & RD_LINEAR) != 0;
         if (mixed) {
             RD_CUDA(launch_precompute_mixed(x, u, q, t->dt / d->dt_det, np, t->n_samples, t->dt, d->flags,
                                             static_cast<RecS*>(d->rec), d->counters, s),
@@ -504,7 +509,8 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
     rd_status st = check_traj(t);
     if (st != RD_OK) return st;
     if (d->precision != RD_MIXED) return fail(RD_ERR_STATE, "the adjoint needs an RD_MIXED detector");
-    if (d->flags & RD_FARFIELD) return fail(RD_ERR_STATE, "the adjoint covers the exact fields, not RD_FARFIELD");
+    if (d->flags & (RD_FARFIELD | RD_LINEAR))
+        return fail(RD_ERR_STATE, "the adjoint covers the exact fields with the held interpolation only");
     if (t->mem != RD_MEM_DEVICE) return fail(RD_ERR_ARG, "the adjoint needs device trajectories");
     if (!gE && !gB) return fail(RD_ERR_ARG, "gE and gB are both NULL");
     if (gdtype != RD_F32 && gdtype != RD_F64) return fail(RD_ERR_ARG, "bad gdtype %d", gdtype);

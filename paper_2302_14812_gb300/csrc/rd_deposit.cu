@@ -129,6 +129,7 @@ struct D64State {
     int b;
     double a;       // arrival (bins) of the previous sample
     double acc[6];
+    double Fp[6];   // RD_LINEAR: field of the previous sample
     int n_below;
     int n_above;
 };
@@ -227,6 +228,50 @@ __device__ __forceinline__ void fp64_deposit(D64State& st, const double* F, doub
     st.a = c;
 }
 
+// RD_LINEAR: the field goes linearly from F0 at st.a to F1 at c; the overlap [u0, u1] of the interval
+// with a bin weighs F0 (u1 - u0) + (F1 - F0) ((u1 - a)^2 - (u0 - a)^2) / (2 (c - a)).
+__device__ __forceinline__ void fp64_lin_part(const double* F0, const double* F1, double a, double c, double u0,
+                                              double u1, double* out, bool add)
+{
+    const double len = u1 - u0;
+    const double ramp = ((u1 - a) * (u1 - a) - (u0 - a) * (u0 - a)) / (2.0 * (c - a));
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double v = F0[i] * len + (F1[i] - F0[i]) * ramp;
+        out[i] = add ? out[i] + v : v;
+    }
+}
+
+__device__ __forceinline__ void fp64_deposit_lin(D64State& st, const double* F0, const double* F1, double c,
+                                                 double* row, int n_bins, int k, int k_begin, int k_end)
+{
+    const double a = st.a;
+    const double fc = floor(c);
+    const int bc = clamp_bin(fc);
+    if (!(c > a)) {
+        st.a = c;
+        return;
+    }
+    if (bc <= st.b) {
+        fp64_lin_part(F0, F1, a, c, a, c, st.acc, true);
+        st.a = c;
+        return;
+    }
+    fp64_lin_part(F0, F1, a, c, a, (double)(st.b + 1), st.acc, true);
+    flush_f64(row, n_bins, st.b, st.acc);
+    const int lo = max(st.b + 1, 0), hi = min(bc - 1, n_bins - 1);
+    for (int j = lo; j <= hi; ++j) {
+        double v[6];
+        fp64_lin_part(F0, F1, a, c, (double)j, (double)(j + 1), v, false);
+        flush_f64(row, n_bins, j, v);
+    }
+    fp64_lin_part(F0, F1, a, c, fc, c, st.acc, false);
+    if (st.b < 0 && bc >= 0) st.n_below = k - k_begin + 1;
+    if (st.b < n_bins && bc >= n_bins) st.n_above = k_end - k + 1;
+    st.b = bc;
+    st.a = c;
+}
+
 __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const DepositParams P,
                                                                        int flags)
 {
@@ -295,6 +340,14 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
         if (!live) atomicAdd(&P.counters->clipped, (unsigned long long)n_int);
     }
     const double q = P.q ? P.q[p] : 1.0;
+    if (P.lin && live) {
+        // field of the sample before the chunk; a trajectory's first interval holds F_1
+        const RecD r0 = rec[k_begin > 1 ? k_begin - 1 : 1];
+        if (ff)
+            fp64_field_ff(r0, ncx, ncy, ncz, Rc, q, flags, st.Fp);
+        else
+            fp64_field(r0, cl, q, flags, st.Fp);
+    }
 
     for (int t = 0; t < n_tiles; ++t) {
         const int buf = t & 1;
@@ -324,7 +377,13 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
                     double R;
                     cbin = arrival_bins(r.xa.x, r.xa.y, r.xa.z, cl, P.t0, k, P.dt, P.inv_dt_det, R);
                 }
-                fp64_deposit(st, F, cbin, row, P.n_bins, k, k_begin, k_end);
+                if (P.lin) {
+                    fp64_deposit_lin(st, st.Fp, F, cbin, row, P.n_bins, k, k_begin, k_end);
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) st.Fp[j] = F[j];
+                } else {
+                    fp64_deposit(st, F, cbin, row, P.n_bins, k, k_begin, k_end);
+                }
             }
             if (t == n_tiles - 1) {
                 flush_f64(row, P.n_bins, st.b, st.acc);

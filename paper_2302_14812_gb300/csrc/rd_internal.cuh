@@ -89,6 +89,7 @@ struct DepositParams {
     float dt_f;
     float du_scale;             // dt / dt_det
     int ff;                     // far-field limit (RD_FARFIELD): Eq. 3, radiation term at (n_c, R_c)
+    int lin;                    // RD_LINEAR: field linear in arrival time over each interval
 };
 
 constexpr int kDepositThreads = 256;   // FP64 kernel: one cell per thread

@@ -40,6 +40,7 @@ struct Cells {
     float rpd[NC];                  // R_{k-1} + dt (far-field limit: 1/R_c)
     float ec[NC];                   // far-field limit: |n_c|^2 - 1 of the rounded direction
     float acc[6][NC];               // E xyz, B xyz of the current bin so far (weights in bins)
+    float gp[6][NC];                // linear interpolation: scaled field of the previous sample
     int bo[NC];                     // row * n_bins + bin being filled (bin may lie outside the window)
     int rb[NC];                     // row * n_bins (row = the cell's index inside the CTA's block)
     bool live[NC];                  // some arrival of the chunk falls inside the window
@@ -177,6 +178,57 @@ __device__ __forceinline__ void multi_edges(Cells& c, int j, const Field& o, con
     }
 }
 
+// Field of the sample in bin-weight units per unit dt: G = (S E', (S/R) d x E').
+__device__ __forceinline__ void scaled_field(const Field& o, float* G)
+{
+    const float sb = o.S * o.rinv;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        G[i] = o.E[i] * o.S;
+        G[3 + i] = o.B[i] * sb;
+    }
+}
+
+// Linear interpolation (RD_LINEAR): over the interval the field goes linearly from G0 = gp (previous
+// sample) to G (this sample); the part [s0, s1] of the interval (dt units from its start, length L)
+// weighs G0 (s1 - s0) + (G - G0) (s1^2 - s0^2) / (2 L).  Interval of cell j passing two or more bin
+// edges (exact walk only): flush the bin being filled, every whole bin, and leave the last, partial
+// bin in the accumulator with the time already in it; fn comes back below W (no edge left for the
+// common path).
+template <bool TRACK>
+__device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* dG, float L, float inv2L,
+                                                const Consts& C, float& fn, int k, int k_begin, int k_end)
+{
+    const float f = fn;
+    if (!(f >= 2.f * C.W)) return;
+    const float f0 = c.f[j];
+    const int b0 = c.bo[j] - c.rb[j];
+    const int m = (int)fminf(floorf(f * C.invW), 16777216.f);      // edges passed, >= 2
+    flush(C, b0, c.bo[j], c.acc[0][j], c.acc[1][j], c.acc[2][j], c.acc[3][j], c.acc[4][j], c.acc[5][j]);
+    // whole bins b0+i, i = 1..m-1, cover [i W, (i+1) W] from the start of bin b0
+    const int lo = max(1, -b0), hi = min(m - 1, C.n_bins - 1 - b0);
+    for (int i = lo; i <= hi; ++i) {
+        const float s0 = fmaf((float)i, C.W, -f0), s1 = s0 + C.W;
+        const float ramp = (s1 * s1 - s0 * s0) * inv2L;
+        float v[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v[q] = fmaf(c.gp[q][j], C.W, dG[q] * ramp);
+        flush(C, b0 + i, c.bo[j] + i, v[0], v[1], v[2], v[3], v[4], v[5]);
+    }
+    // bin b0+m holds [m W, f]
+    const float s0 = fmaf((float)m, C.W, -f0);
+    const float len = fmaf(-(float)m, C.W, f);
+    const float ramp = (L * L - s0 * s0) * inv2L;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) c.acc[q][j] = fmaf(c.gp[q][j], len, dG[q] * ramp);
+    c.bo[j] += m;
+    fn = fminf(fmaxf(len, 0.f), C.W * 0.99999994f);
+    if (TRACK) {
+        if (b0 < 0 && b0 + m >= 0) c.below[j] = k - k_begin + 1;
+        if (b0 < C.n_bins && b0 + m >= C.n_bins) c.above[j] = k_end - k + 1;
+    }
+}
+
 // Walk modes.  kFast: the common step, with no code for an interval that passes two or more bin
 // edges; such an interval sets the cell's time to -inf, after which the cell crosses no edge and
 // flushes nothing for the rest of the tile.  kExact: the same arithmetic plus the multi-edge case;
@@ -191,12 +243,13 @@ enum { kFast = 0, kExact = 1 };
 // flushes the bin and starts the next one with the rest of the interval.  LAST: the interval ends
 // on the exact FP64 anchors.  TRACK: bins may lie outside the window (checked, clipped intervals
 // counted).  ok: kExact only, false from the interval that stopped the fast walk onwards.
-template <int MODE, bool LAST, bool TRACK, bool FF>
+template <int MODE, bool LAST, bool TRACK, bool FF, bool LIN>
 __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, const int* bo_end,
                                      const float* f_end, int k, int k_begin, int k_end, bool* ok)
 {
     Field o[NC];
     float fn[NC];
+    float G[NC][6], dG[NC][6], L[NC], inv2L[NC], ramp1[NC];     // linear interpolation only
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         if (FF)
@@ -210,12 +263,25 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
         } else {
             t = fmaf(o[j].num, o[j].rden, c.f[j]);
         }
-        const float ws = (fminf(t, C.W) - c.f[j]) * o[j].S;
-        const float wb = ws * o[j].rinv;
+        if (LIN) {
+            scaled_field(o[j], G[j]);
+            L[j] = t - c.f[j];
+            inv2L[j] = 0.5f * fast_rcp(L[j]);
+            const float len1 = fminf(t, C.W) - c.f[j];
+            ramp1[j] = (len1 * len1) * inv2L[j];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            c.acc[i][j] = fmaf(o[j].E[i], ws, c.acc[i][j]);
-            c.acc[3 + i][j] = fmaf(o[j].B[i], wb, c.acc[3 + i][j]);
+            for (int i = 0; i < 6; ++i) {
+                dG[j][i] = G[j][i] - c.gp[i][j];
+                c.acc[i][j] = fmaf(c.gp[i][j], len1, fmaf(dG[j][i], ramp1[j], c.acc[i][j]));
+            }
+        } else {
+            const float ws = (fminf(t, C.W) - c.f[j]) * o[j].S;
+            const float wb = ws * o[j].rinv;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                c.acc[i][j] = fmaf(o[j].E[i], ws, c.acc[i][j]);
+                c.acc[3 + i][j] = fmaf(o[j].B[i], wb, c.acc[3 + i][j]);
+            }
         }
         if (MODE == kFast)
             t = t < 2.f * C.W ? t : -INFINITY;
@@ -225,7 +291,12 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
     }
     if (MODE == kExact) {
 #pragma unroll
-        for (int j = 0; j < NC; ++j) multi_edges<TRACK>(c, j, o[j], C, fn[j], k, k_begin, k_end);
+        for (int j = 0; j < NC; ++j) {
+            if (LIN)
+                multi_edges_lin<TRACK>(c, j, dG[j], L[j], inv2L[j], C, fn[j], k, k_begin, k_end);
+            else
+                multi_edges<TRACK>(c, j, o[j], C, fn[j], k, k_begin, k_end);
+        }
     }
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
@@ -237,12 +308,18 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
                 red_add_v4(a, c.acc[0][j], c.acc[1][j], c.acc[2][j], c.acc[3][j]);
                 red_add_v2(a + 4, c.acc[4][j], c.acc[5][j]);
                 const float rem = fn[j] - C.W;
-                const float rs = rem * o[j].S;
-                const float rbw = rs * o[j].rinv;
+                if (LIN) {
+                    const float ramp2 = fmaf(0.5f, L[j], -ramp1[j]);
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    c.acc[i][j] = o[j].E[i] * rs;
-                    c.acc[3 + i][j] = o[j].B[i] * rbw;
+                    for (int i = 0; i < 6; ++i) c.acc[i][j] = fmaf(c.gp[i][j], rem, dG[j][i] * ramp2);
+                } else {
+                    const float rs = rem * o[j].S;
+                    const float rbw = rs * o[j].rinv;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        c.acc[i][j] = o[j].E[i] * rs;
+                        c.acc[3 + i][j] = o[j].B[i] * rbw;
+                    }
                 }
                 c.f[j] = rem;
                 c.bo[j] += 1;
@@ -257,12 +334,21 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
             red_add_v4_if(pr, a, c.acc[0][j], c.acc[1][j], c.acc[2][j], c.acc[3][j]);
             red_add_v2_if(pr, a + 4, c.acc[4][j], c.acc[5][j]);
             const float rem = fn[j] - C.W;
-            const float rs = rem * o[j].S;
-            const float rbw = rs * o[j].rinv;
+            if (LIN) {
+                const float ramp2 = fmaf(0.5f, L[j], -ramp1[j]);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                c.acc[i][j] = cr ? o[j].E[i] * rs : c.acc[i][j];
-                c.acc[3 + i][j] = cr ? o[j].B[i] * rbw : c.acc[3 + i][j];
+                for (int i = 0; i < 6; ++i) {
+                    const float v = fmaf(c.gp[i][j], rem, dG[j][i] * ramp2);
+                    c.acc[i][j] = cr ? v : c.acc[i][j];
+                }
+            } else {
+                const float rs = rem * o[j].S;
+                const float rbw = rs * o[j].rinv;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    c.acc[i][j] = cr ? o[j].E[i] * rs : c.acc[i][j];
+                    c.acc[3 + i][j] = cr ? o[j].B[i] * rbw : c.acc[3 + i][j];
+                }
             }
             c.f[j] = cr ? rem : fn[j];
             if (TRACK) {
@@ -270,6 +356,10 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
                 if (cr && b == C.n_bins - 1) c.above[j] = k_end - k + 1;
             }
             c.bo[j] += cr ? 1 : 0;
+        }
+        if (LIN) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) c.gp[i][j] = G[j][i];
         }
     }
 }
@@ -280,62 +370,74 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
 constexpr int kUnroll = RD_UNROLL > 0 ? RD_UNROLL : 1;   // samples per loop iteration
 
 // Per-thread copy of the walk state at the start of a tile, in shared memory ([word][thread]).
-constexpr int kSaveWords = NC * 11;
+constexpr int kSaveCell = 17;               // f, rpd, bo, below, above, acc[6], gp[6]
+constexpr int kSaveWords = NC * kSaveCell;
 
+template <bool LIN>
 __device__ __forceinline__ void save_state(const Cells& c, float (*sv)[kMixedThreads], int tid)
 {
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        sv[j * 11 + 0][tid] = c.f[j];
-        sv[j * 11 + 1][tid] = c.rpd[j];
-        sv[j * 11 + 2][tid] = __int_as_float(c.bo[j]);
-        sv[j * 11 + 3][tid] = __int_as_float(c.below[j]);
-        sv[j * 11 + 4][tid] = __int_as_float(c.above[j]);
+        sv[j * kSaveCell + 0][tid] = c.f[j];
+        sv[j * kSaveCell + 1][tid] = c.rpd[j];
+        sv[j * kSaveCell + 2][tid] = __int_as_float(c.bo[j]);
+        sv[j * kSaveCell + 3][tid] = __int_as_float(c.below[j]);
+        sv[j * kSaveCell + 4][tid] = __int_as_float(c.above[j]);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) sv[j * 11 + 5 + i][tid] = c.acc[i][j];
+        for (int i = 0; i < 6; ++i) sv[j * kSaveCell + 5 + i][tid] = c.acc[i][j];
+        if (LIN) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) sv[j * kSaveCell + 11 + i][tid] = c.gp[i][j];
+        }
     }
 }
 
+template <bool LIN>
 __device__ __forceinline__ void restore_state(Cells& c, float (*sv)[kMixedThreads], int tid)
 {
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        c.f[j] = sv[j * 11 + 0][tid];
-        c.rpd[j] = sv[j * 11 + 1][tid];
-        c.bo[j] = __float_as_int(sv[j * 11 + 2][tid]);
-        c.below[j] = __float_as_int(sv[j * 11 + 3][tid]);
-        c.above[j] = __float_as_int(sv[j * 11 + 4][tid]);
+        c.f[j] = sv[j * kSaveCell + 0][tid];
+        c.rpd[j] = sv[j * kSaveCell + 1][tid];
+        c.bo[j] = __float_as_int(sv[j * kSaveCell + 2][tid]);
+        c.below[j] = __float_as_int(sv[j * kSaveCell + 3][tid]);
+        c.above[j] = __float_as_int(sv[j * kSaveCell + 4][tid]);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) c.acc[i][j] = sv[j * 11 + 5 + i][tid];
+        for (int i = 0; i < 6; ++i) c.acc[i][j] = sv[j * kSaveCell + 5 + i][tid];
+        if (LIN) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) c.gp[i][j] = sv[j * kSaveCell + 11 + i][tid];
+        }
     }
 }
 
-template <bool TRACK, bool FF>
+template <bool TRACK, bool FF, bool LIN>
 __device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, bool last_tile, const Consts& C,
                                           const int* bo_end, const float* f_end, int k0, int k_begin, int k_end,
                                           float (*sv)[kMixedThreads])
 {
     const int tid = threadIdx.x;
     const int n_regular = last_tile ? cnt - 1 : cnt;
-    save_state(c, sv, tid);
+    save_state<LIN>(c, sv, tid);
     bool ok[NC];
 #pragma unroll kUnroll
     for (int i = 0; i < n_regular; ++i)
-        step<kFast, false, TRACK, FF>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok);
-    if (last_tile) step<kFast, true, TRACK, FF>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok);
+        step<kFast, false, TRACK, FF, LIN>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok);
+    if (last_tile)
+        step<kFast, true, TRACK, FF, LIN>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok);
     bool stopped = false;
 #pragma unroll
     for (int j = 0; j < NC; ++j) stopped = stopped || c.f[j] == -INFINITY;
     if (__any_sync(0xffffffffu, stopped)) {
         // some interval of a cell of this warp passed two or more bin edges: walk the tile again
-        restore_state(c, sv, tid);
+        restore_state<LIN>(c, sv, tid);
 #pragma unroll
         for (int j = 0; j < NC; ++j) ok[j] = true;
 #pragma unroll 1
         for (int i = 0; i < n_regular; ++i)
-            step<kExact, false, TRACK, FF>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok);
+            step<kExact, false, TRACK, FF, LIN>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok);
         if (last_tile)
-            step<kExact, true, TRACK, FF>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok);
+            step<kExact, true, TRACK, FF, LIN>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok);
     }
 }
 
@@ -345,7 +447,7 @@ __device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, b
 // CTA.  tile / bar: the CTA's shared staging buffers; g_base counts the tiles the CTA staged
 // before this item (it selects buffer and mbarrier phase, so the buffers carry over between items).
 // Returns false if a bounded wait ran out (the error is recorded; the CTA must stop).
-template <bool FF>
+template <bool FF, bool LIN>
 __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int cb, int ch,
                                              RecS (*tile)[kTileSteps], uint64_t* bar, float (*sv)[kMixedThreads],
                                              unsigned& g_base)
@@ -446,6 +548,24 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
         }
     }
     // clip tracking costs instructions in the bin-crossing path: only CTAs that need it use it
+    if (LIN) {
+        // field of the sample before the chunk; a trajectory's first interval holds F_1 (sample 0
+        // has no field), so the first chunk starts from the field of sample 1 itself
+        const RecS r0 = rec[k_begin > 1 ? k_begin - 1 : 1];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            Field o;
+            float rtmp = c.rpd[j];
+            if (FF)
+                field_at_ff(r0, c.px[j], c.py[j], c.pz[j], c.rpd[j], c.ec[j], o);
+            else
+                field_at(r0, c.px[j], c.py[j], c.pz[j], rtmp, C, o);
+            float G[6];
+            scaled_field(o, G);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) c.gp[i][j] = G[i];
+        }
+    }
     const bool track = __syncthreads_or(partial) != 0;
 
     for (int t = 0; t < n_tiles; ++t) {
@@ -466,9 +586,9 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
         const int cnt = min(kTileSteps, k_end - k0 + 1);
         const bool last_tile = (t == n_tiles - 1);
         if (track)
-            walk_tile<true, FF>(c, tile[buf], cnt, last_tile, C, bo_end, f_end, k0, k_begin, k_end, sv);
+            walk_tile<true, FF, LIN>(c, tile[buf], cnt, last_tile, C, bo_end, f_end, k0, k_begin, k_end, sv);
         else
-            walk_tile<false, FF>(c, tile[buf], cnt, last_tile, C, bo_end, f_end, k0, k_begin, k_end, sv);
+            walk_tile<false, FF, LIN>(c, tile[buf], cnt, last_tile, C, bo_end, f_end, k0, k_begin, k_end, sv);
         __syncthreads();
         if (tid == 0 && t + 2 < n_tiles) {
             fence_proxy_async();
@@ -506,7 +626,7 @@ __device__ __forceinline__ void init_staging(uint64_t* bar)
     __syncthreads();
 }
 
-template <bool FF>
+template <bool FF, bool LIN>
 __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_mixed(const DepositParams P)
 {
     __shared__ __align__(128) RecS tile[2][kTileSteps];
@@ -519,7 +639,7 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_m
     const int cb = (int)(rest % (unsigned)P.n_cell_blocks);
     const int ch = (int)(rest / (unsigned)P.n_cell_blocks);
     unsigned g = 0;
-    (void)deposit_item<FF>(P, p, cb, ch, tile, bar, sv, g);
+    (void)deposit_item<FF, LIN>(P, p, cb, ch, tile, bar, sv, g);
 }
 
 // Persistent form: the resident CTAs draw work items of all problems from one counter.
@@ -554,8 +674,13 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS)
         const long long rest = local / P.n_part;
         const int cb = (int)(rest % P.n_cell_blocks);
         const int ch = (int)(rest / P.n_cell_blocks);
-        const bool ok = P.ff ? deposit_item<true>(P, p, cb, ch, tile, bar, sv, g)
-                             : deposit_item<false>(P, p, cb, ch, tile, bar, sv, g);
+        bool ok;
+        if (P.lin)
+            ok = P.ff ? deposit_item<true, true>(P, p, cb, ch, tile, bar, sv, g)
+                      : deposit_item<false, true>(P, p, cb, ch, tile, bar, sv, g);
+        else
+            ok = P.ff ? deposit_item<true, false>(P, p, cb, ch, tile, bar, sv, g)
+                      : deposit_item<false, false>(P, p, cb, ch, tile, bar, sv, g);
         if (!ok) break;
     }
 }
@@ -581,10 +706,14 @@ cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s)
     const long long blocks = (long long)p.n_cell_blocks * p.n_part * p.n_chunks;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if (p.ff)
-        k_deposit_mixed<true><<<(unsigned)blocks, kMixedThreads, 0, s>>>(p);
+    if (p.ff && p.lin)
+        k_deposit_mixed<true, true><<<(unsigned)blocks, kMixedThreads, 0, s>>>(p);
+    else if (p.ff)
+        k_deposit_mixed<true, false><<<(unsigned)blocks, kMixedThreads, 0, s>>>(p);
+    else if (p.lin)
+        k_deposit_mixed<false, true><<<(unsigned)blocks, kMixedThreads, 0, s>>>(p);
     else
-        k_deposit_mixed<false><<<(unsigned)blocks, kMixedThreads, 0, s>>>(p);
+        k_deposit_mixed<false, false><<<(unsigned)blocks, kMixedThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

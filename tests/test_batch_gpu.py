@@ -209,3 +209,16 @@ def test_batch_record_budget_splits_into_groups():
         assert rel_l2(E, Es) <= 2e-6 and rel_l2(B, Bs) <= 2e-6
     for d in dets:
         d.close()
+
+
+def test_batch_mixes_modes():
+    """One batch with a linear-interpolation problem, a far-field problem and a plain one (each
+    work item follows its own problem's mode) equals the separate deposits."""
+    import torch
+    probs = small_problems()[:3]
+    probs[0][1].flags = W.RD_NEAR | W.RD_FAR | W.RD_LINEAR
+    probs[1][1].flags = W.RD_FAR | W.RD_FARFIELD
+    sep = run_separate(probs)
+    res = run_batch(probs, torch.cuda.Stream())
+    for (E, B), (Es, Bs) in zip(res[0], sep):
+        assert rel_l2(E, Es) <= 2e-6 and rel_l2(B, Bs) <= 2e-6

@@ -281,3 +281,49 @@ def test_farfield_flag_checks():
         d.adjoint(x, u, None, tr.t0, tr.dt, torch.zeros((1, 64, 3), dtype=torch.float32, device="cuda"))
     assert ei.value.status == rd.RD_ERR_STATE
     d.close()
+
+
+# --------------------------------------------------------------------------------------------
+# linear-in-time interpolation (RD_LINEAR), alone and with the far-field limit
+# --------------------------------------------------------------------------------------------
+def _linear_cases():
+    out = []
+    for tr, det in _farfield_cases():               # same inputs as the far-field cases
+        det.flags = W.RD_NEAR | W.RD_FAR | W.RD_LINEAR
+        out.append((tr, det))
+    tr, det = _farfield_cases()[1]
+    det.flags = W.RD_FAR | W.RD_FARFIELD | W.RD_LINEAR
+    out.append((tr, det))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", [0, 1, 2, 3])
+def test_linear_interpolation(precision, case):
+    """Window cuts and per-cell origins; the undulator ensemble; intervals spanning several bins
+    in tracked and untracked blocks; the undulator in the far-field limit: every cell against the
+    oracle's linear interpolation (clipped counts exact in FP64)."""
+    tr, det = _linear_cases()[case]
+    check(tr, det, precision)
+
+
+def test_linear_interpolation_chunks_and_particle_splits():
+    """Step chunks of 64 and 100 intervals and two calls over particle halves: each chunk starts
+    from the field of the sample before it, so the result does not depend on the split."""
+    import torch
+    tr, det = _linear_cases()[0]
+    full = rd.RadiationDetector.from_workload(det, "mixed")
+    full.deposit(torch.from_numpy(tr.x).cuda(), torch.from_numpy(tr.u).cuda(), torch.from_numpy(tr.q).cuda(),
+                 tr.t0, tr.dt)
+    Ef, Bf = full.read()
+    full.close()
+    for chunk in (64, 100):
+        d = rd.RadiationDetector.from_workload(det, "mixed")
+        d.set_chunk(chunk)
+        for sl in (slice(0, 2), slice(2, tr.n_part)):
+            one = tr.subset(range(tr.n_part)[sl])
+            d.deposit(torch.from_numpy(one.x).cuda(), torch.from_numpy(one.u).cuda(),
+                      torch.from_numpy(one.q).cuda(), one.t0, one.dt)
+        E, B = d.read()
+        d.close()
+        assert rel_l2(E, Ef) <= 2e-6 and rel_l2(B, Bf) <= 2e-6
