@@ -175,7 +175,9 @@ RD_API rd_status rd_read_fields(rd_detector* det, void* E, void* B, int32_t dtyp
  * trajectory would (up to FP32 summation order and, in RD_MIXED, the placement of the FP64
  * arrival-time anchors).  The first call after creation or rd_stream_reset has nothing in front
  * of its first sample (as in rd_deposit_trajectories).  A continuing call must have the same
- * n_part and dt, and t0 equal to the stored last time + dt; otherwise RD_ERR_STATE.  Memory: the
+ * n_part and dt, and t0 equal to the stored last time + dt; otherwise RD_ERR_STATE.  With RD_LINEAR
+ * the detector keeps the last two samples (the field of the last one needs its betadot), so every
+ * stretch's first interval is interpolated like the others.  Memory: the
  * new samples are copied (host or device) behind the stored ones into detector-held scratch,
  * 48 bytes per particle and sample.  Each call pays a record precompute, a launch and FP64 arrival
  * anchors at both ends of its stretch: hand over several steps per call where the caller can.

@@ -54,11 +54,12 @@ struct rd_detector {
     int spec_n = 0;
     std::vector<float2> spec_tw_host;
     // streamed deposits: the last sample (x, u) of every particle from the previous call
-    void* strm_last = nullptr;       // [2][n_part][3] doubles
+    void* strm_last = nullptr;       // x then u, each [n_part][2][3] doubles (last samples)
     size_t strm_last_bytes = 0;
     void* strm_stage = nullptr;      // this call's samples with the stored one in front, and q
     size_t strm_stage_bytes = 0;
     int strm_n_part = -1;            // -1: no stream in progress
+    int strm_have = 0;               // samples kept per particle (1, or 2 with RD_LINEAR)
     double strm_t_last = 0.0;
     double strm_dt = 0.0;
     std::vector<unsigned long long> graph_key;
@@ -203,6 +204,7 @@ void fill_mixed_params(DepositParams& P, const rd_detector* d, const rd_traj* t,
     P.n_samples = t->n_samples;
     P.n_part = np;
     P.chunk = chunk;
+    P.k_first = 1;
     P.n_chunks = (S + chunk - 1) / chunk;
     P.n_cell_blocks = (d->n_pix + kMixedCellsPerCta - 1) / kMixedCellsPerCta;
     P.t0 = t->t0;
@@ -352,14 +354,16 @@ rd_status rd_zero_fields(rd_detector* d, rd_stream stream)
     return RD_OK;
 }
 
-rd_status rd_deposit_trajectories(rd_detector* d, const rd_traj* t, rd_stream stream)
+// Deposit intervals k_first..S of t (k_first > 1: the earlier samples only provide the
+// previous quantities, used by streamed calls).
+static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream, int k_first)
 {
     g_err.clear();
     if (!d) return fail(RD_ERR_ARG, "detector is NULL");
     rd_status st = check_traj(t);
     if (st != RD_OK) return st;
     const int S = t->n_samples - 1;
-    if (t->n_part == 0 || S < 1) return RD_OK;
+    if (t->n_part == 0 || S < k_first) return RD_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool mixed = d->precision == RD_MIXED;
     const size_t rec_size = mixed ? sizeof(RecS) : sizeof(RecD);
@@ -377,7 +381,7 @@ rd_status rd_deposit_trajectories(rd_detector* d, const rd_traj* t, rd_stream st
     }
     const int n_cell_blocks = (d->n_pix + kDepositThreads - 1) / kDepositThreads;
     static_assert(kDepositThreads == kMixedCellsPerCta, "both deposit kernels cover 256 cells per CTA");
-    const int chunk = choose_chunk(d, std::min(pc, t->n_part), S, n_cell_blocks);
+    const int chunk = choose_chunk(d, std::min(pc, t->n_part), S - k_first + 1, n_cell_blocks);
 
     for (int p0 = 0; p0 < t->n_part; p0 += pc) {
         const int np = std::min(pc, t->n_part - p0);
@@ -408,7 +412,8 @@ rd_status rd_deposit_trajectories(rd_detector* d, const rd_traj* t, rd_stream st
         P.n_samples = t->n_samples;
         P.n_part = np;
         P.chunk = chunk;
-        P.n_chunks = (S + chunk - 1) / chunk;
+        P.k_first = k_first;
+        P.n_chunks = (S - k_first + chunk) / chunk;
         P.n_cell_blocks = n_cell_blocks;
         P.t0 = t->t0;
         P.dt = t->dt;
@@ -433,8 +438,13 @@ rd_status rd_deposit_trajectories(rd_detector* d, const rd_traj* t, rd_stream st
             RD_CUDA(launch_deposit_fp64(P, d->flags, s), "deposit (fp64)");
         }
     }
-    d->n_deposits += (long long)t->n_part * S * d->n_pix;
+    d->n_deposits += (long long)t->n_part * (S - k_first + 1) * d->n_pix;
     return RD_OK;
+}
+
+rd_status rd_deposit_trajectories(rd_detector* d, const rd_traj* t, rd_stream stream)
+{
+    return deposit_from(d, t, stream, 1);
 }
 
 rd_status rd_read_fields(rd_detector* d, void* E, void* B, int32_t dtype, int32_t mem, rd_stream stream)
@@ -830,27 +840,31 @@ rd_status rd_deposit_stream(rd_detector* d, const rd_traj* t, rd_stream stream)
             return fail(RD_ERR_STATE, "streamed call starts at t0 = %.17g, the stream continues at %.17g", t->t0,
                         expect);
     }
+    // samples kept between calls: the last one (its interval to the first new sample), and with
+    // RD_LINEAR the one before it too (the field of the last sample needs its betadot)
+    const int keep = (d->flags & RD_LINEAR) ? 2 : 1;
+    const int have = cont ? d->strm_have : 0;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int np = t->n_part, m = t->n_samples, ns = m + (cont ? 1 : 0);
-    const size_t row = sizeof(double) * 3 * (size_t)ns, mrow = sizeof(double) * 3 * (size_t)m, one = 3 * sizeof(double);
+    const int np = t->n_part, m = t->n_samples, ns = m + have;
+    const size_t one = 3 * sizeof(double);
+    const size_t row = one * (size_t)ns, mrow = one * (size_t)m;
     st = ensure(&d->strm_stage, &d->strm_stage_bytes, 2 * row * np + sizeof(double) * np, s, "stream staging");
     if (st != RD_OK) return st;
     if (!cont) {
-        st = ensure(&d->strm_last, &d->strm_last_bytes, 2 * one * np, s, "stream state");
+        st = ensure(&d->strm_last, &d->strm_last_bytes, 2 * one * 2 * np, s, "stream state");
         if (st != RD_OK) return st;
     }
     double* xs = static_cast<double*>(d->strm_stage);
     double* us = xs + (size_t)np * ns * 3;
     double* qs = us + (size_t)np * ns * 3;
-    double* lx = static_cast<double*>(d->strm_last);
-    double* lu = lx + (size_t)np * 3;
+    double* lx = static_cast<double*>(d->strm_last);        // [np][have][3]
+    double* lu = lx + (size_t)np * 2 * 3;
     const cudaMemcpyKind kind = t->mem == RD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    const size_t off = cont ? 3 : 0;
-    RD_CUDA(cudaMemcpy2DAsync(xs + off, row, t->x, mrow, mrow, np, kind, s), "stream x");
-    RD_CUDA(cudaMemcpy2DAsync(us + off, row, t->u, mrow, mrow, np, kind, s), "stream u");
-    if (cont) {
-        RD_CUDA(cudaMemcpy2DAsync(xs, row, lx, one, one, np, cudaMemcpyDeviceToDevice, s), "stream x");
-        RD_CUDA(cudaMemcpy2DAsync(us, row, lu, one, one, np, cudaMemcpyDeviceToDevice, s), "stream u");
+    RD_CUDA(cudaMemcpy2DAsync(xs + 3 * have, row, t->x, mrow, mrow, np, kind, s), "stream x");
+    RD_CUDA(cudaMemcpy2DAsync(us + 3 * have, row, t->u, mrow, mrow, np, kind, s), "stream u");
+    if (have > 0) {
+        RD_CUDA(cudaMemcpy2DAsync(xs, row, lx, one * have, one * have, np, cudaMemcpyDeviceToDevice, s), "stream x");
+        RD_CUDA(cudaMemcpy2DAsync(us, row, lu, one * have, one * have, np, cudaMemcpyDeviceToDevice, s), "stream u");
     }
     if (t->q) RD_CUDA(cudaMemcpyAsync(qs, t->q, sizeof(double) * np, kind, s), "stream q");
     rd_traj staged = *t;
@@ -859,14 +873,19 @@ rd_status rd_deposit_stream(rd_detector* d, const rd_traj* t, rd_stream stream)
     staged.u = us;
     staged.q = t->q ? qs : nullptr;
     staged.mem = RD_MEM_DEVICE;
-    staged.t0 = cont ? t->t0 - t->dt : t->t0;
-    st = rd_deposit_trajectories(d, &staged, stream);
+    staged.t0 = t->t0 - have * t->dt;
+    // intervals already deposited by earlier calls are not deposited again
+    st = deposit_from(d, &staged, stream, have > 1 ? 2 : 1);
     if (st != RD_OK) return st;
-    RD_CUDA(cudaMemcpy2DAsync(lx, one, xs + 3 * (size_t)(ns - 1), row, one, np, cudaMemcpyDeviceToDevice, s),
+    const int kept = std::min(keep, ns);
+    RD_CUDA(cudaMemcpy2DAsync(lx, one * kept, xs + 3 * (size_t)(ns - kept), row, one * kept, np,
+                              cudaMemcpyDeviceToDevice, s),
             "stream state");
-    RD_CUDA(cudaMemcpy2DAsync(lu, one, us + 3 * (size_t)(ns - 1), row, one, np, cudaMemcpyDeviceToDevice, s),
+    RD_CUDA(cudaMemcpy2DAsync(lu, one * kept, us + 3 * (size_t)(ns - kept), row, one * kept, np,
+                              cudaMemcpyDeviceToDevice, s),
             "stream state");
     d->strm_n_part = np;
+    d->strm_have = kept;
     d->strm_t_last = t->t0 + (double)(m - 1) * t->dt;
     d->strm_dt = t->dt;
     return RD_OK;

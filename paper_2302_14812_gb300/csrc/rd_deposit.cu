@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
     const int cb = (int)(rest % (unsigned)P.n_cell_blocks);
     const int c = (int)(rest / (unsigned)P.n_cell_blocks);
     const int S = P.n_samples - 1;
-    const int k_begin = 1 + c * P.chunk;
+    const int k_begin = P.k_first + c * P.chunk;
     const int k_end = min(S, k_begin + P.chunk - 1);
     const int n_int = k_end - k_begin + 1;
     const int n_tiles = (n_int + kTileSteps - 1) / kTileSteps;

@@ -79,6 +79,8 @@ struct DepositParams {
     int n_samples;              // S + 1
     int n_part;
     int chunk;                  // intervals per work item
+    int k_first;                // first interval deposited (1, or 2 for a streamed call that carries
+                                // two earlier samples)
     int n_chunks;               // ceil(S / chunk)
     int n_cell_blocks;          // ceil(n_pix / cells per CTA)
     float W;                    // mixed: bin width in units of dt (dt_det / dt)

@@ -453,7 +453,7 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
                                              unsigned& g_base)
 {
     const int S = P.n_samples - 1;
-    const int k_begin = 1 + ch * P.chunk;
+    const int k_begin = P.k_first + ch * P.chunk;
     const int k_end = min(S, k_begin + P.chunk - 1);
     const int n_int = k_end - k_begin + 1;
     const int n_tiles = (n_int + kTileSteps - 1) / kTileSteps;

@@ -133,6 +133,7 @@ extern "C" rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix
             P.n_samples = t->n_samples;
             P.n_part = np;
             P.chunk = chunk;
+            P.k_first = 1;
             P.n_chunks = (S + chunk - 1) / chunk;
             P.n_cell_blocks = n_cell_blocks;
             P.t0 = t->t0;

@@ -53,9 +53,15 @@ def _stretches(n, sizes):
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-6)])
 @pytest.mark.parametrize("where", ["device", "host"])
-def test_stream_equals_single_call(precision, tol, where):
+@pytest.mark.parametrize("linear", [False, True])
+def test_stream_equals_single_call(precision, tol, where, linear):
+    """Stretches of 1, 1, 7, 64, 1, 150, 3 and the rest; with RD_LINEAR the detector keeps two
+    samples per particle so that the first interval of every stretch is interpolated like the
+    others."""
     import torch
     tr, det = _case()
+    if linear:
+        det.flags = W.RD_NEAR | W.RD_FAR | W.RD_LINEAR
     ref = rd.RadiationDetector.from_workload(det, precision)
     ref.deposit(torch.from_numpy(tr.x).cuda(), torch.from_numpy(tr.u).cuda(), torch.from_numpy(tr.q).cuda(),
                 tr.t0, tr.dt)
