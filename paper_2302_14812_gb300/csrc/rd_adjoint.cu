@@ -82,9 +82,12 @@ __device__ __forceinline__ float warp_sum6(const float* v, int lane)
 
 // One interval k of one cell: forward field, gathered seed, VJP.  Returns in `out` the finished
 // gradient of sample k-1 (d/dx, d/dbeta) and keeps sample k's partial in c.pend.
-template <bool LAST>
+// EXACT = false (fast walk): an interval that passes two or more bin edges is not handled; the cell
+// is stopped instead (stop = true, its time becomes -inf and its outputs are discarded by the
+// caller until the tile is walked again with EXACT = true from its saved start).
+template <bool LAST, bool EXACT>
 __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointParams& P, float q,
-                                         float near, float far, int b_end, float f_end, float* out)
+                                         float near, float far, int b_end, float f_end, float* out, bool& stop)
 {
     const float W = P.W;
     // ---- forward: geometry, arrival increment, Eq. 1 ----
@@ -95,7 +98,8 @@ __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointP
     const float bx = nx + r.nbx, by = ny + r.nby, bz = nz + r.nbz;          // n - beta
     const float nb2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
     const float gg = fmaf(bx, r.d2x, fmaf(by, r.d2y, fmaf(bz, r.d2z, nb2 + r.gd)));
-    const float du = fmaf(r.dtg, rinv, gg) * fast_rcp(fmaf(c.Rpd, rinv, 1.f));
+    const float num = fmaf(r.dtg, rinv, gg);
+    const float rden = fast_rcp(fmaf(c.Rpd, rinv, 1.f));
     c.Rpd = fmaf(r2, rinv, P.dt_f);
     const float kap = fmaf(nb2, 0.5f, -r.nhig2);
     const float ik = fast_rcp(kap);
@@ -111,7 +115,7 @@ __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointP
     float gs0[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) gs0[i] = c.g[i];
-    const float fn = LAST ? fmaf((float)(b_end - c.b), W, f_end) : c.f + du;
+    const float fn = LAST ? fmaf((float)(b_end - c.b), W, f_end) : fmaf(num, rden, c.f);
     float G[6];
     if (fn < W) {
         const float w = (fn - c.f) * P.du_scale;
@@ -124,7 +128,11 @@ __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointP
         for (int i = 0; i < 6; ++i) G[i] = c.g[i] * w1;
         float rem = fn - W;
         c.b += 1;
-        if (rem >= W) {
+        if (!EXACT && rem >= W) {
+            stop = true;
+            rem = -INFINITY;
+        }
+        if (EXACT && rem >= W) {
             // whole bins inside the interval (bounded by the window)
             const float nf = floorf(rem * P.invW);
             const int nfull = (int)fminf(nf, 16777216.f);
@@ -205,6 +213,7 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
     __shared__ __align__(128) RecS tile[2][kTileSteps];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float red[kAdjointThreads / 32][kTileSteps][6];
+    __shared__ float sv[18][kAdjointThreads];
 
     const unsigned bid = blockIdx.x;
     const int p = (int)(bid % (unsigned)P.n_part);
@@ -285,17 +294,63 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
         const int k0 = k_begin + t * kTileSteps;
         const int cnt = min(kTileSteps, k_end - k0 + 1);
         const bool last_tile = (t == n_tiles - 1);
+        // walk state at the tile start: the exact walk restarts from it
+        sv[0][tid] = c.f;
+        sv[1][tid] = c.Rpd;
+        sv[2][tid] = __int_as_float(c.b);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            sv[3 + i][tid] = c.g[i];
+            sv[9 + i][tid] = c.pend[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) sv[15 + i][tid] = c.np[i];
+        int kstop = cnt;                              // step at which the fast walk stopped this cell
         for (int i = 0; i < cnt; ++i) {
             float out[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (live) {
+                bool st = false;
                 if (last_tile && i == cnt - 1)
-                    adj_step<true>(c, tile[buf][i], P, q, near, far, b_end, f_end, out);
+                    adj_step<true, false>(c, tile[buf][i], P, q, near, far, b_end, f_end, out, st);
                 else
-                    adj_step<false>(c, tile[buf][i], P, q, near, far, 0, 0.f, out);
+                    adj_step<false, false>(c, tile[buf][i], P, q, near, far, 0, 0.f, out, st);
+                kstop = (st && kstop == cnt) ? i : kstop;
             }
+#pragma unroll
+            for (int j = 0; j < 6; ++j) out[j] = i >= kstop ? 0.f : out[j];
             const float v = warp_sum6(out, lane);
             const int j = lane >> 2;
             if ((lane & 3) == 0 && j < 6) red[warp][i][j] = v;
+        }
+        if (__any_sync(0xffffffffu, kstop < cnt)) {
+            // some interval of this warp passed two or more bin edges: walk the tile again exactly and
+            // add the stopped cells' outputs from their stopping step on
+            c.f = sv[0][tid];
+            c.Rpd = sv[1][tid];
+            c.b = __float_as_int(sv[2][tid]);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                c.g[i] = sv[3 + i][tid];
+                c.pend[i] = sv[9 + i][tid];
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) c.np[i] = sv[15 + i][tid];
+#pragma unroll 1
+            for (int i = 0; i < cnt; ++i) {
+                float out[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (live) {
+                    bool st = false;
+                    if (last_tile && i == cnt - 1)
+                        adj_step<true, true>(c, tile[buf][i], P, q, near, far, b_end, f_end, out, st);
+                    else
+                        adj_step<false, true>(c, tile[buf][i], P, q, near, far, 0, 0.f, out, st);
+                }
+#pragma unroll
+                for (int j = 0; j < 6; ++j) out[j] = i >= kstop ? out[j] : 0.f;
+                const float v = warp_sum6(out, lane);
+                const int j = lane >> 2;
+                if ((lane & 3) == 0 && j < 6) red[warp][i][j] += v;
+            }
         }
         __syncthreads();
         // sample k0 - 1 + i gets the sum over the CTA's warps
