@@ -19,6 +19,9 @@ namespace rd {
 
 namespace {
 
+// Bin of a stopped cell: far below any window (and far enough from int32 limits for b_end - b).
+constexpr int kParkedBin = -(1 << 29);
+
 struct ACell {
     float Px, Py, Pz;
     float f;            // time spent in bin b, units of dt
@@ -83,8 +86,8 @@ __device__ __forceinline__ float warp_sum6(const float* v, int lane)
 // One interval k of one cell: forward field, gathered seed, VJP.  Returns in `out` the finished
 // gradient of sample k-1 (d/dx, d/dbeta) and keeps sample k's partial in c.pend.
 // EXACT = false (fast walk): an interval that passes two or more bin edges is not handled; the cell
-// is stopped instead (stop = true, its time becomes -inf and its outputs are discarded by the
-// caller until the tile is walked again with EXACT = true from its saved start).
+// is stopped instead (stop = true; it outputs zeros until the tile is walked again with EXACT = true
+// from its saved start).
 template <bool LAST, bool EXACT>
 __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointParams& P, float q,
                                          float near, float far, int b_end, float f_end, float* out, bool& stop)
@@ -129,8 +132,18 @@ __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointP
         float rem = fn - W;
         c.b += 1;
         if (!EXACT && rem >= W) {
+            // stop the cell for the rest of the tile: with its seeds and pending partials zero and its
+            // bin parked far below the window (seed loads there return zero), every output it makes
+            // from this step on is exactly zero
             stop = true;
-            rem = -INFINITY;
+            c.b = kParkedBin;
+            rem = 0.f;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                G[i] = 0.f;
+                gs0[i] = 0.f;
+                c.pend[i] = 0.f;
+            }
         }
         if (EXACT && rem >= W) {
             // whole bins inside the interval (bounded by the window)
@@ -316,8 +329,6 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
                     adj_step<false, false>(c, tile[buf][i], P, q, near, far, 0, 0.f, out, st);
                 kstop = (st && kstop == cnt) ? i : kstop;
             }
-#pragma unroll
-            for (int j = 0; j < 6; ++j) out[j] = i >= kstop ? 0.f : out[j];
             const float v = warp_sum6(out, lane);
             const int j = lane >> 2;
             if ((lane & 3) == 0 && j < 6) red[warp][i][j] = v;
