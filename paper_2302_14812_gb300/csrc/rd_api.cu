@@ -668,6 +668,17 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
     std::vector<int> group_first{0};          // group g = segs[group_first[g], group_first[g + 1])
     std::vector<long long> item_off{0};       // per segment, restarting at 0 in every group
     size_t used = 0, rec_need = 256;
+    // Step chunks: the persistent launch fills the GPU from all problems at once, so a small problem
+    // keeps full-length chunks (fewer FP64 anchors) unless the whole batch is too small to fill it.
+    long long items_full = 0;
+    for (int i = 0; i < n; ++i) {
+        const int S = trajs[i].n_samples - 1;
+        if (trajs[i].n_part == 0 || S < 1) continue;
+        const int ncb = (dets[i]->n_pix + kMixedCellsPerCta - 1) / kMixedCellsPerCta;
+        const int ck = dets[i]->chunk_override > 0 ? std::min(dets[i]->chunk_override, S) : std::min(kDefaultChunk, S);
+        items_full += (long long)ncb * trajs[i].n_part * ((S + ck - 1) / ck);
+    }
+    const bool full_chunks = items_full >= 152LL * 8;
     for (int i = 0; i < n; ++i) {
         const rd_traj& t = trajs[i];
         const int S = t.n_samples - 1;
@@ -675,7 +686,9 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
         const size_t per_part = sizeof(RecS) * (size_t)t.n_samples;
         const size_t budget = std::max(d0->batch_budget, per_part);
         const int ncb = (dets[i]->n_pix + kMixedCellsPerCta - 1) / kMixedCellsPerCta;
-        const int chunk = choose_chunk(dets[i], t.n_part, S, ncb);
+        const int chunk = full_chunks ? (dets[i]->chunk_override > 0 ? std::min(dets[i]->chunk_override, S)
+                                                                      : std::min(kDefaultChunk, S))
+                                      : choose_chunk(dets[i], t.n_part, S, ncb);
         for (int p0 = 0; p0 < t.n_part;) {
             if (budget - std::min(used, budget) < per_part) {      // close the group
                 group_first.push_back((int)segs.size());
