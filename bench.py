@@ -40,6 +40,8 @@ UNIT = "deposits/s"
 #                integrating accumulation into the running bin 17
 #   per bin edge crossed: starting the next bin with the rest of the interval 9
 FLOPS_PER_DEPOSIT_MIXED = 75
+WORKLOAD_UNDULATOR = ("undulator ensemble: 1000 e- (gamma 20, K 1, 10 periods) x 4000 steps, "
+                      "128x128-cell spherical cap at 1e4 periods x 2048 bins")
 FLOPS_PER_CROSSING_MIXED = 9
 # FP32 peak derived from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -230,8 +232,7 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": "undulator ensemble 1000 e- (gamma 20, K 1) x 4000 steps, 128x128 cells x 2048 bins",
-                   "sample": sample},
+        "config": {"workload": WORKLOAD_UNDULATOR, "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -602,8 +603,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "precision": "mixed: FP32 fields and accumulation, arrival times FP64-anchored per 1024-step chunk",
-        "config": {"workload": "undulator ensemble: 1000 e- (gamma 20, K 1, 10 periods) x 4000 steps, "
-                               "128x128-cell spherical cap at 1e4 periods x 2048 bins",
+        "config": {"workload": WORKLOAD_UNDULATOR,
                    "deposits_per_step_per_gpu": deposits, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (x,u 192 MB; records 256 MB; fields 1.07 GB)"},
         "gpu_launches": launches,
