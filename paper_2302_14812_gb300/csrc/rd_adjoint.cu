@@ -115,20 +115,18 @@ __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointP
     const float Bx = fmaf(ny, Ez, -nz * Ey), By = fmaf(nz, Ex, -nx * Ez), Bz = fmaf(nx, Ey, -ny * Ex);
 
     // ---- transpose of the integrating deposit: gathered seed and end-point seeds ----
-    float gs0[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) gs0[i] = c.g[i];
+    // F_k . g(bin(u_{k-1})): the seed of the bin the interval starts in
+    float a_beg = Ex * c.g[0] + Ey * c.g[1] + Ez * c.g[2] + Bx * c.g[3] + By * c.g[4] + Bz * c.g[5];
+    float a_end = a_beg;
     const float fn = LAST ? fmaf((float)(b_end - c.b), W, f_end) : fmaf(num, rden, c.f);
+    // the part of the interval inside bin b, then (on a crossing) the rest in the next bin(s)
+    const float w1 = (fminf(fn, W) - c.f) * P.du_scale;
     float G[6];
-    if (fn < W) {
-        const float w = (fn - c.f) * P.du_scale;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) G[i] = c.g[i] * w;
+    for (int i = 0; i < 6; ++i) G[i] = c.g[i] * w1;
+    if (fn < W) {
         c.f = fn;
     } else {
-        const float w1 = (W - c.f) * P.du_scale;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) G[i] = c.g[i] * w1;
         float rem = fn - W;
         c.b += 1;
         if (!EXACT && rem >= W) {
@@ -138,10 +136,10 @@ __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointP
             stop = true;
             c.b = kParkedBin;
             rem = 0.f;
+            a_beg = 0.f;
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
                 G[i] = 0.f;
-                gs0[i] = 0.f;
                 c.pend[i] = 0.f;
             }
         }
@@ -165,38 +163,43 @@ __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointP
 #pragma unroll
         for (int i = 0; i < 6; ++i) G[i] = fmaf(c.g[i], w2, G[i]);
         c.f = rem;
+        // F_k . g(bin(u_k))
+        a_end = Ex * c.g[0] + Ey * c.g[1] + Ez * c.g[2] + Bx * c.g[3] + By * c.g[4] + Bz * c.g[5];
     }
-    // F_k . g(bin(u_k)) and F_k . g(bin(u_{k-1}))
-    const float a_end = Ex * c.g[0] + Ey * c.g[1] + Ez * c.g[2] + Bx * c.g[3] + By * c.g[4] + Bz * c.g[5];
-    const float a_beg = Ex * gs0[0] + Ey * gs0[1] + Ez * gs0[2] + Bx * gs0[3] + By * gs0[4] + Bz * gs0[5];
 
     // ---- VJP of Eq. 1 with B = n x E, seed (GE, GB) = G ----
     const float GEx = G[0], GEy = G[1], GEz = G[2], GBx = G[3], GBy = G[4], GBz = G[5];
     // L = E.H + n.(E x GB),  H = GE + GB x n
-    const float Hx = GEx + (GBy * nz - GBz * ny), Hy = GEy + (GBz * nx - GBx * nz), Hz = GEz + (GBx * ny - GBy * nx);
-    float gnx = Ey * GBz - Ez * GBy, gny = Ez * GBx - Ex * GBz, gnz = Ex * GBy - Ey * GBx;
-    const float gsv = Vx * Hx + Vy * Hy + Vz * Hz;                 // d/ds
+    const float Hx = fmaf(GBy, nz, fmaf(-GBz, ny, GEx));
+    const float Hy = fmaf(GBz, nx, fmaf(-GBx, nz, GEy));
+    const float Hz = fmaf(GBx, ny, fmaf(-GBy, nx, GEz));
+    float gnx = fmaf(Ey, GBz, -Ez * GBy), gny = fmaf(Ez, GBx, -Ex * GBz), gnz = fmaf(Ex, GBy, -Ey * GBx);
+    const float gsv = fmaf(Vx, Hx, fmaf(Vy, Hy, Vz * Hz));         // d/ds
     const float gVx = s * Hx, gVy = s * Hy, gVz = s * Hz;          // d/dV
-    const float gc1 = bx * gVx + by * gVy + bz * gVz;             // d/dc1
-    const float gk = -(bdx * gVx + bdy * gVy + bdz * gVz) - 3.f * gsv * s * ik;   // d/dkappa
+    const float gc1 = fmaf(bx, gVx, fmaf(by, gVy, bz * gVz));      // d/dc1
+    const float gss = gsv * s;
+    // d/dkappa, with ds/dkappa = -3 s / kappa
+    const float gk = -fmaf(bdx, gVx, fmaf(bdy, gVy, fmaf(bdz, gVz, 3.f * gss * ik)));
     // V = (n - beta) c1 - kappa betadot;  c1 = gamma^-2/R + n.betadot;  kappa = 1 - n.beta
     const float betx = -r.nbx, bety = -r.nby, betz = -r.nbz;
-    gnx += c1 * gVx + gc1 * bdx - gk * betx;
-    gny += c1 * gVy + gc1 * bdy - gk * bety;
-    gnz += c1 * gVz + gc1 * bdz - gk * betz;
-    const float gig2 = gc1 * rinv * near;                          // d/d(gamma^-2), gamma^-2 = 1 - beta^2
-    const float gbetx = -c1 * gVx - gk * nx - 2.f * gig2 * betx;
-    const float gbety = -c1 * gVy - gk * ny - 2.f * gig2 * bety;
-    const float gbetz = -c1 * gVz - gk * nz - 2.f * gig2 * betz;
-    const float gbdx = (-kap * gVx + gc1 * nx) * far, gbdy = (-kap * gVy + gc1 * ny) * far,
-                gbdz = (-kap * gVz + gc1 * nz) * far;              // d/dbetadot
+    gnx = fmaf(c1, gVx, fmaf(gc1, bdx, fmaf(-gk, betx, gnx)));
+    gny = fmaf(c1, gVy, fmaf(gc1, bdy, fmaf(-gk, bety, gny)));
+    gnz = fmaf(c1, gVz, fmaf(gc1, bdz, fmaf(-gk, betz, gnz)));
+    const float g2 = -2.f * (gc1 * rinv * near);                  // d/d(gamma^-2) x (-2), gamma^-2 = 1 - beta^2
+    const float gbetx = fmaf(-c1, gVx, fmaf(-gk, nx, g2 * betx));
+    const float gbety = fmaf(-c1, gVy, fmaf(-gk, ny, g2 * bety));
+    const float gbetz = fmaf(-c1, gVz, fmaf(-gk, nz, g2 * betz));
+    const float kf = kap * far, gcf = gc1 * far;                   // d/dbetadot
+    const float gbdx = fmaf(gcf, nx, -kf * gVx), gbdy = fmaf(gcf, ny, -kf * gVy), gbdz = fmaf(gcf, nz, -kf * gVz);
     // R: s = q/(kappa^3 R), c1 contains gamma^-2/R, and the arrival time u_k contains R/dt_det
-    const float gR = -gsv * s * rinv - gc1 * r.ig2n * rinv * rinv + a_end * P.inv_dt_det_f;
-    // d = x_cell - x:  n = d/R, dR/dd = n
-    const float ndg = nx * gnx + ny * gny + nz * gnz;
-    const float gdx = (gnx - nx * ndg) * rinv + gR * nx;
-    const float gdy = (gny - ny * ndg) * rinv + gR * ny;
-    const float gdz = (gnz - nz * ndg) * rinv + gR * nz;
+    const float gR = fmaf(a_end, P.inv_dt_det_f, -(fmaf(gc1 * r.ig2n, rinv, gss) * rinv));
+    // d = x_cell - x:  n = d/R, dn/dd = (I - n n^T)/R, dR/dd = n, so
+    //   d/dd = gn/R + n (gR - n.gn/R)
+    const float ndg = fmaf(nx, gnx, fmaf(ny, gny, nz * gnz));
+    const float tn = fmaf(-ndg, rinv, gR);
+    const float gdx = fmaf(gnx, rinv, nx * tn);
+    const float gdy = fmaf(gny, rinv, ny * tn);
+    const float gdz = fmaf(gnz, rinv, nz * tn);
     const float inv_dt = P.inv_dt_f;
 
     // sample k-1: its arrival time starts this interval; betadot_k depends on beta_{k-1}
@@ -219,14 +222,48 @@ __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointP
     c.np[2] = nz;
 }
 
+
+constexpr int NA = kAdjointCells;
+constexpr int kSaveWords = 18;             // f, Rpd, b, g[6], pend[6], np[3]
+
+__device__ __forceinline__ void save_cell(const ACell& c, float (*sv)[kAdjointThreads], int tid)
+{
+    sv[0][tid] = c.f;
+    sv[1][tid] = c.Rpd;
+    sv[2][tid] = __int_as_float(c.b);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        sv[3 + i][tid] = c.g[i];
+        sv[9 + i][tid] = c.pend[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) sv[15 + i][tid] = c.np[i];
+}
+
+__device__ __forceinline__ void restore_cell(ACell& c, float (*sv)[kAdjointThreads], int tid)
+{
+    c.f = sv[0][tid];
+    c.Rpd = sv[1][tid];
+    c.b = __float_as_int(sv[2][tid]);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        c.g[i] = sv[3 + i][tid];
+        c.pend[i] = sv[9 + i][tid];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c.np[i] = sv[15 + i][tid];
+}
+
 }  // namespace
 
+// One CTA = (step chunk, block of kAdjointThreads x NA cells, particle); thread tid walks cells
+// tid + j kAdjointThreads of the block (j < NA), whose outputs it adds before the warp sum.
 __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_mixed(const AdjointParams P)
 {
     __shared__ __align__(128) RecS tile[2][kTileSteps];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float red[kAdjointThreads / 32][kTileSteps][6];
-    __shared__ float sv[18][kAdjointThreads];
+    __shared__ float sv[NA][kSaveWords][kAdjointThreads];
 
     const unsigned bid = blockIdx.x;
     const int p = (int)(bid % (unsigned)P.n_part);
@@ -240,7 +277,6 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
     const int n_tiles = (n_int + kTileSteps - 1) / kTileSteps;
     const RecS* rec = P.rec + (size_t)p * P.n_samples;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int cell = cb * kAdjointThreads + tid;
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -260,35 +296,42 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
     const float q = P.q ? (float)P.q[p] : 1.f;
     const float near = (P.flags & RD_NEAR) ? 1.f : 0.f, far = (P.flags & RD_FAR) ? 1.f : 0.f;
     const double* xp = P.x + (size_t)p * P.n_samples * 3;
-    ACell c;
-    bool live = false;
-    int b_end = 0;
-    float f_end = 0.f;
+    ACell c[NA];
+    bool live[NA];
+    int b_end[NA];
+    float f_end[NA];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) c.pend[i] = 0.f;
-    if (cell < P.n_pix) {
-        const D4 cl = P.cells[cell];
-        const double* xa = xp + 3 * (size_t)(k_begin - 1);
-        const double* xe = xp + 3 * (size_t)k_end;
-        double Ra, Re;
-        const double ua = arrival_bins(xa[0], xa[1], xa[2], cl, P.t0, k_begin - 1, P.dt, P.inv_dt_det, Ra);
-        const double ue = arrival_bins(xe[0], xe[1], xe[2], cl, P.t0, k_end, P.dt, P.inv_dt_det, Re);
-        live = (ue > 0.0) && (ua < (double)P.n_bins);
-        if (live) {
-            const double fa = floor(ua), fe = floor(ue);
-            c.b = clamp_bin(fa);
-            c.f = (float)(ua - fa) * P.W;
-            b_end = clamp_bin(fe);
-            f_end = (float)(ue - fe) * P.W;
-            c.Rpd = (float)Ra + P.dt_f;
-            c.Px = (float)cl.x;
-            c.Py = (float)cl.y;
-            c.Pz = (float)cl.z;
-            c.row = P.seed + (size_t)cell * P.n_bins * 8;
-            load_seed(c.row, P.n_bins, c.b, c.g);
-            c.np[0] = (float)((cl.x - xa[0]) / Ra);
-            c.np[1] = (float)((cl.y - xa[1]) / Ra);
-            c.np[2] = (float)((cl.z - xa[2]) / Ra);
+    for (int j = 0; j < NA; ++j) {
+        live[j] = false;
+        b_end[j] = 0;
+        f_end[j] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) c[j].pend[i] = 0.f;
+        const int cell = cb * kAdjointCellsPerCta + j * kAdjointThreads + tid;
+        if (cell < P.n_pix) {
+            const D4 cl = P.cells[cell];
+            const double* xa = xp + 3 * (size_t)(k_begin - 1);
+            const double* xe = xp + 3 * (size_t)k_end;
+            double Ra, Re;
+            const double ua = arrival_bins(xa[0], xa[1], xa[2], cl, P.t0, k_begin - 1, P.dt, P.inv_dt_det, Ra);
+            const double ue = arrival_bins(xe[0], xe[1], xe[2], cl, P.t0, k_end, P.dt, P.inv_dt_det, Re);
+            live[j] = (ue > 0.0) && (ua < (double)P.n_bins);
+            if (live[j]) {
+                const double fa = floor(ua), fe = floor(ue);
+                c[j].b = clamp_bin(fa);
+                c[j].f = (float)(ua - fa) * P.W;
+                b_end[j] = clamp_bin(fe);
+                f_end[j] = (float)(ue - fe) * P.W;
+                c[j].Rpd = (float)Ra + P.dt_f;
+                c[j].Px = (float)cl.x;
+                c[j].Py = (float)cl.y;
+                c[j].Pz = (float)cl.z;
+                c[j].row = P.seed + (size_t)cell * P.n_bins * 8;
+                load_seed(c[j].row, P.n_bins, c[j].b, c[j].g);
+                c[j].np[0] = (float)((cl.x - xa[0]) / Ra);
+                c[j].np[1] = (float)((cl.y - xa[1]) / Ra);
+                c[j].np[2] = (float)((cl.z - xa[2]) / Ra);
+            }
         }
     }
 
@@ -308,59 +351,54 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
         const int cnt = min(kTileSteps, k_end - k0 + 1);
         const bool last_tile = (t == n_tiles - 1);
         // walk state at the tile start: the exact walk restarts from it
-        sv[0][tid] = c.f;
-        sv[1][tid] = c.Rpd;
-        sv[2][tid] = __int_as_float(c.b);
+        int kstop[NA];                                // step at which the fast walk stopped each cell
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            sv[3 + i][tid] = c.g[i];
-            sv[9 + i][tid] = c.pend[i];
+        for (int j = 0; j < NA; ++j) {
+            save_cell(c[j], sv[j], tid);
+            kstop[j] = cnt;
         }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) sv[15 + i][tid] = c.np[i];
-        int kstop = cnt;                              // step at which the fast walk stopped this cell
         for (int i = 0; i < cnt; ++i) {
             float out[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (live) {
-                bool st = false;
-                if (last_tile && i == cnt - 1)
-                    adj_step<true, false>(c, tile[buf][i], P, q, near, far, b_end, f_end, out, st);
-                else
-                    adj_step<false, false>(c, tile[buf][i], P, q, near, far, 0, 0.f, out, st);
-                kstop = (st && kstop == cnt) ? i : kstop;
+            const RecS& r = tile[buf][i];
+#pragma unroll
+            for (int j = 0; j < NA; ++j) {
+                if (live[j]) {
+                    bool st = false;
+                    float o[6];
+                    if (last_tile && i == cnt - 1)
+                        adj_step<true, false>(c[j], r, P, q, near, far, b_end[j], f_end[j], o, st);
+                    else
+                        adj_step<false, false>(c[j], r, P, q, near, far, 0, 0.f, o, st);
+                    kstop[j] = (st && kstop[j] == cnt) ? i : kstop[j];
+#pragma unroll
+                    for (int e = 0; e < 6; ++e) out[e] = j == 0 ? o[e] : out[e] + o[e];
+                }
             }
             const float v = warp_sum6(out, lane);
-            const int j = lane >> 2;
-            if ((lane & 3) == 0 && j < 6) red[warp][i][j] = v;
+            const int e = lane >> 2;
+            if ((lane & 3) == 0 && e < 6) red[warp][i][e] = v;
         }
-        if (__any_sync(0xffffffffu, kstop < cnt)) {
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            if (!__any_sync(0xffffffffu, kstop[j] < cnt)) continue;
             // some interval of this warp passed two or more bin edges: walk the tile again exactly and
             // add the stopped cells' outputs from their stopping step on
-            c.f = sv[0][tid];
-            c.Rpd = sv[1][tid];
-            c.b = __float_as_int(sv[2][tid]);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                c.g[i] = sv[3 + i][tid];
-                c.pend[i] = sv[9 + i][tid];
-            }
-#pragma unroll
-            for (int i = 0; i < 3; ++i) c.np[i] = sv[15 + i][tid];
+            restore_cell(c[j], sv[j], tid);
 #pragma unroll 1
             for (int i = 0; i < cnt; ++i) {
                 float out[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                if (live) {
+                if (live[j]) {
                     bool st = false;
                     if (last_tile && i == cnt - 1)
-                        adj_step<true, true>(c, tile[buf][i], P, q, near, far, b_end, f_end, out, st);
+                        adj_step<true, true>(c[j], tile[buf][i], P, q, near, far, b_end[j], f_end[j], out, st);
                     else
-                        adj_step<false, true>(c, tile[buf][i], P, q, near, far, 0, 0.f, out, st);
+                        adj_step<false, true>(c[j], tile[buf][i], P, q, near, far, 0, 0.f, out, st);
                 }
 #pragma unroll
-                for (int j = 0; j < 6; ++j) out[j] = i >= kstop ? out[j] : 0.f;
+                for (int e = 0; e < 6; ++e) out[e] = i >= kstop[j] ? out[e] : 0.f;
                 const float v = warp_sum6(out, lane);
-                const int j = lane >> 2;
-                if ((lane & 3) == 0 && j < 6) red[warp][i][j] += v;
+                const int e = lane >> 2;
+                if ((lane & 3) == 0 && e < 6) red[warp][i][e] += v;
             }
         }
         __syncthreads();
@@ -387,12 +425,15 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
     }
     // the chunk's last sample keeps the partial of its last interval
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        const float v = warp_sum(live ? c.pend[j] : 0.f);
+    for (int e = 0; e < 6; ++e) {
+        float pv = 0.f;
+#pragma unroll
+        for (int j = 0; j < NA; ++j) pv += live[j] ? c[j].pend[e] : 0.f;
+        const float v = warp_sum(pv);
         if (lane == 0 && v != 0.f) {
             const size_t o = ((size_t)p * P.n_samples + (size_t)k_end) * 3;
-            if (j < 3) atomicAdd(P.gx + o + j, (double)v);
-            else atomicAdd(P.gbeta + o + (j - 3), (double)v);
+            if (e < 3) atomicAdd(P.gx + o + e, (double)v);
+            else atomicAdd(P.gbeta + o + (e - 3), (double)v);
         }
     }
 }

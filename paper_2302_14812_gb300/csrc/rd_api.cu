@@ -539,7 +539,7 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
     if (st != RD_OK) return st;
     st = ensure(&d->gbeta, &d->gbeta_bytes, per_part_gb * pc, s, "gradient scratch");
     if (st != RD_OK) return st;
-    const int n_cell_blocks = (d->n_pix + kAdjointThreads - 1) / kAdjointThreads;
+    const int n_cell_blocks = (d->n_pix + kAdjointCellsPerCta - 1) / kAdjointCellsPerCta;
     const int chunk = std::max(1, std::min(d->adjoint_chunk, S));
     for (int p0 = 0; p0 < t->n_part; p0 += pc) {
         const int np = std::min(pc, t->n_part - p0);

@@ -144,10 +144,15 @@ struct AdjointParams {
 #ifndef RD_ADJ_THREADS
 #define RD_ADJ_THREADS 128
 #endif
-#ifndef RD_ADJ_MINBLOCKS
-#define RD_ADJ_MINBLOCKS 6
+#ifndef RD_ADJ_CELLS
+#define RD_ADJ_CELLS 1
 #endif
-constexpr int kAdjointThreads = RD_ADJ_THREADS;   // one cell per thread
+#ifndef RD_ADJ_MINBLOCKS
+#define RD_ADJ_MINBLOCKS (RD_ADJ_CELLS == 1 ? 6 : 4)
+#endif
+constexpr int kAdjointThreads = RD_ADJ_THREADS;
+constexpr int kAdjointCells = RD_ADJ_CELLS;       // cells per thread
+constexpr int kAdjointCellsPerCta = kAdjointThreads * kAdjointCells;
 cudaError_t launch_pack_seed(const void* gE, const void* gB, int dtype, int n_pix, int n_bins, float* seed,
                              cudaStream_t s);
 cudaError_t launch_adjoint_mixed(const AdjointParams& p, cudaStream_t s);
