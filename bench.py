@@ -175,6 +175,27 @@ def profile_traffic():
     return float(m.group(1)) if h.group(1) == cur else None
 
 
+def host_link_gbs(host_out, host_in, reps: int = 3):
+    """Plain copy rates between pinned host memory and the device (GB/s), for reading the e2e number:
+    the readback of one field array (device -> host) and the upload of the positions (host -> device)."""
+    import torch
+    dev_out = torch.empty(host_out.shape, dtype=host_out.dtype, device="cuda")
+    dev_in = torch.empty(host_in.shape, dtype=host_in.dtype, device="cuda")
+    rates = {}
+    for name, dst, src in (("d2h_gbs", host_out, dev_out), ("h2d_gbs", dev_in, host_in)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        rates[name] = reps * src.numel() * src.element_size() / (e0.elapsed_time(e1) / 1e3) / 1e9
+    del dev_out, dev_in
+    return rates
+
+
 def oracle_rate(tr, det, target_s: float, sel_seed: int = 0):
     """Run the oracle on a bounded sample of cells (all particles and steps); returns
     (deposits/s, seconds, n_cells, threads, sel)."""
@@ -579,7 +600,8 @@ def main():
         e2e = {"value": deposits * world * args.steps / secs, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * secs / args.steps,
-               "pipeline": "2 detectors on 2 CUDA streams: copies of one step overlap the next step's deposit"}
+               "pipeline": "2 detectors on 2 CUDA streams: copies of one step overlap the next step's deposit",
+               "host_link": host_link_gbs(Ehs[0], xh)}
     mixed.close()
 
     # ---------------- FP64 CPU oracle on a bounded sample (rank 0, N = 1 only) ----------------

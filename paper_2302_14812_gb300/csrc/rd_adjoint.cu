@@ -83,6 +83,29 @@ __device__ __forceinline__ float warp_sum6(const float* v, int lane)
     return c;
 }
 
+// Sums over the warp's lanes of the outputs of ns <= kSub steps, staged as st[step][value][lane]:
+// lane r < 6 ns sums row r (step r / 6, value r % 6) into dst[r] (= red[warp][first step][0] + r).
+// Each lane reads its row as eight 16-byte chunks starting at a lane-dependent chunk, so that the
+// lanes of one load spread over all banks.
+constexpr int kSub = 4;
+
+__device__ __forceinline__ void sum_rows(const float (*st)[6][32], int ns, int lane, float* dst)
+{
+    if (lane < 6 * ns) {
+        const float4* row = reinterpret_cast<const float4*>(&st[lane / 6][lane % 6][0]);
+        float4 a = row[lane & 7];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) {
+            const float4 b = row[(q + lane) & 7];
+            a.x += b.x;
+            a.y += b.y;
+            a.z += b.z;
+            a.w += b.w;
+        }
+        dst[lane] = (a.x + a.y) + (a.z + a.w);
+    }
+}
+
 // One interval k of one cell: forward field, gathered seed, VJP.  Returns in `out` the finished
 // gradient of sample k-1 (d/dx, d/dbeta) and keeps sample k's partial in c.pend.
 // EXACT = false (fast walk): an interval that passes two or more bin edges is not handled; the cell
@@ -263,6 +286,7 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
     __shared__ __align__(128) RecS tile[2][kTileSteps];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float red[kAdjointThreads / 32][kTileSteps][6];
+    __shared__ __align__(16) float stage[kAdjointThreads / 32][kSub][6][32];
     __shared__ float sv[NA][kSaveWords][kAdjointThreads];
 
     const unsigned bid = blockIdx.x;
@@ -374,9 +398,16 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
                     for (int e = 0; e < 6; ++e) out[e] = j == 0 ? o[e] : out[e] + o[e];
                 }
             }
-            const float v = warp_sum6(out, lane);
-            const int e = lane >> 2;
-            if ((lane & 3) == 0 && e < 6) red[warp][i][e] = v;
+            // per-lane outputs to the warp's staging rows; every kSub steps (and at the tile's end)
+            // the warp sums them into red[warp]
+            const int sub = i & (kSub - 1);
+#pragma unroll
+            for (int e = 0; e < 6; ++e) stage[warp][sub][e][lane] = out[e];
+            if (sub == kSub - 1 || i == cnt - 1) {
+                __syncwarp();
+                sum_rows(stage[warp], sub + 1, lane, &red[warp][i - sub][0]);
+                __syncwarp();
+            }
         }
 #pragma unroll
         for (int j = 0; j < NA; ++j) {

@@ -81,6 +81,34 @@ __device__ __forceinline__ void flush(const Consts& C, int b, int bo, float e0, 
     }
 }
 
+// B of a bin.  Far-field limit: every sample of a cell has the same n_c and scale (1/R_c folded
+// into S, 1/R = 1), so B = n_c x E holds for each sample's weighted field and hence for the bin
+// sums: the walk carries E only and forms B when the bin is written.  Otherwise B is carried.
+template <bool FF>
+__device__ __forceinline__ void bin_b(const Cells& c, int j, const float* e, const float* carried, float* b)
+{
+    if (FF) {
+        b[0] = fmaf(c.py[j], e[2], -(c.pz[j] * e[1]));
+        b[1] = fmaf(c.pz[j], e[0], -(c.px[j] * e[2]));
+        b[2] = fmaf(c.px[j], e[1], -(c.py[j] * e[0]));
+    } else {
+        b[0] = carried[0];
+        b[1] = carried[1];
+        b[2] = carried[2];
+    }
+}
+
+// Add bin b of cell j from its accumulator.
+template <bool FF>
+__device__ __forceinline__ void flush_acc(const Consts& C, const Cells& c, int j, int b, int bo)
+{
+    const float e[3] = {c.acc[0][j], c.acc[1][j], c.acc[2][j]};
+    const float cb[3] = {c.acc[3][j], c.acc[4][j], c.acc[5][j]};
+    float bb[3];
+    bin_b<FF>(c, j, e, cb, bb);
+    flush(C, b, bo, e[0], e[1], e[2], bb[0], bb[1], bb[2]);
+}
+
 // Eq. 1 with B = n x E at one cell:
 //   E = q/(kappa^3 R) [ (n - beta)(gamma^-2/R + n.betadot) - betadot kappa ]
 //     = S E',  S = 1/(kappa^2 R),  E' = -q [(n - beta)(-c1/kappa) + betadot],  c1 = gamma^-2/R + n.betadot
@@ -151,7 +179,7 @@ __device__ __forceinline__ void field_at_ff(const RecS& r, float nx, float ny, f
 // Interval of cell j that passes two or more bin edges (rare): flush the bin being filled and the
 // whole bins inside the interval, leaving the state one edge short so that the common path below
 // finishes the step (it flushes the last whole bin and starts the next).
-template <bool TRACK>
+template <bool TRACK, bool FF>
 __device__ __forceinline__ void multi_edges(Cells& c, int j, const Field& o, const Consts& C, float& fn, int k,
                                             int k_begin, int k_end)
 {
@@ -159,7 +187,7 @@ __device__ __forceinline__ void multi_edges(Cells& c, int j, const Field& o, con
     if (!(f >= 2.f * C.W)) return;
     const int b0 = c.bo[j] - c.rb[j];
     const int m = (int)fminf(floorf(f * C.invW), 16777216.f);      // edges passed, >= 2
-    flush(C, b0, c.bo[j], c.acc[0][j], c.acc[1][j], c.acc[2][j], c.acc[3][j], c.acc[4][j], c.acc[5][j]);
+    flush_acc<FF>(C, c, j, b0, c.bo[j]);
     const float fs = C.W * o.S, fb = fs * o.rinv;
     // whole bins b0+1 .. b0+m-2 now; bin b0+m-1 is left in the accumulator for the common path
     const int lo = max(b0 + 1, 0), hi = min(b0 + m - 2, C.n_bins - 1);
@@ -168,7 +196,7 @@ __device__ __forceinline__ void multi_edges(Cells& c, int j, const Field& o, con
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         c.acc[i][j] = o.E[i] * fs;
-        c.acc[3 + i][j] = o.B[i] * fb;
+        if (!FF) c.acc[3 + i][j] = o.B[i] * fb;
     }
     c.bo[j] += m - 1;
     fn = fminf(fmaxf(fmaf(-(float)(m - 1), C.W, f), C.W), C.W * 1.99999988f);
@@ -195,16 +223,17 @@ __device__ __forceinline__ void scaled_field(const Field& o, float* G)
 // edges (exact walk only): flush the bin being filled, every whole bin, and leave the last, partial
 // bin in the accumulator with the time already in it; fn comes back below W (no edge left for the
 // common path).
-template <bool TRACK>
+template <bool TRACK, bool FF>
 __device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* dG, float L, float inv2L,
                                                 const Consts& C, float& fn, int k, int k_begin, int k_end)
 {
+    constexpr int NF = FF ? 3 : 6;                                  // carried field components
     const float f = fn;
     if (!(f >= 2.f * C.W)) return;
     const float f0 = c.f[j];
     const int b0 = c.bo[j] - c.rb[j];
     const int m = (int)fminf(floorf(f * C.invW), 16777216.f);      // edges passed, >= 2
-    flush(C, b0, c.bo[j], c.acc[0][j], c.acc[1][j], c.acc[2][j], c.acc[3][j], c.acc[4][j], c.acc[5][j]);
+    flush_acc<FF>(C, c, j, b0, c.bo[j]);
     // whole bins b0+i, i = 1..m-1, cover [i W, (i+1) W] from the start of bin b0
     const int lo = max(1, -b0), hi = min(m - 1, C.n_bins - 1 - b0);
     for (int i = lo; i <= hi; ++i) {
@@ -212,7 +241,8 @@ __device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* dG
         const float ramp = (s1 * s1 - s0 * s0) * inv2L;
         float v[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) v[q] = fmaf(c.gp[q][j], C.W, dG[q] * ramp);
+        for (int q = 0; q < NF; ++q) v[q] = fmaf(c.gp[q][j], C.W, dG[q] * ramp);
+        bin_b<FF>(c, j, v, v + 3, v + 3);
         flush(C, b0 + i, c.bo[j] + i, v[0], v[1], v[2], v[3], v[4], v[5]);
     }
     // bin b0+m holds [m W, f]
@@ -220,7 +250,7 @@ __device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* dG
     const float len = fmaf(-(float)m, C.W, f);
     const float ramp = (L * L - s0 * s0) * inv2L;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) c.acc[q][j] = fmaf(c.gp[q][j], len, dG[q] * ramp);
+    for (int q = 0; q < NF; ++q) c.acc[q][j] = fmaf(c.gp[q][j], len, dG[q] * ramp);
     c.bo[j] += m;
     fn = fminf(fmaxf(len, 0.f), C.W * 0.99999994f);
     if (TRACK) {
@@ -247,6 +277,7 @@ template <int MODE, bool LAST, bool TRACK, bool FF, bool LIN>
 __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, const int* bo_end,
                                      const float* f_end, int k, int k_begin, int k_end, bool* ok)
 {
+    constexpr int NF = FF ? 3 : 6;                  // carried field components (far field: E only)
     Field o[NC];
     float fn[NC];
     float G[NC][6], dG[NC][6], L[NC], inv2L[NC], ramp1[NC];     // linear interpolation only
@@ -270,7 +301,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
             const float len1 = fminf(t, C.W) - c.f[j];
             ramp1[j] = (len1 * len1) * inv2L[j];
 #pragma unroll
-            for (int i = 0; i < 6; ++i) {
+            for (int i = 0; i < NF; ++i) {
                 dG[j][i] = G[j][i] - c.gp[i][j];
                 c.acc[i][j] = fmaf(c.gp[i][j], len1, fmaf(dG[j][i], ramp1[j], c.acc[i][j]));
             }
@@ -280,7 +311,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 c.acc[i][j] = fmaf(o[j].E[i], ws, c.acc[i][j]);
-                c.acc[3 + i][j] = fmaf(o[j].B[i], wb, c.acc[3 + i][j]);
+                if (!FF) c.acc[3 + i][j] = fmaf(o[j].B[i], wb, c.acc[3 + i][j]);
             }
         }
         if (MODE == kFast)
@@ -293,9 +324,9 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             if (LIN)
-                multi_edges_lin<TRACK>(c, j, dG[j], L[j], inv2L[j], C, fn[j], k, k_begin, k_end);
+                multi_edges_lin<TRACK, FF>(c, j, dG[j], L[j], inv2L[j], C, fn[j], k, k_begin, k_end);
             else
-                multi_edges<TRACK>(c, j, o[j], C, fn[j], k, k_begin, k_end);
+                multi_edges<TRACK, FF>(c, j, o[j], C, fn[j], k, k_begin, k_end);
         }
     }
 #pragma unroll
@@ -305,20 +336,24 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
         if (MODE == kFast && !TRACK) {
             if (cr) {
                 float* a = bin_addr(C, c.bo[j]);
-                red_add_v4(a, c.acc[0][j], c.acc[1][j], c.acc[2][j], c.acc[3][j]);
-                red_add_v2(a + 4, c.acc[4][j], c.acc[5][j]);
+                const float e[3] = {c.acc[0][j], c.acc[1][j], c.acc[2][j]};
+                const float cb[3] = {c.acc[3][j], c.acc[4][j], c.acc[5][j]};
+                float bb[3];
+                bin_b<FF>(c, j, e, cb, bb);
+                red_add_v4(a, e[0], e[1], e[2], bb[0]);
+                red_add_v2(a + 4, bb[1], bb[2]);
                 const float rem = fn[j] - C.W;
                 if (LIN) {
                     const float ramp2 = fmaf(0.5f, L[j], -ramp1[j]);
 #pragma unroll
-                    for (int i = 0; i < 6; ++i) c.acc[i][j] = fmaf(c.gp[i][j], rem, dG[j][i] * ramp2);
+                    for (int i = 0; i < NF; ++i) c.acc[i][j] = fmaf(c.gp[i][j], rem, dG[j][i] * ramp2);
                 } else {
                     const float rs = rem * o[j].S;
                     const float rbw = rs * o[j].rinv;
 #pragma unroll
                     for (int i = 0; i < 3; ++i) {
                         c.acc[i][j] = o[j].E[i] * rs;
-                        c.acc[3 + i][j] = o[j].B[i] * rbw;
+                        if (!FF) c.acc[3 + i][j] = o[j].B[i] * rbw;
                     }
                 }
                 c.f[j] = rem;
@@ -331,13 +366,17 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
             const bool go = MODE == kFast || !ok[j];
             const bool pr = cr && go && (!TRACK || (unsigned)b < (unsigned)C.n_bins);
             float* a = bin_addr(C, c.bo[j]);
-            red_add_v4_if(pr, a, c.acc[0][j], c.acc[1][j], c.acc[2][j], c.acc[3][j]);
-            red_add_v2_if(pr, a + 4, c.acc[4][j], c.acc[5][j]);
+            const float e[3] = {c.acc[0][j], c.acc[1][j], c.acc[2][j]};
+            const float cb[3] = {c.acc[3][j], c.acc[4][j], c.acc[5][j]};
+            float bb[3];
+            bin_b<FF>(c, j, e, cb, bb);
+            red_add_v4_if(pr, a, e[0], e[1], e[2], bb[0]);
+            red_add_v2_if(pr, a + 4, bb[1], bb[2]);
             const float rem = fn[j] - C.W;
             if (LIN) {
                 const float ramp2 = fmaf(0.5f, L[j], -ramp1[j]);
 #pragma unroll
-                for (int i = 0; i < 6; ++i) {
+                for (int i = 0; i < NF; ++i) {
                     const float v = fmaf(c.gp[i][j], rem, dG[j][i] * ramp2);
                     c.acc[i][j] = cr ? v : c.acc[i][j];
                 }
@@ -347,7 +386,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
                     c.acc[i][j] = cr ? o[j].E[i] * rs : c.acc[i][j];
-                    c.acc[3 + i][j] = cr ? o[j].B[i] * rbw : c.acc[3 + i][j];
+                    if (!FF) c.acc[3 + i][j] = cr ? o[j].B[i] * rbw : c.acc[3 + i][j];
                 }
             }
             c.f[j] = cr ? rem : fn[j];
@@ -359,7 +398,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
         }
         if (LIN) {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) c.gp[i][j] = G[j][i];
+            for (int i = 0; i < NF; ++i) c.gp[i][j] = G[j][i];
         }
     }
 }
@@ -373,9 +412,10 @@ constexpr int kUnroll = RD_UNROLL > 0 ? RD_UNROLL : 1;   // samples per loop ite
 constexpr int kSaveCell = 17;               // f, rpd, bo, below, above, acc[6], gp[6]
 constexpr int kSaveWords = NC * kSaveCell;
 
-template <bool LIN>
+template <bool FF, bool LIN>
 __device__ __forceinline__ void save_state(const Cells& c, float (*sv)[kMixedThreads], int tid)
 {
+    constexpr int NF = FF ? 3 : 6;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         sv[j * kSaveCell + 0][tid] = c.f[j];
@@ -384,17 +424,18 @@ __device__ __forceinline__ void save_state(const Cells& c, float (*sv)[kMixedThr
         sv[j * kSaveCell + 3][tid] = __int_as_float(c.below[j]);
         sv[j * kSaveCell + 4][tid] = __int_as_float(c.above[j]);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) sv[j * kSaveCell + 5 + i][tid] = c.acc[i][j];
+        for (int i = 0; i < NF; ++i) sv[j * kSaveCell + 5 + i][tid] = c.acc[i][j];
         if (LIN) {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) sv[j * kSaveCell + 11 + i][tid] = c.gp[i][j];
+            for (int i = 0; i < NF; ++i) sv[j * kSaveCell + 11 + i][tid] = c.gp[i][j];
         }
     }
 }
 
-template <bool LIN>
+template <bool FF, bool LIN>
 __device__ __forceinline__ void restore_state(Cells& c, float (*sv)[kMixedThreads], int tid)
 {
+    constexpr int NF = FF ? 3 : 6;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         c.f[j] = sv[j * kSaveCell + 0][tid];
@@ -403,10 +444,10 @@ __device__ __forceinline__ void restore_state(Cells& c, float (*sv)[kMixedThread
         c.below[j] = __float_as_int(sv[j * kSaveCell + 3][tid]);
         c.above[j] = __float_as_int(sv[j * kSaveCell + 4][tid]);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) c.acc[i][j] = sv[j * kSaveCell + 5 + i][tid];
+        for (int i = 0; i < NF; ++i) c.acc[i][j] = sv[j * kSaveCell + 5 + i][tid];
         if (LIN) {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) c.gp[i][j] = sv[j * kSaveCell + 11 + i][tid];
+            for (int i = 0; i < NF; ++i) c.gp[i][j] = sv[j * kSaveCell + 11 + i][tid];
         }
     }
 }
@@ -418,7 +459,7 @@ __device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, b
 {
     const int tid = threadIdx.x;
     const int n_regular = last_tile ? cnt - 1 : cnt;
-    save_state<LIN>(c, sv, tid);
+    save_state<FF, LIN>(c, sv, tid);
     bool ok[NC];
 #pragma unroll kUnroll
     for (int i = 0; i < n_regular; ++i)
@@ -430,7 +471,7 @@ __device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, b
     for (int j = 0; j < NC; ++j) stopped = stopped || c.f[j] == -INFINITY;
     if (__any_sync(0xffffffffu, stopped)) {
         // some interval of a cell of this warp passed two or more bin edges: walk the tile again
-        restore_state<LIN>(c, sv, tid);
+        restore_state<FF, LIN>(c, sv, tid);
 #pragma unroll
         for (int j = 0; j < NC; ++j) ok[j] = true;
 #pragma unroll 1
@@ -563,7 +604,7 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
             float G[6];
             scaled_field(o, G);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) c.gp[i][j] = G[i];
+            for (int i = 0; i < 6; ++i) c.gp[i][j] = G[i];      // far field: only E is read
         }
     }
     const bool track = __syncthreads_or(partial) != 0;
@@ -603,8 +644,7 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         if (c.live[j]) {
-            flush(C, c.bo[j] - c.rb[j], c.bo[j], c.acc[0][j], c.acc[1][j], c.acc[2][j], c.acc[3][j], c.acc[4][j],
-                  c.acc[5][j]);
+            flush_acc<FF>(C, c, j, c.bo[j] - c.rb[j], c.bo[j]);
             clip += (unsigned long long)min(n_int, c.below[j] + c.above[j]);
         }
     }
