@@ -83,16 +83,15 @@ __device__ __forceinline__ float warp_sum6(const float* v, int lane)
     return c;
 }
 
-// Sums over the warp's lanes of the outputs of ns <= kSub steps, staged as st[step][value][lane]:
-// lane r < 6 ns sums row r (step r / 6, value r % 6) into dst[r] (= red[warp][first step][0] + r).
-// Each lane reads its row as eight 16-byte chunks starting at a lane-dependent chunk, so that the
-// lanes of one load spread over all banks.
+// Sums over the warp's lanes of the outputs of ns <= kSub steps, staged as [step][value][lane]:
+// lane r < 6 ns sums row r (step r / 6, value r % 6; `row` points at it) into dst[r]
+// (= red[warp][first step][0] + r).  Each lane reads its row as eight 16-byte chunks starting at a
+// lane-dependent chunk, so that the lanes of one load spread over all banks.
 constexpr int kSub = 4;
 
-__device__ __forceinline__ void sum_rows(const float (*st)[6][32], int ns, int lane, float* dst)
+__device__ __forceinline__ void sum_rows(const float4* row, int ns, int lane, float* dst)
 {
     if (lane < 6 * ns) {
-        const float4* row = reinterpret_cast<const float4*>(&st[lane / 6][lane % 6][0]);
         float4 a = row[lane & 7];
 #pragma unroll
         for (int q = 1; q < 8; ++q) {
@@ -321,16 +320,25 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
     const float near = (P.flags & RD_NEAR) ? 1.f : 0.f, far = (P.flags & RD_FAR) ? 1.f : 0.f;
     const double* xp = P.x + (size_t)p * P.n_samples * 3;
     ACell c[NA];
-    bool live[NA];
     int b_end[NA];
     float f_end[NA];
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
-        live[j] = false;
+        // a cell with no arrival in the window (or past the last cell) walks the same steps from a
+        // time that never reaches a bin edge, with zero seeds and partials: all its outputs are
+        // exactly zero, and the step needs no per-cell branch
+        c[j].b = 0;
+        c[j].f = -1e30f;
         b_end[j] = 0;
-        f_end[j] = 0.f;
+        f_end[j] = -1e30f;
+        c[j].Rpd = 1e6f;
+        c[j].Px = 1e6f;
+        c[j].Py = c[j].Pz = 0.f;
+        c[j].row = P.seed;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) c[j].pend[i] = 0.f;
+        for (int i = 0; i < 6; ++i) c[j].pend[i] = c[j].g[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) c[j].np[i] = 0.f;
         const int cell = cb * kAdjointCellsPerCta + j * kAdjointThreads + tid;
         if (cell < P.n_pix) {
             const D4 cl = P.cells[cell];
@@ -339,8 +347,7 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
             double Ra, Re;
             const double ua = arrival_bins(xa[0], xa[1], xa[2], cl, P.t0, k_begin - 1, P.dt, P.inv_dt_det, Ra);
             const double ue = arrival_bins(xe[0], xe[1], xe[2], cl, P.t0, k_end, P.dt, P.inv_dt_det, Re);
-            live[j] = (ue > 0.0) && (ua < (double)P.n_bins);
-            if (live[j]) {
+            if ((ue > 0.0) && (ua < (double)P.n_bins)) {
                 const double fa = floor(ua), fe = floor(ue);
                 c[j].b = clamp_bin(fa);
                 c[j].f = (float)(ua - fa) * P.W;
@@ -359,6 +366,8 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
         }
     }
 
+    float* const my_stage = &stage[warp][0][0][lane];                     // + (step * 6 + value) * 32
+    const float4* const my_row = reinterpret_cast<const float4*>(&stage[warp][0][0][0]) + 8 * lane;
     for (int t = 0; t < n_tiles; ++t) {
         const int buf = t & 1;
         const bool ok = mbar_wait_bounded(&bar[buf], (unsigned)(t >> 1) & 1u);
@@ -382,30 +391,28 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
             kstop[j] = cnt;
         }
         for (int i = 0; i < cnt; ++i) {
-            float out[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float out[6];
             const RecS& r = tile[buf][i];
 #pragma unroll
             for (int j = 0; j < NA; ++j) {
-                if (live[j]) {
-                    bool st = false;
-                    float o[6];
-                    if (last_tile && i == cnt - 1)
-                        adj_step<true, false>(c[j], r, P, q, near, far, b_end[j], f_end[j], o, st);
-                    else
-                        adj_step<false, false>(c[j], r, P, q, near, far, 0, 0.f, o, st);
-                    kstop[j] = (st && kstop[j] == cnt) ? i : kstop[j];
+                bool st = false;
+                float o[6];
+                if (last_tile && i == cnt - 1)
+                    adj_step<true, false>(c[j], r, P, q, near, far, b_end[j], f_end[j], o, st);
+                else
+                    adj_step<false, false>(c[j], r, P, q, near, far, 0, 0.f, o, st);
+                kstop[j] = (st && kstop[j] == cnt) ? i : kstop[j];
 #pragma unroll
-                    for (int e = 0; e < 6; ++e) out[e] = j == 0 ? o[e] : out[e] + o[e];
-                }
+                for (int e = 0; e < 6; ++e) out[e] = j == 0 ? o[e] : out[e] + o[e];
             }
             // per-lane outputs to the warp's staging rows; every kSub steps (and at the tile's end)
             // the warp sums them into red[warp]
             const int sub = i & (kSub - 1);
 #pragma unroll
-            for (int e = 0; e < 6; ++e) stage[warp][sub][e][lane] = out[e];
+            for (int e = 0; e < 6; ++e) my_stage[(sub * 6 + e) * 32] = out[e];
             if (sub == kSub - 1 || i == cnt - 1) {
                 __syncwarp();
-                sum_rows(stage[warp], sub + 1, lane, &red[warp][i - sub][0]);
+                sum_rows(my_row, sub + 1, lane, &red[warp][i - sub][0]);
                 __syncwarp();
             }
         }
@@ -417,14 +424,12 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
             restore_cell(c[j], sv[j], tid);
 #pragma unroll 1
             for (int i = 0; i < cnt; ++i) {
-                float out[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                if (live[j]) {
-                    bool st = false;
-                    if (last_tile && i == cnt - 1)
-                        adj_step<true, true>(c[j], tile[buf][i], P, q, near, far, b_end[j], f_end[j], out, st);
-                    else
-                        adj_step<false, true>(c[j], tile[buf][i], P, q, near, far, 0, 0.f, out, st);
-                }
+                float out[6];
+                bool st = false;
+                if (last_tile && i == cnt - 1)
+                    adj_step<true, true>(c[j], tile[buf][i], P, q, near, far, b_end[j], f_end[j], out, st);
+                else
+                    adj_step<false, true>(c[j], tile[buf][i], P, q, near, far, 0, 0.f, out, st);
 #pragma unroll
                 for (int e = 0; e < 6; ++e) out[e] = i >= kstop[j] ? out[e] : 0.f;
                 const float v = warp_sum6(out, lane);
@@ -459,7 +464,7 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
     for (int e = 0; e < 6; ++e) {
         float pv = 0.f;
 #pragma unroll
-        for (int j = 0; j < NA; ++j) pv += live[j] ? c[j].pend[e] : 0.f;
+        for (int j = 0; j < NA; ++j) pv += c[j].pend[e];
         const float v = warp_sum(pv);
         if (lane == 0 && v != 0.f) {
             const size_t o = ((size_t)p * P.n_samples + (size_t)k_end) * 3;
