@@ -196,6 +196,36 @@ def test_empty_and_degenerate_inputs():
         d.close()
 
 
+def test_mixed_maximum_bins_per_cell():
+    """RD_MIXED at its largest row (2^22 bins) with a full 256-cell block, so that field offsets
+    (row * n_bins + bin) reach 2^30 - 1.  Every cell's arrivals lie in the last few thousand bins;
+    for odd cells they run past the window's end (clipped there).  Intervals span 1-15 bins (the
+    exact re-walk handles them).  Cells at both ends of both halves of the block against the
+    oracle; device-side readback (the detector holds 34 GB)."""
+    import torch
+    n_bins = 1 << 22
+    tr = W.random_smooth(2, 200, 0.02, max_u=2.0, seed=21)
+    pos = W.spherical_cap(16, 12.0, 0.6)
+    t = tr.t0 + tr.dt * np.arange(tr.n_samples)
+    arr = t[None, None, :] + np.linalg.norm(pos[:, None, None, :] - tr.x[None], axis=-1)
+    dt_det = 2.5e-3
+    first = np.where(np.arange(pos.shape[0]) % 2 == 0, n_bins - 3500, n_bins - 1500)
+    det = W.Detector(pos, arr.min(axis=(1, 2)) - first * dt_det, 0.0, dt_det, n_bins)
+    d = rd.RadiationDetector.from_workload(det, "mixed")
+    d.deposit(torch.from_numpy(tr.x).cuda(), torch.from_numpy(tr.u).cuda(), torch.from_numpy(tr.q).cuda(),
+              tr.t0, tr.dt)
+    assert d.stats().n_clipped > 0
+    E, B = d.read("float32", "cuda")
+    sel = np.array([0, 1, 127, 128, 254, 255], dtype=np.int32)
+    Eg = E[torch.from_numpy(sel).long().cuda()].double().cpu().numpy()
+    Bg = B[torch.from_numpy(sel).long().cuda()].double().cpu().numpy()
+    del E, B
+    d.close()
+    Eo, Bo, _ = oracle.deposit(tr, det, sel)
+    assert np.any(Eo[:, -1] != 0.0)                   # odd cells reach the last bin
+    assert rel_l2(Eg, Eo) <= TOL["mixed"] and rel_l2(Bg, Bo) <= TOL["mixed"]
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_window_entirely_missed_counts_clipped(precision):
     tr = W.random_smooth(2, 90, 0.03, seed=8)
