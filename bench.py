@@ -40,11 +40,15 @@ UNIT = "deposits/s"
 #                integrating accumulation into the running bin 17
 #   per bin edge crossed: starting the next bin with the rest of the interval 9
 FLOPS_PER_DEPOSIT_MIXED = 75
-WORKLOAD_UNDULATOR = ("undulator ensemble: 1000 e- (gamma 20, K 1, 10 periods) x 4000 steps, "
-                      "128x128-cell spherical cap at 1e4 periods x 2048 bins")
 FLOPS_PER_CROSSING_MIXED = 9
+# FP64 operations of the plain kernel per deposit, counted from its source the same way (square
+# root, division and floor count 1 each): arrival time (Eq. 2) 14, Eq. 1 with B = n x E 64,
+# accumulation into the running bin 14.
+FLOPS_PER_DEPOSIT_FP64 = 92
 # FP32 peak derived from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+WORKLOAD_UNDULATOR = ("undulator ensemble: 1000 e- (gamma 20, K 1, 10 periods) x 4000 steps, "
+                      "128x128-cell spherical cap at 1e4 periods x 2048 bins")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "deposit_mixed_undulator_ncu.md")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2302_14812_gb300", "csrc", "rd_mixed.cu")
 
@@ -529,7 +533,9 @@ def main():
         rel_b = float(np.linalg.norm(B_mixed - B64) / np.linalg.norm(B64))
         fp64_info = {"value": deposits * world / (ms64 / 1e3), "ms_per_step": ms64,
                      "speedup_mixed_vs_fp64": ms64 / ms_step,
-                     "mixed_rel_l2_vs_fp64_gpu": {"E": rel_e, "B": rel_b}}
+                     "mixed_rel_l2_vs_fp64_gpu": {"E": rel_e, "B": rel_b},
+                     "achieved_fp64_tflops": FLOPS_PER_DEPOSIT_FP64 * deposits / (ms64 / 1e3) / 1e12,
+                     "flops_per_deposit": FLOPS_PER_DEPOSIT_FP64}
         f64.close()
         del E64, B64
 
@@ -616,6 +622,13 @@ def main():
                   "mixed_rel_l2_E": float(np.linalg.norm(E_mixed[sel] - Eo) / np.linalg.norm(Eo)),
                   "mixed_rel_l2_B": float(np.linalg.norm(B_mixed[sel] - Bo) / np.linalg.norm(Bo))}
 
+    # measured FMA throughput of this GPU (after the timed regions): a second denominator beside the
+    # derived FP32 peak, and the FP64 one for the plain path
+    fma32, fma64 = rd.rd_measure_fma_peaks()
+    if fp64_info is not None:
+        fp64_info["peak_measured_fma_tflops"] = fma64
+        fp64_info["frac_of_measured"] = fp64_info["achieved_fp64_tflops"] / fma64 if fma64 > 0 else None
+
     crossings = st.n_bin_crossings            # of the last timed step (each step starts from zero)
     flops_step = FLOPS_PER_DEPOSIT_MIXED * deposits + FLOPS_PER_CROSSING_MIXED * crossings
     achieved = flops_step / (kernel_ms / 1e3) / 1e12
@@ -632,6 +645,7 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_deposit_mixed", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "peak_measured_fma": fma32, "frac_of_measured_fma": achieved / fma32 if fma32 > 0 else None,
                      "kernel_ms": kernel_ms, "flops_per_deposit": FLOPS_PER_DEPOSIT_MIXED,
                      "flops_per_crossing": FLOPS_PER_CROSSING_MIXED, "bin_crossings_per_step": crossings,
                      "traffic": traffic},

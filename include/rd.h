@@ -300,6 +300,16 @@ RD_API rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix_t0,
                                     const rd_traj* traj, float* fields, uint32_t* errors,
                                     rd_stream stream);
 
+/*
+ * Diagnostic, not part of the deposit: the FP32 and FP64 fused multiply-add throughput of the
+ * current device, measured by a microbenchmark (independent FMA chains on every SM, one launch
+ * of about 20 ms per precision, timed with CUDA events on `stream`).  These are the denominators
+ * of the roofline of the deposit kernels, which are bound by FP32 (RD_MIXED) and FP64 (RD_FP64)
+ * arithmetic.  Results in TFLOP/s (one FMA = 2 flops); either pointer may be NULL to skip that
+ * precision.  Synchronous; allocates and frees a few KB of device memory.
+ */
+RD_API rd_status rd_measure_fma_peaks(double* fp32_tflops, double* fp64_tflops, rd_stream stream);
+
 /* Message for the last failing call on this thread ("" if none).  Valid until the next call. */
 RD_API const char* rd_last_error(void);
 

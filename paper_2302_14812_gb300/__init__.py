@@ -27,7 +27,7 @@ __all__ = [
     "rd_deposit_trajectories", "rd_read_fields", "rd_synchronize", "rd_get_stats",
     "rd_set_timing", "rd_adjoint_trajectories", "rd_deposit_batch", "rd_set_chunk", "rd_autotune",
     "rd_set_batch_budget", "rd_power_spectrum", "rd_deposit_stream", "rd_stream_reset",
-    "rd_deposit_noalloc", "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
+    "rd_deposit_noalloc", "rd_measure_fma_peaks", "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
 ]
 
 RD_OK, RD_ERR_ARG, RD_ERR_CUDA, RD_ERR_OOM, RD_ERR_STATE, RD_ERR_TIMEOUT, RD_ERR_BOUNDS, RD_ERR_INPUT = range(8)
@@ -106,6 +106,7 @@ def load_library(build_if_missing: bool = True):
             "rd_autotune": ([P, ctypes.POINTER(rd_traj), P, ctypes.POINTER(I)], I),
             "rd_deposit_noalloc": ([P, P, I, ctypes.c_double, ctypes.c_double, I, I, ctypes.POINTER(rd_traj), P,
                                     ctypes.POINTER(ctypes.c_uint32), P], I),
+            "rd_measure_fma_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P], I),
             "rd_last_error": ([], ctypes.c_char_p),
             "rd_version": ([], ctypes.c_char_p),
         }
@@ -231,6 +232,15 @@ def rd_deposit_noalloc(pix_pos_ptr, pix_t0_ptr, n_pix: int, t_min: float, dt_det
 
 def rd_set_timing(det: int, enable: bool) -> None:
     _check(load_library().rd_set_timing(det, 1 if enable else 0), "rd_set_timing")
+
+
+def rd_measure_fma_peaks(stream=None):
+    """(FP32, FP64) fused multiply-add throughput of the current device in TFLOP/s, measured by
+    the library's microbenchmark (diagnostic; one FMA = 2 flops)."""
+    f32, f64 = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    lib = load_library()
+    _check(lib.rd_measure_fma_peaks(ctypes.byref(f32), ctypes.byref(f64), _stream_ptr(stream)), "rd_measure_fma_peaks")
+    return f32.value, f64.value
 
 
 def rd_last_error() -> str:

@@ -235,6 +235,16 @@ const char* rd_last_error(void) { return g_err.c_str(); }
 
 const char* rd_version(void) { return "rd 0.1 (sm_103a)"; }
 
+rd_status rd_measure_fma_peaks(double* fp32_tflops, double* fp64_tflops, rd_stream stream)
+{
+    g_err.clear();
+    if (fp32_tflops) *fp32_tflops = 0.0;
+    if (fp64_tflops) *fp64_tflops = 0.0;
+    RD_CUDA(measure_fma_peaks(reinterpret_cast<cudaStream_t>(stream), fp32_tflops, fp64_tflops),
+            "rd_measure_fma_peaks");
+    return RD_OK;
+}
+
 rd_status rd_create_detector(const rd_detector_desc* desc, rd_stream stream, rd_detector** out)
 {
     g_err.clear();

@@ -143,16 +143,18 @@ __device__ __forceinline__ void flush_f64(double* row, int n_bins, int b, const 
     }
 }
 
-__device__ __forceinline__ void fp64_field(const RecD& r, const D4& cl, double q, int flags,
+// Eq. 1 at one cell; R = |x_cell - x_k| as computed for the arrival time (Eq. 2).
+__device__ __forceinline__ void fp64_field(const RecD& r, const D4& cl, double R, double q, int flags,
                                            double* F)
 {
     const double dx = cl.x - r.xa.x, dy = cl.y - r.xa.y, dz = cl.z - r.xa.z;
-    const double R = sqrt(dx * dx + dy * dy + dz * dz);
-    const double rinv = 1.0 / R;
+    // kappa R = R - beta.d; one division gives both 1/R and 1/kappa = R / (kappa R)
+    const double kR = R - (r.bb.x * dx + r.bb.y * dy + r.bb.z * dz);
+    const double inv = 1.0 / (R * kR);
+    const double rinv = kR * inv;
+    const double ik = (R * R) * inv;
     const double nx = dx * rinv, ny = dy * rinv, nz = dz * rinv;
     const double bx = nx - r.bb.x, by = ny - r.bb.y, bz = nz - r.bb.z;
-    const double kap = 1.0 - (r.bb.x * nx + r.bb.y * ny + r.bb.z * nz);
-    const double ik = 1.0 / kap;
     const double ik3 = ik * ik * ik;
     double Ex = 0.0, Ey = 0.0, Ez = 0.0;
     if (flags & RD_NEAR) {
@@ -343,10 +345,13 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
     if (P.lin && live) {
         // field of the sample before the chunk; a trajectory's first interval holds F_1
         const RecD r0 = rec[k_begin > 1 ? k_begin - 1 : 1];
-        if (ff)
+        if (ff) {
             fp64_field_ff(r0, ncx, ncy, ncz, Rc, q, flags, st.Fp);
-        else
-            fp64_field(r0, cl, q, flags, st.Fp);
+        } else {
+            double R0;
+            (void)arrival_bins(r0.xa.x, r0.xa.y, r0.xa.z, cl, P.t0, 0, P.dt, P.inv_dt_det, R0);
+            fp64_field(r0, cl, R0, q, flags, st.Fp);
+        }
     }
 
     for (int t = 0; t < n_tiles; ++t) {
@@ -373,9 +378,9 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
                     fp64_field_ff(r, ncx, ncy, ncz, Rc, q, flags, F);
                     cbin = arrival_bins_ff(r.xa.x, r.xa.y, r.xa.z, ncx, ncy, ncz, Rc, cl.w, P.t0, k, P.dt, P.inv_dt_det);
                 } else {
-                    fp64_field(r, cl, q, flags, F);
                     double R;
                     cbin = arrival_bins(r.xa.x, r.xa.y, r.xa.z, cl, P.t0, k, P.dt, P.inv_dt_det, R);
+                    fp64_field(r, cl, R, q, flags, F);
                 }
                 if (P.lin) {
                     fp64_deposit_lin(st, st.Fp, F, cbin, row, P.n_bins, k, k_begin, k_end);

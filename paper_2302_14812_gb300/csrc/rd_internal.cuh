@@ -159,6 +159,9 @@ cudaError_t launch_adjoint_mixed(const AdjointParams& p, cudaStream_t s);
 cudaError_t launch_gbeta_to_gu(const double* u, const double* gbeta, double* gu, long long n_samples_total,
                                cudaStream_t s);
 
+// FMA throughput of the current device (rd_peaks.cu): TFLOP/s, one FMA = 2 flops
+cudaError_t measure_fma_peaks(cudaStream_t s, double* fp32_tflops, double* fp64_tflops);
+
 cudaError_t launch_read_fields(const void* fields, int precision, int n_pix, int n_bins, void* E,
                                void* B, int dtype, cudaStream_t s);
 // power spectra (rd_spectrum.cu): twiddles exp(-2 pi i j / N), j < N/2, computed on the host

@@ -357,3 +357,12 @@ def test_linear_interpolation_chunks_and_particle_splits():
         E, B = d.read()
         d.close()
         assert rel_l2(E, Ef) <= 2e-6 and rel_l2(B, Bf) <= 2e-6
+
+
+def test_measure_fma_peaks_plausible():
+    """The FMA microbenchmark (roofline denominator): FP32 within the 152-SM part's range
+    (at most 152 x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s; a run far below that would be a
+    broken probe), FP64 positive and well below FP32 on this part."""
+    f32, f64 = rd.rd_measure_fma_peaks()
+    assert 20.0 < f32 < 85.0, f32
+    assert 0.05 < f64 < f32, (f32, f64)
