@@ -42,9 +42,9 @@ UNIT = "deposits/s"
 FLOPS_PER_DEPOSIT_MIXED = 75
 FLOPS_PER_CROSSING_MIXED = 9
 # FP64 operations of the plain kernel per deposit, counted from its source the same way (square
-# root, division and floor count 1 each): arrival time (Eq. 2) 14, Eq. 1 with B = n x E 64,
+# root, division and floor count 1 each): arrival time (Eq. 2) 14, Eq. 1 with B = n x E 56,
 # accumulation into the running bin 14.
-FLOPS_PER_DEPOSIT_FP64 = 92
+FLOPS_PER_DEPOSIT_FP64 = 84
 # FP32 peak derived from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 WORKLOAD_UNDULATOR = ("undulator ensemble: 1000 e- (gamma 20, K 1, 10 periods) x 4000 steps, "

@@ -143,10 +143,14 @@ __device__ __forceinline__ void flush_f64(double* row, int n_bins, int b, const 
     }
 }
 
-// Eq. 1 at one cell; R = |x_cell - x_k| as computed for the arrival time (Eq. 2).
+// Eq. 1 at one cell; R = |x_cell - x_k| as computed for the arrival time (Eq. 2).  With |n| = 1,
+// n x ((n - beta) x betadot) = (n - beta)(n.betadot) - kappa betadot, so both terms share one form:
+//   E = q / (kappa^3 R) [(n - beta)(gamma^-2 / R + n.betadot) - kappa betadot],   B = n x E
+// (gamma^-2 / R: velocity term, RD_NEAR; the rest: acceleration term, RD_FAR).
 __device__ __forceinline__ void fp64_field(const RecD& r, const D4& cl, double R, double q, int flags,
                                            double* F)
 {
+    const double near = (flags & RD_NEAR) ? 1.0 : 0.0, far = (flags & RD_FAR) ? 1.0 : 0.0;
     const double dx = cl.x - r.xa.x, dy = cl.y - r.xa.y, dz = cl.z - r.xa.z;
     // kappa R = R - beta.d; one division gives both 1/R and 1/kappa = R / (kappa R)
     const double kR = R - (r.bb.x * dx + r.bb.y * dy + r.bb.z * dz);
@@ -155,23 +159,12 @@ __device__ __forceinline__ void fp64_field(const RecD& r, const D4& cl, double R
     const double ik = (R * R) * inv;
     const double nx = dx * rinv, ny = dy * rinv, nz = dz * rinv;
     const double bx = nx - r.bb.x, by = ny - r.bb.y, bz = nz - r.bb.z;
-    const double ik3 = ik * ik * ik;
-    double Ex = 0.0, Ey = 0.0, Ez = 0.0;
-    if (flags & RD_NEAR) {
-        const double cn = q * r.bb.w * ik3 * rinv * rinv;
-        Ex = cn * bx;
-        Ey = cn * by;
-        Ez = cn * bz;
-    }
-    if (flags & RD_FAR) {
-        const double wx = by * r.bd.z - bz * r.bd.y;
-        const double wy = bz * r.bd.x - bx * r.bd.z;
-        const double wz = bx * r.bd.y - by * r.bd.x;
-        const double cf = q * ik3 * rinv;
-        Ex += cf * (ny * wz - nz * wy);
-        Ey += cf * (nz * wx - nx * wz);
-        Ez += cf * (nx * wy - ny * wx);
-    }
+    const double c1 = near * (r.bb.w * rinv) + far * (nx * r.bd.x + ny * r.bd.y + nz * r.bd.z);
+    const double kb = far * (kR * rinv);
+    const double s = q * (ik * ik * ik) * rinv;
+    const double Ex = s * (bx * c1 - kb * r.bd.x);
+    const double Ey = s * (by * c1 - kb * r.bd.y);
+    const double Ez = s * (bz * c1 - kb * r.bd.z);
     F[0] = Ex;
     F[1] = Ey;
     F[2] = Ez;
