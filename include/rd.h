@@ -310,6 +310,17 @@ RD_API rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix_t0,
  */
 RD_API rd_status rd_measure_fma_peaks(double* fp32_tflops, double* fp64_tflops, rd_stream stream);
 
+/*
+ * Diagnostic, not part of the deposit: checks the failure path of the kernels' bounded waits.
+ * One CTA waits, with the same bounded mbarrier wait the deposit and adjoint kernels use for their
+ * staged records, on a phase that nothing completes; after limit_ms (1..2000) the wait gives up,
+ * the CTA records the expiry as those kernels do and returns, and this call reports it.
+ * Returns RD_ERR_TIMEOUT when the expiry was detected and reported (the expected outcome; the
+ * device stays usable), RD_ERR_STATE if it was not, RD_ERR_ARG for a limit outside the range,
+ * RD_ERR_CUDA if a CUDA call failed.  Synchronous on `stream`.
+ */
+RD_API rd_status rd_check_bounded_wait(int32_t limit_ms, rd_stream stream);
+
 /* Message for the last failing call on this thread ("" if none).  Valid until the next call. */
 RD_API const char* rd_last_error(void);
 

@@ -27,7 +27,7 @@ __all__ = [
     "rd_deposit_trajectories", "rd_read_fields", "rd_synchronize", "rd_get_stats",
     "rd_set_timing", "rd_adjoint_trajectories", "rd_deposit_batch", "rd_set_chunk", "rd_autotune",
     "rd_set_batch_budget", "rd_power_spectrum", "rd_deposit_stream", "rd_stream_reset",
-    "rd_deposit_noalloc", "rd_measure_fma_peaks", "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
+    "rd_deposit_noalloc", "rd_measure_fma_peaks", "rd_check_bounded_wait", "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
 ]
 
 RD_OK, RD_ERR_ARG, RD_ERR_CUDA, RD_ERR_OOM, RD_ERR_STATE, RD_ERR_TIMEOUT, RD_ERR_BOUNDS, RD_ERR_INPUT = range(8)
@@ -107,6 +107,7 @@ def load_library(build_if_missing: bool = True):
             "rd_deposit_noalloc": ([P, P, I, ctypes.c_double, ctypes.c_double, I, I, ctypes.POINTER(rd_traj), P,
                                     ctypes.POINTER(ctypes.c_uint32), P], I),
             "rd_measure_fma_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P], I),
+            "rd_check_bounded_wait": ([I, P], I),
             "rd_last_error": ([], ctypes.c_char_p),
             "rd_version": ([], ctypes.c_char_p),
         }
@@ -241,6 +242,12 @@ def rd_measure_fma_peaks(stream=None):
     lib = load_library()
     _check(lib.rd_measure_fma_peaks(ctypes.byref(f32), ctypes.byref(f64), _stream_ptr(stream)), "rd_measure_fma_peaks")
     return f32.value, f64.value
+
+
+def rd_check_bounded_wait(limit_ms: int = 20, stream=None) -> int:
+    """Run the bounded-wait check (diagnostic); returns its status, RD_ERR_TIMEOUT when the wait ran
+    out and was reported as the kernels report it (no exception for that expected outcome)."""
+    return int(load_library().rd_check_bounded_wait(int(limit_ms), _stream_ptr(stream)))
 
 
 def rd_last_error() -> str:

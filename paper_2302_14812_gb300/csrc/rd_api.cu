@@ -235,6 +235,25 @@ const char* rd_last_error(void) { return g_err.c_str(); }
 
 const char* rd_version(void) { return "rd 0.1 (sm_103a)"; }
 
+rd_status rd_check_bounded_wait(int32_t limit_ms, rd_stream stream)
+{
+    g_err.clear();
+    if (limit_ms < 1 || limit_ms > 2000) return fail(RD_ERR_ARG, "limit_ms %d outside [1, 2000]", limit_ms);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned* dev = nullptr;
+    RD_CUDA(cudaMalloc(&dev, sizeof(unsigned)), "rd_check_bounded_wait");
+    DevCounters c{};
+    cudaError_t e = cudaMemsetAsync(dev, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = launch_wait_probe((unsigned long long)limit_ms * 1000000ull, dev, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&c.errors, dev, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dev);
+    RD_CUDA(e, "rd_check_bounded_wait");
+    const rd_status st = latched(c);
+    if (st == RD_OK) return fail(RD_ERR_STATE, "the bounded wait did not report its expiry");
+    return st;
+}
+
 rd_status rd_measure_fma_peaks(double* fp32_tflops, double* fp64_tflops, rd_stream stream)
 {
     g_err.clear();

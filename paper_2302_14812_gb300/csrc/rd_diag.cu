@@ -1,3 +1,5 @@
+// Diagnostics.
+//
 // FMA throughput of the device, measured: the denominator for the roofline of the deposit kernels,
 // which are bound by FP32 (mixed) and FP64 (plain) arithmetic rather than by memory or tensor cores.
 //
@@ -73,7 +75,28 @@ cudaError_t measure(int sms, cudaStream_t s, T* sink, double target_ms, double* 
     return err;
 }
 
+// One CTA waits, with the kernels' bounded wait, for phase 0 of an mbarrier that expects one arrival
+// and gets none: the wait runs out after limit_ns and the CTA records RD_ERR_TIMEOUT the way the
+// deposit and adjoint kernels do, then returns.  Nothing is left in flight.
+__global__ void k_wait_probe(unsigned long long limit_ns, unsigned* errors)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded_ns(&bar, 0u, limit_ns);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(errors, ERRBIT_TIMEOUT);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_probe(unsigned long long limit_ns, unsigned* errors, cudaStream_t s)
+{
+    k_wait_probe<<<1, 32, 0, s>>>(limit_ns, errors);
+    return cudaGetLastError();
+}
 
 cudaError_t measure_fma_peaks(cudaStream_t s, double* fp32_tflops, double* fp64_tflops)
 {

@@ -159,8 +159,11 @@ cudaError_t launch_adjoint_mixed(const AdjointParams& p, cudaStream_t s);
 cudaError_t launch_gbeta_to_gu(const double* u, const double* gbeta, double* gu, long long n_samples_total,
                                cudaStream_t s);
 
-// FMA throughput of the current device (rd_peaks.cu): TFLOP/s, one FMA = 2 flops
+// diagnostics (rd_diag.cu): FMA throughput of the current device in TFLOP/s (one FMA = 2 flops), and one
+// CTA whose bounded wait on an mbarrier phase that nothing completes runs out after limit_ns (the
+// expiry is recorded in *errors as the kernels record it)
 cudaError_t measure_fma_peaks(cudaStream_t s, double* fp32_tflops, double* fp64_tflops);
+cudaError_t launch_wait_probe(unsigned long long limit_ns, unsigned* errors, cudaStream_t s);
 
 cudaError_t launch_read_fields(const void* fields, int precision, int n_pix, int n_bins, void* E,
                                void* B, int dtype, cudaStream_t s);
@@ -232,14 +235,19 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Wait for an mbarrier phase for at most kWaitLimitNs; false if it did not complete in time.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity)
+// Wait for an mbarrier phase for at most limit_ns; false if it did not complete in time.
+__device__ __forceinline__ bool mbar_wait_bounded_ns(uint64_t* bar, unsigned parity, unsigned long long limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kWaitLimitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity)
+{
+    return mbar_wait_bounded_ns(bar, parity, kWaitLimitNs);
 }
 
 // Fire-and-forget vector reductions into global memory (sm_90+).

@@ -366,3 +366,17 @@ def test_measure_fma_peaks_plausible():
     f32, f64 = rd.rd_measure_fma_peaks()
     assert 20.0 < f32 < 85.0, f32
     assert 0.05 < f64 < f32, (f32, f64)
+
+
+def test_bounded_wait_runs_out_and_reports():
+    """The kernels' bounded mbarrier wait, on a phase that nothing completes, gives up after its limit
+    and the expiry comes back as RD_ERR_TIMEOUT; the context stays usable (a deposit afterwards
+    matches the oracle)."""
+    import time
+    t = time.perf_counter()
+    assert rd.rd_check_bounded_wait(20) == rd.RD_ERR_TIMEOUT
+    assert time.perf_counter() - t < 5.0
+    assert "bounded wait" in rd.rd_last_error()
+    tr = W.random_smooth(2, 60, 0.03, seed=31)
+    det = W.Detector(W.spherical_cap(3, 12.0, 0.5), None, 9.0, 0.02, 300)
+    check(tr, det, "mixed")
