@@ -115,8 +115,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv") \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/rd_clocks_{os.getpid()}.csv"
+        # raw samples: RD_CLOCKS_CSV if set (a per-rank suffix is added), else a temporary file
+        base = os.environ.get("RD_CLOCKS_CSV")
+        self.path = (f"{base}.rank{gpu_index}" if base else f"/tmp/rd_clocks_{os.getpid()}_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
