@@ -217,15 +217,19 @@ RD_API rd_status rd_set_timing(rd_detector* det, int32_t enable);
  * gE, gB: d L / d E_det and d L / d B_det, [n_pix][n_bins][3] of type gdtype (RD_F32/RD_F64) in
  * device memory; either may be NULL (zero).  Accumulates (+=) d L / d x into gx and d L / d u
  * into gu, both [n_part][n_samples][3] FP64 in device memory, for the deposit this detector would
- * make from `traj` (same windows, flags and arithmetic as its forward RD_MIXED path).
+ * make from `traj` (same windows, flags and arithmetic as its forward path of the same precision).
  * The transpose of the integrating deposit (Section 3.2) per (particle, interval, cell): the seed
  * gathered over the bins the arrival interval covers drives the derivative of Eq. 1 (field of the
  * interval's sample); the bins at the two ends of the interval move with the arrival times of
  * Eq. 2, contributing (F_k - F_{k+1}) . g at each sample's arrival bin; beta = u/sqrt(1+u^2) and the
  * backward difference betadot couple neighbouring samples.  Nothing per triple is stored: the
- * forward quantities are recomputed from x and u, restarting from exact FP64 arrival times every
- * 250 samples.  FP32 field arithmetic, FP64 gradient sums across cells.
- * Requirements: detector RD_MIXED (else RD_ERR_STATE), traj->mem RD_MEM_DEVICE (else RD_ERR_ARG).
+ * forward quantities are recomputed from x and u.  RD_MIXED: FP32 field arithmetic with the
+ * forward path's FP32 arrival-time walk, restarting from exact FP64 arrival times every 250
+ * samples, FP64 gradient sums across cells (relative error ~1e-5, set by FP32 rounding in the
+ * differences of neighbouring samples).  RD_FP64: everything in FP64, Eq. 2 for every sample (the
+ * plain form; relative error ~1e-12, at the FP64 rate of the GPU).
+ * Requirements: flags without RD_FARFIELD and RD_LINEAR (else RD_ERR_STATE), traj->mem
+ * RD_MEM_DEVICE (else RD_ERR_ARG).
  */
 RD_API rd_status rd_adjoint_trajectories(rd_detector* det, const rd_traj* traj, const void* gE,
                                          const void* gB, int32_t gdtype, double* gx, double* gu,

@@ -456,7 +456,7 @@ def deposit_batch(detectors, trajectories, stream=None):
 
 
 class DepositFunction:
-    """Differentiable deposit: (x, u) -> (E, B) through a RadiationDetector (mixed precision).
+    """Differentiable deposit: (x, u) -> (E, B) through a RadiationDetector (mixed or FP64).
 
     forward: zero the detector, deposit, return E, B as float64 CUDA tensors [n_pix][n_bins][3];
     backward: the adjoint kernel gives d loss / d x and d loss / d u.  q, t0 and dt are constants.

@@ -474,6 +474,287 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
     }
 }
 
+// =============================================================================================
+// Plain FP64 adjoint: the transpose of the plain FP64 deposit (arrival time from Eq. 2 for every
+// sample, Eq. 1 in FP64, every bin of an interval gathered in one pass).  Per (cell, interval k):
+//   G_k = sum_b w_b g_b over the bins b of [u_{k-1}, u_k] (w_b = overlap in bins)
+//   d loss / d u_k += F_k . g(bin(u_k)),  d loss / d u_{k-1} -= F_k . g(bin(u_{k-1})),  du/dR = 1/dt_det
+// and the vector-Jacobian product of
+//   E = s V,  s = q / (kappa^3 R),  V = (n - beta) c1 - kappa betadot,  c1 = gamma^-2 / R + n.betadot,
+//   B = n x E,  kappa = 1 - n.beta,  n = d / R,  d = x_cell - x_k,  gamma^-2 = 1 - beta^2,
+//   betadot_k = (beta_k - beta_{k-1}) / dt
+// with seed (G_E, G_B) = G_k.  The same algebra as the mixed kernel, all in FP64.
+// =============================================================================================
+namespace {
+
+struct A64Cell {
+    double u;           // arrival (bins) of the previous sample
+    int b;              // its bin
+    double g[6];        // seed of bin b (zero outside the window)
+    double np[3];       // n of the previous sample
+    double pend[6];     // partial gradient of the previous sample: d/dx (3), d/dbeta (3)
+};
+
+__device__ __forceinline__ void load_seed64(const double* row, int n_bins, int b, double* g)
+{
+    if ((unsigned)b < (unsigned)n_bins) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) g[i] = row[(size_t)b * 6 + i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) g[i] = 0.0;
+    }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One interval k of one cell; returns in out the finished gradient of sample k-1.
+__device__ __forceinline__ void adj64_step(A64Cell& c, const RecD& r, const D4& cl, const double* row,
+                                           const AdjointParams& P, int k, double q, double near, double far,
+                                           double* out)
+{
+    // ---- forward: arrival time (Eq. 2) and Eq. 1 ----
+    double R;
+    const double u = arrival_bins(r.xa.x, r.xa.y, r.xa.z, cl, P.t0, k, P.dt, P.inv_dt_det, R);
+    const double dx = cl.x - r.xa.x, dy = cl.y - r.xa.y, dz = cl.z - r.xa.z;
+    const double betx = r.bb.x, bety = r.bb.y, betz = r.bb.z;
+    const double g2m = near * r.bb.w;                                   // gamma^-2 (velocity term)
+    const double bdx = far * r.bd.x, bdy = far * r.bd.y, bdz = far * r.bd.z;   // betadot (acceleration term)
+    const double kR = R - (betx * dx + bety * dy + betz * dz);          // kappa R
+    const double inv = 1.0 / (R * kR);
+    const double rinv = kR * inv;
+    const double ik = (R * R) * inv;                                    // 1 / kappa
+    const double kap = kR * rinv;
+    const double nx = dx * rinv, ny = dy * rinv, nz = dz * rinv;
+    const double bx = nx - betx, by = ny - bety, bz = nz - betz;
+    const double c1 = g2m * rinv + (nx * bdx + ny * bdy + nz * bdz);
+    const double s = q * (ik * ik * ik) * rinv;
+    const double Vx = bx * c1 - kap * bdx, Vy = by * c1 - kap * bdy, Vz = bz * c1 - kap * bdz;
+    const double Ex = s * Vx, Ey = s * Vy, Ez = s * Vz;
+    const double Bx = ny * Ez - nz * Ey, By = nz * Ex - nx * Ez, Bz = nx * Ey - ny * Ex;
+
+    // ---- transpose of the integrating deposit ----
+    const double a_beg = Ex * c.g[0] + Ey * c.g[1] + Ez * c.g[2] + Bx * c.g[3] + By * c.g[4] + Bz * c.g[5];
+    const int b1 = clamp_bin(floor(u));
+    double G[6];
+    if (b1 <= c.b) {
+        const double w = u - c.u;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) G[i] = c.g[i] * w;
+    } else {
+        const double w0 = (double)(c.b + 1) - c.u;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) G[i] = c.g[i] * w0;
+        // whole bins strictly inside the interval, bounded by the window
+        const int lo = max(c.b + 1, 0), hi = min(b1 - 1, P.n_bins - 1);
+        for (int b = lo; b <= hi; ++b) {
+            double t[6];
+            load_seed64(row, P.n_bins, b, t);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) G[i] += t[i];
+        }
+        load_seed64(row, P.n_bins, b1, c.g);
+        const double w1 = u - (double)b1;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) G[i] += c.g[i] * w1;
+        c.b = b1;
+    }
+    c.u = u;
+    const double a_end = Ex * c.g[0] + Ey * c.g[1] + Ez * c.g[2] + Bx * c.g[3] + By * c.g[4] + Bz * c.g[5];
+
+    // ---- VJP of Eq. 1 with B = n x E, seed (GE, GB) = G ----
+    const double GEx = G[0], GEy = G[1], GEz = G[2], GBx = G[3], GBy = G[4], GBz = G[5];
+    // L = E.H + n.(E x GB),  H = GE + GB x n
+    const double Hx = GEx + (GBy * nz - GBz * ny), Hy = GEy + (GBz * nx - GBx * nz), Hz = GEz + (GBx * ny - GBy * nx);
+    double gnx = Ey * GBz - Ez * GBy, gny = Ez * GBx - Ex * GBz, gnz = Ex * GBy - Ey * GBx;
+    const double gsv = Vx * Hx + Vy * Hy + Vz * Hz;                   // d/ds
+    const double gVx = s * Hx, gVy = s * Hy, gVz = s * Hz;            // d/dV
+    const double gc1 = bx * gVx + by * gVy + bz * gVz;                // d/dc1
+    const double gk = -(bdx * gVx + bdy * gVy + bdz * gVz) - 3.0 * gsv * s * ik;   // d/dkappa
+    gnx += c1 * gVx + gc1 * bdx - gk * betx;
+    gny += c1 * gVy + gc1 * bdy - gk * bety;
+    gnz += c1 * gVz + gc1 * bdz - gk * betz;
+    const double gig2 = gc1 * rinv * near;                            // d/d(gamma^-2)
+    const double gbetx = -c1 * gVx - gk * nx - 2.0 * gig2 * betx;
+    const double gbety = -c1 * gVy - gk * ny - 2.0 * gig2 * bety;
+    const double gbetz = -c1 * gVz - gk * nz - 2.0 * gig2 * betz;
+    const double gbdx = (gc1 * nx - kap * gVx) * far, gbdy = (gc1 * ny - kap * gVy) * far,
+                 gbdz = (gc1 * nz - kap * gVz) * far;                 // d/dbetadot
+    // R: s = q/(kappa^3 R), c1 contains gamma^-2/R, the arrival time u_k contains R/dt_det
+    const double gR = a_end * P.inv_dt_det - gsv * s * rinv - gc1 * g2m * rinv * rinv;
+    // d = x_cell - x: d/dd = gn/R + n (gR - n.gn/R)
+    const double ndg = nx * gnx + ny * gny + nz * gnz;
+    const double tn = gR - ndg * rinv;
+    const double gdx = gnx * rinv + nx * tn, gdy = gny * rinv + ny * tn, gdz = gnz * rinv + nz * tn;
+    const double inv_dt = 1.0 / P.dt;
+
+    // sample k-1: its arrival time starts this interval; betadot_k depends on beta_{k-1}
+    const double cb = a_beg * P.inv_dt_det;
+    out[0] = c.pend[0] + cb * c.np[0];
+    out[1] = c.pend[1] + cb * c.np[1];
+    out[2] = c.pend[2] + cb * c.np[2];
+    out[3] = c.pend[3] - gbdx * inv_dt;
+    out[4] = c.pend[4] - gbdy * inv_dt;
+    out[5] = c.pend[5] - gbdz * inv_dt;
+    // sample k (partial until the next interval adds its terms)
+    c.pend[0] = -gdx;
+    c.pend[1] = -gdy;
+    c.pend[2] = -gdz;
+    c.pend[3] = gbetx + gbdx * inv_dt;
+    c.pend[4] = gbety + gbdy * inv_dt;
+    c.pend[5] = gbetz + gbdz * inv_dt;
+    c.np[0] = nx;
+    c.np[1] = ny;
+    c.np[2] = nz;
+}
+
+}  // namespace
+
+// One CTA = (step chunk, block of 128 cells, particle); one cell per thread.  Per step the six
+// gradient components are summed over each warp (shuffles), the warps' sums over the CTA per
+// tile, and added to the FP64 buffers with atomics.
+__global__ void __launch_bounds__(kAdjointFp64Threads) k_adjoint_fp64(const AdjointParams P)
+{
+    __shared__ __align__(128) RecD tile[2][kTileSteps];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ double red[kAdjointFp64Threads / 32][kTileSteps][6];
+
+    const unsigned bid = blockIdx.x;
+    const int p = (int)(bid % (unsigned)P.n_part);
+    const unsigned rest = bid / (unsigned)P.n_part;
+    const int cb = (int)(rest % (unsigned)P.n_cell_blocks);
+    const int ch = (int)(rest / (unsigned)P.n_cell_blocks);
+    const int S = P.n_samples - 1;
+    const int k_begin = 1 + ch * P.chunk;
+    const int k_end = min(S, k_begin + P.chunk - 1);
+    const int n_int = k_end - k_begin + 1;
+    const int n_tiles = (n_int + kTileSteps - 1) / kTileSteps;
+    const RecD* rec = P.recd + (size_t)p * P.n_samples;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cell = cb * kAdjointFp64Threads + tid;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int t = 0; t < 2 && t < n_tiles; ++t) {
+            const int k0 = k_begin + t * kTileSteps;
+            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k0 + 1) * sizeof(RecD);
+            mbar_arrive_expect_tx(&bar[t], bytes);
+            bulk_g2s(tile[t], rec + k0, bytes, &bar[t]);
+        }
+    }
+
+    const double q = P.q ? P.q[p] : 1.0;
+    const double near = (P.flags & RD_NEAR) ? 1.0 : 0.0, far = (P.flags & RD_FAR) ? 1.0 : 0.0;
+    const double* xp = P.x + (size_t)p * P.n_samples * 3;
+    A64Cell c;
+    D4 cl = {0.0, 0.0, 0.0, 0.0};
+    const double* row = P.seedd;
+    bool live = false;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) c.pend[i] = c.g[i] = 0.0;
+    c.u = 0.0;
+    c.b = 0;
+    c.np[0] = c.np[1] = c.np[2] = 0.0;
+    if (cell < P.n_pix) {
+        cl = P.cells[cell];
+        const double* xa = xp + 3 * (size_t)(k_begin - 1);
+        const double* xe = xp + 3 * (size_t)k_end;
+        double Ra, Re;
+        const double ua = arrival_bins(xa[0], xa[1], xa[2], cl, P.t0, k_begin - 1, P.dt, P.inv_dt_det, Ra);
+        const double ue = arrival_bins(xe[0], xe[1], xe[2], cl, P.t0, k_end, P.dt, P.inv_dt_det, Re);
+        live = (ue > 0.0) && (ua < (double)P.n_bins);
+        if (live) {
+            row = P.seedd + (size_t)cell * P.n_bins * 6;
+            c.u = ua;
+            c.b = clamp_bin(floor(ua));
+            load_seed64(row, P.n_bins, c.b, c.g);
+            c.np[0] = (cl.x - xa[0]) / Ra;
+            c.np[1] = (cl.y - xa[1]) / Ra;
+            c.np[2] = (cl.z - xa[2]) / Ra;
+        }
+    }
+
+    for (int t = 0; t < n_tiles; ++t) {
+        const int buf = t & 1;
+        const bool ok = mbar_wait_bounded(&bar[buf], (unsigned)(t >> 1) & 1u);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(&P.counters->errors, ERRBIT_TIMEOUT);
+                for (int u = t; u < t + 2 && u < n_tiles; ++u)
+                    (void)mbar_wait_bounded(&bar[u & 1], (unsigned)(u >> 1) & 1u);
+            }
+            __syncthreads();
+            return;
+        }
+        const int k0 = k_begin + t * kTileSteps;
+        const int cnt = min(kTileSteps, k_end - k0 + 1);
+        for (int i = 0; i < cnt; ++i) {
+            double out[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            if (live) adj64_step(c, tile[buf][i], cl, row, P, k0 + i, q, near, far, out);
+#pragma unroll
+            for (int e = 0; e < 6; ++e) {
+                const double v = warp_sum_d(out[e]);
+                if (lane == 0) red[warp][i][e] = v;
+            }
+        }
+        __syncthreads();
+        // sample k0 - 1 + i gets the sum over the CTA's warps
+        for (int e = tid; e < cnt * 6; e += kAdjointFp64Threads) {
+            const int i = e / 6, j = e - 6 * (e / 6);
+            double v = 0.0;
+#pragma unroll
+            for (int w = 0; w < kAdjointFp64Threads / 32; ++w) v += red[w][i][j];
+            if (v != 0.0) {
+                const size_t o = ((size_t)p * P.n_samples + (size_t)(k0 - 1 + i)) * 3;
+                if (j < 3) atomicAdd(P.gx + o + j, v);
+                else atomicAdd(P.gbeta + o + (j - 3), v);
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && t + 2 < n_tiles) {
+            fence_proxy_async();
+            const int k2 = k_begin + (t + 2) * kTileSteps;
+            const unsigned bytes = (unsigned)min(kTileSteps, k_end - k2 + 1) * sizeof(RecD);
+            mbar_arrive_expect_tx(&bar[buf], bytes);
+            bulk_g2s(tile[buf], rec + k2, bytes, &bar[buf]);
+        }
+    }
+    // the chunk's last sample keeps the partial of its last interval
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        const double v = warp_sum_d(live ? c.pend[e] : 0.0);
+        if (lane == 0 && v != 0.0) {
+            const size_t o = ((size_t)p * P.n_samples + (size_t)k_end) * 3;
+            if (e < 3) atomicAdd(P.gx + o + e, v);
+            else atomicAdd(P.gbeta + o + (e - 3), v);
+        }
+    }
+}
+
+// upstream gradient (E, B) [n_pix][n_bins][3] of any type -> [n_pix][n_bins][6] double
+template <typename T>
+__global__ void k_pack_seed64(const T* __restrict__ gE, const T* __restrict__ gB, long long n, double* __restrict__ seed)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            seed[6 * i + c] = gE ? (double)gE[3 * i + c] : 0.0;
+            seed[6 * i + 3 + c] = gB ? (double)gB[3 * i + c] : 0.0;
+        }
+    }
+}
+
 // upstream gradient (E, B) [n_pix][n_bins][3] of any type -> field layout [n_pix][n_bins][8] float
 template <typename T>
 __global__ void k_pack_seed(const T* __restrict__ gE, const T* __restrict__ gB, long long n, float* __restrict__ seed)
@@ -541,6 +822,28 @@ cudaError_t launch_adjoint_mixed(const AdjointParams& p, cudaStream_t s)
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     k_adjoint_mixed<<<(unsigned)blocks, kAdjointThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_seed64(const void* gE, const void* gB, int dtype, int n_pix, int n_bins, double* seed,
+                               cudaStream_t s)
+{
+    const long long n = (long long)n_pix * n_bins;
+    if (dtype == RD_F32)
+        k_pack_seed64<float><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const float*>(gE),
+                                                            static_cast<const float*>(gB), n, seed);
+    else
+        k_pack_seed64<double><<<grid_for(n, 256), 256, 0, s>>>(static_cast<const double*>(gE),
+                                                             static_cast<const double*>(gB), n, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_fp64(const AdjointParams& p, cudaStream_t s)
+{
+    const long long blocks = (long long)p.n_cell_blocks * p.n_part * p.n_chunks;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_adjoint_fp64<<<(unsigned)blocks, kAdjointFp64Threads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

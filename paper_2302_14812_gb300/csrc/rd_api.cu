@@ -547,7 +547,6 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
     if (!d) return fail(RD_ERR_ARG, "detector is NULL");
     rd_status st = check_traj(t);
     if (st != RD_OK) return st;
-    if (d->precision != RD_MIXED) return fail(RD_ERR_STATE, "the adjoint needs an RD_MIXED detector");
     if (d->flags & (RD_FARFIELD | RD_LINEAR))
         return fail(RD_ERR_STATE, "the adjoint covers the exact fields with the held interpolation only");
     if (t->mem != RD_MEM_DEVICE) return fail(RD_ERR_ARG, "the adjoint needs device trajectories");
@@ -557,10 +556,14 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
     const int S = t->n_samples - 1;
     if (t->n_part == 0 || S < 1) return RD_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool fp64 = d->precision == RD_FP64;
     st = ensure(&d->seed, &d->seed_bytes, d->field_bytes, s, "seed scratch");
     if (st != RD_OK) return st;
-    RD_CUDA(launch_pack_seed(gE, gB, gdtype, d->n_pix, d->n_bins, static_cast<float*>(d->seed), s), "pack seed");
-    const size_t per_part_rec = sizeof(RecS) * (size_t)t->n_samples;
+    if (fp64)
+        RD_CUDA(launch_pack_seed64(gE, gB, gdtype, d->n_pix, d->n_bins, static_cast<double*>(d->seed), s), "pack seed");
+    else
+        RD_CUDA(launch_pack_seed(gE, gB, gdtype, d->n_pix, d->n_bins, static_cast<float*>(d->seed), s), "pack seed");
+    const size_t per_part_rec = (fp64 ? sizeof(RecD) : sizeof(RecS)) * (size_t)t->n_samples;
     const size_t per_part_gb = 3 * sizeof(double) * (size_t)t->n_samples;
     const size_t budget = (size_t)1 << 31;
     const int pc = (int)std::max<size_t>(1, std::min<size_t>((size_t)t->n_part, budget / (per_part_rec + per_part_gb)));
@@ -568,21 +571,29 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
     if (st != RD_OK) return st;
     st = ensure(&d->gbeta, &d->gbeta_bytes, per_part_gb * pc, s, "gradient scratch");
     if (st != RD_OK) return st;
-    const int n_cell_blocks = (d->n_pix + kAdjointCellsPerCta - 1) / kAdjointCellsPerCta;
+    const int cells_per_cta = fp64 ? kAdjointFp64Threads : kAdjointCellsPerCta;
+    const int n_cell_blocks = (d->n_pix + cells_per_cta - 1) / cells_per_cta;
     const int chunk = std::max(1, std::min(d->adjoint_chunk, S));
     for (int p0 = 0; p0 < t->n_part; p0 += pc) {
         const int np = std::min(pc, t->n_part - p0);
         const size_t off = (size_t)p0 * t->n_samples * 3;
         RD_CUDA(cudaMemsetAsync(d->gbeta, 0, per_part_gb * np, s), "clear gradient scratch");
-        RD_CUDA(launch_precompute_mixed(t->x + off, t->u + off, nullptr, 0.0, np, t->n_samples, t->dt, d->flags,
-                                        static_cast<RecS*>(d->rec), d->counters, s),
-                "precompute");
+        if (fp64)
+            RD_CUDA(launch_precompute_fp64(t->x + off, t->u + off, np, t->n_samples, t->dt, static_cast<RecD*>(d->rec),
+                                           d->counters, s),
+                    "precompute");
+        else
+            RD_CUDA(launch_precompute_mixed(t->x + off, t->u + off, nullptr, 0.0, np, t->n_samples, t->dt, d->flags,
+                                            static_cast<RecS*>(d->rec), d->counters, s),
+                    "precompute");
         AdjointParams P;
-        P.rec = static_cast<const RecS*>(d->rec);
+        P.rec = fp64 ? nullptr : static_cast<const RecS*>(d->rec);
+        P.recd = fp64 ? static_cast<const RecD*>(d->rec) : nullptr;
+        P.seedd = fp64 ? static_cast<const double*>(d->seed) : nullptr;
         P.x = t->x + off;
         P.q = t->q ? t->q + p0 : nullptr;
         P.cells = d->cells;
-        P.seed = static_cast<const float*>(d->seed);
+        P.seed = fp64 ? nullptr : static_cast<const float*>(d->seed);
         P.gx = gx + off;
         P.gbeta = static_cast<double*>(d->gbeta);
         P.counters = d->counters;
@@ -605,7 +616,7 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
         P.inv_dt_f = (float)(1.0 / t->dt);
         {
             LaunchTimer timer(d, s);
-            RD_CUDA(launch_adjoint_mixed(P, s), "adjoint");
+            RD_CUDA(fp64 ? launch_adjoint_fp64(P, s) : launch_adjoint_mixed(P, s), "adjoint");
         }
         RD_CUDA(launch_gbeta_to_gu(t->u + off, static_cast<const double*>(d->gbeta), gu + off,
                                    (long long)np * t->n_samples, s),

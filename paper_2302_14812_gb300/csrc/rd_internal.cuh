@@ -127,11 +127,13 @@ int batch_grid();   // resident CTAs of the persistent batch kernel on the curre
 cudaError_t launch_deposit_fp64(const DepositParams& p, int flags, cudaStream_t s);
 // adjoint (rd_adjoint.cu)
 struct AdjointParams {
-    const RecS* rec;            // [n_part][n_samples]
+    const RecS* rec;            // [n_part][n_samples] (mixed kernel)
+    const RecD* recd;           // [n_part][n_samples] (FP64 kernel)
     const double* x;            // [n_part][n_samples][3] FP64 positions (anchors)
     const double* q;            // [n_part] or null
     const D4* cells;            // [n_pix]
     const float* seed;          // [n_pix][n_bins][8] upstream gradient (E xyz, B xyz) in field layout
+    const double* seedd;        // [n_pix][n_bins][6] the same in FP64 (FP64 kernel)
     double* gx;                 // [n_part][n_samples][3] += d loss / d x
     double* gbeta;              // [n_part][n_samples][3] += d loss / d beta (scratch, FP64)
     DevCounters* counters;
@@ -156,6 +158,10 @@ constexpr int kAdjointCellsPerCta = kAdjointThreads * kAdjointCells;
 cudaError_t launch_pack_seed(const void* gE, const void* gB, int dtype, int n_pix, int n_bins, float* seed,
                              cudaStream_t s);
 cudaError_t launch_adjoint_mixed(const AdjointParams& p, cudaStream_t s);
+cudaError_t launch_pack_seed64(const void* gE, const void* gB, int dtype, int n_pix, int n_bins, double* seed,
+                               cudaStream_t s);
+cudaError_t launch_adjoint_fp64(const AdjointParams& p, cudaStream_t s);
+constexpr int kAdjointFp64Threads = 128;   // FP64 adjoint: one cell per thread
 cudaError_t launch_gbeta_to_gu(const double* u, const double* gbeta, double* gu, long long n_samples_total,
                                cudaStream_t s);
 
