@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--pm-chunk", type=int, default=10_000, help="electrons generated and deposited per chunk")
     ap.add_argument("--adjoint-particles", type=int, default=10_000,
                     help="electrons of the adjoint workload (1e4 = the full configuration)")
+    ap.add_argument("--adjoint-fp64-particles", type=int, default=100,
+                    help="electrons of the adjoint workload given to the FP64 adjoint (0 = skip that leg)")
     ap.add_argument("--batch-scale", type=float, default=0.1,
                     help="particle-count scale of the 64-problem set (memory: every problem resident)")
     return ap.parse_args()
@@ -356,6 +358,31 @@ def run_adjoint_workload(args):
         ms = e0.elapsed_time(e1) / args.steps
         res[name] = {"ms_per_step": ms, "value": deposits / (ms / 1e3),
                      "kernel_ms": st.kernel_ms / max(1, st.kernel_launches)}
+
+    # the plain FP64 adjoint on the first particles of the same workload, and the two adjoints'
+    # agreement there
+    fp64 = None
+    n64 = min(args.adjoint_fp64_particles, tr.n_part)
+    if n64 > 0:
+        sub = tr.subset(list(range(n64)))
+        x64, u64, q64 = (torch.from_numpy(a).cuda() for a in (sub.x, sub.u, sub.q))
+        d64 = rd.RadiationDetector.from_workload(det, "fp64")
+        d64.adjoint(x64, u64, q64, sub.t0, sub.dt, gE)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gx64, gu64 = d64.adjoint(x64, u64, q64, sub.t0, sub.dt, gE)
+        e1.record()
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        gxm, gum = d.adjoint(x64, u64, q64, sub.t0, sub.dt, gE)
+        torch.cuda.synchronize()
+        rate64 = W.deposits(sub, det) / (ms64 / 1e3)
+        fp64 = {"particles": n64, "ms_per_step": ms64, "value": rate64,
+                "mixed_speedup": res["adjoint"]["value"] / rate64,
+                "mixed_vs_fp64_rel_l2": {"x": float(torch.linalg.norm(gxm - gx64) / torch.linalg.norm(gx64)),
+                                         "u": float(torch.linalg.norm(gum - gu64) / torch.linalg.norm(gu64))}}
+        d64.close()
     d.close()
     line = {"metric": "deposits/sec of the adjoint (gather) kernel, gradient wrt positions and momenta",
             "value": res["adjoint"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -363,7 +390,7 @@ def run_adjoint_workload(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{tr.n_part} undulator e- (gamma 10, K 1) x 2000 steps, 64x64 cap x 1024 "
                                    "bins, anchors recomputed every 250 samples", "deposits_per_step": deposits},
-            "forward": res["forward"], "adjoint": res["adjoint"],
+            "forward": res["forward"], "adjoint": res["adjoint"], "fp64_adjoint": fp64,
             "adjoint_over_forward_time": res["adjoint"]["ms_per_step"] / res["forward"]["ms_per_step"]}
     print(json.dumps(line), flush=True)
 
