@@ -600,9 +600,12 @@ def main():
         h2d = (xh.numel() + uh.numel() + qh.numel()) * 8
         d2h = (Eh.numel() + Bh.numel()) * 4
 
-        # Two detectors on two CUDA streams: while one step's readback (and the next step's upload)
-        # runs on the copy engines, the other detector's deposit runs on the SMs.  Every step still
-        # uploads its trajectories from pinned host memory and reads its fields back to the host.
+        # Two detectors on two CUDA streams.  Step i is enqueued as upload + deposit + readback
+        # (asynchronous, into pinned host memory) on stream i % 2; the host then waits for step i-1
+        # and checks its errors.  So step i+1's upload runs on a copy engine during step i's
+        # kernel, step i's readback conversion runs before step i+1's kernel, and its copy to the
+        # host during that kernel.  Every step uploads its trajectories from pinned host memory
+        # and reads its fields back to the host.
         streams = [torch.cuda.Stream(), torch.cuda.Stream()]
         pair = [mixed, rd.RadiationDetector.from_workload(det, "mixed")]
         Ehs = [Eh, torch.empty_like(Eh).pin_memory()]
@@ -611,17 +614,18 @@ def main():
         def enqueue(i):
             pair[i % 2].zero(streams[i % 2])
             pair[i % 2].deposit(xh, uh, qh, tr.t0, tr.dt, stream=streams[i % 2])   # H2D inside the call
-
-        def finish(i):     # readback to host memory; returns when that stream's work is done
             rd.rd_read_fields(pair[i % 2].handle, Ehs[i % 2].data_ptr(), Bhs[i % 2].data_ptr(), rd.RD_F32,
-                              rd.RD_MEM_HOST, streams[i % 2])
+                              rd.RD_MEM_HOST_ASYNC, streams[i % 2])
+
+        def finish(i):     # step i's fields are on the host once its stream is done
+            pair[i % 2].synchronize(streams[i % 2])
 
         def run(n):
-            enqueue(0)
             for i in range(n):
-                if i + 1 < n:
-                    enqueue(i + 1)
-                finish(i)
+                enqueue(i)
+                if i > 0:
+                    finish(i - 1)
+            finish(n - 1)
         run(max(2, args.warmup))
         torch.cuda.synchronize()
         barrier()

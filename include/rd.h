@@ -72,8 +72,9 @@ enum { RD_FP64 = 0, RD_MIXED = 1 };
  * trajectory still holds the field of sample 1).  Not supported by rd_adjoint_trajectories.
  */
 enum { RD_NEAR = 1, RD_FAR = 2, RD_FARFIELD = 4, RD_LINEAR = 8 };
-/* where a caller buffer lives */
-enum { RD_MEM_DEVICE = 0, RD_MEM_HOST = 1 };
+/* where a caller buffer lives; RD_MEM_HOST_ASYNC: pinned host memory written asynchronously
+ * (rd_read_fields only) */
+enum { RD_MEM_DEVICE = 0, RD_MEM_HOST = 1, RD_MEM_HOST_ASYNC = 2 };
 /* element type of caller field / gradient-seed buffers */
 enum { RD_F32 = 0, RD_F64 = 1 };
 /* field whose power spectrum rd_power_spectrum computes */
@@ -159,9 +160,15 @@ RD_API rd_status rd_deposit_trajectories(rd_detector* det, const rd_traj* traj, 
 
 /*
  * Copy the accumulated fields out as E[n_pix][n_bins][3] and B[n_pix][n_bins][3] (either may be
- * NULL) of type dtype (RD_F32 / RD_F64) into memory of kind mem.  To host memory the call
- * synchronises the stream and then reports latched kernel errors; to device memory it is
- * asynchronous.  Errors: RD_ERR_ARG, RD_ERR_CUDA, RD_ERR_OOM, latched errors.
+ * NULL) of type dtype (RD_F32 / RD_F64) into memory of kind mem.  To host memory (RD_MEM_HOST)
+ * the call synchronises the stream and then reports latched kernel errors; to device memory it is
+ * asynchronous.  RD_MEM_HOST_ASYNC: E and B are page-locked host memory (cudaHostAlloc or
+ * registered); the layout conversion and the device-to-host copies are enqueued on the stream and
+ * the call returns at once, so that a caller can enqueue the next deposit (on another detector and
+ * stream) behind them and overlap the copies with its kernel.  The host buffers are complete once
+ * the stream has been synchronised (rd_synchronize then reports latched errors); the detector's
+ * readback scratch is reused by its next read, which must come after that.  Errors: RD_ERR_ARG,
+ * RD_ERR_CUDA, RD_ERR_OOM, latched errors.
  */
 RD_API rd_status rd_read_fields(rd_detector* det, void* E, void* B, int32_t dtype, int32_t mem,
                          rd_stream stream);

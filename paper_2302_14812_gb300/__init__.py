@@ -22,7 +22,7 @@ from .build import build as build_library
 __all__ = [
     "RD_OK", "RD_ERR_ARG", "RD_ERR_CUDA", "RD_ERR_OOM", "RD_ERR_STATE", "RD_ERR_TIMEOUT",
     "RD_ERR_BOUNDS", "RD_ERR_INPUT", "RD_FP64", "RD_MIXED", "RD_NEAR", "RD_FAR", "RD_MEM_DEVICE",
-    "RD_MEM_HOST", "RD_F32", "RD_F64", "RDError", "rd_detector_desc", "rd_traj", "rd_stats",
+    "RD_MEM_HOST", "RD_MEM_HOST_ASYNC", "RD_F32", "RD_F64", "RDError", "rd_detector_desc", "rd_traj", "rd_stats",
     "load_library", "library_path", "rd_create_detector", "rd_destroy", "rd_zero_fields",
     "rd_deposit_trajectories", "rd_read_fields", "rd_synchronize", "rd_get_stats",
     "rd_set_timing", "rd_adjoint_trajectories", "rd_deposit_batch", "rd_set_chunk", "rd_autotune",
@@ -33,7 +33,7 @@ __all__ = [
 RD_OK, RD_ERR_ARG, RD_ERR_CUDA, RD_ERR_OOM, RD_ERR_STATE, RD_ERR_TIMEOUT, RD_ERR_BOUNDS, RD_ERR_INPUT = range(8)
 RD_FP64, RD_MIXED = 0, 1
 RD_NEAR, RD_FAR, RD_FARFIELD, RD_LINEAR = 1, 2, 4, 8
-RD_MEM_DEVICE, RD_MEM_HOST = 0, 1
+RD_MEM_DEVICE, RD_MEM_HOST, RD_MEM_HOST_ASYNC = 0, 1, 2
 RD_F32, RD_F64 = 0, 1
 RD_SPEC_E, RD_SPEC_B = 0, 1
 

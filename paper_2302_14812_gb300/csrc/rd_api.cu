@@ -481,7 +481,7 @@ rd_status rd_read_fields(rd_detector* d, void* E, void* B, int32_t dtype, int32_
     g_err.clear();
     if (!d) return fail(RD_ERR_ARG, "detector is NULL");
     if (dtype != RD_F32 && dtype != RD_F64) return fail(RD_ERR_ARG, "bad dtype %d", dtype);
-    if (mem != RD_MEM_DEVICE && mem != RD_MEM_HOST) return fail(RD_ERR_ARG, "bad mem %d", mem);
+    if (mem != RD_MEM_DEVICE && mem != RD_MEM_HOST && mem != RD_MEM_HOST_ASYNC) return fail(RD_ERR_ARG, "bad mem %d", mem);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (!E && !B) return RD_OK;
     const size_t elem = dtype == RD_F32 ? sizeof(float) : sizeof(double);
@@ -499,6 +499,7 @@ rd_status rd_read_fields(rd_detector* d, void* E, void* B, int32_t dtype, int32_
             "rd_read_fields");
     if (E) RD_CUDA(cudaMemcpyAsync(E, dE, one, cudaMemcpyDeviceToHost, s), "copy E to host");
     if (B) RD_CUDA(cudaMemcpyAsync(B, dB, one, cudaMemcpyDeviceToHost, s), "copy B to host");
+    if (mem == RD_MEM_HOST_ASYNC) return RD_OK;
     DevCounters c;
     RD_CUDA(cudaMemcpyAsync(&c, d->counters, sizeof c, cudaMemcpyDeviceToHost, s), "read counters");
     RD_CUDA(cudaStreamSynchronize(s), "rd_read_fields");

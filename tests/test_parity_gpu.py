@@ -268,6 +268,13 @@ def test_read_fields_device_and_f32():
     torch.cuda.synchronize()
     assert np.array_equal(E32, E64.astype(np.float32))
     assert np.array_equal(Ed.cpu().numpy(), E32) and np.array_equal(Bd.cpu().numpy(), B32)
+    # asynchronous readback into page-locked host memory, on a side stream
+    s = torch.cuda.Stream()
+    Ea = torch.empty((det.n_pix, det.n_bins, 3), dtype=torch.float32).pin_memory()
+    Ba = torch.empty_like(Ea).pin_memory()
+    rd.rd_read_fields(d.handle, Ea.data_ptr(), Ba.data_ptr(), rd.RD_F32, rd.RD_MEM_HOST_ASYNC, s)
+    d.synchronize(s)
+    assert np.array_equal(Ea.numpy(), E32) and np.array_equal(Ba.numpy(), B32)
     d.close()
 
 
