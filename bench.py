@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-farfield", action="store_true", help="skip the far-field-limit leg")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the linear-interpolation, streaming and spectrum legs")
     ap.add_argument("--workload", choices=["undulator", "batch", "adjoint", "plasma_mirror"], default="undulator",
                     help="undulator: the headline deposit; batch: 64 uneven problems, one persistent "
                          "launch vs separate launches; adjoint: gradient kernel")
@@ -180,6 +182,15 @@ def profile_traffic():
         return None
     cur = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
     return float(m.group(1)) if h.group(1) == cur else None
+
+
+def hbm_peak():
+    """(GB/s, kind): the measured copy bandwidth of this machine's GPUs if recorded, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
 
 
 def host_link_gbs(host_out, host_in, reps: int = 3):
@@ -589,6 +600,68 @@ def main():
                    "speedup_vs_exact": ms_step / ms_ff,
                    "mode": "far-field limit: Eq. 3 arrival times, radiation term at the cell direction"}
 
+    # ------- linear interpolation, streamed stretches and spectra on the same workload -------
+    variants = None
+    if not args.no_variants:
+        variants = {}
+
+        def timed(fn, n):
+            for _ in range(max(1, min(args.warmup, 2))):
+                fn()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(n):
+                fn()
+            e1.record(stream)
+            barrier()
+            return slowest(e0.elapsed_time(e1)) / n
+
+        det_lin = W.Detector(det.pix_pos, det.pix_t0, det.t_min, det.dt_det, det.n_bins,
+                             W.RD_NEAR | W.RD_FAR | W.RD_LINEAR)
+        ld = rd.RadiationDetector.from_workload(det_lin, "mixed")
+
+        def lin_step():
+            ld.zero()
+            ld.deposit(xd, ud, qd, tr.t0, tr.dt)
+        ms_lin = timed(lin_step, 2)
+        ld.close()
+        variants["linear"] = {"value": deposits * world / (ms_lin / 1e3), "ms_per_step": ms_lin,
+                              "vs_held": ms_step / ms_lin,
+                              "mode": "RD_LINEAR: field linear in arrival time over each interval"}
+
+        n_str = 8
+        bounds = np.linspace(0, tr.n_samples, n_str + 1).astype(int)
+        pieces = [(xd[:, a:b].contiguous(), ud[:, a:b].contiguous(), tr.t0 + a * tr.dt)
+                  for a, b in zip(bounds[:-1], bounds[1:])]
+        sd = rd.RadiationDetector.from_workload(det, "mixed")
+
+        def stream_step():
+            sd.stream_reset()
+            sd.zero()
+            for px, pu, pt0 in pieces:
+                sd.deposit_stream(px, pu, qd, pt0, tr.dt)
+        ms_str = timed(stream_step, 2)
+        E_str, _ = sd.read("float64", "cpu")
+        sd.close()
+        del pieces
+        variants["stream"] = {"value": deposits * world / (ms_str / 1e3), "ms_per_step": ms_str,
+                              "stretches": n_str, "vs_single_call": ms_step / ms_str,
+                              "rel_l2_E_vs_single_call": float(np.linalg.norm(E_str - E_mixed) / np.linalg.norm(E_mixed)),
+                              "mode": f"rd_deposit_stream: the trajectories handed over in {n_str} stretches"}
+        del E_str
+
+        ms_sp = timed(lambda: mixed.power_spectrum("E"), 3)
+        nbytes = det.n_pix * det.n_bins * 32 + det.n_pix * (det.n_bins // 2 + 1) * 4
+        peak, kind = hbm_peak()
+        gbs = nbytes / (ms_sp / 1e3) / 1e9
+        variants["spectrum"] = {"ms": ms_sp, "spectra_per_s": det.n_pix * world / (ms_sp / 1e3),
+                                "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                             "frac": gbs / peak, "peak_kind": kind,
+                                             "bytes": nbytes,
+                                             "bytes_kind": "field sectors read (32 B per bin and cell) + spectrum written"},
+                                "mode": "rd_power_spectrum of E: two FP32 transforms per cell in shared memory"}
+
     # ---------------- end to end through the C ABI with host buffers ----------------
     e2e = None
     if not args.no_e2e:
@@ -596,7 +669,7 @@ def main():
         uh = torch.from_numpy(tr.u).pin_memory()
         qh = torch.from_numpy(tr.q).pin_memory()
         Eh = torch.empty((det.n_pix, det.n_bins, 3), dtype=torch.float32).pin_memory()
-        Bh = torch.empty_like(Eh)
+        Bh = torch.empty_like(Eh).pin_memory()
         h2d = (xh.numel() + uh.numel() + qh.numel()) * 8
         d2h = (Eh.numel() + Bh.numel()) * 4
 
@@ -684,6 +757,7 @@ def main():
         "clocks": clocks,
         "fp64_gpu": fp64_info,
         "farfield": ff_info,
+        "variants": variants,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "parity_vs_oracle": parity,

@@ -853,8 +853,9 @@ rd_status rd_power_spectrum(rd_detector* d, int32_t which, float* out, rd_stream
     const int N = d->n_bins;
     if (N < 2 || (N & (N - 1)) != 0) return fail(RD_ERR_ARG, "n_bins must be a power of two >= 2 (got %d)", N);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const size_t work = sizeof(float2) * 2 * (size_t)d->n_pix * N;
-    rd_status st = ensure(&d->spec, &d->spec_bytes, 2 * work, s, "spectrum scratch");
+    // work arrays for the pass-per-launch transform of long series (none for the fused one)
+    const size_t work = spectrum_fused(N) ? 0 : sizeof(float2) * 2 * (size_t)d->n_pix * N;
+    rd_status st = work ? ensure(&d->spec, &d->spec_bytes, 2 * work, s, "spectrum scratch") : RD_OK;
     if (st != RD_OK) return st;
     if (d->spec_n != N) {
         st = ensure(&d->spec_tw, &d->spec_tw_bytes, sizeof(float2) * (N / 2), s, "twiddles");
@@ -867,8 +868,8 @@ rd_status rd_power_spectrum(rd_detector* d, int32_t which, float* out, rd_stream
                 "twiddles");
         d->spec_n = N;
     }
-    float2* z = static_cast<float2*>(d->spec);
-    float2* y = reinterpret_cast<float2*>(static_cast<char*>(d->spec) + work);
+    float2* z = work ? static_cast<float2*>(d->spec) : nullptr;
+    float2* y = work ? reinterpret_cast<float2*>(static_cast<char*>(d->spec) + work) : nullptr;
     RD_CUDA(launch_power_spectrum(d->fields, d->precision, d->n_pix, N, which == RD_SPEC_B ? 3 : 0, z, y,
                                   static_cast<const float2*>(d->spec_tw), (float)(d->dt_det * d->dt_det), out, s),
             "power spectrum");

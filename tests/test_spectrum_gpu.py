@@ -55,6 +55,29 @@ def test_power_spectrum_equals_fft_of_fields(precision):
     d.close()
 
 
+@pytest.mark.parametrize("n_bins", [2, 8192, 16384])
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_power_spectrum_lengths(n_bins, precision):
+    """The shortest series, the longest transformed in shared memory (8192) and the shortest
+    transformed by passes over the whole batch (16384), against numpy's FFT of the same fields."""
+    import torch
+    rng = np.random.default_rng(n_bins)
+    tr = W.random_smooth(2, 300, 0.02, max_u=2.0, seed=9)
+    pos = rng.normal(size=(37, 3)) * 15.0
+    dt_det = 8.0 / n_bins
+    det = W.Detector(pos, None, 10.0, dt_det, n_bins)
+    d = rd.RadiationDetector.from_workload(det, precision)
+    d.deposit(torch.from_numpy(tr.x).cuda(), torch.from_numpy(tr.u).cuda(), torch.from_numpy(tr.q).cuda(),
+              tr.t0, tr.dt)
+    E, B = d.read()
+    assert np.any(E != 0.0)
+    for field, F in (("E", E), ("B", B)):
+        P = d.power_spectrum(field).cpu().numpy()
+        assert P.shape == (det.n_pix, n_bins // 2 + 1)
+        assert rel_l2(P, numpy_power(F, det.dt_det)) <= 1e-5
+    d.close()
+
+
 def test_power_spectrum_needs_power_of_two_bins():
     det = W.Detector(np.array([[10.0, 0.0, 0.0]]), None, 0.0, 0.1, 1000)
     d = rd.RadiationDetector.from_workload(det, "mixed")
