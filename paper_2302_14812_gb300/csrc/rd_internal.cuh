@@ -175,7 +175,7 @@ cudaError_t launch_read_fields(const void* fields, int precision, int n_pix, int
                                void* B, int dtype, cudaStream_t s);
 // power spectra (rd_spectrum.cu): twiddles exp(-2 pi i j / N), j < N/2, computed on the host
 void fill_twiddles(float2* host, int N);
-constexpr int kFusedMaxN = 8192;   // longest series transformed in shared memory (20 N bytes per CTA)
+constexpr int kFusedMaxN = 8192;   // longest series transformed in shared memory (24.5 N bytes per CTA)
 bool spectrum_fused(int N);
 cudaError_t launch_power_spectrum(const void* fields, int precision, int n_pix, int N, int c0, float2* z,
                                   float2* y, const float2* tw, float scale, float* P, cudaStream_t s);

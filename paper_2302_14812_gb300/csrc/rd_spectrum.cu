@@ -79,52 +79,120 @@ __global__ void k_spectrum_power(const float2* __restrict__ X, int n_pix, int N,
     }
 }
 
+// The three components c0..c0+2 (E: c0 = 0, B: c0 = 3) of bin b of a cell's row, with vector loads.
+template <typename T, int STRIDE>
+struct Load3;
+template <>
+struct Load3<float, 8> {
+    static __device__ __forceinline__ float3 get(const float* row, int b, int c0)
+    {
+        const float* v = row + (size_t)b * 8;
+        const float4 a = __ldg(reinterpret_cast<const float4*>(v));
+        if (c0 == 0) return make_float3(a.x, a.y, a.z);
+        const float2 c = __ldg(reinterpret_cast<const float2*>(v + 4));
+        return make_float3(a.w, c.x, c.y);
+    }
+};
+template <>
+struct Load3<double, 6> {
+    static __device__ __forceinline__ float3 get(const double* row, int b, int c0)
+    {
+        const double* v = row + (size_t)b * 6;
+        if (c0 == 0) {
+            const double2 a = __ldg(reinterpret_cast<const double2*>(v));
+            return make_float3((float)a.x, (float)a.y, (float)__ldg(v + 2));
+        }
+        const double2 c = __ldg(reinterpret_cast<const double2*>(v + 4));
+        return make_float3((float)__ldg(v + 3), (float)c.x, (float)c.y);
+    }
+};
+
+// Shared-memory index of element i of a transform: one float2 of padding after every 32, so that
+// the bit-reversed stores of the load phase (consecutive bins -> elements N/32 apart) spread over
+// the banks.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
+
 __device__ __forceinline__ void butterfly(float2* z, int i0, int i1, float2 w)
 {
-    const float2 a = z[i0], b = cmul(z[i1], w);
-    z[i0] = make_float2(a.x + b.x, a.y + b.y);
-    z[i1] = make_float2(a.x - b.x, a.y - b.y);
+    const float2 a = z[pad(i0)], b = cmul(z[pad(i1)], w);
+    z[pad(i0)] = make_float2(a.x + b.x, a.y + b.y);
+    z[pad(i1)] = make_float2(a.x - b.x, a.y - b.y);
 }
 
-// One CTA per cell at a time (persistent over cells).  Shared memory: Z1[N], Z2[N], twiddles[N/2].
-// The bins are loaded in bit-reversed order, so in-place decimation-in-time butterflies (span h,
-// twiddle exp(-2 pi i p / (2h)) = tw[p N / (2h)]) leave the transforms in natural order.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// Two stages at once on the four elements i0 + {0, h, 2h, 3h} (i0 = 4 G h + p, p < h): span h
+// pairs (0, 1) and (2, 3) with twiddle w1 = exp(-2 pi i p / (2h)), then span 2h pairs (0, 2) with
+// w2a = exp(-2 pi i p / (4h)) and (1, 3) with w2b = exp(-2 pi i (p + h) / (4h)).
+__device__ __forceinline__ void butterfly2x2(float2* z, int i0, int h, float2 w1, float2 w2a, float2 w2b)
+{
+    const float2 a0 = z[pad(i0)], a1 = cmul(z[pad(i0 + h)], w1);
+    const float2 a2 = z[pad(i0 + 2 * h)], a3 = cmul(z[pad(i0 + 3 * h)], w1);
+    const float2 b0 = cadd(a0, a1), b1 = csub(a0, a1), b2 = cmul(cadd(a2, a3), w2a), b3 = cmul(csub(a2, a3), w2b);
+    z[pad(i0)] = cadd(b0, b2);
+    z[pad(i0 + 2 * h)] = csub(b0, b2);
+    z[pad(i0 + h)] = cadd(b1, b3);
+    z[pad(i0 + 3 * h)] = csub(b1, b3);
+}
+
+// One CTA per cell at a time (persistent over cells).  Shared memory: Z1 and Z2 (N elements each,
+// padded) and the twiddles of every stage, stage h (span h) holding exp(-2 pi i p / (2h)), p < h,
+// at h - 1 + p (contiguous in p, so a warp's lanes read consecutive entries).  The bins are loaded
+// in bit-reversed order, so in-place decimation-in-time butterflies leave the transforms in
+// natural order.
 template <typename T, int STRIDE>
 __global__ void __launch_bounds__(256) k_spectrum_fused(const T* __restrict__ fields, int n_pix, int N, int logN,
                                                         int c0, const float2* __restrict__ tw_g, float scale,
                                                         float* __restrict__ P)
 {
     extern __shared__ float2 sm[];
+    const int zlen = pad(N - 1) + 1;
     float2* z1 = sm;
-    float2* z2 = sm + N;
-    float2* tw = sm + 2 * N;
+    float2* z2 = sm + zlen;
+    float2* tw = sm + 2 * zlen;
     const int half_n = N >> 1;
-    for (int j = threadIdx.x; j < half_n; j += blockDim.x) tw[j] = tw_g[j];
+    for (int h = 1; h < N; h <<= 1) {
+        const int step = half_n / h;
+        for (int p = threadIdx.x; p < h; p += blockDim.x) tw[h - 1 + p] = tw_g[p * step];
+    }
     const int nk = half_n + 1;
     for (int cell = blockIdx.x; cell < n_pix; cell += gridDim.x) {
-        const T* f = fields + (size_t)cell * N * STRIDE + c0;
+        const T* row = fields + (size_t)cell * N * STRIDE;
+#pragma unroll 4
         for (int b = threadIdx.x; b < N; b += blockDim.x) {
-            const int r = (int)(__brev((unsigned)b) >> (32 - logN));
-            const T* v = f + (size_t)b * STRIDE;
-            z1[r] = make_float2((float)v[0], (float)v[1]);
-            z2[r] = make_float2((float)v[2], 0.f);
+            const int r = pad((int)(__brev((unsigned)b) >> (32 - logN)));
+            const float3 v = Load3<T, STRIDE>::get(row, b, c0);
+            z1[r] = make_float2(v.x, v.y);
+            z2[r] = make_float2(v.z, 0.f);
         }
         __syncthreads();
-        for (int h = 1; h < N; h <<= 1) {
-            const int step = half_n / h;
+        int h = 1;
+        for (; 4 * h <= N; h <<= 2) {                 // stages of span h and 2h in one pass
+            const float2* wa = tw + (h - 1);
+            const float2* wb = tw + (2 * h - 1);
+            for (int t = threadIdx.x; t < (N >> 2); t += blockDim.x) {
+                const int G = t / h, p = t - G * h;
+                const int i0 = 4 * G * h + p;
+                const float2 w1 = wa[p], w2a = wb[p], w2b = wb[p + h];
+                butterfly2x2(z1, i0, h, w1, w2a, w2b);
+                butterfly2x2(z2, i0, h, w1, w2a, w2b);
+            }
+            __syncthreads();
+        }
+        if (h < N) {                                  // odd number of stages: the last, span N/2
+            const float2* wh = tw + (h - 1);
             for (int t = threadIdx.x; t < half_n; t += blockDim.x) {
-                const int g = t / h, p = t - g * h;
-                const int i0 = 2 * g * h + p;
-                const float2 w = tw[p * step];
-                butterfly(z1, i0, i0 + h, w);
-                butterfly(z2, i0, i0 + h, w);
+                const float2 w = wh[t];
+                butterfly(z1, t, t + h, w);
+                butterfly(z2, t, t + h, w);
             }
             __syncthreads();
         }
         float* out = P + (size_t)cell * nk;
         for (int k = threadIdx.x; k < nk; k += blockDim.x) {
             const int km = (N - k) & (N - 1);
-            const float2 a = z1[k], am = z1[km], c = z2[k];
+            const float2 a = z1[pad(k)], am = z1[pad(km)], c = z2[pad(k)];
             const float pxy = 0.5f * (a.x * a.x + a.y * a.y + am.x * am.x + am.y * am.y);
             out[k] = scale * (pxy + (c.x * c.x + c.y * c.y));
         }
@@ -160,7 +228,7 @@ cudaError_t launch_power_spectrum(const void* fields, int precision, int n_pix, 
     if (spectrum_fused(N)) {
         int logN = 0;
         while ((1 << logN) < N) ++logN;
-        const size_t smem = sizeof(float2) * (2 * (size_t)N + N / 2);
+        const size_t smem = sizeof(float2) * (2 * (size_t)(N + N / 32) + N);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
