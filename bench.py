@@ -693,17 +693,22 @@ def main():
         def finish(i):     # step i's fields are on the host once its stream is done
             pair[i % 2].synchronize(streams[i % 2])
 
-        def run(n):
+        def run(n, t0):      # returns the host time at which each step's fields had arrived
+            done = []
             for i in range(n):
                 enqueue(i)
                 if i > 0:
                     finish(i - 1)
+                    done.append(time.perf_counter() - t0)
             finish(n - 1)
-        run(max(2, args.warmup))
+            done.append(time.perf_counter() - t0)
+            return done
+        mixed.set_timing(False)
+        run(max(2, args.warmup), time.perf_counter())
         torch.cuda.synchronize()
         barrier()
         t = time.perf_counter()
-        run(args.steps)
+        done = run(args.steps, t)
         torch.cuda.synchronize()
         barrier()
         secs = slowest(time.perf_counter() - t)
@@ -711,6 +716,7 @@ def main():
         e2e = {"value": deposits * world * args.steps / secs, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * secs / args.steps,
+               "step_done_ms": [round(1e3 * v, 2) for v in done],
                "pipeline": "2 detectors on 2 CUDA streams: copies of one step overlap the next step's deposit",
                "host_link": host_link_gbs(Ehs[0], xh)}
     mixed.close()

@@ -219,12 +219,13 @@ __device__ __forceinline__ void scaled_field(const Field& o, float* G)
 
 // Linear interpolation (RD_LINEAR): over the interval the field goes linearly from G0 = gp (previous
 // sample) to G (this sample); the part [s0, s1] of the interval (dt units from its start, length L)
-// weighs G0 (s1 - s0) + (G - G0) (s1^2 - s0^2) / (2 L).  Interval of cell j passing two or more bin
+// weighs G0 (s1 - s0) + (G - G0) (s1^2 - s0^2) / (2 L) = G0 (s1 - s0 - ramp) + G ramp with
+// ramp = (s1^2 - s0^2) / (2 L).  Interval of cell j passing two or more bin
 // edges (exact walk only): flush the bin being filled, every whole bin, and leave the last, partial
 // bin in the accumulator with the time already in it; fn comes back below W (no edge left for the
 // common path).
 template <bool TRACK, bool FF>
-__device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* dG, float L, float inv2L,
+__device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* G, float L, float inv2L,
                                                 const Consts& C, float& fn, int k, int k_begin, int k_end)
 {
     constexpr int NF = FF ? 3 : 6;                                  // carried field components
@@ -241,7 +242,7 @@ __device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* dG
         const float ramp = (s1 * s1 - s0 * s0) * inv2L;
         float v[6];
 #pragma unroll
-        for (int q = 0; q < NF; ++q) v[q] = fmaf(c.gp[q][j], C.W, dG[q] * ramp);
+        for (int q = 0; q < NF; ++q) v[q] = fmaf(c.gp[q][j], C.W - ramp, G[q] * ramp);
         bin_b<FF>(c, j, v, v + 3, v + 3);
         flush(C, b0 + i, c.bo[j] + i, v[0], v[1], v[2], v[3], v[4], v[5]);
     }
@@ -250,7 +251,7 @@ __device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* dG
     const float len = fmaf(-(float)m, C.W, f);
     const float ramp = (L * L - s0 * s0) * inv2L;
 #pragma unroll
-    for (int q = 0; q < NF; ++q) c.acc[q][j] = fmaf(c.gp[q][j], len, dG[q] * ramp);
+    for (int q = 0; q < NF; ++q) c.acc[q][j] = fmaf(c.gp[q][j], len - ramp, G[q] * ramp);
     c.bo[j] += m;
     fn = fminf(fmaxf(len, 0.f), C.W * 0.99999994f);
     if (TRACK) {
@@ -280,7 +281,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
     constexpr int NF = FF ? 3 : 6;                  // carried field components (far field: E only)
     Field o[NC];
     float fn[NC];
-    float G[NC][6], dG[NC][6], L[NC], inv2L[NC], ramp1[NC];     // linear interpolation only
+    float G[NC][6], L[NC], inv2L[NC], ramp1[NC];               // linear interpolation only
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         if (FF)
@@ -300,11 +301,10 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
             inv2L[j] = 0.5f * fast_rcp(L[j]);
             const float len1 = fminf(t, C.W) - c.f[j];
             ramp1[j] = (len1 * len1) * inv2L[j];
+            // G0 (s1 - s0) + (G - G0) ramp = G0 (s1 - s0 - ramp) + G ramp
+            const float a1 = len1 - ramp1[j];
 #pragma unroll
-            for (int i = 0; i < NF; ++i) {
-                dG[j][i] = G[j][i] - c.gp[i][j];
-                c.acc[i][j] = fmaf(c.gp[i][j], len1, fmaf(dG[j][i], ramp1[j], c.acc[i][j]));
-            }
+            for (int i = 0; i < NF; ++i) c.acc[i][j] = fmaf(c.gp[i][j], a1, fmaf(G[j][i], ramp1[j], c.acc[i][j]));
         } else {
             const float ws = (fminf(t, C.W) - c.f[j]) * o[j].S;
             const float wb = ws * o[j].rinv;
@@ -324,7 +324,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             if (LIN)
-                multi_edges_lin<TRACK, FF>(c, j, dG[j], L[j], inv2L[j], C, fn[j], k, k_begin, k_end);
+                multi_edges_lin<TRACK, FF>(c, j, G[j], L[j], inv2L[j], C, fn[j], k, k_begin, k_end);
             else
                 multi_edges<TRACK, FF>(c, j, o[j], C, fn[j], k, k_begin, k_end);
         }
@@ -346,7 +346,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
                 if (LIN) {
                     const float ramp2 = fmaf(0.5f, L[j], -ramp1[j]);
 #pragma unroll
-                    for (int i = 0; i < NF; ++i) c.acc[i][j] = fmaf(c.gp[i][j], rem, dG[j][i] * ramp2);
+                    for (int i = 0; i < NF; ++i) c.acc[i][j] = fmaf(c.gp[i][j], rem - ramp2, G[j][i] * ramp2);
                 } else {
                     const float rs = rem * o[j].S;
                     const float rbw = rs * o[j].rinv;
@@ -377,7 +377,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
                 const float ramp2 = fmaf(0.5f, L[j], -ramp1[j]);
 #pragma unroll
                 for (int i = 0; i < NF; ++i) {
-                    const float v = fmaf(c.gp[i][j], rem, dG[j][i] * ramp2);
+                    const float v = fmaf(c.gp[i][j], rem - ramp2, G[j][i] * ramp2);
                     c.acc[i][j] = cr ? v : c.acc[i][j];
                 }
             } else {
