@@ -679,19 +679,28 @@ def main():
         # kernel, step i's readback conversion runs before step i+1's kernel, and its copy to the
         # host during that kernel.  Every step uploads its trajectories from pinned host memory
         # and reads its fields back to the host.
+        # The readback runs on a high-priority stream (after the deposit's event), so that its layout
+        # conversion is dispatched ahead of the CTAs of the next step's kernel, which is already
+        # queued on the other stream.
         streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        top = torch.cuda.Stream.priority_range()[1] if hasattr(torch.cuda.Stream, "priority_range") else -1
+        rstreams = [torch.cuda.Stream(priority=top), torch.cuda.Stream(priority=top)]
         pair = [mixed, rd.RadiationDetector.from_workload(det, "mixed")]
         Ehs = [Eh, torch.empty_like(Eh).pin_memory()]
         Bhs = [Bh, torch.empty_like(Bh).pin_memory()]
 
         def enqueue(i):
-            pair[i % 2].zero(streams[i % 2])
-            pair[i % 2].deposit(xh, uh, qh, tr.t0, tr.dt, stream=streams[i % 2])   # H2D inside the call
-            rd.rd_read_fields(pair[i % 2].handle, Ehs[i % 2].data_ptr(), Bhs[i % 2].data_ptr(), rd.RD_F32,
-                              rd.RD_MEM_HOST_ASYNC, streams[i % 2])
+            j = i % 2
+            pair[j].zero(streams[j])
+            pair[j].deposit(xh, uh, qh, tr.t0, tr.dt, stream=streams[j])   # H2D inside the call
+            ev = torch.cuda.Event()
+            ev.record(streams[j])
+            rstreams[j].wait_event(ev)
+            rd.rd_read_fields(pair[j].handle, Ehs[j].data_ptr(), Bhs[j].data_ptr(), rd.RD_F32,
+                              rd.RD_MEM_HOST_ASYNC, rstreams[j])
 
-        def finish(i):     # step i's fields are on the host once its stream is done
-            pair[i % 2].synchronize(streams[i % 2])
+        def finish(i):     # step i's fields are on the host once its readback stream is done
+            pair[i % 2].synchronize(rstreams[i % 2])
 
         def run(n, t0):      # returns the host time at which each step's fields had arrived
             done = []
@@ -717,7 +726,8 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * secs / args.steps,
                "step_done_ms": [round(1e3 * v, 2) for v in done],
-               "pipeline": "2 detectors on 2 CUDA streams: copies of one step overlap the next step's deposit",
+               "pipeline": "2 detectors on 2 CUDA streams, readbacks on high-priority streams: copies of one step "
+                           "overlap the next step's deposit",
                "host_link": host_link_gbs(Ehs[0], xh)}
     mixed.close()
 

@@ -29,6 +29,7 @@ struct rd_detector {
     void* fields = nullptr;          // internal accumulators
     size_t field_bytes = 0;
     DevCounters* counters = nullptr;
+    DevCounters* host_counters = nullptr;   // page-locked copy target of `counters`
     void* rec = nullptr;             // per-sample records
     size_t rec_bytes = 0;
     void* stage = nullptr;           // device copy of host trajectories
@@ -329,6 +330,7 @@ rd_status rd_create_detector(const rd_detector_desc* desc, rd_stream stream, rd_
     cudaError_t e = cudaMalloc(&d->cells, sizeof(D4) * cells.size());
     if (e == cudaSuccess) e = cudaMalloc(&d->fields, d->field_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&d->counters, sizeof(DevCounters));
+    if (e == cudaSuccess) e = cudaMallocHost(&d->host_counters, sizeof(DevCounters));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d->cells, cells.data(), sizeof(D4) * cells.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d->fields, 0, d->field_bytes, s);
@@ -339,6 +341,7 @@ rd_status rd_create_detector(const rd_detector_desc* desc, rd_stream stream, rd_
         cudaFree(d->cells);
         cudaFree(d->fields);
         cudaFree(d->counters);
+        cudaFreeHost(d->host_counters);
         delete d;
         return st;
     }
@@ -356,6 +359,7 @@ rd_status rd_destroy(rd_detector* d)
     cudaFree(d->cells);
     cudaFree(d->fields);
     cudaFree(d->counters);
+    cudaFreeHost(d->host_counters);
     cudaFree(d->rec);
     cudaFree(d->stage);
     cudaFree(d->readback);
@@ -500,10 +504,10 @@ rd_status rd_read_fields(rd_detector* d, void* E, void* B, int32_t dtype, int32_
     if (E) RD_CUDA(cudaMemcpyAsync(E, dE, one, cudaMemcpyDeviceToHost, s), "copy E to host");
     if (B) RD_CUDA(cudaMemcpyAsync(B, dB, one, cudaMemcpyDeviceToHost, s), "copy B to host");
     if (mem == RD_MEM_HOST_ASYNC) return RD_OK;
-    DevCounters c;
-    RD_CUDA(cudaMemcpyAsync(&c, d->counters, sizeof c, cudaMemcpyDeviceToHost, s), "read counters");
+    RD_CUDA(cudaMemcpyAsync(d->host_counters, d->counters, sizeof(DevCounters), cudaMemcpyDeviceToHost, s),
+            "read counters");
     RD_CUDA(cudaStreamSynchronize(s), "rd_read_fields");
-    return latched(c);
+    return latched(*d->host_counters);
 }
 
 rd_status rd_synchronize(rd_detector* d, rd_stream stream)
@@ -511,9 +515,10 @@ rd_status rd_synchronize(rd_detector* d, rd_stream stream)
     g_err.clear();
     if (!d) return fail(RD_ERR_ARG, "detector is NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    DevCounters c;
-    RD_CUDA(cudaMemcpyAsync(&c, d->counters, sizeof c, cudaMemcpyDeviceToHost, s), "read counters");
+    RD_CUDA(cudaMemcpyAsync(d->host_counters, d->counters, sizeof(DevCounters), cudaMemcpyDeviceToHost, s),
+            "read counters");
     RD_CUDA(cudaStreamSynchronize(s), "rd_synchronize");
+    const DevCounters c = *d->host_counters;
     if (c.errors) {
         RD_CUDA(cudaMemsetAsync(&d->counters->errors, 0, sizeof(unsigned), s), "clear errors");
         RD_CUDA(cudaStreamSynchronize(s), "rd_synchronize");
@@ -526,9 +531,10 @@ rd_status rd_get_stats(rd_detector* d, rd_stream stream, rd_stats* out)
     g_err.clear();
     if (!d || !out) return fail(RD_ERR_ARG, "detector/out is NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    DevCounters c;
-    RD_CUDA(cudaMemcpyAsync(&c, d->counters, sizeof c, cudaMemcpyDeviceToHost, s), "read counters");
+    RD_CUDA(cudaMemcpyAsync(d->host_counters, d->counters, sizeof(DevCounters), cudaMemcpyDeviceToHost, s),
+            "read counters");
     RD_CUDA(cudaStreamSynchronize(s), "rd_get_stats");
+    const DevCounters c = *d->host_counters;
     out->n_clipped = (int64_t)c.clipped;
     out->n_bin_crossings = (int64_t)c.crossings;
     out->n_deposits = d->n_deposits;
