@@ -27,6 +27,7 @@ struct ACell {
     float f;            // time spent in bin b, units of dt
     float Rpd;          // R_{k-1} + dt
     int b;              // current bin
+    int bx;             // bin of the previous arrival time for its end-point term (b unless corrected)
     float g[6];         // seed of bin b (zero outside the window)
     float np[3];        // n of the previous sample
     float pend[6];      // partial gradient of the previous sample: d/dx (3), d/dbeta (3)
@@ -110,9 +111,25 @@ __device__ __forceinline__ void sum_rows(const float4* row, int ns, int lane, fl
 // EXACT = false (fast walk): an interval that passes two or more bin edges is not handled; the cell
 // is stopped instead (stop = true; it outputs zeros until the tile is walked again with EXACT = true
 // from its saved start).
+// Bin of sample k's arrival time at cell `cell`, from Eq. 2 in FP64 (the walk's FP32 position can
+// be off by ~1e-5 bin; near a bin edge that decides the bin of the end-point terms).
+__device__ __forceinline__ int exact_bin(const AdjointParams& P, const double* xp, int cell, int k)
+{
+    const D4 cl = P.cells[cell];
+    const double* xk = xp + 3 * (size_t)k;
+    double R;
+    return clamp_bin(floor(arrival_bins(xk[0], xk[1], xk[2], cl, P.t0, k, P.dt, P.inv_dt_det, R)));
+}
+
+__device__ __forceinline__ float dot6(float Ex, float Ey, float Ez, float Bx, float By, float Bz, const float* g)
+{
+    return Ex * g[0] + Ey * g[1] + Ez * g[2] + Bx * g[3] + By * g[4] + Bz * g[5];
+}
+
 template <bool LAST, bool EXACT>
 __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointParams& P, float q,
-                                         float near, float far, int b_end, float f_end, float* out, bool& stop)
+                                         float near, float far, int b_end, float f_end, float* out, bool& stop,
+                                         const double* xp, int cell, int k)
 {
     const float W = P.W;
     // ---- forward: geometry, arrival increment, Eq. 1 ----
@@ -138,8 +155,14 @@ __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointP
 
     // ---- transpose of the integrating deposit: gathered seed and end-point seeds ----
     // F_k . g(bin(u_{k-1})): the seed of the bin the interval starts in
-    float a_beg = Ex * c.g[0] + Ey * c.g[1] + Ez * c.g[2] + Bx * c.g[3] + By * c.g[4] + Bz * c.g[5];
-    float a_end = a_beg;
+    const float a_walk = dot6(Ex, Ey, Ez, Bx, By, Bz, c.g);
+    float a_beg = a_walk;
+    if (c.bx != c.b) {
+        float t[6];
+        load_seed(c.row, P.n_bins, c.bx, t);
+        a_beg = dot6(Ex, Ey, Ez, Bx, By, Bz, t);
+    }
+    float a_end = a_walk;
     const float fn = LAST ? fmaf((float)(b_end - c.b), W, f_end) : fmaf(num, rden, c.f);
     // the part of the interval inside bin b, then (on a crossing) the rest in the next bin(s)
     const float w1 = (fminf(fn, W) - c.f) * P.du_scale;
@@ -186,8 +209,20 @@ __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointP
         for (int i = 0; i < 6; ++i) G[i] = fmaf(c.g[i], w2, G[i]);
         c.f = rem;
         // F_k . g(bin(u_k))
-        a_end = Ex * c.g[0] + Ey * c.g[1] + Ez * c.g[2] + Bx * c.g[3] + By * c.g[4] + Bz * c.g[5];
+        a_end = dot6(Ex, Ey, Ez, Bx, By, Bz, c.g);
     }
+    // the end-point terms take the bin of the exact arrival time: rarely another one than the walk's,
+    // and only where the walk ends within P.edge_tol of a bin edge (not for stopped or inert cells)
+    int b_arr = c.b;
+    if (!LAST && c.b > kParkedBin / 2 && ((c.f >= 0.f && c.f < P.edge_tol) || c.f > W - P.edge_tol)) {
+        b_arr = exact_bin(P, xp, cell, k);
+        if (b_arr != c.b) {
+            float t[6];
+            load_seed(c.row, P.n_bins, b_arr, t);
+            a_end = dot6(Ex, Ey, Ez, Bx, By, Bz, t);
+        }
+    }
+    c.bx = b_arr;
 
     // ---- VJP of Eq. 1 with B = n x E, seed (GE, GB) = G ----
     const float GEx = G[0], GEy = G[1], GEz = G[2], GBx = G[3], GBy = G[4], GBz = G[5];
@@ -246,7 +281,7 @@ __device__ __forceinline__ void adj_step(ACell& c, const RecS& r, const AdjointP
 
 
 constexpr int NA = kAdjointCells;
-constexpr int kSaveWords = 18;             // f, Rpd, b, g[6], pend[6], np[3]
+constexpr int kSaveWords = 19;             // f, Rpd, b, g[6], pend[6], np[3], bx
 
 __device__ __forceinline__ void save_cell(const ACell& c, float (*sv)[kAdjointThreads], int tid)
 {
@@ -260,6 +295,7 @@ __device__ __forceinline__ void save_cell(const ACell& c, float (*sv)[kAdjointTh
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) sv[15 + i][tid] = c.np[i];
+    sv[18][tid] = __int_as_float(c.bx);
 }
 
 __device__ __forceinline__ void restore_cell(ACell& c, float (*sv)[kAdjointThreads], int tid)
@@ -274,6 +310,7 @@ __device__ __forceinline__ void restore_cell(ACell& c, float (*sv)[kAdjointThrea
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) c.np[i] = sv[15 + i][tid];
+    c.bx = __float_as_int(sv[18][tid]);
 }
 
 }  // namespace
@@ -322,6 +359,7 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
     ACell c[NA];
     int b_end[NA];
     float f_end[NA];
+    int cells[NA];
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
         // a cell with no arrival in the window (or past the last cell) walks the same steps from a
@@ -340,6 +378,7 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
 #pragma unroll
         for (int i = 0; i < 3; ++i) c[j].np[i] = 0.f;
         const int cell = cb * kAdjointCellsPerCta + j * kAdjointThreads + tid;
+        cells[j] = cell;
         if (cell < P.n_pix) {
             const D4 cl = P.cells[cell];
             const double* xa = xp + 3 * (size_t)(k_begin - 1);
@@ -364,6 +403,7 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
                 c[j].np[2] = (float)((cl.z - xa[2]) / Ra);
             }
         }
+        c[j].bx = c[j].b;
     }
 
     float* const my_stage = &stage[warp][0][0][lane];                     // + (step * 6 + value) * 32
@@ -398,9 +438,9 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
                 bool st = false;
                 float o[6];
                 if (last_tile && i == cnt - 1)
-                    adj_step<true, false>(c[j], r, P, q, near, far, b_end[j], f_end[j], o, st);
+                    adj_step<true, false>(c[j], r, P, q, near, far, b_end[j], f_end[j], o, st, xp, cells[j], k0 + i);
                 else
-                    adj_step<false, false>(c[j], r, P, q, near, far, 0, 0.f, o, st);
+                    adj_step<false, false>(c[j], r, P, q, near, far, 0, 0.f, o, st, xp, cells[j], k0 + i);
                 kstop[j] = (st && kstop[j] == cnt) ? i : kstop[j];
 #pragma unroll
                 for (int e = 0; e < 6; ++e) out[e] = j == 0 ? o[e] : out[e] + o[e];
@@ -427,9 +467,11 @@ __global__ void __launch_bounds__(kAdjointThreads, RD_ADJ_MINBLOCKS) k_adjoint_m
                 float out[6];
                 bool st = false;
                 if (last_tile && i == cnt - 1)
-                    adj_step<true, true>(c[j], tile[buf][i], P, q, near, far, b_end[j], f_end[j], out, st);
+                    adj_step<true, true>(c[j], tile[buf][i], P, q, near, far, b_end[j], f_end[j], out, st, xp,
+                                         cells[j], k0 + i);
                 else
-                    adj_step<false, true>(c[j], tile[buf][i], P, q, near, far, 0, 0.f, out, st);
+                    adj_step<false, true>(c[j], tile[buf][i], P, q, near, far, 0, 0.f, out, st, xp, cells[j],
+                                          k0 + i);
 #pragma unroll
                 for (int e = 0; e < 6; ++e) out[e] = i >= kstop[j] ? out[e] : 0.f;
                 const float v = warp_sum6(out, lane);

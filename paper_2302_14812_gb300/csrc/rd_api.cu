@@ -621,6 +621,7 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
         P.invW = (float)(t->dt / d->dt_det);
         P.inv_dt_det_f = (float)(1.0 / d->dt_det);
         P.inv_dt_f = (float)(1.0 / t->dt);
+        P.edge_tol = (float)(1e-4 * d->dt_det / t->dt);     // 1e-4 bin, ten times the walk's drift
         {
             LaunchTimer timer(d, s);
             RD_CUDA(fp64 ? launch_adjoint_fp64(P, s) : launch_adjoint_mixed(P, s), "adjoint");

@@ -142,6 +142,8 @@ struct AdjointParams {
     double t0, dt, inv_dt_det;
     float dt_f, du_scale, W, invW;
     float inv_dt_det_f, inv_dt_f;   // 1/dt_det and 1/dt in FP32 (no conversion or division per step)
+    float edge_tol;             // mixed: distance (dt units) from a bin edge below which an arrival's bin
+                                // is taken from Eq. 2 in FP64 for its end-point terms
 };
 #ifndef RD_ADJ_THREADS
 #define RD_ADJ_THREADS 128
