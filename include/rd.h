@@ -233,11 +233,11 @@ RD_API rd_status rd_set_timing(rd_detector* det, int32_t enable);
  * forward quantities are recomputed from x and u.  RD_MIXED: FP32 field arithmetic with the
  * forward path's FP32 arrival-time walk, restarting from exact FP64 arrival times every 250
  * samples, FP64 gradient sums across cells (relative error ~1e-5, set by FP32 rounding in the
- * differences of neighbouring samples; the derivative through an arrival time takes the seed of
- * the bin the walk puts that arrival in, so the few arrivals within the walk's drift (~1e-5 bin)
- * of a bin edge -- 0.2 % of the position coordinates on a 1e4-distance undulator workload -- get
- * the neighbouring bin's seed there).  RD_FP64: everything in FP64, Eq. 2 for every sample (the
- * plain form; relative error ~1e-12 against the exact derivative, at the FP64 rate of the GPU).
+ * differences of neighbouring samples).  The derivative through an arrival time takes the seed of
+ * the bin that arrival lies in; where the FP32 walk ends within 1e-4 bin of an edge (its drift is
+ * ~1e-5 bin) that bin is taken from Eq. 2 in FP64.  RD_FP64: everything in FP64, Eq. 2 for every
+ * sample (the plain form; relative error ~1e-12 against the exact derivative, at the FP64 rate of
+ * the GPU).
  * Requirements: flags without RD_FARFIELD and RD_LINEAR (else RD_ERR_STATE), traj->mem
  * RD_MEM_DEVICE (else RD_ERR_ARG).
  */
