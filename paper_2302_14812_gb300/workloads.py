@@ -136,6 +136,21 @@ def circular_orbit(gamma: float = 5.0, radius: float = 1.0, n_steps: int = 2000,
     return Trajectories(x[None].copy(), u[None].copy(), np.array([q]), t0, dt)
 
 
+def helical_orbit(gamma: float = 57.3, K: float = 0.8, omega0: float = 1.0, n_steps: int = 400,
+                  dt: float = 0.1, q: float = -1.0, t0: float = 0.0) -> Trajectories:
+    """One charge on a helix along +x (Section 3.3 example: gamma 57.3, K = gamma r0 omega0 = 0.8,
+    omega0 = 1, dt = 0.1).  Analytic at every sample: x = (beta_x t, r0 cos w t, r0 sin w t),
+    beta = (beta_x, -r0 w sin w t, r0 w cos w t), r0 = K / (gamma w), beta_x from gamma."""
+    b_perp = K / gamma
+    r0 = b_perp / omega0
+    b_x = math.sqrt(1.0 - 1.0 / gamma ** 2 - b_perp ** 2)
+    t = t0 + dt * np.arange(n_steps + 1)
+    ph = omega0 * t
+    x = np.stack([b_x * t, r0 * np.cos(ph), r0 * np.sin(ph)], axis=-1)
+    u = gamma * np.stack([np.full_like(ph, b_x), -b_perp * np.sin(ph), b_perp * np.cos(ph)], axis=-1)
+    return Trajectories(x[None].copy(), u[None].copy(), np.array([q]), t0, dt)
+
+
 def circular_ensemble(n_part: int, n_steps: int, gamma: float = 5.0, radius: float = 1.0,
                       n_orbits: float = 4.0, seed: int = 5, q: float = -1.0) -> Trajectories:
     """n_part charges on the same circular orbit (x-y plane) with random phases."""
@@ -455,6 +470,21 @@ def config_undulator(n_part: int = 1000, n_steps: int = 4000, n_side: int = 128,
     t_min, dt_det = axial_window(distance, n_steps * tr.dt, bz_bar, theta_corner, transverse,
                                  n_bins)
     det = Detector(pos, None, t_min, dt_det, n_bins, RD_NEAR | RD_FAR, (n_side, n_side))
+    return tr, det
+
+
+def config_helical(n_side: int = 64, n_steps: int = 400, n_bins: int = 8192, gamma: float = 57.3, K: float = 0.8,
+                   distance: float = 1e6, aperture: float = 0.1, dt_det: float = 1.33e-5):
+    """Section 3.3 example: one electron on a helix along +x (gamma 57.3, K 0.8, omega0 = 1,
+    dt = 0.1), spherical detector of n_side^2 cells spanning `aperture` rad around +x at R = 1e6,
+    bins of 1.33e-5.  Each cell's time origin is its earliest arrival minus 20 bins."""
+    tr = helical_orbit(gamma=gamma, K=K, n_steps=n_steps)
+    pos = spherical_cap(n_side, distance, 0.5 * aperture, axis=0)
+    k = np.arange(tr.n_samples)
+    tk = tr.t0 + k * tr.dt
+    first = np.array([np.min(tk + np.linalg.norm(p - tr.x[0], axis=1)) for p in pos])
+    det = Detector(pos, first - 20.0 * dt_det - distance, distance, dt_det, n_bins, RD_NEAR | RD_FAR,
+                   (n_side, n_side))
     return tr, det
 
 

@@ -400,6 +400,32 @@ def test_undulator_on_axis_spectrum(oracle_lib):
     assert abs(got / (F(3) / F(1)) - 1.0) < 3e-2
 
 
+def test_helical_on_axis_rotating_field(oracle_lib):
+    """Section 3.3 helix (gamma 57.3, K 0.8, omega0 = 1, dt = 0.1) seen on its axis at R = 1e6.
+    On the axis the arrival times advance by dt (1 - beta_x) per sample (Eq. 2), so bins of
+    2 dt (1 - beta_x) starting at the first arrival hold exactly two samples each, and the field
+    there is the radiation term n x ((n - beta) x betadot) = -(1 - beta_x) betadot_perp: a transverse
+    vector of fixed length turning with the particle.  Hence the bins' (E_y + i E_z) turn by exactly
+    2 omega0 dt = 0.2 rad per bin in the particle's sense, keep their length (up to the 1/R drift
+    over the 40 time units, 4e-5), and E_x is ~1e-8 of them (velocity term)."""
+    gam, K, dt = 57.3, 0.8, 0.1
+    tr = W.helical_orbit(gamma=gam, K=K, n_steps=400, dt=dt)
+    D = 1e6
+    bx = math.sqrt(1.0 - 1.0 / gam ** 2 - (K / gam) ** 2)
+    dt_det = 2.0 * dt * (1.0 - bx)
+    P = np.array([[D, 0.0, 0.0]])
+    t_first = tr.t0 + float(np.sqrt(np.sum((P[0] - tr.x[0, 0]) ** 2)))
+    det = W.Detector(P, None, t_first, dt_det, 210)
+    E, _, _ = oracle.deposit(tr, det)
+    E = E[0][2:195]                                  # whole bins inside the 200 the samples fill
+    Z = E[:, 1] + 1j * E[:, 2]
+    dphi = np.angle(Z[1:] / Z[:-1])
+    assert np.max(np.abs(dphi - 2.0 * dt)) < 1e-6, dphi
+    mag = np.abs(Z)
+    assert mag.max() / mag.min() - 1.0 < 1e-4
+    assert np.max(np.abs(E[:, 0])) < 1e-6 * mag.min()
+
+
 def test_time_shift_invariance(oracle_lib):
     """Shifting the emission times and the window together changes nothing; shifting the
     emission alone by m bins moves the record by m bins (Eq. 2 is translation covariant)."""

@@ -153,6 +153,17 @@ def test_plasma_mirror_reduced(precision):
     check(tr, det, precision, sel=sel)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_helical_section_3_3_full_size(precision):
+    """The Section 3.3 example at its size: one electron on a helix (gamma 57.3, K 0.8, dt 0.1,
+    400 steps), 64x64 spherical detector over 0.1 rad around the axis at R = 1e6, 8192 bins of
+    1.33e-5 (118 bins per radiation period on the axis), per-cell time origins.  The oracle
+    computes 8 cells from the centre to the corners."""
+    tr, det = W.config_helical()
+    sel = np.array([0, 63, 31 * 64 + 31, 32 * 64 + 32, 31 * 64 + 40, 2000, 64 * 63, 64 * 64 - 1], dtype=np.int32)
+    check(tr, det, precision, sel=sel)
+
+
 # --------------------------------------------------------------------------------------------
 # edge cases and API behaviour
 # --------------------------------------------------------------------------------------------
