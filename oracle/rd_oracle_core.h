@@ -178,6 +178,9 @@ static int FN(deposit_interval_lin)(SCALAR a, SCALAR c, const SCALAR F0[6], cons
  *   step's field to the interpolator); sample 0 only provides the previous quantities.
  * flags bit 8: from interval 2 on, the field varies linearly from F_{k-1} to F_k over the
  * interval (deposit_interval_lin); interval 1 holds F_1 (sample 0 has no field: no betadot).
+ * flags bit 16: from interval 2 on, the interval holds the field of its first sample, F_{k-1}
+ * (the other reading of which field the interpolation holds: the worked example of Section 3.2
+ * writes, for the interval ending at t'_4, the field at t'_3); interval 1 holds F_1.
  * x, u point at this particle's samples [n_samples][3]; row is [n_bins][6] (E xyz, B xyz).
  * Returns the number of intervals that had a part outside the window.
  */
@@ -201,6 +204,8 @@ static long long FN(pixel_particle)(const SCALAR* x, const SCALAR* u, int n_samp
         SCALAR c = FN(bin_coord)(t0, k, dt, xk, P, T0, inv_dt_det, flags);
         if ((flags & 8) && k > 1)
             clipped += FN(deposit_interval_lin)(a, c, Fprev, F, n_bins, row);
+        else if ((flags & 16) && k > 1)
+            clipped += FN(deposit_interval)(a, c, Fprev, n_bins, row);
         else
             clipped += FN(deposit_interval)(a, c, F, n_bins, row);
         for (int i = 0; i < 6; ++i) Fprev[i] = F[i];

@@ -30,6 +30,7 @@ RD_NEAR = 1
 RD_FAR = 2
 RD_FARFIELD = 4
 RD_LINEAR = 8
+RD_HOLD_PREV = 16
 
 
 @dataclasses.dataclass

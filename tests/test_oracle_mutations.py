@@ -44,6 +44,9 @@ MUTATIONS = {
                             "SCALAR ramp = ((u1 - a) * (u1 - a) - (u0 - a) * (u0 - a)) / (c - a);"),
     "linear_ends_exchanged": ("row[6 * b + i] += F0[i] * len + (F1[i] - F0[i]) * ramp;",
                               "row[6 * b + i] += F1[i] * len + (F0[i] - F1[i]) * ramp;"),
+    # held-previous field: the current sample's field held instead
+    "hold_previous_uses_current": ("clipped += FN(deposit_interval)(a, c, Fprev, n_bins, row);",
+                                   "clipped += FN(deposit_interval)(a, c, F, n_bins, row);"),
 }
 
 

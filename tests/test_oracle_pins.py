@@ -706,6 +706,47 @@ def test_linear_interpolation_brute_force(oracle_lib):
         np.testing.assert_allclose(got[b], val.mean(axis=0), rtol=2e-5, atol=2e-6 * np.abs(got).max())
 
 
+def test_hold_previous_sum_rule(oracle_lib):
+    """Held-previous-field variant (flags bit 16): with every arrival inside the window the bins add
+    up to F_1 (u_1 - u_0) + sum_{k>=2} F_{k-1} (u_k - u_{k-1})."""
+    tr = W.random_smooth(2, 60, 0.02, max_u=2.0, seed=4)
+    P = np.array([[-9.0, 6.0, 4.0]])
+    det = W.Detector(P, None, 0.0, 0.05, 2000, flags=W.RD_NEAR | W.RD_FAR | W.RD_HOLD_PREV)
+    E, B, clipped = oracle.deposit(tr, det)
+    assert clipped == 0
+    want = np.zeros(6)
+    for p in range(tr.n_part):
+        F, u = _sample_fields(tr, p, P[0], W.RD_NEAR | W.RD_FAR)
+        want += F[1] * (u[1] - u[0])
+        for k in range(2, tr.n_samples):
+            want += F[k - 1] * (u[k] - u[k - 1])
+    got = np.concatenate([E[0].sum(axis=0), B[0].sum(axis=0)])
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+
+
+def test_hold_previous_brute_force(oracle_lib):
+    """One particle, 12 samples, bins about as long as the intervals: each bin equals a fine
+    midpoint-rule integral of the emission that holds F_{k-1} over interval k (F_1 over the first)."""
+    tr = W.random_smooth(1, 11, 0.05, max_u=1.5, seed=10)
+    P = np.array([[-2.0, 3.0, 1.0]])
+    F, u = _sample_fields(tr, 0, P[0], W.RD_NEAR | W.RD_FAR)
+    lo = int(np.floor(u[0])) - 1
+    det = W.Detector(P, None, lo * 0.05, 0.05, int(np.ceil(u[-1])) - lo + 2,
+                     flags=W.RD_NEAR | W.RD_FAR | W.RD_HOLD_PREV)
+    E, B, clipped = oracle.deposit(tr, det)
+    assert clipped == 0
+    uu = u - lo
+    got = np.concatenate([E[0], B[0]], axis=1)
+    n_sub = 20000
+    for b in range(det.n_bins):
+        s = b + (np.arange(n_sub) + 0.5) / n_sub
+        val = np.zeros((n_sub, 6))
+        for k in range(1, tr.n_samples):
+            m = (s >= uu[k - 1]) & (s < uu[k])
+            val[m] = F[max(k - 1, 1)]
+        np.testing.assert_allclose(got[b], val.mean(axis=0), rtol=2e-4, atol=2e-5 * np.abs(got).max())
+
+
 def test_linear_interpolation_is_second_order(oracle_lib):
     """Velocity field of a circular orbit (gamma 2) at a cell 6.4 orbit radii away: halving dt cuts
     the change of the deposit fourfold with the linear interpolation and twofold with the held
