@@ -69,9 +69,13 @@ enum { RD_FP64 = 0, RD_MIXED = 1 };
  * RD_LINEAR (with any of the above) replaces the held field of the integrating deposit by a field
  * that varies linearly in arrival time over each interval, from the field of sample k-1 to that
  * of sample k (second order in dt where the held field is first order; the first interval of a
- * trajectory still holds the field of sample 1).  Not supported by rd_adjoint_trajectories.
+ * trajectory still holds the field of sample 1).  RD_HOLD_PREV (instead of RD_LINEAR) holds the
+ * field of sample k-1 over interval k (the reading of Section 3.2's worked example, which writes
+ * the field at the interval's start; first order like the default, which holds the field of
+ * sample k as Algorithm 2 passes it); interval 1 holds the field of sample 1.  Neither is
+ * supported by rd_adjoint_trajectories.
  */
-enum { RD_NEAR = 1, RD_FAR = 2, RD_FARFIELD = 4, RD_LINEAR = 8 };
+enum { RD_NEAR = 1, RD_FAR = 2, RD_FARFIELD = 4, RD_LINEAR = 8, RD_HOLD_PREV = 16 };
 /* where a caller buffer lives; RD_MEM_HOST_ASYNC: pinned host memory written asynchronously
  * (rd_read_fields only) */
 enum { RD_MEM_DEVICE = 0, RD_MEM_HOST = 1, RD_MEM_HOST_ASYNC = 2 };
@@ -98,7 +102,8 @@ typedef struct {
     double dt_det;             /* > 0                                                           */
     int32_t n_bins;            /* >= 1; <= 4194304 (2^22) for RD_MIXED                          */
     int32_t precision;         /* RD_MIXED or RD_FP64                                           */
-    int32_t flags;             /* RD_NEAR | RD_FAR (0 = both), or RD_FAR | RD_FARFIELD; | RD_LINEAR */
+    int32_t flags;             /* RD_NEAR | RD_FAR (0 = both), or RD_FAR | RD_FARFIELD;
+                                  | RD_LINEAR or | RD_HOLD_PREV                                   */
 } rd_detector_desc;
 
 /*
@@ -238,7 +243,7 @@ RD_API rd_status rd_set_timing(rd_detector* det, int32_t enable);
  * ~1e-5 bin) that bin is taken from Eq. 2 in FP64.  RD_FP64: everything in FP64, Eq. 2 for every
  * sample (the plain form; relative error ~1e-12 against the exact derivative, at the FP64 rate of
  * the GPU).
- * Requirements: flags without RD_FARFIELD and RD_LINEAR (else RD_ERR_STATE), traj->mem
+ * Requirements: flags without RD_FARFIELD, RD_LINEAR and RD_HOLD_PREV (else RD_ERR_STATE), traj->mem
  * RD_MEM_DEVICE (else RD_ERR_ARG).
  */
 RD_API rd_status rd_adjoint_trajectories(rd_detector* det, const rd_traj* traj, const void* gE,

@@ -60,7 +60,7 @@ struct rd_detector {
     void* strm_stage = nullptr;      // this call's samples with the stored one in front, and q
     size_t strm_stage_bytes = 0;
     int strm_n_part = -1;            // -1: no stream in progress
-    int strm_have = 0;               // samples kept per particle (1, or 2 with RD_LINEAR)
+    int strm_have = 0;               // samples kept per particle (1, or 2 with RD_LINEAR / RD_HOLD_PREV)
     double strm_t_last = 0.0;
     double strm_dt = 0.0;
     std::vector<unsigned long long> graph_key;
@@ -214,7 +214,8 @@ void fill_mixed_params(DepositParams& P, const rd_detector* d, const rd_traj* t,
     P.dt_f = (float)t->dt;
     P.du_scale = (float)(t->dt / d->dt_det);
     P.ff = (d->flags & RD_FARFIELD) != 0;
-    P.lin = (d->flags & RD_LINEAR) != 0;
+    P.lin = (d->flags & (RD_LINEAR | RD_HOLD_PREV)) != 0;
+    P.ramp = (d->flags & RD_LINEAR) ? 1.f : 0.f;
     P.W = (float)(d->dt_det / t->dt);
     P.invW = (float)(t->dt / d->dt_det);
 }
@@ -278,8 +279,10 @@ rd_status rd_create_detector(const rd_detector_desc* desc, rd_stream stream, rd_
     if (desc->precision != RD_MIXED && desc->precision != RD_FP64)
         return fail(RD_ERR_ARG, "bad precision %d", desc->precision);
     if (desc->mem != RD_MEM_DEVICE && desc->mem != RD_MEM_HOST) return fail(RD_ERR_ARG, "bad desc->mem");
-    if (desc->flags & ~(RD_NEAR | RD_FAR | RD_FARFIELD | RD_LINEAR))
+    if (desc->flags & ~(RD_NEAR | RD_FAR | RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV))
         return fail(RD_ERR_ARG, "bad flags %d", desc->flags);
+    if ((desc->flags & RD_LINEAR) && (desc->flags & RD_HOLD_PREV))
+        return fail(RD_ERR_ARG, "RD_LINEAR and RD_HOLD_PREV are alternatives");
     if ((desc->flags & (RD_NEAR | RD_FAR)) == 0 && desc->flags != 0)
         return fail(RD_ERR_ARG, "flags %d select no term of Eq. 1 (RD_NEAR and/or RD_FAR)", desc->flags);
     if ((desc->flags & RD_FARFIELD) && (desc->flags & RD_NEAR))
@@ -456,7 +459,8 @@ static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream
         P.W = (float)(d->dt_det / t->dt);
         P.invW = (float)(t->dt / d->dt_det);
         P.ff = (d->flags & RD_FARFIELD) != 0;
-        P.lin = (d->flags & RD_LINEAR) != 0;
+        P.lin = (d->flags & (RD_LINEAR | RD_HOLD_PREV)) != 0;
+        P.ramp = (d->flags & RD_LINEAR) ? 1.f : 0.f;
         if (mixed) {
             RD_CUDA(launch_precompute_mixed(x, u, q, t->dt / d->dt_det, np, t->n_samples, t->dt, d->flags,
                                             static_cast<RecS*>(d->rec), d->counters, s),
@@ -554,7 +558,7 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
     if (!d) return fail(RD_ERR_ARG, "detector is NULL");
     rd_status st = check_traj(t);
     if (st != RD_OK) return st;
-    if (d->flags & (RD_FARFIELD | RD_LINEAR))
+    if (d->flags & (RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV))
         return fail(RD_ERR_STATE, "the adjoint covers the exact fields with the held interpolation only");
     if (t->mem != RD_MEM_DEVICE) return fail(RD_ERR_ARG, "the adjoint needs device trajectories");
     if (!gE && !gB) return fail(RD_ERR_ARG, "gE and gB are both NULL");
@@ -903,8 +907,8 @@ rd_status rd_deposit_stream(rd_detector* d, const rd_traj* t, rd_stream stream)
                         expect);
     }
     // samples kept between calls: the last one (its interval to the first new sample), and with
-    // RD_LINEAR the one before it too (the field of the last sample needs its betadot)
-    const int keep = (d->flags & RD_LINEAR) ? 2 : 1;
+    // RD_LINEAR / RD_HOLD_PREV the one before it too (the field of the last sample needs its betadot)
+    const int keep = (d->flags & (RD_LINEAR | RD_HOLD_PREV)) ? 2 : 1;
     const int have = cont ? d->strm_have : 0;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int np = t->n_part, m = t->n_samples, ns = m + have;

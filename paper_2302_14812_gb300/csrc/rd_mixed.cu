@@ -52,6 +52,7 @@ struct Consts {
     float W;                        // bin width / dt
     float invW;
     float DT;
+    float ramp;                     // linear interpolation: 1; held previous field: 0 (no ramp terms)
     int n_bins;
     float* base;                    // field row 0 of the CTA's cell block
 };
@@ -217,7 +218,8 @@ __device__ __forceinline__ void scaled_field(const Field& o, float* G)
     }
 }
 
-// Linear interpolation (RD_LINEAR): over the interval the field goes linearly from G0 = gp (previous
+// Linear interpolation (RD_LINEAR; with the ramp terms scaled to zero, C.ramp = 0, the previous field
+// held over the interval, RD_HOLD_PREV): over the interval the field goes linearly from G0 = gp (previous
 // sample) to G (this sample); the part [s0, s1] of the interval (dt units from its start, length L)
 // weighs G0 (s1 - s0) + (G - G0) (s1^2 - s0^2) / (2 L) = G0 (s1 - s0 - ramp) + G ramp with
 // ramp = (s1^2 - s0^2) / (2 L).  Interval of cell j passing two or more bin
@@ -298,7 +300,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
         if (LIN) {
             scaled_field(o[j], G[j]);
             L[j] = t - c.f[j];
-            inv2L[j] = 0.5f * fast_rcp(L[j]);
+            inv2L[j] = (0.5f * C.ramp) * fast_rcp(fmaxf(L[j], 1e-30f));
             const float len1 = fminf(t, C.W) - c.f[j];
             ramp1[j] = (len1 * len1) * inv2L[j];
             // G0 (s1 - s0) + (G - G0) ramp = G0 (s1 - s0 - ramp) + G ramp
@@ -344,7 +346,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
                 red_add_v2(a + 4, bb[1], bb[2]);
                 const float rem = fn[j] - C.W;
                 if (LIN) {
-                    const float ramp2 = fmaf(0.5f, L[j], -ramp1[j]);
+                    const float ramp2 = fmaf(0.5f * C.ramp, L[j], -ramp1[j]);
 #pragma unroll
                     for (int i = 0; i < NF; ++i) c.acc[i][j] = fmaf(c.gp[i][j], rem - ramp2, G[j][i] * ramp2);
                 } else {
@@ -374,7 +376,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
             red_add_v2_if(pr, a + 4, bb[1], bb[2]);
             const float rem = fn[j] - C.W;
             if (LIN) {
-                const float ramp2 = fmaf(0.5f, L[j], -ramp1[j]);
+                const float ramp2 = fmaf(0.5f * C.ramp, L[j], -ramp1[j]);
 #pragma unroll
                 for (int i = 0; i < NF; ++i) {
                     const float v = fmaf(c.gp[i][j], rem - ramp2, G[j][i] * ramp2);
@@ -516,6 +518,7 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
     C.W = P.W;
     C.invW = P.invW;
     C.DT = P.dt_f;
+    C.ramp = P.ramp;
     C.n_bins = P.n_bins;
     C.base = static_cast<float*>(P.fields) + (size_t)cb * kMixedCellsPerCta * P.n_bins * 8;
 

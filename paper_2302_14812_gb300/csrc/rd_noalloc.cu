@@ -82,7 +82,9 @@ extern "C" rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix
         return set_last_error(RD_ERR_ARG, "rd_deposit_noalloc: n_pix exceeds its maximum of 262144 cells");
     if (!(dt_det > 0.0) || !isfinite(dt_det) || !isfinite(t_min))
         return set_last_error(RD_ERR_ARG, "dt_det must be finite and > 0, t_min finite");
-    if (flags & ~(RD_NEAR | RD_FAR | RD_FARFIELD | RD_LINEAR)) return set_last_error(RD_ERR_ARG, "bad flags");
+    if (flags & ~(RD_NEAR | RD_FAR | RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV))
+        return set_last_error(RD_ERR_ARG, "bad flags");
+    if ((flags & RD_LINEAR) && (flags & RD_HOLD_PREV)) return set_last_error(RD_ERR_ARG, "bad flags");
     if ((flags & RD_FARFIELD) && (flags & RD_NEAR))
         return set_last_error(RD_ERR_ARG, "RD_FARFIELD cannot be combined with RD_NEAR");
     if (t->n_part < 0 || t->n_samples < 1 || !(t->dt > 0.0) || !isfinite(t->dt) || !isfinite(t->t0))
@@ -144,7 +146,8 @@ extern "C" rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix
             P.W = (float)(dt_det / t->dt);
             P.invW = (float)(t->dt / dt_det);
             P.ff = (fl & RD_FARFIELD) != 0;
-            P.lin = (fl & RD_LINEAR) != 0;
+            P.lin = (fl & (RD_LINEAR | RD_HOLD_PREV)) != 0;
+            P.ramp = (fl & RD_LINEAR) ? 1.f : 0.f;
             e = launch_deposit_mixed(P, s);
         }
     }

@@ -77,6 +77,12 @@ def test_argument_errors_without_gpu():
     assert "RD_FARFIELD" in rd.rd_last_error()
     d.flags = 8
     assert lib.rd_create_detector(ctypes.byref(d), None, ctypes.byref(h)) == rd.RD_ERR_ARG
+    # the two interpolation variants are alternatives; unknown bits are refused
+    d.flags = rd.RD_NEAR | rd.RD_FAR | rd.RD_LINEAR | rd.RD_HOLD_PREV
+    assert lib.rd_create_detector(ctypes.byref(d), None, ctypes.byref(h)) == rd.RD_ERR_ARG
+    assert "alternatives" in rd.rd_last_error()
+    d.flags = rd.RD_NEAR | 32
+    assert lib.rd_create_detector(ctypes.byref(d), None, ctypes.byref(h)) == rd.RD_ERR_ARG
     assert lib.rd_set_batch_budget(None, 0) == rd.RD_ERR_ARG
     assert lib.rd_deposit_stream(None, None, None) == rd.RD_ERR_ARG
     assert lib.rd_stream_reset(None) == rd.RD_ERR_ARG

@@ -355,6 +355,51 @@ def test_linear_interpolation(precision, case):
     check(tr, det, precision)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", [0, 1, 2, 3])
+def test_hold_previous_field(precision, case):
+    """RD_HOLD_PREV (interval k holds the field of sample k-1) on the same four cases as the linear
+    interpolation, every cell against the oracle."""
+    tr, det = _linear_cases()[case]
+    det.flags = (det.flags & ~W.RD_LINEAR) | W.RD_HOLD_PREV
+    check(tr, det, precision)
+
+
+def test_hold_previous_streamed_and_batched():
+    """RD_HOLD_PREV through rd_deposit_stream (stretches of 1, 7, 64 and the rest) and through one
+    batched launch with a held-current problem beside it: the same fields as one plain call."""
+    import torch
+    tr, det = _linear_cases()[0]
+    det.flags = W.RD_NEAR | W.RD_FAR | W.RD_HOLD_PREV
+    ref = rd.RadiationDetector.from_workload(det, "mixed")
+    xd, ud, qd = (torch.from_numpy(a).cuda() for a in (tr.x, tr.u, tr.q))
+    ref.deposit(xd, ud, qd, tr.t0, tr.dt)
+    Er, Br = ref.read()
+    d = rd.RadiationDetector.from_workload(det, "mixed")
+    k = 0
+    for m in (1, 7, 64, tr.n_samples):
+        b = min(tr.n_samples, k + m)
+        d.deposit_stream(xd[:, k:b].contiguous(), ud[:, k:b].contiguous(), qd, tr.t0 + k * tr.dt, tr.dt)
+        k = b
+        if k >= tr.n_samples:
+            break
+    E, B = d.read()
+    assert rel_l2(E, Er) <= 2e-6 and rel_l2(B, Br) <= 2e-6
+    d.close()
+    det_held = W.Detector(det.pix_pos, det.pix_t0, det.t_min, det.dt_det, det.n_bins, W.RD_NEAR | W.RD_FAR)
+    dets = [rd.RadiationDetector.from_workload(det, "mixed"), rd.RadiationDetector.from_workload(det_held, "mixed")]
+    keep = rd.deposit_batch(dets, [(xd, ud, qd, tr.t0, tr.dt)] * 2)
+    E0, B0 = dets[0].read()
+    assert rel_l2(E0, Er) <= 2e-6 and rel_l2(B0, Br) <= 2e-6
+    Eh, _, _ = oracle.deposit(tr, det_held, np.array([0, 5], dtype=np.int32))
+    E1, _ = dets[1].read()
+    assert rel_l2(E1[[0, 5]], Eh) <= 1e-4
+    for dd in dets:
+        dd.close()
+    ref.close()
+    del keep
+
+
 def test_linear_interpolation_chunks_and_particle_splits():
     """Step chunks of 64 and 100 intervals and two calls over particle halves: each chunk starts
     from the field of the sample before it, so the result does not depend on the split."""
