@@ -214,8 +214,7 @@ void fill_mixed_params(DepositParams& P, const rd_detector* d, const rd_traj* t,
     P.dt_f = (float)t->dt;
     P.du_scale = (float)(t->dt / d->dt_det);
     P.ff = (d->flags & RD_FARFIELD) != 0;
-    P.lin = (d->flags & (RD_LINEAR | RD_HOLD_PREV)) != 0;
-    P.ramp = (d->flags & RD_LINEAR) ? 1.f : 0.f;
+    P.lin = (d->flags & RD_LINEAR) ? 1 : (d->flags & RD_HOLD_PREV) ? 2 : 0;
     P.W = (float)(d->dt_det / t->dt);
     P.invW = (float)(t->dt / d->dt_det);
 }
@@ -459,8 +458,7 @@ static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream
         P.W = (float)(d->dt_det / t->dt);
         P.invW = (float)(t->dt / d->dt_det);
         P.ff = (d->flags & RD_FARFIELD) != 0;
-        P.lin = (d->flags & (RD_LINEAR | RD_HOLD_PREV)) != 0;
-        P.ramp = (d->flags & RD_LINEAR) ? 1.f : 0.f;
+        P.lin = (d->flags & RD_LINEAR) ? 1 : (d->flags & RD_HOLD_PREV) ? 2 : 0;
         if (mixed) {
             RD_CUDA(launch_precompute_mixed(x, u, q, t->dt / d->dt_det, np, t->n_samples, t->dt, d->flags,
                                             static_cast<RecS*>(d->rec), d->counters, s),

@@ -376,8 +376,8 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
                     fp64_field(r, cl, R, q, flags, F);
                 }
                 if (P.lin) {
-                    // RD_HOLD_PREV (ramp 0): the previous field at both ends, i.e. held
-                    fp64_deposit_lin(st, st.Fp, P.ramp != 0.f ? F : st.Fp, cbin, row, P.n_bins, k, k_begin, k_end);
+                    // RD_HOLD_PREV (lin 2): the previous field at both ends, i.e. held
+                    fp64_deposit_lin(st, st.Fp, P.lin == 1 ? F : st.Fp, cbin, row, P.n_bins, k, k_begin, k_end);
 #pragma unroll
                     for (int j = 0; j < 6; ++j) st.Fp[j] = F[j];
                 } else {

@@ -91,8 +91,8 @@ struct DepositParams {
     float dt_f;
     float du_scale;             // dt / dt_det
     int ff;                     // far-field limit (RD_FARFIELD): Eq. 3, radiation term at (n_c, R_c)
-    int lin;                    // RD_LINEAR or RD_HOLD_PREV: the walk carries the previous sample's field
-    float ramp;                 // 1: linear in arrival time (RD_LINEAR); 0: the previous field held
+    int lin;                    // 0: held field; 1: linear in arrival time (RD_LINEAR); 2: the previous
+                                // sample's field held (RD_HOLD_PREV); 1 and 2 carry the previous field
 };
 
 constexpr int kDepositThreads = 256;   // FP64 kernel: one cell per thread

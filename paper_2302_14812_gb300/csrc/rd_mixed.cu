@@ -52,7 +52,6 @@ struct Consts {
     float W;                        // bin width / dt
     float invW;
     float DT;
-    float ramp;                     // linear interpolation: 1; held previous field: 0 (no ramp terms)
     int n_bins;
     float* base;                    // field row 0 of the CTA's cell block
 };
@@ -218,7 +217,7 @@ __device__ __forceinline__ void scaled_field(const Field& o, float* G)
     }
 }
 
-// Linear interpolation (RD_LINEAR; with the ramp terms scaled to zero, C.ramp = 0, the previous field
+// Linear interpolation (RD_LINEAR; with the ramp terms scaled to zero, ramp = 0, the previous field
 // held over the interval, RD_HOLD_PREV): over the interval the field goes linearly from G0 = gp (previous
 // sample) to G (this sample); the part [s0, s1] of the interval (dt units from its start, length L)
 // weighs G0 (s1 - s0) + (G - G0) (s1^2 - s0^2) / (2 L) = G0 (s1 - s0 - ramp) + G ramp with
@@ -278,7 +277,7 @@ enum { kFast = 0, kExact = 1 };
 // counted).  ok: kExact only, false from the interval that stopped the fast walk onwards.
 template <int MODE, bool LAST, bool TRACK, bool FF, bool LIN>
 __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, const int* bo_end,
-                                     const float* f_end, int k, int k_begin, int k_end, bool* ok)
+                                     const float* f_end, int k, int k_begin, int k_end, bool* ok, float ramp)
 {
     constexpr int NF = FF ? 3 : 6;                  // carried field components (far field: E only)
     Field o[NC];
@@ -300,7 +299,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
         if (LIN) {
             scaled_field(o[j], G[j]);
             L[j] = t - c.f[j];
-            inv2L[j] = (0.5f * C.ramp) * fast_rcp(fmaxf(L[j], 1e-30f));
+            inv2L[j] = (0.5f * ramp) * fast_rcp(fmaxf(L[j], 1e-30f));
             const float len1 = fminf(t, C.W) - c.f[j];
             ramp1[j] = (len1 * len1) * inv2L[j];
             // G0 (s1 - s0) + (G - G0) ramp = G0 (s1 - s0 - ramp) + G ramp
@@ -346,7 +345,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
                 red_add_v2(a + 4, bb[1], bb[2]);
                 const float rem = fn[j] - C.W;
                 if (LIN) {
-                    const float ramp2 = fmaf(0.5f * C.ramp, L[j], -ramp1[j]);
+                    const float ramp2 = fmaf(0.5f * ramp, L[j], -ramp1[j]);
 #pragma unroll
                     for (int i = 0; i < NF; ++i) c.acc[i][j] = fmaf(c.gp[i][j], rem - ramp2, G[j][i] * ramp2);
                 } else {
@@ -376,7 +375,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
             red_add_v2_if(pr, a + 4, bb[1], bb[2]);
             const float rem = fn[j] - C.W;
             if (LIN) {
-                const float ramp2 = fmaf(0.5f * C.ramp, L[j], -ramp1[j]);
+                const float ramp2 = fmaf(0.5f * ramp, L[j], -ramp1[j]);
 #pragma unroll
                 for (int i = 0; i < NF; ++i) {
                     const float v = fmaf(c.gp[i][j], rem - ramp2, G[j][i] * ramp2);
@@ -456,8 +455,8 @@ __device__ __forceinline__ void restore_state(Cells& c, float (*sv)[kMixedThread
 
 template <bool TRACK, bool FF, bool LIN>
 __device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, bool last_tile, const Consts& C,
-                                          const int* bo_end, const float* f_end, int k0, int k_begin, int k_end,
-                                          float (*sv)[kMixedThreads])
+                                          float ramp, const int* bo_end, const float* f_end, int k0, int k_begin,
+                                          int k_end, float (*sv)[kMixedThreads])
 {
     const int tid = threadIdx.x;
     const int n_regular = last_tile ? cnt - 1 : cnt;
@@ -465,9 +464,9 @@ __device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, b
     bool ok[NC];
 #pragma unroll kUnroll
     for (int i = 0; i < n_regular; ++i)
-        step<kFast, false, TRACK, FF, LIN>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok);
+        step<kFast, false, TRACK, FF, LIN>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok, ramp);
     if (last_tile)
-        step<kFast, true, TRACK, FF, LIN>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok);
+        step<kFast, true, TRACK, FF, LIN>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok, ramp);
     bool stopped = false;
 #pragma unroll
     for (int j = 0; j < NC; ++j) stopped = stopped || c.f[j] == -INFINITY;
@@ -478,9 +477,9 @@ __device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, b
         for (int j = 0; j < NC; ++j) ok[j] = true;
 #pragma unroll 1
         for (int i = 0; i < n_regular; ++i)
-            step<kExact, false, TRACK, FF, LIN>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok);
+            step<kExact, false, TRACK, FF, LIN>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok, ramp);
         if (last_tile)
-            step<kExact, true, TRACK, FF, LIN>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok);
+            step<kExact, true, TRACK, FF, LIN>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok, ramp);
     }
 }
 
@@ -518,7 +517,6 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
     C.W = P.W;
     C.invW = P.invW;
     C.DT = P.dt_f;
-    C.ramp = P.ramp;
     C.n_bins = P.n_bins;
     C.base = static_cast<float*>(P.fields) + (size_t)cb * kMixedCellsPerCta * P.n_bins * 8;
 
@@ -630,9 +628,11 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
         const int cnt = min(kTileSteps, k_end - k0 + 1);
         const bool last_tile = (t == n_tiles - 1);
         if (track)
-            walk_tile<true, FF, LIN>(c, tile[buf], cnt, last_tile, C, bo_end, f_end, k0, k_begin, k_end, sv);
+            walk_tile<true, FF, LIN>(c, tile[buf], cnt, last_tile, C, P.lin == 1 ? 1.f : 0.f, bo_end, f_end, k0,
+                                     k_begin, k_end, sv);
         else
-            walk_tile<false, FF, LIN>(c, tile[buf], cnt, last_tile, C, bo_end, f_end, k0, k_begin, k_end, sv);
+            walk_tile<false, FF, LIN>(c, tile[buf], cnt, last_tile, C, P.lin == 1 ? 1.f : 0.f, bo_end, f_end, k0,
+                                      k_begin, k_end, sv);
         __syncthreads();
         if (tid == 0 && t + 2 < n_tiles) {
             fence_proxy_async();

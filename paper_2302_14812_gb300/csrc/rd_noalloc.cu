@@ -146,8 +146,7 @@ extern "C" rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix
             P.W = (float)(dt_det / t->dt);
             P.invW = (float)(t->dt / dt_det);
             P.ff = (fl & RD_FARFIELD) != 0;
-            P.lin = (fl & (RD_LINEAR | RD_HOLD_PREV)) != 0;
-            P.ramp = (fl & RD_LINEAR) ? 1.f : 0.f;
+            P.lin = (fl & RD_LINEAR) ? 1 : (fl & RD_HOLD_PREV) ? 2 : 0;
             e = launch_deposit_mixed(P, s);
         }
     }
