@@ -18,6 +18,7 @@ exchange); ranks meet only at the timing barriers and the max-over-ranks time re
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import math
@@ -716,11 +717,14 @@ def main():
         run(max(2, args.warmup), time.perf_counter())
         torch.cuda.synchronize()
         barrier()
+        gc.collect()
+        gc.disable()            # no collector pause between a step's enqueue and the next one's
         t = time.perf_counter()
         done = run(args.steps, t)
         torch.cuda.synchronize()
         barrier()
         secs = slowest(time.perf_counter() - t)
+        gc.enable()
         pair[1].close()
         e2e = {"value": deposits * world * args.steps / secs, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
