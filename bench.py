@@ -631,6 +631,19 @@ def main():
                               "vs_held": ms_step / ms_lin,
                               "mode": "RD_LINEAR: field linear in arrival time over each interval"}
 
+        det_prev = W.Detector(det.pix_pos, det.pix_t0, det.t_min, det.dt_det, det.n_bins,
+                              W.RD_NEAR | W.RD_FAR | W.RD_HOLD_PREV)
+        pd = rd.RadiationDetector.from_workload(det_prev, "mixed")
+
+        def prev_step():
+            pd.zero()
+            pd.deposit(xd, ud, qd, tr.t0, tr.dt)
+        ms_prev = timed(prev_step, 2)
+        pd.close()
+        variants["hold_prev"] = {"value": deposits * world / (ms_prev / 1e3), "ms_per_step": ms_prev,
+                                 "vs_held": ms_step / ms_prev,
+                                 "mode": "RD_HOLD_PREV: interval k holds the field of sample k-1"}
+
         n_str = 8
         bounds = np.linspace(0, tr.n_samples, n_str + 1).astype(int)
         pieces = [(xd[:, a:b].contiguous(), ud[:, a:b].contiguous(), tr.t0 + a * tr.dt)
