@@ -165,7 +165,7 @@ class ClockSampler:
         pw = np.array([num(r[3]) for r in rows])
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(np.nanmax(mx)),
+        return {"sm_mhz": float(np.nanmedian(sm)), "sm_min_mhz": float(np.nanmin(sm)), "sm_max_mhz": float(np.nanmax(mx)),
                 "power_w_max": float(np.nanmax(pw)), "samples": len(rows), "reasons": reasons}
 
 
@@ -732,17 +732,19 @@ def main():
         barrier()
         gc.collect()
         gc.disable()            # no collector pause between a step's enqueue and the next one's
-        t = time.perf_counter()
-        done = run(args.steps, t)
-        torch.cuda.synchronize()
-        barrier()
-        secs = slowest(time.perf_counter() - t)
+        with ClockSampler(local_rank) as e2e_clk:
+            t = time.perf_counter()
+            done = run(args.steps, t)
+            torch.cuda.synchronize()
+            barrier()
+            secs = slowest(time.perf_counter() - t)
         gc.enable()
         pair[1].close()
         e2e = {"value": deposits * world * args.steps / secs, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * secs / args.steps,
                "step_done_ms": [round(1e3 * v, 2) for v in done],
+               "clocks": e2e_clk.summary(),
                "pipeline": "2 detectors on 2 CUDA streams, readbacks on high-priority streams: copies of one step "
                            "overlap the next step's deposit",
                "host_link": host_link_gbs(Ehs[0], xh)}
