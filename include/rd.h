@@ -320,6 +320,21 @@ RD_API rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix_t0,
                                     rd_stream stream);
 
 /*
+ * Run-time coupling (Section 3.1: the deposit runs as a sub-step right after the particle push,
+ * from the new positions and momenta and the stored previous ones).  Advances n_part charges by
+ * n_steps Boris steps of dt in a uniform magnetic field B[3] (host array; c = 1, qm = charge to mass
+ * ratio, the same for every particle): t = (qm dt / 2) B / gamma, s = 2 t / (1 + |t|^2),
+ * u' = u + u x t, u <- u + u' x s, x <- x + dt u / gamma (|u|, hence gamma, is kept; u turns about
+ * B by 2 atan(|t|) per step).  x, u: the state [n_part][3] FP64 in device memory, updated in place.
+ * x_out, u_out: [n_part][n_steps][3] FP64 in device memory, the new samples (after a state at time
+ * t, sample k is at t + (k + 1) dt), laid out as rd_deposit_stream takes a stretch of new samples.
+ * Asynchronous on `stream`.  RD_ERR_ARG for a negative count, a NULL pointer or a non-finite dt,
+ * qm or field.
+ */
+RD_API rd_status rd_push_boris(int32_t n_part, int32_t n_steps, double dt, const double* B, double qm,
+                               double* x, double* u, double* x_out, double* u_out, rd_stream stream);
+
+/*
  * Diagnostic, not part of the deposit: the FP32 and FP64 fused multiply-add throughput of the
  * current device, measured by a microbenchmark (independent FMA chains on every SM, one launch
  * of about 20 ms per precision, timed with CUDA events on `stream`).  These are the denominators

@@ -27,7 +27,7 @@ __all__ = [
     "rd_deposit_trajectories", "rd_read_fields", "rd_synchronize", "rd_get_stats",
     "rd_set_timing", "rd_adjoint_trajectories", "rd_deposit_batch", "rd_set_chunk", "rd_autotune",
     "rd_set_batch_budget", "rd_power_spectrum", "rd_deposit_stream", "rd_stream_reset",
-    "rd_deposit_noalloc", "rd_measure_fma_peaks", "rd_check_bounded_wait", "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
+    "rd_deposit_noalloc", "rd_measure_fma_peaks", "rd_check_bounded_wait", "rd_push_boris", "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
 ]
 
 RD_OK, RD_ERR_ARG, RD_ERR_CUDA, RD_ERR_OOM, RD_ERR_STATE, RD_ERR_TIMEOUT, RD_ERR_BOUNDS, RD_ERR_INPUT = range(8)
@@ -108,6 +108,8 @@ def load_library(build_if_missing: bool = True):
                                     ctypes.POINTER(ctypes.c_uint32), P], I),
             "rd_measure_fma_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P], I),
             "rd_check_bounded_wait": ([I, P], I),
+            "rd_push_boris": ([I, I, ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                               P, P, P, P, P], I),
             "rd_last_error": ([], ctypes.c_char_p),
             "rd_version": ([], ctypes.c_char_p),
         }
@@ -242,6 +244,25 @@ def rd_measure_fma_peaks(stream=None):
     lib = load_library()
     _check(lib.rd_measure_fma_peaks(ctypes.byref(f32), ctypes.byref(f64), _stream_ptr(stream)), "rd_measure_fma_peaks")
     return f32.value, f64.value
+
+
+def rd_push_boris(x, u, n_steps: int, dt: float, B, qm: float, x_out=None, u_out=None, stream=None):
+    """Advance the charges with state x, u ([n_part][3] float64 CUDA tensors, updated in place) by
+    n_steps Boris steps in the uniform field B; returns the new samples (x_out, u_out),
+    [n_part][n_steps][3] CUDA tensors (allocated unless given)."""
+    import torch
+    for a in (x, u):
+        if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous() and a.dim() == 2 and a.shape[1] == 3):
+            raise ValueError("x and u must be contiguous float64 CUDA tensors [n_part][3]")
+    n = x.shape[0]
+    if x_out is None:
+        x_out = torch.empty((n, n_steps, 3), dtype=torch.float64, device=x.device)
+    if u_out is None:
+        u_out = torch.empty((n, n_steps, 3), dtype=torch.float64, device=x.device)
+    b = (ctypes.c_double * 3)(*[float(v) for v in B])
+    _check(load_library().rd_push_boris(int(n), int(n_steps), float(dt), b, float(qm), x.data_ptr(), u.data_ptr(),
+                                        x_out.data_ptr(), u_out.data_ptr(), _stream_ptr(stream)), "rd_push_boris")
+    return x_out, u_out
 
 
 def rd_check_bounded_wait(limit_ms: int = 20, stream=None) -> int:

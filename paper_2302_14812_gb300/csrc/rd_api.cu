@@ -236,6 +236,20 @@ const char* rd_last_error(void) { return g_err.c_str(); }
 
 const char* rd_version(void) { return "rd 0.1 (sm_103a)"; }
 
+rd_status rd_push_boris(int32_t n_part, int32_t n_steps, double dt, const double* B, double qm, double* x,
+                        double* u, double* x_out, double* u_out, rd_stream stream)
+{
+    g_err.clear();
+    if (n_part < 0 || n_steps < 0) return fail(RD_ERR_ARG, "negative count (n_part %d, n_steps %d)", n_part, n_steps);
+    if (!B || !isfinite(dt) || !isfinite(qm) || !isfinite(B[0]) || !isfinite(B[1]) || !isfinite(B[2]))
+        return fail(RD_ERR_ARG, "B is NULL, or dt, qm or B not finite");
+    if (n_part == 0 || n_steps == 0) return RD_OK;
+    if (!x || !u || !x_out || !u_out) return fail(RD_ERR_ARG, "state or output pointer is NULL");
+    RD_CUDA(launch_push_boris(n_part, n_steps, dt, B, qm, x, u, x_out, u_out, reinterpret_cast<cudaStream_t>(stream)),
+            "rd_push_boris");
+    return RD_OK;
+}
+
 rd_status rd_check_bounded_wait(int32_t limit_ms, rd_stream stream)
 {
     g_err.clear();

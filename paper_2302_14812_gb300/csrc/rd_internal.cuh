@@ -168,6 +168,9 @@ constexpr int kAdjointFp64Threads = 128;   // FP64 adjoint: one cell per thread
 cudaError_t launch_gbeta_to_gu(const double* u, const double* gbeta, double* gu, long long n_samples_total,
                                cudaStream_t s);
 
+// run-time coupling (rd_push.cu): Boris steps in a uniform magnetic field B[3] (host array)
+cudaError_t launch_push_boris(int n_part, int n_steps, double dt, const double* B, double qm, double* x, double* u,
+                              double* x_out, double* u_out, cudaStream_t s);
 // diagnostics (rd_diag.cu): FMA throughput of the current device in TFLOP/s (one FMA = 2 flops), and one
 // CTA whose bounded wait on an mbarrier phase that nothing completes runs out after limit_ns (the
 // expiry is recorded in *errors as the kernels record it)

@@ -152,6 +152,29 @@ def helical_orbit(gamma: float = 57.3, K: float = 0.8, omega0: float = 1.0, n_st
     return Trajectories(x[None].copy(), u[None].copy(), np.array([q]), t0, dt)
 
 
+def boris_uniform_field(x0: np.ndarray, u0: np.ndarray, n_steps: int, dt: float, B, qm: float,
+                        q: float = -1.0, t0: float = 0.0) -> Trajectories:
+    """Charges pushed by the Boris method (Boris 1970) in a uniform magnetic field B (c = 1, qm the
+    charge-to-mass ratio): per step t = (qm dt/2) B/gamma, s = 2t/(1+|t|^2), u' = u + u x t,
+    u <- u + u' x s, x <- x + dt u/gamma.  x0, u0: [n_part][3]; samples k = 0..n_steps."""
+    B = np.asarray(B, dtype=np.float64)
+    x = np.array(x0, dtype=np.float64)
+    u = np.array(u0, dtype=np.float64)
+    g = np.sqrt(1.0 + np.sum(u * u, axis=1))
+    t = (0.5 * qm * dt / g)[:, None] * B[None, :]
+    s = (2.0 / (1.0 + np.sum(t * t, axis=1)))[:, None] * t
+    w = (dt / g)[:, None]
+    X = np.empty((x.shape[0], n_steps + 1, 3))
+    U = np.empty_like(X)
+    X[:, 0], U[:, 0] = x, u
+    for k in range(n_steps):
+        v = u + np.cross(u, t)
+        u = u + np.cross(v, s)
+        x = x + w * u
+        X[:, k + 1], U[:, k + 1] = x, u
+    return Trajectories(X, U, np.full(x.shape[0], q), t0, dt)
+
+
 def circular_ensemble(n_part: int, n_steps: int, gamma: float = 5.0, radius: float = 1.0,
                       n_orbits: float = 4.0, seed: int = 5, q: float = -1.0) -> Trajectories:
     """n_part charges on the same circular orbit (x-y plane) with random phases."""

@@ -108,3 +108,65 @@ def test_stream_continuity_checks_and_reset():
     assert rel_l2(E2, E3) <= 2e-6 and np.abs(E1).max() > 0
     one.close()
     d.close()
+
+
+def _boris_case():
+    rng = np.random.default_rng(17)
+    n = 6
+    u0 = np.stack([rng.uniform(-0.5, 0.5, n), rng.uniform(1.0, 3.0, n), rng.uniform(0.5, 2.0, n)], axis=1)
+    x0 = rng.normal(size=(n, 3)) * 0.1
+    B, qm, dt, n_steps = (0.0, 0.0, 1.5), -1.0, 0.05, 400
+    tr = W.boris_uniform_field(x0, u0, n_steps, dt, B, qm)
+    pos = rng.normal(size=(300, 3))
+    pos = 30.0 * pos / np.linalg.norm(pos, axis=1, keepdims=True)
+    t_end = n_steps * dt
+    det = W.Detector(pos, None, 30.0 - 25.0, 0.02, int((t_end + 50.0) / 0.02))
+    return tr, det, x0, u0, B, qm, dt, n_steps
+
+
+def test_boris_pusher_matches_the_recurrence():
+    """rd_push_boris against the same Boris recurrence in numpy (FP64, 400 steps in chunks of 50):
+    samples agree to rounding, |u| is kept and u turns about B by 2 atan(|t|) per step."""
+    import torch
+    tr, _, x0, u0, B, qm, dt, n_steps = _boris_case()
+    x = torch.from_numpy(x0.copy()).cuda()
+    u = torch.from_numpy(u0.copy()).cuda()
+    xs, us = [], []
+    for _ in range(n_steps // 50):
+        xo, uo = rd.rd_push_boris(x, u, 50, dt, B, qm)
+        xs.append(xo.cpu().numpy())
+        us.append(uo.cpu().numpy())
+    X, U = np.concatenate(xs, axis=1), np.concatenate(us, axis=1)
+    assert np.max(np.abs(X - tr.x[:, 1:])) <= 1e-12 * np.max(np.abs(tr.x))
+    assert np.max(np.abs(U - tr.u[:, 1:])) <= 1e-12 * np.max(np.abs(tr.u))
+    g = np.sqrt(1.0 + np.sum(u0 * u0, axis=1))
+    phi = 2.0 * np.arctan(0.5 * abs(qm) * dt * np.linalg.norm(B) / g)
+    ang = np.unwrap(np.arctan2(U[:, :, 1], U[:, :, 0]), axis=1)
+    assert np.max(np.abs(np.abs(ang[:, -1] - ang[:, 0]) - (n_steps - 1) * phi)) < 1e-10
+    assert np.max(np.abs(np.linalg.norm(U, axis=2) - np.linalg.norm(u0, axis=1)[:, None])) < 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_runtime_coupling_push_then_deposit(precision, tol):
+    """The run-time mode of Section 3.1: every 50 Boris steps on the device, the new samples are
+    deposited at once by rd_deposit_stream (the first call carries the initial state as sample 0).
+    Against the oracle's deposit of the numpy Boris trajectory, every cell."""
+    import torch
+    tr, det, x0, u0, B, qm, dt, n_steps = _boris_case()
+    d = rd.RadiationDetector.from_workload(det, precision)
+    x = torch.from_numpy(x0.copy()).cuda()
+    u = torch.from_numpy(u0.copy()).cuda()
+    q = torch.from_numpy(tr.q).cuda()
+    for c in range(n_steps // 50):
+        xo, uo = rd.rd_push_boris(x, u, 50, dt, B, qm)
+        if c == 0:
+            xo = torch.cat([torch.from_numpy(x0).cuda()[:, None], xo], dim=1).contiguous()
+            uo = torch.cat([torch.from_numpy(u0).cuda()[:, None], uo], dim=1).contiguous()
+            d.deposit_stream(xo, uo, q, tr.t0, dt)
+        else:
+            d.deposit_stream(xo, uo, q, tr.t0 + (50 * c + 1) * dt, dt)
+    E, B_ = d.read()
+    d.close()
+    Eo, Bo, clipped = oracle.deposit(tr, det)
+    assert clipped == 0
+    assert rel_l2(E, Eo) <= tol and rel_l2(B_, Bo) <= tol

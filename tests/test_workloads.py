@@ -40,3 +40,24 @@ def test_plasma_mirror_detector_window_covers_arrivals():
         ub = (tr.t0 + k[None] * tr.dt + R - (det.t_min + det.pix_t0[:, None])) / det.dt_det
         assert ub.min() > 0.0 and ub.max() < det.n_bins
     assert math.isclose(det.dt_det, 5.0 * tr.dt)
+
+
+def test_boris_generator_rotation_closed_form():
+    """The numpy Boris generator: in a uniform field |u| is kept and u turns about B by exactly
+    2 atan(|t|) per step, t = (qm dt/2) |B| / gamma (the Boris rotation); chords stay below c."""
+    rng = np.random.default_rng(3)
+    u0 = rng.normal(size=(5, 3))
+    x0 = rng.normal(size=(5, 3))
+    B, qm, dt, n = np.array([0.3, -0.4, 1.2]), 2.0, 0.03, 500
+    tr = W.boris_uniform_field(x0, u0, n, dt, B, qm)
+    assert np.max(np.abs(np.linalg.norm(tr.u, axis=2) - np.linalg.norm(u0, axis=1)[:, None])) < 1e-12
+    bh = B / np.linalg.norm(B)
+    perp = tr.u - np.sum(tr.u * bh, axis=2, keepdims=True) * bh
+    e1 = perp[:, 0] / np.linalg.norm(perp[:, 0], axis=1, keepdims=True)
+    e2 = np.cross(bh, e1)
+    ang = np.unwrap(np.arctan2(np.sum(perp * e2[:, None], axis=2), np.sum(perp * e1[:, None], axis=2)), axis=1)
+    g = np.sqrt(1.0 + np.sum(u0 * u0, axis=1))
+    phi = 2.0 * np.arctan(0.5 * qm * dt * np.linalg.norm(B) / g)
+    assert np.max(np.abs(np.abs(ang[:, -1]) - n * phi)) < 1e-10
+    chord = np.linalg.norm(np.diff(tr.x, axis=1), axis=2) / dt
+    assert chord.max() < 1.0
