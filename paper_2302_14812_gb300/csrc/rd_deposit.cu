@@ -1,13 +1,13 @@
-// Deposit kernels: per-sample precompute, the mixed-precision deposit, the plain FP64 deposit
-// and the field readout.
+// Per-sample precompute (both precisions), the plain FP64 deposit and the field readout (the
+// mixed-precision deposit is in rd_mixed.cu).
 //
-// Work decomposition (both deposit kernels): one CTA = 256 detector cells (one per thread) x one
+// Work decomposition of the FP64 deposit: one CTA = 256 detector cells (one per thread) x one
 // particle x one chunk of consecutive intervals.  The chunk's per-sample records are streamed
 // through shared memory in tiles of 64 samples by bulk asynchronous copies (double buffered,
-// mbarrier completion); every thread reads each record as a broadcast.  Each thread walks its
-// cell's arrival times forward in k (they increase for sub-luminal chords), keeps the bin it is
-// filling in registers and adds the bin to global memory with vector reductions only when its
-// arrival time leaves the bin.
+// mbarrier completion); every thread reads each record as a broadcast.  Each thread evaluates its
+// cell's arrival time from Eq. 2 for every sample (they increase for sub-luminal chords), keeps
+// the bin it is filling in registers and adds the bin to global memory only when its arrival time
+// leaves the bin.
 #include <math.h>
 
 #include "rd_internal.cuh"
