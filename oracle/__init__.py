@@ -7,6 +7,9 @@ package, and the two share no code.
 Parity of each function:
   field, beta, arrival_time, bin_coord, deposit_interval, deposit  -- pinned by tests/test_oracle_*.py
   deposit_dir (complex-step derivative)                            -- pinned by central finite differences
+  deposit_ext (long double evaluation of deposit)                   -- pinned against deposit where FP64 rounding
+                                                                      is negligible, and against the rounding
+                                                                      bound of Eq. 2 where it is not
 """
 from __future__ import annotations
 
@@ -66,6 +69,8 @@ def _load():
             lib.rdo_deposit.argtypes = [ctypes.POINTER(_Problem), ctypes.c_void_p, ctypes.c_int32, D, D,
                                         ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
             lib.rdo_deposit.restype = ctypes.c_int32
+            lib.rdo_deposit_ext.argtypes = lib.rdo_deposit.argtypes
+            lib.rdo_deposit_ext.restype = ctypes.c_int32
             lib.rdo_deposit_dir.argtypes = [ctypes.POINTER(_Problem), ctypes.c_void_p, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_double, D, D, ctypes.c_int32]
@@ -178,6 +183,24 @@ def deposit(tr, det, sel=None, n_threads=None):
     if st != 0:
         raise OracleError({1: "bad arguments", 2: "invalid trajectory (chord speed >= 1 or not finite)",
                            3: "out of memory"}.get(st, f"status {st}"))
+    return E, B, int(clipped.value)
+
+
+def deposit_ext(tr, det, sel=None, n_threads=None):
+    """deposit() evaluated in long double (same formulas, longer mantissa): measures the rounding
+    of the FP64 evaluation, chiefly Eq. 2's t + R where R is large and a step's arrival increment
+    dt (1 - beta.n) is small."""
+    lib = _load()
+    keep = []
+    pr = _problem(tr, det, keep)
+    sp, n_sel = _selection(det, sel, keep)
+    E = np.zeros((n_sel, det.n_bins, 3))
+    B = np.zeros((n_sel, det.n_bins, 3))
+    clipped = ctypes.c_int64(0)
+    st = lib.rdo_deposit_ext(ctypes.byref(pr), sp, n_sel, _dp(E), _dp(B),
+                             int(n_threads or default_threads()), ctypes.byref(clipped))
+    if st != 0:
+        raise OracleError(f"rdo_deposit_ext status {st}")
     return E, B, int(clipped.value)
 
 

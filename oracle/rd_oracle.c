@@ -55,6 +55,22 @@
 #undef S_SQRT
 #undef RE
 
+/* ---- extended-precision instantiation ----
+ * The same formulas with long double particle quantities, arrival times and sums (64-bit
+ * mantissa on x86-64, 113-bit on AArch64).  Cell positions, t_k = t0 + k dt and 1/dt_det stay
+ * FP64 inputs, as in the other two.  Used to measure the rounding of the FP64 evaluation itself:
+ * Eq. 2 adds R (large) to t, so a step's arrival increment dt (1 - beta.n) keeps only
+ * ulp(R) / (dt kappa) of its digits, which grows as gamma^2 R. */
+#define SCALAR long double
+#define SUFFIX e
+#define S_SQRT(v) sqrtl(v)
+#define RE(v) ((double)(v))
+#include "rd_oracle_core.h"
+#undef SCALAR
+#undef SUFFIX
+#undef S_SQRT
+#undef RE
+
 typedef struct {
     int32_t n_pix;
     const double* pix_pos;   /* [n_pix][3] */
@@ -219,6 +235,45 @@ static void* run_cstep(void* arg)
     return NULL;
 }
 
+static void* run_ext(void* arg)
+{
+    rdo_job* jb = (rdo_job*)arg;
+    const rdo_problem* pr = jb->pr;
+    const int nb = pr->n_bins;
+    const size_t ns = (size_t)pr->n_samples;
+    const double inv_dt_det = 1.0 / pr->dt_det;
+    long double* row = (long double*)malloc(sizeof(long double) * 6 * (size_t)nb);
+    long double* xs = (long double*)malloc(sizeof(long double) * 3 * ns);
+    long double* us = (long double*)malloc(sizeof(long double) * 3 * ns);
+    if (!row || !xs || !us) { free(row); free(xs); free(us); jb->status = 3; return NULL; }
+    for (int32_t s = jb->tid; s < jb->n_sel; s += jb->n_threads) {
+        const int32_t j = jb->sel ? jb->sel[s] : s;
+        const double* P = pr->pix_pos + 3 * (size_t)j;
+        const double T0 = pr->t_min + (pr->pix_t0 ? pr->pix_t0[j] : 0.0);
+        for (size_t i = 0; i < 6 * (size_t)nb; ++i) row[i] = 0.0L;
+        for (int32_t p = 0; p < pr->n_part; ++p) {
+            for (size_t i = 0; i < 3 * ns; ++i) {
+                xs[i] = pr->x[3 * ns * (size_t)p + i];
+                us[i] = pr->u[3 * ns * (size_t)p + i];
+            }
+            const double qp = pr->q ? pr->q[p] : 1.0;
+            jb->clipped += pixel_particle_e(xs, us, pr->n_samples, qp, pr->t0, pr->dt, P, T0, inv_dt_det,
+                                            nb, pr->flags, row);
+        }
+        double* Eo = jb->E + 3 * (size_t)nb * (size_t)s;
+        double* Bo = jb->B + 3 * (size_t)nb * (size_t)s;
+        for (int b = 0; b < nb; ++b)
+            for (int i = 0; i < 3; ++i) {
+                Eo[3 * b + i] = (double)row[6 * b + i];
+                Bo[3 * b + i] = (double)row[6 * b + 3 + i];
+            }
+    }
+    free(row);
+    free(xs);
+    free(us);
+    return NULL;
+}
+
 static int run_threads(rdo_job* proto, int32_t n_threads, void* (*fn)(void*), long long* clipped)
 {
     if (n_threads < 1) n_threads = 1;
@@ -274,6 +329,31 @@ int32_t rdo_deposit(const rdo_problem* pr, const int32_t* sel, int32_t n_sel, do
     proto.B = B;
     long long c = 0;
     st = run_threads(&proto, n_threads, run_real, &c);
+    if (n_clipped) *n_clipped = (int64_t)c;
+    return st;
+}
+
+/* rdo_deposit evaluated in long double (extended-precision instantiation above); same
+ * arguments, outputs rounded to FP64. */
+int32_t rdo_deposit_ext(const rdo_problem* pr, const int32_t* sel, int32_t n_sel, double* E, double* B,
+                        int32_t n_threads, int64_t* n_clipped)
+{
+    int st = check_problem(pr);
+    if (st) return st;
+    if (n_sel < 0 || (n_sel > 0 && (!E || !B))) return 1;
+    for (int32_t s = 0; s < n_sel; ++s) {
+        int32_t j = sel ? sel[s] : s;
+        if (j < 0 || j >= pr->n_pix) return 1;
+    }
+    rdo_job proto;
+    memset(&proto, 0, sizeof proto);
+    proto.pr = pr;
+    proto.sel = sel;
+    proto.n_sel = n_sel;
+    proto.E = E;
+    proto.B = B;
+    long long c = 0;
+    st = run_threads(&proto, n_threads, run_ext, &c);
     if (n_clipped) *n_clipped = (int64_t)c;
     return st;
 }

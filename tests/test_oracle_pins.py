@@ -763,3 +763,68 @@ def test_linear_interpolation_is_second_order(oracle_lib):
         ratios[fl] = np.linalg.norm(Ds[0] - Ds[1]) / np.linalg.norm(Ds[1] - Ds[2])
     assert 1.8 < ratios[W.RD_NEAR] < 2.2, ratios
     assert 3.5 < ratios[W.RD_NEAR | W.RD_LINEAR] < 4.5, ratios
+
+
+# --------------------------------------------------------------------------------------------
+# Rounding of the FP64 evaluation itself (extended-precision instantiation)
+# --------------------------------------------------------------------------------------------
+def _undulator_one(gamma):
+    tr, det = W.config_undulator(n_part=1, n_steps=2000, n_side=16, n_bins=2048, gamma=gamma, K=1.0,
+                                 distance=1e4)
+    return tr, det, 8 * 16 + 8
+
+
+def _sum_rule_mp(tr, det, j):
+    """sum_k F_k (u_k - u_{k-1}) with the arrival coordinates u_k of Eq. 2 taken in 40-digit
+    arithmetic (mpmath) from the same FP64 inputs, and F_k from the oracle's field (Eq. 1)."""
+    mpmath = pytest.importorskip("mpmath")
+    with mpmath.workdps(40):
+        P = [mpmath.mpf(float(v)) for v in det.pix_pos[j]]
+        T0 = mpmath.mpf(det.t_min) + mpmath.mpf(0.0 if det.pix_t0 is None else float(det.pix_t0[j]))
+        us = []
+        for k in range(tr.n_samples):
+            d = [P[i] - mpmath.mpf(float(tr.x[0, k, i])) for i in range(3)]
+            t = mpmath.mpf(tr.t0) + k * mpmath.mpf(tr.dt)
+            us.append((t + mpmath.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2) - T0) / mpmath.mpf(det.dt_det))
+        du = np.array([float(us[k] - us[k - 1]) for k in range(1, tr.n_samples)])
+    F = np.zeros((tr.n_samples - 1, 3))
+    for k in range(1, tr.n_samples):
+        b = oracle.beta(tr.u[0, k])
+        bp = oracle.beta(tr.u[0, k - 1])
+        F[k - 1] = oracle.field(tr.x[0, k], b, (b - bp) / tr.dt, det.pix_pos[j], tr.q[0], det.flags)[0]
+    return (F * du[:, None]).sum(0)
+
+
+def test_extended_precision_agrees_at_benchmark_gamma(oracle_lib):
+    """At gamma 20 (the undulator workload's geometry, R = 1e4) the FP64 and the long double
+    evaluations of the deposit agree to 1e-7: the FP64 oracle's own rounding is negligible there."""
+    tr, det = W.config_undulator(n_part=3, n_steps=2000, n_side=16, n_bins=2048, gamma=20.0, K=1.0,
+                                 distance=1e4)
+    sel = np.array([0, 7, 136, 255], dtype=np.int32)
+    E64, B64, c64 = oracle.deposit(tr, det, sel)
+    Ee, Be, ce = oracle.deposit_ext(tr, det, sel)
+    assert c64 == ce == 0
+    assert np.linalg.norm(E64 - Ee) / np.linalg.norm(Ee) < 1e-7
+    assert np.linalg.norm(B64 - Be) / np.linalg.norm(Be) < 1e-7
+
+
+@pytest.mark.parametrize("gamma", [20.0, 1000.0])
+def test_extended_precision_sum_rule(oracle_lib, gamma):
+    """Sum rule of the integrator (Section 3.2) with exact arrival times: the long double deposit
+    meets it to 1e-6 of the total.  At gamma 1000 the whole pulse of an electron on a cell is
+    shorter than a bin, so the bins hold the small residual of an oscillating field (about 1/400 of
+    sum |F| du), and Eq. 2's t + R in FP64 keeps only ulp(R) / (dt kappa) of each step's arrival
+    increment: the FP64 deposit misses the same sum by far more than the long double one."""
+    tr, det, j = _undulator_one(gamma)
+    sel = np.array([j], dtype=np.int32)
+    want = _sum_rule_mp(tr, det, j)
+    Ee, _, ce = oracle.deposit_ext(tr, det, sel)
+    E64, _, c64 = oracle.deposit(tr, det, sel)
+    assert c64 == ce == 0
+    err_ext = np.abs(Ee[0].sum(0) - want).max() / np.abs(want).max()
+    err_64 = np.abs(E64[0].sum(0) - want).max() / np.abs(want).max()
+    assert err_ext < 1e-6, err_ext
+    if gamma >= 1000.0:
+        assert err_64 > 100.0 * err_ext, (err_64, err_ext)
+    else:
+        assert err_64 < 1e-6, err_64
