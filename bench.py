@@ -51,7 +51,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 WORKLOAD_UNDULATOR = ("undulator ensemble: 1000 e- (gamma 20, K 1, 10 periods) x 4000 steps, "
                       "128x128-cell spherical cap at 1e4 periods x 2048 bins")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "deposit_mixed_undulator_ncu.md")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_2302_14812_gb300", "csrc", "rd_mixed.cu")
+# the headline kernel and the files that fix its launch (work items, step chunk, shapes): the
+# committed traffic figure holds only for the revision it was captured on
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2302_14812_gb300", "csrc", f)
+                  for f in ("rd_mixed.cu", "rd_internal.cuh", "rd_api.cu")]
 
 
 def parse():
@@ -172,7 +175,7 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------------------
 def profile_traffic():
     """DRAM bytes per launch of the mixed deposit kernel from the committed ncu summary, if the
-    summary was taken on the current kernel source (else None)."""
+    summary was taken on the current kernel and launch sources (else None)."""
     try:
         txt = open(PROFILE_SUMMARY).read()
     except OSError:
@@ -181,8 +184,16 @@ def profile_traffic():
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", txt)
     if not m or not h:
         return None
-    cur = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
-    return float(m.group(1)) if h.group(1) == cur else None
+    return float(m.group(1)) if h.group(1) == kernel_sources_sha() else None
+
+
+def kernel_sources_sha() -> str:
+    """sha256 over the concatenated KERNEL_SOURCES."""
+    sha = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            sha.update(fh.read())
+    return sha.hexdigest()
 
 
 def hbm_peak():
@@ -777,7 +788,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "precision": "mixed: FP32 fields and accumulation, arrival times FP64-anchored per 1024-step chunk",
+        "precision": "mixed: FP32 fields and accumulation, arrival times FP64-anchored at both ends of each step chunk (up to 4096 intervals)",
         "config": {"workload": WORKLOAD_UNDULATOR,
                    "deposits_per_step_per_gpu": deposits, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (x,u 192 MB; records 256 MB; fields 1.07 GB)"},

@@ -278,7 +278,7 @@ RD_API rd_status rd_set_batch_budget(rd_detector* det, long long bytes);
 
 /*
  * Steps per work item (the step chunk between exact FP64 arrival anchors) for this detector's
- * deposits; 0 = automatic (1024, halved while the grid would be too small to fill the GPU).
+ * deposits; 0 = automatic (4096, halved while the grid would be too small to fill the GPU).
  */
 RD_API rd_status rd_set_chunk(rd_detector* det, int32_t chunk);
 

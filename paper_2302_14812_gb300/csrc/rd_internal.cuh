@@ -110,7 +110,7 @@ constexpr int kMixedMaxBins = 1 << 22;         // bins per cell of an RD_MIXED d
 #define RD_TILE_STEPS 64
 #endif
 constexpr int kTileSteps = RD_TILE_STEPS;   // intervals per shared-memory tile
-constexpr int kDefaultChunk = 1024;    // intervals per work item (one FP64 anchor at each end)
+constexpr int kDefaultChunk = 4096;    // intervals per work item (one FP64 anchor at each end)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // give up a wait after 2 s
 
 // launchers (rd_deposit.cu)
