@@ -50,6 +50,11 @@ FLOPS_PER_DEPOSIT_FP64 = 84
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 WORKLOAD_UNDULATOR = ("undulator ensemble: 1000 e- (gamma 20, K 1, 10 periods) x 4000 steps, "
                       "128x128-cell spherical cap at 1e4 periods x 2048 bins")
+
+
+def undulator_workload(n_part: int) -> str:
+    """Workload name of the undulator ensemble with n_part electrons (the headline has 1000)."""
+    return WORKLOAD_UNDULATOR.replace("1000 e-", f"{n_part} e-", 1)
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "deposit_mixed_undulator_ncu.md")
 # the headline kernel and the files that fix its launch (work items, step chunk, shapes): the
 # committed traffic figure holds only for the revision it was captured on
@@ -283,7 +288,7 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": WORKLOAD_UNDULATOR, "sample": sample},
+        "config": {"workload": undulator_workload(tr.n_part), "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -783,13 +788,13 @@ def main():
     crossings = st.n_bin_crossings            # of the last timed step (each step starts from zero)
     flops_step = FLOPS_PER_DEPOSIT_MIXED * deposits + FLOPS_PER_CROSSING_MIXED * crossings
     achieved = flops_step / (kernel_ms / 1e3) / 1e12
-    traffic = profile_traffic()
+    traffic = profile_traffic() if tr.n_part == 1000 else None     # the summary covers the full-size launch
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "precision": "mixed: FP32 fields and accumulation, arrival times FP64-anchored at both ends of each step chunk (up to 4096 intervals)",
-        "config": {"workload": WORKLOAD_UNDULATOR,
+        "config": {"workload": undulator_workload(tr.n_part),
                    "deposits_per_step_per_gpu": deposits, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (x,u 192 MB; records 256 MB; fields 1.07 GB)"},
         "gpu_launches": launches,
