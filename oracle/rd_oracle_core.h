@@ -1,10 +1,11 @@
 /*
  * Scalar-generic core of the FP64 oracle.  TEST INFRASTRUCTURE ONLY: see rd_oracle.c.
  *
- * Included twice by rd_oracle.c: once with SCALAR = double (the oracle proper) and once with
+ * Included three times by rd_oracle.c: with SCALAR = double (the oracle proper), with
  * SCALAR = double complex (complex-step differentiation: perturbing one input by i*h gives
  * d(output)/d(input) = Im(output)/h exactly up to rounding, because every operation used here
- * is analytic; comparisons and floor() act on real parts only).
+ * is analytic; comparisons and floor() act on real parts only) and with SCALAR = long double
+ * (the same evaluation with a longer mantissa, to measure the rounding of the FP64 one).
  *
  * Macros expected: SCALAR, SUFFIX, S_SQRT(x), RE(x).
  */
