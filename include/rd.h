@@ -308,7 +308,7 @@ RD_API rd_status rd_autotune(rd_detector* det, const rd_traj* traj, rd_stream st
  *     (1 << RD_ERR_INPUT for a rejected sample); given, the call synchronises the stream.
  * Scratch: one 64 MiB array inside the library, held by every GPU that loads it until the process
  * exits.  Limits: n_pix <= 262144, n_bins <= 4194304, and one particle's samples must fit the 56 MiB record area
- * (n_samples <= 917504); larger requests return RD_ERR_ARG.  Particles are processed in chunks
+ * (n_samples <= 917500); larger requests return RD_ERR_ARG.  Particles are processed in chunks
  * that fit.  The first call on a device looks up the array's device address (once per device);
  * make that first call before any stream capture.  Every call shares the array, which keeps the
  * last call's contents: calls that overlap on the GPU (other streams, other host threads) race and

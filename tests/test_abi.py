@@ -87,3 +87,32 @@ def test_argument_errors_without_gpu():
     assert lib.rd_deposit_stream(None, None, None) == rd.RD_ERR_ARG
     assert lib.rd_stream_reset(None) == rd.RD_ERR_ARG
     assert lib.rd_set_chunk(None, 0) == rd.RD_ERR_ARG
+    # the other entry points refuse bad arguments before any CUDA call
+    assert lib.rd_synchronize(None, None) == rd.RD_ERR_ARG
+    assert lib.rd_get_stats(None, None, None) == rd.RD_ERR_ARG
+    assert lib.rd_set_timing(None, 1) == rd.RD_ERR_ARG
+    assert lib.rd_adjoint_trajectories(None, None, None, None, 0, None, None, None) == rd.RD_ERR_ARG
+    assert lib.rd_deposit_batch(0, None, None, None) == rd.RD_ERR_ARG
+    assert lib.rd_autotune(None, None, None, None) == rd.RD_ERR_ARG
+    assert lib.rd_power_spectrum(None, 0, None, None) == rd.RD_ERR_ARG
+    assert lib.rd_check_bounded_wait(0, None) == rd.RD_ERR_ARG
+    assert lib.rd_check_bounded_wait(2001, None) == rd.RD_ERR_ARG
+    B = (ctypes.c_double * 3)(0.0, 0.0, 1.0)
+    assert lib.rd_push_boris(-1, 1, 0.1, B, 1.0, None, None, None, None, None) == rd.RD_ERR_ARG
+    assert lib.rd_push_boris(1, 1, 0.1, None, 1.0, None, None, None, None, None) == rd.RD_ERR_ARG
+    assert lib.rd_push_boris(1, 1, 0.1, B, 1.0, None, None, None, None, None) == rd.RD_ERR_ARG
+    B[2] = float("nan")
+    assert lib.rd_push_boris(1, 1, 0.1, B, 1.0, None, None, None, None, None) == rd.RD_ERR_ARG
+    assert lib.rd_push_boris(0, 5, 0.1, (ctypes.c_double * 3)(), 1.0, None, None, None, None, None) == rd.RD_OK
+    # rd_deposit_noalloc: one particle's records must fit the 56 MiB record area (917500 samples)
+    t = rd.rd_traj()
+    t.n_part, t.n_samples, t.mem, t.t0, t.dt = 1, 917501, rd.RD_MEM_DEVICE, 0.0, 0.1
+    t.x = t.u = 16                                    # never dereferenced: the size check comes first
+    cells = (ctypes.c_double * 3)()
+    assert lib.rd_deposit_noalloc(ctypes.cast(cells, ctypes.c_void_p), None, 1, 0.0, 0.1, 8, 0, ctypes.byref(t),
+                                  16, None, None) == rd.RD_ERR_ARG
+    assert "917500" in rd.rd_last_error()
+    t.mem = rd.RD_MEM_HOST
+    assert lib.rd_deposit_noalloc(ctypes.cast(cells, ctypes.c_void_p), None, 1, 0.0, 0.1, 8, 0, ctypes.byref(t),
+                                  16, None, None) == rd.RD_ERR_ARG
+    assert "device trajectories" in rd.rd_last_error()
