@@ -46,8 +46,8 @@ FLOPS_PER_CROSSING_MIXED = 9
 # root, division and floor count 1 each): arrival time (Eq. 2) 14, Eq. 1 with B = n x E 56,
 # accumulation into the running bin 14.
 FLOPS_PER_DEPOSIT_FP64 = 84
-# FP32 peak derived from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# FP32 lanes per multiprocessor of this architecture (sm_103a: 4 sub-partitions x 32).
+FP32_LANES_PER_SM = 128
 WORKLOAD_UNDULATOR = ("undulator ensemble: 1000 e- (gamma 20, K 1, 10 periods) x 4000 steps, "
                       "128x128-cell spherical cap at 1e4 periods x 2048 bins")
 
@@ -199,6 +199,22 @@ def kernel_sources_sha() -> str:
         with open(f, "rb") as fh:
             sha.update(fh.read())
     return sha.hexdigest()
+
+
+def fp32_peak(sm_mhz):
+    """(TFLOP/s, description): FP32 FMA peak derived from this device's multiprocessor count, its
+    FP32 lanes and the median SM clock sampled during the timed region (max clock if none)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz, src = sm_mhz, "median SM clock sampled during the timed region"
+    if not mhz or not math.isfinite(mhz):
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                mhz, src = float(json.load(f)["sm_max_mhz"]), "maximum SM clock of this pool's GPUs"
+        except (OSError, KeyError, ValueError):
+            mhz, src = 2070.0, "nominal maximum SM clock"
+    tf = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    return tf, f"derived: {sms} SM x {FP32_LANES_PER_SM} FP32 lanes x 2 x {mhz:.0f} MHz ({src})"
 
 
 def hbm_peak():
@@ -788,6 +804,7 @@ def main():
     crossings = st.n_bin_crossings            # of the last timed step (each step starts from zero)
     flops_step = FLOPS_PER_DEPOSIT_MIXED * deposits + FLOPS_PER_CROSSING_MIXED * crossings
     achieved = flops_step / (kernel_ms / 1e3) / 1e12
+    peak32, peak_kind = fp32_peak(clocks.get("sm_mhz"))
     traffic = profile_traffic() if tr.n_part == 1000 else None     # the summary covers the full-size launch
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -799,8 +816,8 @@ def main():
                    "l2": "inputs larger than L2 (x,u 192 MB; records 256 MB; fields 1.07 GB)"},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "k_deposit_mixed", "achieved": achieved,
-                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "peak": peak32, "unit": "TFLOP/s", "frac": achieved / peak32,
+                     "peak_kind": peak_kind,
                      "peak_measured_fma": fma32, "frac_of_measured_fma": achieved / fma32 if fma32 > 0 else None,
                      "kernel_ms": kernel_ms, "flops_per_deposit": FLOPS_PER_DEPOSIT_MIXED,
                      "flops_per_crossing": FLOPS_PER_CROSSING_MIXED, "bin_crossings_per_step": crossings,

@@ -305,7 +305,11 @@ RD_API rd_status rd_autotune(rd_detector* det, const rd_traj* traj, rd_stream st
  *   fields: caller-allocated device accumulators float[n_pix][n_bins][8], per bin
  *     (Ex, Ey, Ez, Bx, By, Bz, unused, unused); the call ACCUMULATES (+=) into them.
  *   errors: NULL, or a host pointer that receives this call's latched kernel error bits
- *     (1 << RD_ERR_INPUT for a rejected sample); given, the call synchronises the stream.
+ *     (1 << RD_ERR_INPUT for a rejected sample or a cell with a non-finite position or time origin);
+ *     given, the call synchronises the stream.  With errors == NULL the bits are not reported to
+ *     anyone: the next call clears them before it starts.
+ *   flags are checked as rd_create_detector checks them (RD_ERR_ARG for a set that selects no term
+ *     of Eq. 1, e.g. RD_LINEAR or RD_FARFIELD alone).
  * Scratch: one 64 MiB array inside the library, held by every GPU that loads it until the process
  * exits.  Limits: n_pix <= 262144, n_bins <= 4194304, and one particle's samples must fit the 56 MiB record area
  * (n_samples <= 917500); larger requests return RD_ERR_ARG.  Particles are processed in chunks

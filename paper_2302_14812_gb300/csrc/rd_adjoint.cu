@@ -837,13 +837,7 @@ __global__ void k_gbeta_to_gu(const double* __restrict__ u, const double* __rest
     }
 }
 
-static int grid_for(long long n, int threads)
-{
-    long long g = (n + threads - 1) / threads;
-    if (g > 152LL * 16) g = 152LL * 16;
-    if (g < 1) g = 1;
-    return (int)g;
-}
+static int grid_for(long long n, int threads) { return grid_stride_blocks(n, threads, 16); }
 
 cudaError_t launch_pack_seed(const void* gE, const void* gB, int dtype, int n_pix, int n_bins, float* seed,
                              cudaStream_t s)

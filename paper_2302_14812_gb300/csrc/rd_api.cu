@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -141,15 +142,11 @@ rd_status check_traj(const rd_traj* t)
     return RD_OK;
 }
 
-// Intervals per work item: the default unless the grid would leave the GPU idle.
+// Intervals per work item: the detector's override, else the default rule.
 int choose_chunk(const rd_detector* d, int n_part, int S, int n_cell_blocks)
 {
     if (d->chunk_override > 0) return std::min(d->chunk_override, S);
-    int chunk = std::min(kDefaultChunk, S);
-    const long long want = 152LL * 8;   // resident CTAs for a few waves
-    while (chunk > 64 && (long long)n_cell_blocks * n_part * ((S + chunk - 1) / chunk) < want)
-        chunk /= 2;
-    return std::max(1, chunk);
+    return auto_chunk(n_cell_blocks, n_part, S);
 }
 
 // Bracket one deposit-kernel launch with events when timing is on.
@@ -228,6 +225,44 @@ rd_status set_last_error(rd_status st, const char* msg)
     g_err = msg ? msg : "";
     return st;
 }
+
+int sm_count()
+{
+    constexpr int kMaxDev = 256;
+    static std::atomic<int> cache[kMaxDev];        // 0: not queried yet
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev >= 0 && dev < kMaxDev && (n = cache[dev].load(std::memory_order_relaxed)) > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+    if (dev >= 0 && dev < kMaxDev) cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
+int grid_stride_blocks(long long n, int threads, int per_sm)
+{
+    long long g = (n + threads - 1) / threads;
+    g = std::min(g, (long long)sm_count() * per_sm);
+    return (int)std::max(1LL, g);
+}
+
+int auto_chunk(long long n_cell_blocks, long long n_part, int S)
+{
+    int chunk = std::min(kDefaultChunk, S);
+    const long long want = 8LL * sm_count();       // resident CTAs for a few waves
+    while (chunk > 64 && n_cell_blocks * n_part * ((S + chunk - 1) / chunk) < want) chunk /= 2;
+    return std::max(1, chunk);
+}
+
+const char* flags_error(int flags)
+{
+    if (flags & ~(RD_NEAR | RD_FAR | RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV)) return "unknown flag bits";
+    if ((flags & RD_LINEAR) && (flags & RD_HOLD_PREV)) return "RD_LINEAR and RD_HOLD_PREV are alternatives";
+    if ((flags & (RD_NEAR | RD_FAR)) == 0 && flags != 0)
+        return "flags select no term of Eq. 1 (RD_NEAR and/or RD_FAR)";
+    if ((flags & RD_FARFIELD) && (flags & RD_NEAR))
+        return "RD_FARFIELD keeps only the radiation term: RD_NEAR cannot be combined with it";
+    return nullptr;
+}
 }  // namespace rd
 
 extern "C" {
@@ -292,14 +327,7 @@ rd_status rd_create_detector(const rd_detector_desc* desc, rd_stream stream, rd_
     if (desc->precision != RD_MIXED && desc->precision != RD_FP64)
         return fail(RD_ERR_ARG, "bad precision %d", desc->precision);
     if (desc->mem != RD_MEM_DEVICE && desc->mem != RD_MEM_HOST) return fail(RD_ERR_ARG, "bad desc->mem");
-    if (desc->flags & ~(RD_NEAR | RD_FAR | RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV))
-        return fail(RD_ERR_ARG, "bad flags %d", desc->flags);
-    if ((desc->flags & RD_LINEAR) && (desc->flags & RD_HOLD_PREV))
-        return fail(RD_ERR_ARG, "RD_LINEAR and RD_HOLD_PREV are alternatives");
-    if ((desc->flags & (RD_NEAR | RD_FAR)) == 0 && desc->flags != 0)
-        return fail(RD_ERR_ARG, "flags %d select no term of Eq. 1 (RD_NEAR and/or RD_FAR)", desc->flags);
-    if ((desc->flags & RD_FARFIELD) && (desc->flags & RD_NEAR))
-        return fail(RD_ERR_ARG, "RD_FARFIELD keeps only the radiation term: RD_NEAR cannot be combined with it");
+    if (const char* why = flags_error(desc->flags)) return fail(RD_ERR_ARG, "bad flags %d: %s", desc->flags, why);
     if (desc->precision == RD_MIXED && desc->n_bins > kMixedMaxBins)
         return fail(RD_ERR_ARG, "an RD_MIXED detector holds at most %d bins per cell (got %d)", kMixedMaxBins,
                     desc->n_bins);
@@ -742,7 +770,7 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
         const int ck = dets[i]->chunk_override > 0 ? std::min(dets[i]->chunk_override, S) : std::min(kDefaultChunk, S);
         items_full += (long long)ncb * trajs[i].n_part * ((S + ck - 1) / ck);
     }
-    const bool full_chunks = items_full >= 152LL * 8;
+    const bool full_chunks = items_full >= 8LL * sm_count();
     for (int i = 0; i < n; ++i) {
         const rd_traj& t = trajs[i];
         const int S = t.n_samples - 1;

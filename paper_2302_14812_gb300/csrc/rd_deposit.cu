@@ -427,13 +427,7 @@ __global__ void k_read(const Tin* __restrict__ fields, long long n, Tout* __rest
 // =============================================================================================
 // launchers
 // =============================================================================================
-static int grid_for(long long n, int threads)
-{
-    long long g = (n + threads - 1) / threads;
-    if (g > 152LL * 16) g = 152LL * 16;
-    if (g < 1) g = 1;
-    return (int)g;
-}
+static int grid_for(long long n, int threads) { return grid_stride_blocks(n, threads, 16); }
 
 cudaError_t launch_precompute_mixed(const double* x, const double* u, const double* q, double qscale, int n_part,
                                     int n_samples, double dt, int flags, RecS* rec, DevCounters* counters,

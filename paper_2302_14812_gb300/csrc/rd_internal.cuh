@@ -113,6 +113,17 @@ constexpr int kTileSteps = RD_TILE_STEPS;   // intervals per shared-memory tile
 constexpr int kDefaultChunk = 4096;    // intervals per work item (one FP64 anchor at each end)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // give up a wait after 2 s
 
+// host helpers (rd_api.cu)
+int sm_count();    // multiprocessors of the current device (queried once per device)
+// CTAs of a grid-stride kernel over n items: enough for n at `threads` per CTA, at most per_sm
+// CTAs per multiprocessor of the current device, at least one
+int grid_stride_blocks(long long n, int threads, int per_sm);
+// Default intervals per work item of the deposit kernels: kDefaultChunk (at most S), halved while
+// the grid (cell blocks x particles x chunks) would hold fewer than 8 CTAs per multiprocessor.
+int auto_chunk(long long n_cell_blocks, long long n_part, int S);
+// Check of a detector's `flags` (include/rd.h): null if valid, else the reason.
+const char* flags_error(int flags);
+
 // launchers (rd_deposit.cu)
 // qscale != 0: deposit records, betadot and gamma^-2 terms multiplied by -q_p * qscale (q null:
 // unit charges); qscale == 0: plain records (adjoint).

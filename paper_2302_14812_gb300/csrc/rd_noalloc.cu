@@ -57,12 +57,17 @@ rd_status scratch_address(unsigned char** out)
     return RD_OK;
 }
 
-// cell table (x, y, z, T0 = t_min + pix_t0) from the caller's arrays
+// cell table (x, y, z, T0 = t_min + pix_t0) from the caller's arrays; a cell with a non-finite
+// position or time origin latches ERRBIT_INPUT (the call's deposits are then undefined)
 __global__ void k_cell_table(const double* __restrict__ pos, const double* __restrict__ t0, int n, double t_min,
-                             D4* __restrict__ cells)
+                             D4* __restrict__ cells, DevCounters* counters)
 {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-        cells[j] = D4{pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], t_min + (t0 ? t0[j] : 0.0)};
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const D4 c{pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], t_min + (t0 ? t0[j] : 0.0)};
+        if (!isfinite(c.x) || !isfinite(c.y) || !isfinite(c.z) || !isfinite(c.w))
+            atomicOr(&counters->errors, ERRBIT_INPUT);
+        cells[j] = c;
+    }
 }
 
 }  // namespace
@@ -82,11 +87,7 @@ extern "C" rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix
         return set_last_error(RD_ERR_ARG, "rd_deposit_noalloc: n_pix exceeds its maximum of 262144 cells");
     if (!(dt_det > 0.0) || !isfinite(dt_det) || !isfinite(t_min))
         return set_last_error(RD_ERR_ARG, "dt_det must be finite and > 0, t_min finite");
-    if (flags & ~(RD_NEAR | RD_FAR | RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV))
-        return set_last_error(RD_ERR_ARG, "bad flags");
-    if ((flags & RD_LINEAR) && (flags & RD_HOLD_PREV)) return set_last_error(RD_ERR_ARG, "bad flags");
-    if ((flags & RD_FARFIELD) && (flags & RD_NEAR))
-        return set_last_error(RD_ERR_ARG, "RD_FARFIELD cannot be combined with RD_NEAR");
+    if (const char* why = flags_error(flags)) return set_last_error(RD_ERR_ARG, why);
     if (t->n_part < 0 || t->n_samples < 1 || !(t->dt > 0.0) || !isfinite(t->dt) || !isfinite(t->t0))
         return set_last_error(RD_ERR_ARG, "bad trajectory shape or time axis");
     if (t->mem != RD_MEM_DEVICE) return set_last_error(RD_ERR_ARG, "rd_deposit_noalloc needs device trajectories");
@@ -107,16 +108,14 @@ extern "C" rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix
     // the array keeps the previous call's contents: counters must start at zero
     cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(DevCounters), s);
     if (e == cudaSuccess) {
-        k_cell_table<<<(n_pix + 255) / 256, 256, 0, s>>>(pix_pos, pix_t0, n_pix, t_min, cells);
+        k_cell_table<<<(n_pix + 255) / 256, 256, 0, s>>>(pix_pos, pix_t0, n_pix, t_min, cells, counters);
         e = cudaGetLastError();
     }
     const int S = t->n_samples - 1;
     if (e == cudaSuccess && t->n_part > 0 && S >= 1) {
         const int pc = (int)std::max<size_t>(1, std::min<size_t>((size_t)t->n_part, kRecordBytes / per_part));
         const int n_cell_blocks = (n_pix + kMixedCellsPerCta - 1) / kMixedCellsPerCta;
-        int chunk = std::min(kDefaultChunk, S);
-        while (chunk > 64 && (long long)n_cell_blocks * std::min(pc, t->n_part) * ((S + chunk - 1) / chunk) < 152LL * 8)
-            chunk /= 2;
+        const int chunk = auto_chunk(n_cell_blocks, std::min(pc, t->n_part), S);
         for (int p0 = 0; p0 < t->n_part && e == cudaSuccess; p0 += pc) {
             const int np = std::min(pc, t->n_part - p0);
             const size_t off = (size_t)p0 * t->n_samples * 3;

@@ -200,13 +200,7 @@ __global__ void __launch_bounds__(256) k_spectrum_fused(const T* __restrict__ fi
     }
 }
 
-int grid_for(long long n, int threads)
-{
-    long long g = (n + threads - 1) / threads;
-    if (g > 152LL * 32) g = 152LL * 32;
-    if (g < 1) g = 1;
-    return (int)g;
-}
+int grid_for(long long n, int threads) { return grid_stride_blocks(n, threads, 32); }
 
 }  // namespace
 

@@ -116,3 +116,13 @@ def test_argument_errors_without_gpu():
     assert lib.rd_deposit_noalloc(ctypes.cast(cells, ctypes.c_void_p), None, 1, 0.0, 0.1, 8, 0, ctypes.byref(t),
                                   16, None, None) == rd.RD_ERR_ARG
     assert "device trajectories" in rd.rd_last_error()
+    # rd_deposit_noalloc checks flags as rd_create_detector does: a set that selects no term of
+    # Eq. 1 (the far-field limit or an interpolation variant alone) is refused before any CUDA call
+    t.mem = rd.RD_MEM_DEVICE
+    t.n_samples = 10
+    for flags in (rd.RD_FARFIELD, rd.RD_LINEAR, rd.RD_HOLD_PREV, rd.RD_NEAR | rd.RD_FARFIELD, rd.RD_NEAR | 32,
+                  rd.RD_NEAR | rd.RD_LINEAR | rd.RD_HOLD_PREV):
+        assert lib.rd_deposit_noalloc(ctypes.cast(cells, ctypes.c_void_p), None, 1, 0.0, 0.1, 8, flags,
+                                      ctypes.byref(t), 16, None, None) == rd.RD_ERR_ARG, flags
+    assert "Eq. 1" in (lib.rd_deposit_noalloc(ctypes.cast(cells, ctypes.c_void_p), None, 1, 0.0, 0.1, 8,
+                                              rd.RD_LINEAR, ctypes.byref(t), 16, None, None) and rd.rd_last_error())

@@ -19,6 +19,7 @@ import pytest
 import oracle
 import paper_2302_14812_gb300 as rd
 from paper_2302_14812_gb300 import workloads as W
+from parity import parity_err
 
 pytestmark = pytest.mark.gpu
 
@@ -59,10 +60,6 @@ def oracle_vjp(tr, det, gE, gB, coords, sel=None, threads=None):
     return np.array(out)
 
 
-def rel_l2(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 @pytest.mark.parametrize("seed", [1, 2])
 def test_adjoint_all_coordinates_small(seed, precision):
@@ -77,7 +74,7 @@ def test_adjoint_all_coordinates_small(seed, precision):
     coords_u = [("u", p, k, c) for p in range(tr.n_part) for k in range(tr.n_samples) for c in range(3)]
     ox = oracle_vjp(tr, det, gE, gB, coords_x, threads=4)
     ou = oracle_vjp(tr, det, gE, gB, coords_u, threads=4)
-    ex, eu = rel_l2(gx.reshape(-1), ox), rel_l2(gu.reshape(-1), ou)
+    ex, eu = parity_err(gx.reshape(-1), ox), parity_err(gu.reshape(-1), ou)
     assert ex <= TOL_ADJ[precision] and eu <= TOL_ADJ[precision], (ex, eu)
 
 
@@ -96,7 +93,7 @@ def test_adjoint_clipped_window_and_cell_origins(precision):
     ox = oracle_vjp(tr, det, gE, None, coords_x, threads=4)
     ou = oracle_vjp(tr, det, gE, None, coords_u, threads=4)
     tol = TOL_ADJ[precision]
-    assert rel_l2(gx.reshape(-1), ox) <= tol and rel_l2(gu.reshape(-1), ou) <= tol
+    assert parity_err(gx.reshape(-1), ox) <= tol and parity_err(gu.reshape(-1), ou) <= tol
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
@@ -122,7 +119,7 @@ def test_adjoint_cells_missing_the_window(precision):
     ref = oracle_vjp(tr, det, g, None, coords, threads=4)
     got = np.array([(gx if w == "x" else gu)[p, k, c] for (w, p, k, c) in coords])
     assert np.any(ref != 0.0)
-    assert rel_l2(got, ref) <= TOL_ADJ[precision]
+    assert parity_err(got, ref) <= TOL_ADJ[precision]
 
 
 def _adjoint_config(n_part=10_000):
@@ -153,7 +150,7 @@ def test_adjoint_full_size_sampled_coordinates():
         coords.append((["x", "u"][len(coords) % 2], p, k, int(rng.integers(0, 3))))
     want = oracle_vjp(tr, det, gE, None, coords)
     got = np.array([(gx if w == "x" else gu)[p, k, c] for (w, p, k, c) in coords])
-    assert rel_l2(got, want) <= TOL, (got, want)
+    assert parity_err(got, want) <= TOL, (got, want)
 
 
 def _crosses_bin_edge(tr, det, p, k, c, h):
@@ -184,7 +181,7 @@ def test_mixed_adjoint_against_fp64_adjoint_every_coordinate():
     gxm, gum = gpu_adjoint(tr, det, gE, None, "mixed")
     gx64, gu64 = gpu_adjoint(tr, det, gE, None, "fp64")
     for a, b in ((gxm, gx64), (gum, gu64)):
-        assert rel_l2(a.reshape(-1), b.reshape(-1)) <= 5e-5
+        assert parity_err(a.reshape(-1), b.reshape(-1)) <= 5e-5
         assert np.max(np.abs(a - b)) <= 1e-3 * np.sqrt(np.mean(b * b))
 
 

@@ -10,6 +10,7 @@ import pytest
 import oracle
 import paper_2302_14812_gb300 as rd
 from paper_2302_14812_gb300 import workloads as W
+from parity import parity_err
 
 pytestmark = pytest.mark.gpu
 
@@ -21,10 +22,6 @@ def _cuda():
         pytest.skip("no CUDA device")
     rd.load_library()
     oracle.build()
-
-
-def rel_l2(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def _dev(tr):
@@ -98,13 +95,13 @@ def test_batch_equals_separate_and_oracle(side_stream):
     res = run_batch(probs, stream, repeats=2)
     for rep in res:
         for (E, B), (Es, Bs) in zip(rep, sep):
-            assert rel_l2(E, Es) <= 2e-6 and rel_l2(B, Bs) <= 2e-6
+            assert parity_err(E, Es) <= 2e-6 and parity_err(B, Bs) <= 2e-6
     # oracle on sampled cells of every problem
     rng = np.random.default_rng(0)
     for (tr, det), (E, B) in zip(probs, res[0]):
         sel = np.sort(rng.choice(det.n_pix, size=min(4, det.n_pix), replace=False)).astype(np.int32)
         Eo, Bo, _ = oracle.deposit(tr, det, sel)
-        assert rel_l2(E[sel], Eo) <= 1e-4 and rel_l2(B[sel], Bo) <= 1e-4
+        assert parity_err(E[sel], Eo) <= 1e-4 and parity_err(B[sel], Bo) <= 1e-4
 
 
 def test_batch_with_empty_problem_and_accumulation():
@@ -124,7 +121,7 @@ def test_batch_with_empty_problem_and_accumulation():
         twice = [d.read(stream=stream) for d in dets]
     del keep, keep2
     for (E1, _), (E2, _) in zip(once[:3], twice[:3]):
-        assert rel_l2(E2, 2 * E1) <= 2e-6
+        assert parity_err(E2, 2 * E1) <= 2e-6
     assert np.all(once[3][0] == 0)
     for d in dets:
         d.close()
@@ -141,7 +138,7 @@ def test_autotune_picks_a_chunk_and_result_stays_correct():
     E, B = d.read()
     sel = np.array([0, 100, 255], dtype=np.int32)
     Eo, Bo, _ = oracle.deposit(tr, det, sel)
-    assert rel_l2(E[sel], Eo) <= 1e-4
+    assert parity_err(E[sel], Eo) <= 1e-4
     d.close()
 
 
@@ -173,7 +170,7 @@ def test_uneven_64_problem_set_reduced_particles():
         if i % 8 == 0:
             sel = np.array([det.n_pix // 2], dtype=np.int32)
             Eo, _, _ = oracle.deposit(tr, det, sel)
-            assert rel_l2(Eb[sel].double().cpu().numpy(), Eo) <= 1e-4
+            assert parity_err(Eb[sel].double().cpu().numpy(), Eo) <= 1e-4
         s.close()
         del Eb, Bb, Es, Bs
     del keep
@@ -199,8 +196,8 @@ def test_batch_record_budget_splits_into_groups():
         twice = [d.read(stream=stream) for d in dets]
     del keep, keep2
     for (E, B), (E2, B2), (Es, Bs) in zip(once, twice, sep):
-        assert rel_l2(E, Es) <= 2e-6 and rel_l2(B, Bs) <= 2e-6
-        assert rel_l2(E2, 2 * Es) <= 2e-6 and rel_l2(B2, 2 * Bs) <= 2e-6
+        assert parity_err(E, Es) <= 2e-6 and parity_err(B, Bs) <= 2e-6
+        assert parity_err(E2, 2 * Es) <= 2e-6 and parity_err(B2, 2 * Bs) <= 2e-6
     dets[0].set_batch_budget(0)                                   # back to the default: one group
     for d in dets:
         d.zero(stream)
@@ -209,7 +206,7 @@ def test_batch_record_budget_splits_into_groups():
         again = [d.read(stream=stream) for d in dets]
     del keep
     for (E, B), (Es, Bs) in zip(again, sep):
-        assert rel_l2(E, Es) <= 2e-6 and rel_l2(B, Bs) <= 2e-6
+        assert parity_err(E, Es) <= 2e-6 and parity_err(B, Bs) <= 2e-6
     for d in dets:
         d.close()
 
@@ -224,4 +221,4 @@ def test_batch_mixes_modes():
     sep = run_separate(probs)
     res = run_batch(probs, torch.cuda.Stream())
     for (E, B), (Es, Bs) in zip(res[0], sep):
-        assert rel_l2(E, Es) <= 2e-6 and rel_l2(B, Bs) <= 2e-6
+        assert parity_err(E, Es) <= 2e-6 and parity_err(B, Bs) <= 2e-6

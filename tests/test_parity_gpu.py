@@ -13,6 +13,7 @@ import pytest
 import oracle
 import paper_2302_14812_gb300 as rd
 from paper_2302_14812_gb300 import workloads as W
+from parity import parity_err
 
 pytestmark = pytest.mark.gpu
 
@@ -26,11 +27,6 @@ def _cuda():
         pytest.skip("no CUDA device")
     rd.load_library()
     oracle.build()
-
-
-def rel_l2(a, b):
-    nb = float(np.linalg.norm(b))
-    return float(np.linalg.norm(a - b)) / (nb if nb > 0 else 1.0)
 
 
 def gpu_run(tr, det, precision, where="device", calls=None):
@@ -57,7 +53,7 @@ def check(tr, det, precision, sel=None, where="device", Eo=None, Bo=None, clip_e
         clipped = None
     if sel is not None:
         E, B = E[sel], B[sel]
-    eE, eB = rel_l2(E, Eo), rel_l2(B, Bo)
+    eE, eB = parity_err(E, Eo), parity_err(B, Bo)
     assert np.abs(Eo).max() > 0
     assert eE <= TOL[precision] and eB <= TOL[precision], (precision, eE, eB)
     if clip_exact is None:
@@ -179,11 +175,11 @@ def test_high_gamma_against_extended_precision(gamma):
     for precision in ("fp64", "mixed"):
         E, B, _ = gpu_run(tr, det, precision)
         got[precision] = (E[sel], B[sel])
-        assert rel_l2(E[sel], Ee) <= 1e-4 and rel_l2(B[sel], Be) <= 1e-4, precision
+        assert parity_err(E[sel], Ee) <= 1e-4 and parity_err(B[sel], Be) <= 1e-4, precision
     if gamma <= 300.0:
         E64, B64, _ = oracle.deposit(tr, det, sel)
         E, B = got["fp64"]
-        assert rel_l2(E, E64) <= TOL["fp64"] and rel_l2(B, B64) <= TOL["fp64"]
+        assert parity_err(E, E64) <= TOL["fp64"] and parity_err(B, B64) <= TOL["fp64"]
 
 
 # --------------------------------------------------------------------------------------------
@@ -205,7 +201,7 @@ def test_step_chunks_and_particle_chunks_accumulate(precision):
     Eo, Bo, _ = oracle.deposit(tr, det)
     parts = [tr.subset([0, 1]).steps(0, 77), tr.subset([0, 1]).steps(77, 200), tr.subset([2, 3])]
     E, B, _ = gpu_run(tr, det, precision, calls=parts)
-    assert rel_l2(E, Eo) <= TOL[precision] and rel_l2(B, Bo) <= TOL[precision]
+    assert parity_err(E, Eo) <= TOL[precision] and parity_err(B, Bo) <= TOL[precision]
 
 
 def test_empty_and_degenerate_inputs():
@@ -222,7 +218,7 @@ def test_empty_and_degenerate_inputs():
         d.deposit(torch.from_numpy(tr.x).cuda(), torch.from_numpy(tr.u).cuda(), None, tr.t0, tr.dt)
         E, B = d.read()
         Eo, Bo, _ = oracle.deposit(W.Trajectories(tr.x, tr.u, np.ones(1), tr.t0, tr.dt), det)
-        assert rel_l2(E, Eo) <= TOL[precision]
+        assert parity_err(E, Eo) <= TOL[precision]
         d.zero()
         E, _ = d.read()
         assert np.all(E == 0)
@@ -256,7 +252,7 @@ def test_mixed_maximum_bins_per_cell():
     d.close()
     Eo, Bo, _ = oracle.deposit(tr, det, sel)
     assert np.any(Eo[:, -1] != 0.0)                   # odd cells reach the last bin
-    assert rel_l2(Eg, Eo) <= TOL["mixed"] and rel_l2(Bg, Bo) <= TOL["mixed"]
+    assert parity_err(Eg, Eo) <= TOL["mixed"] and parity_err(Bg, Bo) <= TOL["mixed"]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -406,16 +402,16 @@ def test_hold_previous_streamed_and_batched():
         if k >= tr.n_samples:
             break
     E, B = d.read()
-    assert rel_l2(E, Er) <= 2e-6 and rel_l2(B, Br) <= 2e-6
+    assert parity_err(E, Er) <= 2e-6 and parity_err(B, Br) <= 2e-6
     d.close()
     det_held = W.Detector(det.pix_pos, det.pix_t0, det.t_min, det.dt_det, det.n_bins, W.RD_NEAR | W.RD_FAR)
     dets = [rd.RadiationDetector.from_workload(det, "mixed"), rd.RadiationDetector.from_workload(det_held, "mixed")]
     keep = rd.deposit_batch(dets, [(xd, ud, qd, tr.t0, tr.dt)] * 2)
     E0, B0 = dets[0].read()
-    assert rel_l2(E0, Er) <= 2e-6 and rel_l2(B0, Br) <= 2e-6
+    assert parity_err(E0, Er) <= 2e-6 and parity_err(B0, Br) <= 2e-6
     Eh, _, _ = oracle.deposit(tr, det_held, np.array([0, 5], dtype=np.int32))
     E1, _ = dets[1].read()
-    assert rel_l2(E1[[0, 5]], Eh) <= 1e-4
+    assert parity_err(E1[[0, 5]], Eh) <= 1e-4
     for dd in dets:
         dd.close()
     ref.close()
@@ -441,7 +437,7 @@ def test_linear_interpolation_chunks_and_particle_splits():
                       torch.from_numpy(one.q).cuda(), one.t0, one.dt)
         E, B = d.read()
         d.close()
-        assert rel_l2(E, Ef) <= 2e-6 and rel_l2(B, Bf) <= 2e-6
+        assert parity_err(E, Ef) <= 2e-6 and parity_err(B, Bf) <= 2e-6
 
 
 def test_measure_fma_peaks_plausible():

@@ -13,6 +13,7 @@ import pytest
 import oracle
 import paper_2302_14812_gb300 as rd
 from paper_2302_14812_gb300 import workloads as W
+from parity import parity_err
 
 pytestmark = pytest.mark.gpu
 
@@ -24,10 +25,6 @@ def _cuda():
         pytest.skip("no CUDA device")
     rd.load_library()
     oracle.build()
-
-
-def rel_l2(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def numpy_power(F, dt_det):
@@ -51,7 +48,7 @@ def test_power_spectrum_equals_fft_of_fields(precision):
     for field, F in (("E", E), ("B", B)):
         P = d.power_spectrum(field).cpu().numpy()
         assert P.shape == (det.n_pix, det.n_bins // 2 + 1)
-        assert rel_l2(P, numpy_power(F, det.dt_det)) <= 1e-5
+        assert parity_err(P, numpy_power(F, det.dt_det)) <= 1e-5
     d.close()
 
 
@@ -74,7 +71,7 @@ def test_power_spectrum_lengths(n_bins, precision):
     for field, F in (("E", E), ("B", B)):
         P = d.power_spectrum(field).cpu().numpy()
         assert P.shape == (det.n_pix, n_bins // 2 + 1)
-        assert rel_l2(P, numpy_power(F, det.dt_det)) <= 1e-5
+        assert parity_err(P, numpy_power(F, det.dt_det)) <= 1e-5
     d.close()
 
 
@@ -105,7 +102,7 @@ def test_section4_benchmark_full_size_spectra():
     d.close()
     sel = np.linspace(0, 511, 8).astype(np.int32)
     Eo, _, _ = oracle.deposit(tr, det, sel)
-    assert rel_l2(P[sel], numpy_power(Eo, det.dt_det)) <= 1e-4
+    assert parity_err(P[sel], numpy_power(Eo, det.dt_det)) <= 1e-4
 
     _, wb = W.undulator_params(gam, K, 2.0 * math.pi / 0.1)
     wc = 1.5 * K * gam ** 2 * wb

@@ -13,6 +13,7 @@ import pytest
 import oracle
 import paper_2302_14812_gb300 as rd
 from paper_2302_14812_gb300 import workloads as W
+from parity import parity_err
 
 pytestmark = pytest.mark.gpu
 
@@ -24,10 +25,6 @@ def _cuda():
         pytest.skip("no CUDA device")
     rd.load_library()
     oracle.build()
-
-
-def rel_l2(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def _case():
@@ -75,11 +72,11 @@ def test_stream_equals_single_call(precision, tol, where, linear):
             x, u, q = torch.from_numpy(x).cuda(), torch.from_numpy(u).cuda(), torch.from_numpy(q).cuda()
         d.deposit_stream(x, u, q, tr.t0 + a * tr.dt, tr.dt)
     E, B = d.read()
-    assert rel_l2(E, Er) <= tol and rel_l2(B, Br) <= tol
+    assert parity_err(E, Er) <= tol and parity_err(B, Br) <= tol
     if precision == "mixed":
         sel = np.array([0, 77, 150, 299], dtype=np.int32)
         Eo, Bo, _ = oracle.deposit(tr, det, sel)
-        assert rel_l2(E[sel], Eo) <= 1e-4 and rel_l2(B[sel], Bo) <= 1e-4
+        assert parity_err(E[sel], Eo) <= 1e-4 and parity_err(B[sel], Bo) <= 1e-4
     d.close()
 
 
@@ -105,7 +102,7 @@ def test_stream_continuity_checks_and_reset():
     one = rd.RadiationDetector.from_workload(det, "mixed")
     one.deposit(x[:3, 40:60].contiguous(), u[:3, 40:60].contiguous(), None, tr.t0 + 40 * tr.dt, tr.dt)
     E3, _ = one.read()
-    assert rel_l2(E2, E3) <= 2e-6 and np.abs(E1).max() > 0
+    assert parity_err(E2, E3) <= 2e-6 and np.abs(E1).max() > 0
     one.close()
     d.close()
 
@@ -169,4 +166,4 @@ def test_runtime_coupling_push_then_deposit(precision, tol):
     d.close()
     Eo, Bo, clipped = oracle.deposit(tr, det)
     assert clipped == 0
-    assert rel_l2(E, Eo) <= tol and rel_l2(B_, Bo) <= tol
+    assert parity_err(E, Eo) <= tol and parity_err(B_, Bo) <= tol
