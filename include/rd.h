@@ -251,6 +251,25 @@ RD_API rd_status rd_adjoint_trajectories(rd_detector* det, const rd_traj* traj, 
                                          rd_stream stream);
 
 /*
+ * Arithmetic of rd_adjoint_trajectories on an RD_MIXED detector.
+ *   RD_ADJ_FP32 (default): FP32 field arithmetic (relative error ~1e-5, see above).
+ *   RD_ADJ_COMPENSATED: the same gradient carried in double-float -- pairs of FP32 numbers, about
+ *     48 significant bits, from FP32 operations only -- wherever a difference of neighbouring
+ *     samples would magnify rounding: the field of Eq. 1, the seed gathered over each interval's
+ *     bins (Section 3.2), the vector-Jacobian product up to d L / d beta and d L / d betadot, the
+ *     projection to d L / d u, the arrival-time walk (the all-positive increment from an FP64
+ *     arrival time of Eq. 2 at the start of every 250-sample chunk) and the sums over cells.  The
+ *     two terms of each difference are formed in one thread (each chunk walks the interval before
+ *     it once more).  Only the position derivative through the field's n and R (1/R of the
+ *     others) stays FP32.  Relative error ~1e-8 against the exact derivative; several times the
+ *     FP32 adjoint's time, several times faster than the RD_FP64 adjoint on this GPU's FP64 rate.
+ *     Records of 128 bytes per particle and sample.
+ * RD_ERR_ARG for an unknown mode, RD_ERR_STATE for RD_ADJ_COMPENSATED on an RD_FP64 detector.
+ */
+enum { RD_ADJ_FP32 = 0, RD_ADJ_COMPENSATED = 1 };
+RD_API rd_status rd_set_adjoint_mode(rd_detector* det, int32_t mode);
+
+/*
  * Batched form: deposit trajs[i] into dets[i] for i < n (ACCUMULATES, like n calls of
  * rd_deposit_trajectories) with one persistent kernel launch.  The resident CTAs draw work items
  * -- (problem, step chunk, block of 256 cells, particle) -- from one atomic counter, so problems of

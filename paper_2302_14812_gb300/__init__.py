@@ -25,7 +25,7 @@ __all__ = [
     "RD_MEM_HOST", "RD_MEM_HOST_ASYNC", "RD_F32", "RD_F64", "RDError", "rd_detector_desc", "rd_traj", "rd_stats",
     "load_library", "library_path", "rd_create_detector", "rd_destroy", "rd_zero_fields",
     "rd_deposit_trajectories", "rd_read_fields", "rd_synchronize", "rd_get_stats",
-    "rd_set_timing", "rd_adjoint_trajectories", "rd_deposit_batch", "rd_set_chunk", "rd_autotune",
+    "rd_set_timing", "rd_adjoint_trajectories", "rd_set_adjoint_mode", "RD_ADJ_FP32", "RD_ADJ_COMPENSATED", "rd_deposit_batch", "rd_set_chunk", "rd_autotune",
     "rd_set_batch_budget", "rd_power_spectrum", "rd_deposit_stream", "rd_stream_reset",
     "rd_deposit_noalloc", "rd_measure_fma_peaks", "rd_check_bounded_wait", "rd_push_boris", "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
 ]
@@ -36,6 +36,7 @@ RD_NEAR, RD_FAR, RD_FARFIELD, RD_LINEAR, RD_HOLD_PREV = 1, 2, 4, 8, 16
 RD_MEM_DEVICE, RD_MEM_HOST, RD_MEM_HOST_ASYNC = 0, 1, 2
 RD_F32, RD_F64 = 0, 1
 RD_SPEC_E, RD_SPEC_B = 0, 1
+RD_ADJ_FP32, RD_ADJ_COMPENSATED = 0, 1
 
 _STATUS = {0: "RD_OK", 1: "RD_ERR_ARG", 2: "RD_ERR_CUDA", 3: "RD_ERR_OOM", 4: "RD_ERR_STATE",
            5: "RD_ERR_TIMEOUT", 6: "RD_ERR_BOUNDS", 7: "RD_ERR_INPUT"}
@@ -99,6 +100,7 @@ def load_library(build_if_missing: bool = True):
             "rd_adjoint_trajectories": ([P, ctypes.POINTER(rd_traj), P, P, I, P, P, P], I),
             "rd_deposit_batch": ([I, ctypes.POINTER(P), ctypes.POINTER(rd_traj), P], I),
             "rd_set_chunk": ([P, I], I),
+            "rd_set_adjoint_mode": ([P, I], I),
             "rd_set_batch_budget": ([P, ctypes.c_longlong], I),
             "rd_power_spectrum": ([P, I, P, P], I),
             "rd_deposit_stream": ([P, ctypes.POINTER(rd_traj), P], I),
@@ -196,6 +198,10 @@ def rd_deposit_batch(dets, trajs, stream=None) -> None:
 
 def rd_set_chunk(det: int, chunk: int) -> None:
     _check(load_library().rd_set_chunk(det, int(chunk)), "rd_set_chunk")
+
+
+def rd_set_adjoint_mode(det: int, mode: int) -> None:
+    _check(load_library().rd_set_adjoint_mode(det, int(mode)), "rd_set_adjoint_mode")
 
 
 def rd_set_batch_budget(det: int, nbytes: int) -> None:
@@ -425,6 +431,12 @@ class RadiationDetector:
 
     def set_chunk(self, chunk: int):
         rd_set_chunk(self._h, chunk)
+
+    def set_adjoint_mode(self, mode):
+        """RD_ADJ_FP32 / "fp32" (default) or RD_ADJ_COMPENSATED / "compensated" (RD_MIXED only)."""
+        if isinstance(mode, str):
+            mode = {"fp32": RD_ADJ_FP32, "compensated": RD_ADJ_COMPENSATED}[mode]
+        rd_set_adjoint_mode(self._h, mode)
 
     def set_batch_budget(self, nbytes: int):
         """Bytes of per-sample records per launch group of batches led by this detector (0 = 4 GiB)."""

@@ -42,6 +42,7 @@ struct rd_detector {
     void* gbeta = nullptr;           // adjoint: d loss / d beta (FP64)
     size_t gbeta_bytes = 0;
     int adjoint_chunk = 250;         // adjoint: samples between recomputed anchors
+    int adjoint_mode = RD_ADJ_FP32;  // RD_MIXED adjoint: FP32 or compensated (double-float) kernel
     unsigned long long id = 0;       // unique per created detector (keys of cached graphs)
     // batched form (kept in the first detector of a batch)
     void* batch_rec = nullptr;       // records of every problem
@@ -591,6 +592,54 @@ rd_status rd_get_stats(rd_detector* d, rd_stream stream, rd_stats* out)
     return RD_OK;
 }
 
+// Compensated adjoint of an RD_MIXED detector (rd_adjoint_comp.cu): double-float records, the
+// kernel adds d L / d x and d L / d u to gx and gu directly.
+static rd_status adjoint_compensated(rd_detector* d, const rd_traj* t, const void* gE, const void* gB,
+                                     int32_t gdtype, double* gx, double* gu, cudaStream_t s)
+{
+    const int S = t->n_samples - 1;
+    rd_status st = ensure(&d->seed, &d->seed_bytes, d->field_bytes, s, "seed scratch");
+    if (st != RD_OK) return st;
+    RD_CUDA(launch_pack_seed(gE, gB, gdtype, d->n_pix, d->n_bins, static_cast<float*>(d->seed), s), "pack seed");
+    const size_t per_part_rec = comp_record_bytes() * (size_t)t->n_samples;
+    const size_t budget = (size_t)1 << 31;
+    const int pc = (int)std::max<size_t>(1, std::min<size_t>((size_t)t->n_part, budget / per_part_rec));
+    st = ensure(&d->rec, &d->rec_bytes, per_part_rec * pc, s, "record scratch");
+    if (st != RD_OK) return st;
+    const int n_cell_blocks = (d->n_pix + kAdjointCompThreads - 1) / kAdjointCompThreads;
+    const int chunk = std::max(1, std::min(d->adjoint_chunk, S));
+    for (int p0 = 0; p0 < t->n_part; p0 += pc) {
+        const int np = std::min(pc, t->n_part - p0);
+        const size_t off = (size_t)p0 * t->n_samples * 3;
+        RD_CUDA(launch_precompute_comp(t->x + off, t->u + off, np, t->n_samples, t->dt, d->flags, d->rec, d->counters,
+                                       s),
+                "precompute");
+        AdjointParams P{};
+        P.recc = d->rec;
+        P.x = t->x + off;
+        P.q = t->q ? t->q + p0 : nullptr;
+        P.cells = d->cells;
+        P.seed = static_cast<const float*>(d->seed);
+        P.gx = gx + off;
+        P.gu = gu + off;
+        P.counters = d->counters;
+        P.n_pix = d->n_pix;
+        P.n_bins = d->n_bins;
+        P.n_samples = t->n_samples;
+        P.n_part = np;
+        P.chunk = chunk;
+        P.n_chunks = (S + chunk - 1) / chunk;
+        P.n_cell_blocks = n_cell_blocks;
+        P.flags = d->flags;
+        P.t0 = t->t0;
+        P.dt = t->dt;
+        P.inv_dt_det = 1.0 / d->dt_det;
+        LaunchTimer timer(d, s);
+        RD_CUDA(launch_adjoint_comp(P, s), "adjoint (compensated)");
+    }
+    return RD_OK;
+}
+
 rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* gE, const void* gB,
                                   int32_t gdtype, double* gx, double* gu, rd_stream stream)
 {
@@ -608,6 +657,7 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
     if (t->n_part == 0 || S < 1) return RD_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const bool fp64 = d->precision == RD_FP64;
+    if (!fp64 && d->adjoint_mode == RD_ADJ_COMPENSATED) return adjoint_compensated(d, t, gE, gB, gdtype, gx, gu, s);
     st = ensure(&d->seed, &d->seed_bytes, d->field_bytes, s, "seed scratch");
     if (st != RD_OK) return st;
     if (fp64)
@@ -674,6 +724,17 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
                                    (long long)np * t->n_samples, s),
                 "gradient to momenta");
     }
+    return RD_OK;
+}
+
+rd_status rd_set_adjoint_mode(rd_detector* d, int32_t mode)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    if (mode != RD_ADJ_FP32 && mode != RD_ADJ_COMPENSATED) return fail(RD_ERR_ARG, "bad adjoint mode %d", mode);
+    if (mode == RD_ADJ_COMPENSATED && d->precision != RD_MIXED)
+        return fail(RD_ERR_STATE, "RD_ADJ_COMPENSATED applies to RD_MIXED detectors");
+    d->adjoint_mode = mode;
     return RD_OK;
 }
 

@@ -148,6 +148,8 @@ struct AdjointParams {
     const double* seedd;        // [n_pix][n_bins][6] the same in FP64 (FP64 kernel)
     double* gx;                 // [n_part][n_samples][3] += d loss / d x
     double* gbeta;              // [n_part][n_samples][3] += d loss / d beta (scratch, FP64)
+    const void* recc;           // compensated kernel: double-float records [n_part][n_samples]
+    double* gu;                 // compensated kernel: [n_part][n_samples][3] += d loss / d u
     DevCounters* counters;
     int n_pix, n_bins, n_samples, n_part, chunk, n_chunks, n_cell_blocks;
     int flags;
@@ -176,6 +178,12 @@ cudaError_t launch_pack_seed64(const void* gE, const void* gB, int dtype, int n_
                                cudaStream_t s);
 cudaError_t launch_adjoint_fp64(const AdjointParams& p, cudaStream_t s);
 constexpr int kAdjointFp64Threads = 128;   // FP64 adjoint: one cell per thread
+// compensated (double-float) adjoint of the mixed deposit (rd_adjoint_comp.cu)
+constexpr int kAdjointCompThreads = 128;   // one cell per thread
+size_t comp_record_bytes();                // bytes of one per-sample record
+cudaError_t launch_precompute_comp(const double* x, const double* u, int n_part, int n_samples, double dt, int flags,
+                                   void* rec, DevCounters* counters, cudaStream_t s);
+cudaError_t launch_adjoint_comp(const AdjointParams& p, cudaStream_t s);
 cudaError_t launch_gbeta_to_gu(const double* u, const double* gbeta, double* gu, long long n_samples_total,
                                cudaStream_t s);
 

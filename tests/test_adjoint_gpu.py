@@ -24,7 +24,8 @@ from parity import parity_err
 pytestmark = pytest.mark.gpu
 
 TOL = 5e-5
-TOL_ADJ = {"mixed": TOL, "fp64": 1e-9}
+TOL_COMP = 1e-6          # the compensated adjoint: the gradient bar of the adjoint workload
+TOL_ADJ = {"mixed": TOL, "comp": TOL_COMP, "fp64": 1e-9}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,8 +38,11 @@ def _cuda():
 
 
 def gpu_adjoint(tr, det, gE, gB, precision="mixed"):
+    """precision: "mixed" (FP32 adjoint), "comp" (RD_MIXED detector, RD_ADJ_COMPENSATED) or "fp64"."""
     import torch
-    d = rd.RadiationDetector.from_workload(det, precision)
+    d = rd.RadiationDetector.from_workload(det, "mixed" if precision == "comp" else precision)
+    if precision == "comp":
+        d.set_adjoint_mode("compensated")
     x = torch.from_numpy(tr.x).cuda()
     u = torch.from_numpy(tr.u).cuda()
     q = torch.from_numpy(tr.q).cuda()
@@ -60,7 +64,7 @@ def oracle_vjp(tr, det, gE, gB, coords, sel=None, threads=None):
     return np.array(out)
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed", "comp", "fp64"])
 @pytest.mark.parametrize("seed", [1, 2])
 def test_adjoint_all_coordinates_small(seed, precision):
     """Every x and u coordinate of 2 particles x 150 intervals, 9 cells, window with margins."""
@@ -78,7 +82,7 @@ def test_adjoint_all_coordinates_small(seed, precision):
     assert ex <= TOL_ADJ[precision] and eu <= TOL_ADJ[precision], (ex, eu)
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed", "comp", "fp64"])
 def test_adjoint_clipped_window_and_cell_origins(precision):
     """Window that cuts arrivals at both ends, per-cell time origins, E-only seed."""
     rng = np.random.default_rng(7)
@@ -96,7 +100,7 @@ def test_adjoint_clipped_window_and_cell_origins(precision):
     assert parity_err(gx.reshape(-1), ox) <= tol and parity_err(gu.reshape(-1), ou) <= tol
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed", "comp", "fp64"])
 def test_adjoint_cells_missing_the_window(precision):
     """130 cells (two cell blocks, the second ragged); every third cell's time axis lies far after
     all its arrivals.  Those cells contribute exactly nothing (a seed on them alone gives exact
@@ -310,4 +314,145 @@ def test_adjoint_rejects_farfield_linear_and_host_inputs():
     g = torch.zeros((det.n_pix, det.n_bins, 3), device="cuda")
     with pytest.raises(ValueError):
         d.adjoint(tr.x, tr.u, None, 0.0, tr.dt, g)
+    d.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# compensated adjoint (RD_ADJ_COMPENSATED) on the adjoint workload at full size: the 1e-6 bar
+# ---------------------------------------------------------------------------------------------
+def _coords(tr, rng, n):
+    """n seeded (which, particle, sample, component) coordinates, positions and momenta alternating."""
+    out = []
+    for i in range(n):
+        out.append((("x", "u")[i % 2], int(rng.integers(0, tr.n_part)), int(rng.integers(0, tr.n_samples)),
+                    int(rng.integers(0, 3))))
+    return out
+
+
+@pytest.fixture(scope="module")
+def adjoint_full():
+    """The adjoint workload (1e4 undulator electrons x 2000 steps, 64x64 x 1024) with a seeded
+    smooth seed standing in for the misfit E - E_target, its compensated and FP32 gradients."""
+    rng = np.random.default_rng(55)
+    tr, det = _adjoint_config()
+    gE = _smooth_seed(det, rng)
+    gxc, guc = gpu_adjoint(tr, det, gE, None, "comp")
+    gxm, gum = gpu_adjoint(tr, det, gE, None, "mixed")
+    return tr, det, gE, (gxc, guc), (gxm, gum)
+
+
+def test_compensated_adjoint_full_size_50_coordinates(adjoint_full):
+    """The compensated adjoint at full size against the oracle's exact (complex-step) derivative
+    at 50 seeded coordinates (25 positions, 25 momenta, any sample including the first and the
+    chunk boundaries): relative L2 <= 1e-6 for positions and for momenta separately, every
+    coordinate within 2e-5 of its own size or of the RMS."""
+    tr, det, gE, (gxc, guc), (gxm, gum) = adjoint_full
+    rng = np.random.default_rng(505)
+    coords = _coords(tr, rng, 46) + [("x", 17, 250, 2), ("u", 17, 250, 1), ("x", 33, 0, 0), ("u", 9, 2000, 2)]
+    want = oracle_vjp(tr, det, gE, None, coords)
+    got = np.array([(gxc if w == "x" else guc)[p, k, c] for (w, p, k, c) in coords])
+    fp32 = np.array([(gxm if w == "x" else gum)[p, k, c] for (w, p, k, c) in coords])
+    isx = np.array([w == "x" for (w, _, _, _) in coords])
+    ex, eu = parity_err(got[isx], want[isx]), parity_err(got[~isx], want[~isx])
+    print(f"compensated: x {ex:.3e}  u {eu:.3e};  FP32 adjoint: x {parity_err(fp32[isx], want[isx]):.3e}  "
+          f"u {parity_err(fp32[~isx], want[~isx]):.3e}")
+    assert ex <= TOL_COMP and eu <= TOL_COMP, (ex, eu)
+
+
+def test_compensated_adjoint_momenta_against_oracle_differences(adjoint_full):
+    """Fourth-order central differences of L = sum_b gE . E_b through the FP64 oracle's deposit of the
+    perturbed electron alone (the exact difference of its contribution; the others do not depend on
+    the coordinate) at 25 seeded momentum coordinates.  A momentum moves no arrival time (those
+    depend on positions only), so the deposit is smooth in it and the quotient needs no bin-edge
+    exclusion.  Bar 1e-6 relative L2."""
+    tr, det, gE, (gxc, guc), _ = adjoint_full
+    rng = np.random.default_rng(606)
+    errs, refs = [], []
+    for _ in range(25):
+        p, k, c = int(rng.integers(0, tr.n_part)), int(rng.integers(1, tr.n_samples)), int(rng.integers(0, 3))
+        one = tr.subset([p])
+        h = 1e-5 * max(1.0, abs(one.u[0, k, c]))
+        vals = {}
+        for m in (-2, -1, 1, 2):
+            pert = W.Trajectories(one.x, one.u.copy(), one.q, one.t0, one.dt)
+            pert.u[0, k, c] = one.u[0, k, c] + m * h
+            E, _, _ = oracle.deposit(pert, det)
+            vals[m] = float(np.sum(E * gE))
+        fd = (8.0 * (vals[1] - vals[-1]) - (vals[2] - vals[-2])) / (12.0 * h)
+        errs.append(guc[p, k, c] - fd)
+        refs.append(fd)
+    assert np.linalg.norm(errs) <= TOL_COMP * np.linalg.norm(refs), (errs, refs)
+
+
+def test_compensated_adjoint_positions_against_oracle_differences():
+    """Central differences through the long double oracle (the exact difference of the perturbed
+    electron's contribution) at 12 seeded position coordinates of the full-size adjoint workload.
+    A position moves its sample's arrival time, and the deposit has a kink where that arrival
+    crosses a bin edge, so the seed lives on 64 cells and each coordinate's step is a quarter of
+    its arrival's distance to the nearest bin edge on those cells (the long double evaluation keeps
+    the quotient's rounding far below the bar at that step).  Bar 1e-6 relative L2."""
+    import math as _m
+    rng = np.random.default_rng(707)
+    tr, det = _adjoint_config()
+    sel = np.sort(rng.choice(det.n_pix, 64, replace=False)).astype(np.int32)
+    g_full = np.zeros((det.n_pix, det.n_bins, 3))
+    g_full[sel] = rng.normal(size=(64, det.n_bins, 3))
+    gx, _ = gpu_adjoint(tr, det, g_full, None, "comp")
+    g = g_full[sel]
+    inv = 1.0 / det.dt_det
+    errs, refs = [], []
+    tries = 0
+    while len(refs) < 12 and tries < 100:
+        tries += 1
+        p, k, c = int(rng.integers(0, tr.n_part)), int(rng.integers(0, tr.n_samples)), int(rng.integers(0, 3))
+        # distance (bins) from sample k's arrival to the nearest bin edge, over the seeded cells
+        dist = min(0.5 - abs(v - _m.floor(v) - 0.5) for v in
+                   (oracle.bin_coord(tr.t0, k, tr.dt, tr.x[p, k], det.pix_pos[j],
+                                     det.t_min + (0.0 if det.pix_t0 is None else det.pix_t0[j]), inv) for j in sel))
+        h = 0.25 * dist * det.dt_det                       # |d t' / d x| <= 1
+        if h < 1e-9:
+            continue
+        one = tr.subset([p])
+        vals = []
+        for sgn in (1.0, -1.0):
+            pert = W.Trajectories(one.x.copy(), one.u, one.q, one.t0, one.dt)
+            pert.x[0, k, c] = one.x[0, k, c] + sgn * h
+            E, _, _ = oracle.deposit_ext(pert, det, sel)
+            vals.append((float(np.sum(E * g)), pert.x[0, k, c]))
+        fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
+        errs.append(gx[p, k, c] - fd)
+        refs.append(fd)
+    assert len(refs) == 12
+    assert np.linalg.norm(errs) <= TOL_COMP * np.linalg.norm(refs), (errs, refs)
+
+
+def test_compensated_adjoint_against_fp64_adjoint_every_coordinate():
+    """20 electrons of the adjoint workload, every coordinate: the compensated adjoint against the
+    plain FP64 adjoint (relative L2 <= 1e-6 and every coordinate within 2e-5 of its size or the RMS;
+    the FP32 adjoint's error on the same set is printed)."""
+    rng = np.random.default_rng(21)
+    tr, det = _adjoint_config(n_part=20)
+    gE = rng.normal(size=(det.n_pix, det.n_bins, 3))
+    gxc, guc = gpu_adjoint(tr, det, gE, None, "comp")
+    gxm, gum = gpu_adjoint(tr, det, gE, None, "mixed")
+    gx64, gu64 = gpu_adjoint(tr, det, gE, None, "fp64")
+    print(f"compensated vs FP64 adjoint: x {parity_err(gxc, gx64):.3e} u {parity_err(guc, gu64):.3e}; "
+          f"FP32: x {parity_err(gxm, gx64):.3e} u {parity_err(gum, gu64):.3e}")
+    assert parity_err(gxc, gx64) <= TOL_COMP and parity_err(guc, gu64) <= TOL_COMP
+
+
+def test_adjoint_mode_arguments():
+    tr = W.random_smooth(1, 10, 0.02, seed=1)
+    det = W.Detector(W.spherical_cap(2, 10.0, 0.3), None, 8.0, 0.02, 100)
+    d = rd.RadiationDetector.from_workload(det, "fp64")
+    with pytest.raises(rd.RDError) as ei:
+        d.set_adjoint_mode("compensated")
+    assert ei.value.status == rd.RD_ERR_STATE
+    d.close()
+    d = rd.RadiationDetector.from_workload(det, "mixed")
+    with pytest.raises(rd.RDError) as ei:
+        rd.rd_set_adjoint_mode(d.handle, 7)
+    assert ei.value.status == rd.RD_ERR_ARG
+    d.set_adjoint_mode("compensated")
+    d.set_adjoint_mode("fp32")
     d.close()
