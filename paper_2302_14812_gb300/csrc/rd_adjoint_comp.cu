@@ -31,6 +31,10 @@
 #include "rd_df.cuh"
 #include "rd_internal.cuh"
 
+#ifndef RD_COMP_MINBLOCKS
+#define RD_COMP_MINBLOCKS 2      // resident CTAs per SM the register allotment must allow
+#endif
+
 namespace rd {
 
 namespace {
@@ -59,20 +63,23 @@ __device__ __forceinline__ V3 project_u(const V3& beta, df2 ig, const V3& v)
     return v_scale(v_sub(v, v_scale(beta, bv)), ig);
 }
 
-__device__ __forceinline__ void load_seed(const float* row, int n_bins, int b, float* g)
+// Seed rows in double-float: [n_bins][16] floats per cell, (hi of E xyz, B xyz, 2 unused, lo of the
+// same, 2 unused); an FP64 upstream gradient keeps ~48 of its bits (FP32 would act on the gradient as
+// a noise seed of relative size 2^-24, which the cancellation of neighbouring samples does not damp).
+__device__ __forceinline__ void load_seed(const float* row, int n_bins, int b, df2* g)
 {
     if ((unsigned)b < (unsigned)n_bins) {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(row + (size_t)b * 8));
-        const float4 c = __ldg(reinterpret_cast<const float4*>(row + (size_t)b * 8 + 4));
-        g[0] = a.x;
-        g[1] = a.y;
-        g[2] = a.z;
-        g[3] = a.w;
-        g[4] = c.x;
-        g[5] = c.y;
+        const float4* q = reinterpret_cast<const float4*>(row + (size_t)b * 16);
+        const float4 h0 = __ldg(q), h1 = __ldg(q + 1), l0 = __ldg(q + 2), l1 = __ldg(q + 3);
+        g[0] = {h0.x, l0.x};
+        g[1] = {h0.y, l0.y};
+        g[2] = {h0.z, l0.z};
+        g[3] = {h0.w, l0.w};
+        g[4] = {h1.x, l1.x};
+        g[5] = {h1.y, l1.y};
     } else {
 #pragma unroll
-        for (int i = 0; i < 6; ++i) g[i] = 0.f;
+        for (int i = 0; i < 6; ++i) g[i] = {0.f, 0.f};
     }
 }
 
@@ -95,7 +102,7 @@ struct CCell {
     int b;          // bin of the walk
     int bx;         // bin of the previous sample's arrival for its end-point terms
     df2 Rpd;        // R_{k-1} + dt
-    float g[6];     // seed of bin b (zero outside the window)
+    df2 g[6];       // seed of bin b (zero outside the window)
     const float* row;
     // previous sample k-1
     df2 Fp[6];      // field of interval k-1 (E, B); zero for sample 0
@@ -118,23 +125,24 @@ struct CompConsts {
 
 // Sample j's outputs from its two intervals' terms (j = k-1 when interval k has just been walked,
 // or the last sample S with Fk = 0 and gbdk = 0): position, momentum.
-__device__ __forceinline__ void sample_out(const CCell& c, const df2* Fk, const V3& gbdk, const float* gx_seed,
-                                           const CompConsts& K, float* out)
+// The momentum outputs stay double-float: the sum over cells can cancel far below its terms.
+__device__ __forceinline__ void sample_out(const CCell& c, const df2* Fk, const V3& gbdk, const df2* gx_seed,
+                                           const CompConsts& K, df2* out)
 {
     float dF[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) dF[i] = df_round(df_sub(Fk[i], c.Fp[i]));
     float da = 0.f;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) da = fmaf(dF[i], gx_seed[i], da);
+    for (int i = 0; i < 6; ++i) da = fmaf(dF[i], df_round(gx_seed[i]), da);
     const float a = da * K.inv_dt_det;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) out[i] = fmaf(c.np[i], a, c.gxf[i]);
+    for (int i = 0; i < 3; ++i) out[i] = df_make(fmaf(c.np[i], a, c.gxf[i]));
     const V3 gb = v_add(c.gbetp, v_scale(v_sub(c.gbdp, gbdk), K.inv_dt));
     const V3 gu = project_u(c.bp, c.igp, gb);
-    out[3] = df_round(gu.x);
-    out[4] = df_round(gu.y);
-    out[5] = df_round(gu.z);
+    out[3] = gu.x;
+    out[4] = gu.y;
+    out[5] = gu.z;
 }
 
 }  // namespace
@@ -207,7 +215,7 @@ namespace {
 // belongs to the previous chunk).  LAST: the interval ends on the chunk's FP64 end anchor.
 template <bool LAST>
 __device__ __forceinline__ void comp_step(CCell& c, const RecC& r, const AdjointParams& P, const CompConsts& K,
-                                          df2 q, int b_end, df2 f_end, bool out_on, float* out, const double* xp,
+                                          df2 q, int b_end, df2 f_end, bool out_on, df2* out, const double* xp,
                                           int cell, int k)
 {
     // ---- geometry, arrival increment ----
@@ -247,33 +255,33 @@ __device__ __forceinline__ void comp_step(CCell& c, const RecC& r, const Adjoint
     const df2 F[6] = {E.x, E.y, E.z, B.x, B.y, B.z};
 
     // ---- transpose of the integrating deposit: G = sum_b w_b g_b over [u_{k-1}, u_k] ----
-    float g0[6];                                              // seed of the bin the interval starts in
+    df2 g0[6];                                                // seed of the bin the interval starts in
 #pragma unroll
     for (int i = 0; i < 6; ++i) g0[i] = c.g[i];
     df2 G[6];
     if (!df_ge(fn, 1.0f)) {
         const df2 w = df_sub(fn, c.f);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) G[i] = df_mul_f(w, c.g[i]);
+        for (int i = 0; i < 6; ++i) G[i] = df_mul(w, c.g[i]);
         c.f = fn;
     } else {
         const df2 w0 = df_sub(df_make(1.0f), c.f);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) G[i] = df_mul_f(w0, c.g[i]);
+        for (int i = 0; i < 6; ++i) G[i] = df_mul(w0, c.g[i]);
         const int m = min(df_floor(fn), 1 << 24);             // bin edges passed (>= 1)
         // whole bins b+1 .. b+m-1, bounded by the window
         const int lo = max(c.b + 1, 0), hi = min(c.b + m - 1, P.n_bins - 1);
         for (int bb = lo; bb <= hi; ++bb) {
-            float t[6];
+            df2 t[6];
             load_seed(c.row, P.n_bins, bb, t);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) G[i] = df_add_f(G[i], t[i]);
+            for (int i = 0; i < 6; ++i) G[i] = df_add(G[i], t[i]);
         }
         c.b += m;
         load_seed(c.row, P.n_bins, c.b, c.g);
         const df2 rem = df_sub(fn, df_make((float)m));
 #pragma unroll
-        for (int i = 0; i < 6; ++i) G[i] = df_add(G[i], df_mul_f(rem, c.g[i]));
+        for (int i = 0; i < 6; ++i) G[i] = df_add(G[i], df_mul(rem, c.g[i]));
         c.f = rem;
     }
     // bin of this arrival for its end-point terms: the walk's, or Eq. 2 in FP64 where the walk ends
@@ -306,7 +314,7 @@ __device__ __forceinline__ void comp_step(CCell& c, const RecC& r, const Adjoint
 
     // ---- sample k-1: its two intervals' terms meet here ----
     if (out_on) {
-        float gs[6];
+        df2 gs[6];
         if (c.bx == b_start) {
 #pragma unroll
             for (int i = 0; i < 6; ++i) gs[i] = g0[i];
@@ -356,7 +364,7 @@ __device__ __forceinline__ void comp_step(CCell& c, const RecC& r, const Adjoint
 
 // One CTA = (chunk of intervals, block of 128 cells, particle); thread tid owns cell
 // cb * 128 + tid.  Outputs samples k_begin-1 .. k_end-1 (and S in the last chunk).
-__global__ void __launch_bounds__(kAdjointCompThreads) k_adjoint_comp(const AdjointParams P)
+__global__ void __launch_bounds__(kAdjointCompThreads, RD_COMP_MINBLOCKS) k_adjoint_comp(const AdjointParams P)
 {
     constexpr int NT = kAdjointCompThreads, NW = NT / 32;
     __shared__ __align__(128) RecC tile[2][kTileSteps];
@@ -415,7 +423,7 @@ __global__ void __launch_bounds__(kAdjointCompThreads) k_adjoint_comp(const Adjo
     c.row = P.seed;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        c.g[i] = 0.f;
+        c.g[i] = z;
         c.Fp[i] = z;
     }
     c.gbdp = c.gbetp = c.bp = {z, z, z};
@@ -442,7 +450,7 @@ __global__ void __launch_bounds__(kAdjointCompThreads) k_adjoint_comp(const Adjo
             f_end = df_from_double(ue - fe);
             c.Rpd = df_from_double(Ra + P.dt);
             c.P = {df_from_double(cl.x), df_from_double(cl.y), df_from_double(cl.z)};
-            c.row = P.seed + (size_t)cell * P.n_bins * 8;
+            c.row = P.seed + (size_t)cell * P.n_bins * 16;
             load_seed(c.row, P.n_bins, c.b, c.g);
             // sample 0 (no halo): its arrival starts interval 1; it has no field of its own
             c.np[0] = (float)((cl.x - xa[0]) / Ra);
@@ -471,7 +479,7 @@ __global__ void __launch_bounds__(kAdjointCompThreads) k_adjoint_comp(const Adjo
         const bool last_tile = (t == n_tiles - 1);
         for (int i = 0; i < cnt; ++i) {
             const int k = k0 + i;
-            float out[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            df2 out[6] = {z, z, z, z, z, z};
             const bool out_on = k >= k_begin;
             if (live) {
                 if (last_tile && i == cnt - 1)
@@ -482,7 +490,7 @@ __global__ void __launch_bounds__(kAdjointCompThreads) k_adjoint_comp(const Adjo
             if (out_on) {
 #pragma unroll
                 for (int e = 0; e < 6; ++e) {
-                    const df2 v = warp_sum_df(df_make(out[e]));
+                    const df2 v = warp_sum_df(out[e]);
                     if (lane == 0) red[warp][i][e] = v;
                 }
             }
@@ -490,9 +498,9 @@ __global__ void __launch_bounds__(kAdjointCompThreads) k_adjoint_comp(const Adjo
         // the last sample of the trajectory: interval S's terms only
         const bool tail = last_tile && k_end == S;
         if (tail) {
-            float out[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            df2 out[6] = {z, z, z, z, z, z};
             if (live) {
-                float gs[6];
+                df2 gs[6];
                 load_seed(c.row, P.n_bins, c.bx, gs);
                 const df2 Fz[6] = {z, z, z, z, z, z};
                 const V3 gz = {z, z, z};
@@ -500,7 +508,7 @@ __global__ void __launch_bounds__(kAdjointCompThreads) k_adjoint_comp(const Adjo
             }
 #pragma unroll
             for (int e = 0; e < 6; ++e) {
-                const df2 v = warp_sum_df(df_make(out[e]));
+                const df2 v = warp_sum_df(out[e]);
                 if (lane == 0) red[warp][cnt][e] = v;
             }
         }
@@ -532,7 +540,43 @@ __global__ void __launch_bounds__(kAdjointCompThreads) k_adjoint_comp(const Adjo
     }
 }
 
+// upstream gradient (E, B) [n_pix][n_bins][3] of any type -> double-float seed rows [n_pix][n_bins][16]
+template <typename T>
+__global__ void k_pack_seed_df(const T* __restrict__ gE, const T* __restrict__ gB, long long n, float* __restrict__ seed)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float h[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, l[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int c = 0; c < 3; ++c) {
+            const df2 e = df_from_double(gE ? (double)gE[3 * i + c] : 0.0);
+            const df2 b = df_from_double(gB ? (double)gB[3 * i + c] : 0.0);
+            h[c] = e.hi;
+            l[c] = e.lo;
+            h[3 + c] = b.hi;
+            l[3 + c] = b.lo;
+        }
+        float4* o = reinterpret_cast<float4*>(seed + 16 * i);
+        o[0] = make_float4(h[0], h[1], h[2], h[3]);
+        o[1] = make_float4(h[4], h[5], 0.f, 0.f);
+        o[2] = make_float4(l[0], l[1], l[2], l[3]);
+        o[3] = make_float4(l[4], l[5], 0.f, 0.f);
+    }
+}
+
 size_t comp_record_bytes() { return sizeof(RecC); }
+
+cudaError_t launch_pack_seed_df(const void* gE, const void* gB, int dtype, int n_pix, int n_bins, float* seed,
+                                cudaStream_t s)
+{
+    const long long n = (long long)n_pix * n_bins;
+    const int g = grid_stride_blocks(n, 256, 16);
+    if (dtype == RD_F32)
+        k_pack_seed_df<float><<<g, 256, 0, s>>>(static_cast<const float*>(gE), static_cast<const float*>(gB), n, seed);
+    else
+        k_pack_seed_df<double><<<g, 256, 0, s>>>(static_cast<const double*>(gE), static_cast<const double*>(gB), n,
+                                                 seed);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_precompute_comp(const double* x, const double* u, int n_part, int n_samples, double dt, int flags,
                                    void* rec, DevCounters* counters, cudaStream_t s)

@@ -215,6 +215,7 @@ void fill_mixed_params(DepositParams& P, const rd_detector* d, const rd_traj* t,
     P.lin = (d->flags & RD_LINEAR) ? 1 : (d->flags & RD_HOLD_PREV) ? 2 : 0;
     P.W = (float)(d->dt_det / t->dt);
     P.invW = (float)(t->dt / d->dt_det);
+    P.group = cell_group(P.n_cell_blocks, d->n_bins);
 }
 
 }  // namespace
@@ -252,6 +253,20 @@ int auto_chunk(long long n_cell_blocks, long long n_part, int S)
     const long long want = 8LL * sm_count();       // resident CTAs for a few waves
     while (chunk > 64 && n_cell_blocks * n_part * ((S + chunk - 1) / chunk) < want) chunk /= 2;
     return std::max(1, chunk);
+}
+
+int cell_group(int n_cell_blocks, int n_bins)
+{
+#ifdef RD_GROUP
+    return std::max(1, std::min(n_cell_blocks, RD_GROUP));
+#else
+#ifndef RD_GROUP_SLICE_MB
+#define RD_GROUP_SLICE_MB 40
+#endif
+    const double slice = (double)kMixedCellsPerCta * n_bins * 32.0;
+    const int g = (int)((double)RD_GROUP_SLICE_MB * 1048576.0 / slice);
+    return std::max(1, std::min(n_cell_blocks, g));
+#endif
 }
 
 const char* flags_error(int flags)
@@ -502,6 +517,7 @@ static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream
         P.invW = (float)(t->dt / d->dt_det);
         P.ff = (d->flags & RD_FARFIELD) != 0;
         P.lin = (d->flags & RD_LINEAR) ? 1 : (d->flags & RD_HOLD_PREV) ? 2 : 0;
+        P.group = mixed ? cell_group(n_cell_blocks, d->n_bins) : 1;
         if (mixed) {
             RD_CUDA(launch_precompute_mixed(x, u, q, t->dt / d->dt_det, np, t->n_samples, t->dt, d->flags,
                                             static_cast<RecS*>(d->rec), d->counters, s),
@@ -598,9 +614,9 @@ static rd_status adjoint_compensated(rd_detector* d, const rd_traj* t, const voi
                                      int32_t gdtype, double* gx, double* gu, cudaStream_t s)
 {
     const int S = t->n_samples - 1;
-    rd_status st = ensure(&d->seed, &d->seed_bytes, d->field_bytes, s, "seed scratch");
+    rd_status st = ensure(&d->seed, &d->seed_bytes, 2 * d->field_bytes, s, "seed scratch");   // 64 B per bin
     if (st != RD_OK) return st;
-    RD_CUDA(launch_pack_seed(gE, gB, gdtype, d->n_pix, d->n_bins, static_cast<float*>(d->seed), s), "pack seed");
+    RD_CUDA(launch_pack_seed_df(gE, gB, gdtype, d->n_pix, d->n_bins, static_cast<float*>(d->seed), s), "pack seed");
     const size_t per_part_rec = comp_record_bytes() * (size_t)t->n_samples;
     const size_t budget = (size_t)1 << 31;
     const int pc = (int)std::max<size_t>(1, std::min<size_t>((size_t)t->n_part, budget / per_part_rec));

@@ -93,7 +93,29 @@ struct DepositParams {
     int ff;                     // far-field limit (RD_FARFIELD): Eq. 3, radiation term at (n_c, R_c)
     int lin;                    // 0: held field; 1: linear in arrival time (RD_LINEAR); 2: the previous
                                 // sample's field held (RD_HOLD_PREV); 1 and 2 carry the previous field
+    int group = 1;              // mixed kernel work order: cell blocks per group (cell_group)
 };
+
+#ifdef __CUDACC__
+// Work item (particle p, cell block cb, step chunk ch) of linear index idx for the mixed kernels:
+// chunks slowest; inside a chunk, groups of P.group cell blocks; inside a group the cell block
+// fastest, then the particle.  Consecutive CTAs so take one particle to the group's cell blocks
+// back to back (its staged records are read from DRAM once per group, then from L2) while the
+// resident CTAs reduce into the group's detector slice.  group = 1 is particle-fastest order.
+__device__ __forceinline__ void item_coords(long long idx, const DepositParams& P, int& p, int& cb, int& ch)
+{
+    const long long per_chunk = (long long)P.n_cell_blocks * P.n_part;
+    ch = (int)(idx / per_chunk);
+    long long r = idx - (long long)ch * per_chunk;
+    const int G = P.group;
+    const long long per_group = (long long)G * P.n_part;
+    const int g = (int)(r / per_group);
+    r -= (long long)g * per_group;
+    const int Gg = min(G, P.n_cell_blocks - g * G);
+    cb = g * G + (int)(r % Gg);
+    p = (int)(r / Gg);
+}
+#endif
 
 constexpr int kDepositThreads = 256;   // FP64 kernel: one cell per thread
 #ifndef RD_MIXED_MINBLOCKS
@@ -121,6 +143,9 @@ int grid_stride_blocks(long long n, int threads, int per_sm);
 // Default intervals per work item of the deposit kernels: kDefaultChunk (at most S), halved while
 // the grid (cell blocks x particles x chunks) would hold fewer than 8 CTAs per multiprocessor.
 int auto_chunk(long long n_cell_blocks, long long n_part, int S);
+// Cell blocks per group of the mixed kernels' work order (item_coords): as many as keep the group's
+// detector slice (256 cells x n_bins x 32 bytes per block) within RD_GROUP_SLICE_MB of L2.
+int cell_group(int n_cell_blocks, int n_bins);
 // Check of a detector's `flags` (include/rd.h): null if valid, else the reason.
 const char* flags_error(int flags);
 
@@ -145,6 +170,7 @@ struct AdjointParams {
     const double* q;            // [n_part] or null
     const D4* cells;            // [n_pix]
     const float* seed;          // [n_pix][n_bins][8] upstream gradient (E xyz, B xyz) in field layout
+                                // (compensated kernel: [n_pix][n_bins][16], double-float)
     const double* seedd;        // [n_pix][n_bins][6] the same in FP64 (FP64 kernel)
     double* gx;                 // [n_part][n_samples][3] += d loss / d x
     double* gbeta;              // [n_part][n_samples][3] += d loss / d beta (scratch, FP64)
@@ -181,6 +207,9 @@ constexpr int kAdjointFp64Threads = 128;   // FP64 adjoint: one cell per thread
 // compensated (double-float) adjoint of the mixed deposit (rd_adjoint_comp.cu)
 constexpr int kAdjointCompThreads = 128;   // one cell per thread
 size_t comp_record_bytes();                // bytes of one per-sample record
+// upstream gradient as double-float seed rows [n_pix][n_bins][16] floats (64 bytes per bin)
+cudaError_t launch_pack_seed_df(const void* gE, const void* gB, int dtype, int n_pix, int n_bins, float* seed,
+                                cudaStream_t s);
 cudaError_t launch_precompute_comp(const double* x, const double* u, int n_part, int n_samples, double dt, int flags,
                                    void* rec, DevCounters* counters, cudaStream_t s);
 cudaError_t launch_adjoint_comp(const AdjointParams& p, cudaStream_t s);

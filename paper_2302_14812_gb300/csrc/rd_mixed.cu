@@ -1,9 +1,10 @@
 // Mixed-precision deposit: FP32 Lienard-Wiechert field (Eq. 1) and FP32 accumulation, with the
 // arrival time (Eq. 2) kept FP64-accurate.
 //
-// Work item = (step chunk, block of 256 cells, particle); consecutive CTAs take consecutive
-// particles of the same chunk and cell block, so the CTAs resident at one time all reduce into
-// the same ~(256 cells x chunk span) slice of the detector, which stays in L2.
+// Work item = (step chunk, block of 256 cells, particle), ordered by item_coords: consecutive CTAs
+// take one particle to a small group of cell blocks, then the next particle, so the CTAs resident
+// at one time reduce into the group's slice of the detector, which stays in L2, and each
+// particle's staged records come from DRAM once per group.
 //
 // Each thread walks kMixedCells cells through the chunk; the per-sample constants (RecS) are read
 // once per sample from shared memory and serve all of them.  Per cell the walk carries the bin it
@@ -676,19 +677,15 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_m
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float sv[kSaveWords][kMixedThreads];
     init_staging(bar);
-    const unsigned bid = blockIdx.x;
-    const int p = (int)(bid % (unsigned)P.n_part);
-    const unsigned rest = bid / (unsigned)P.n_part;
-    const int cb = (int)(rest % (unsigned)P.n_cell_blocks);
-    const int ch = (int)(rest / (unsigned)P.n_cell_blocks);
+    int p, cb, ch;
+    item_coords(blockIdx.x, P, p, cb, ch);
     unsigned g = 0;
     (void)deposit_item<FF, LIN>(P, p, cb, ch, tile, bar, sv, g);
 }
 
 // Persistent form: the resident CTAs draw work items of all problems from one counter.
-// Items of problem i are [item_off[i], item_off[i+1]), ordered particle-fastest within a
-// (chunk, cell block) like the single-problem grid.  The counter only grows (atomicAdd): no CTA
-// ever waits on another.
+// Items of problem i are [item_off[i], item_off[i+1]), ordered by item_coords like the
+// single-problem grid.  The counter only grows (atomicAdd): no CTA ever waits on another.
 __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS)
     k_deposit_batch(const DepositParams* __restrict__ probs, const long long* __restrict__ item_off, int n_probs,
                     unsigned long long* next_item)
@@ -712,11 +709,8 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS)
             else hi = mid - 1;
         }
         const DepositParams P = probs[lo];
-        const long long local = item - item_off[lo];
-        const int p = (int)(local % P.n_part);
-        const long long rest = local / P.n_part;
-        const int cb = (int)(rest % P.n_cell_blocks);
-        const int ch = (int)(rest / P.n_cell_blocks);
+        int p, cb, ch;
+        item_coords(item - item_off[lo], P, p, cb, ch);
         bool ok;
         if (P.lin)
             ok = P.ff ? deposit_item<true, true>(P, p, cb, ch, tile, bar, sv, g)
