@@ -319,14 +319,15 @@ def run_batch_workload(args):
     import paper_2302_14812_gb300 as rd
     from paper_2302_14812_gb300 import workloads as W
     rd.load_library()
-    probs = W.batch_problems(64, seed=4, scale=args.batch_scale)
+    # the trajectories are generated on the device (at full scale they hold ~1e11 FP64 values)
+    probs = W.batch_problems_torch(64, seed=4, scale=args.batch_scale)
     stream = torch.cuda.Stream()
     dets, trajs, deposits = [], [], 0
-    for _, tr, det in probs:
+    for _, t, det in probs:
         dets.append(rd.RadiationDetector.from_workload(det, "mixed", stream))
-        trajs.append((torch.from_numpy(tr.x).cuda(), torch.from_numpy(tr.u).cuda(),
-                      torch.from_numpy(tr.q).cuda(), tr.t0, tr.dt))
-        deposits += W.deposits(tr, det)
+        trajs.append(t)
+        deposits += t[0].shape[0] * (t[0].shape[1] - 1) * det.n_pix
+    del probs
     torch.cuda.synchronize()
 
     def separate():

@@ -261,11 +261,11 @@ int cell_group(int n_cell_blocks, int n_bins)
     return std::max(1, std::min(n_cell_blocks, RD_GROUP));
 #else
 #ifndef RD_GROUP_SLICE_MB
-#define RD_GROUP_SLICE_MB 40
+#define RD_GROUP_SLICE_MB 140
 #endif
     const double slice = (double)kMixedCellsPerCta * n_bins * 32.0;
     const int g = (int)((double)RD_GROUP_SLICE_MB * 1048576.0 / slice);
-    return std::max(1, std::min(n_cell_blocks, g));
+    return std::max(1, std::min(std::min(n_cell_blocks, 8), g));
 #endif
 }
 
@@ -864,7 +864,10 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
                 item_off.push_back(0);
                 used = 0;
             }
-            const int np = (int)std::min<size_t>((size_t)(t.n_part - p0), (budget - used) / per_part);
+            // a segment's items are indexed in 32 bits by the kernel
+            const long long per_p = (long long)ncb * ((S + chunk - 1) / chunk);
+            const int np = (int)std::min<long long>(std::min<size_t>((size_t)(t.n_part - p0), (budget - used) / per_part),
+                                                    std::max(1LL, 0x7fffffffLL / per_p));
             segs.push_back({i, p0, np, chunk, used});
             item_off.push_back(item_off.back() + (long long)ncb * np * ((S + chunk - 1) / chunk));
             used += per_part * np;

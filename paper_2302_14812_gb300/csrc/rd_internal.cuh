@@ -102,17 +102,18 @@ struct DepositParams {
 // fastest, then the particle.  Consecutive CTAs so take one particle to the group's cell blocks
 // back to back (its staged records are read from DRAM once per group, then from L2) while the
 // resident CTAs reduce into the group's detector slice.  group = 1 is particle-fastest order.
-__device__ __forceinline__ void item_coords(long long idx, const DepositParams& P, int& p, int& cb, int& ch)
+__device__ __forceinline__ void item_coords(unsigned idx, const DepositParams& P, int& p, int& cb, int& ch)
 {
-    const long long per_chunk = (long long)P.n_cell_blocks * P.n_part;
+    // 32-bit arithmetic: a launch (or a batch segment) holds fewer than 2^31 items (host-checked)
+    const unsigned per_chunk = (unsigned)P.n_cell_blocks * (unsigned)P.n_part;
     ch = (int)(idx / per_chunk);
-    long long r = idx - (long long)ch * per_chunk;
-    const int G = P.group;
-    const long long per_group = (long long)G * P.n_part;
-    const int g = (int)(r / per_group);
-    r -= (long long)g * per_group;
-    const int Gg = min(G, P.n_cell_blocks - g * G);
-    cb = g * G + (int)(r % Gg);
+    unsigned r = idx - (unsigned)ch * per_chunk;
+    const unsigned G = (unsigned)P.group;
+    const unsigned per_group = G * (unsigned)P.n_part;
+    const unsigned g = r / per_group;
+    r -= g * per_group;
+    const unsigned Gg = min(G, (unsigned)P.n_cell_blocks - g * G);
+    cb = (int)(g * G + r % Gg);
     p = (int)(r / Gg);
 }
 #endif
@@ -144,7 +145,7 @@ int grid_stride_blocks(long long n, int threads, int per_sm);
 // the grid (cell blocks x particles x chunks) would hold fewer than 8 CTAs per multiprocessor.
 int auto_chunk(long long n_cell_blocks, long long n_part, int S);
 // Cell blocks per group of the mixed kernels' work order (item_coords): as many as keep the group's
-// detector slice (256 cells x n_bins x 32 bytes per block) within RD_GROUP_SLICE_MB of L2.
+// detector slice (256 cells x n_bins x 32 bytes per block) within RD_GROUP_SLICE_MB, at most 8.
 int cell_group(int n_cell_blocks, int n_bins);
 // Check of a detector's `flags` (include/rd.h): null if valid, else the reason.
 const char* flags_error(int flags);

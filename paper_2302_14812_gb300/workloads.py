@@ -590,6 +590,108 @@ def batch_problems(n_problems: int = 64, seed: int = 4, scale: float = 1.0):
     return out
 
 
+def _integrate_positions_torch(beta_fn, x0, dt: float, n_steps: int, sub: int = 512):
+    """_integrate_positions with PyTorch in FP64 on x0's device: x_k = x0 + sum over steps of the
+    8-node Gauss-Legendre quadrature of beta; beta_fn(t [m], rows slice) -> [rows][m][3]."""
+    import torch
+    f64 = dict(dtype=torch.float64, device=x0.device)
+    n_part = x0.shape[0]
+    k = torch.arange(n_steps, **f64)
+    tn = (dt * (k[:, None] + 0.5 * (1.0 + torch.tensor(_GL_X, **f64)[None, :]))).reshape(-1)
+    glw = torch.tensor(_GL_W, **f64)
+    x = torch.empty((n_part, n_steps + 1, 3), **f64)
+    x[:, 0] = x0
+    for p0 in range(0, n_part, sub):
+        p1 = min(n_part, p0 + sub)
+        b = beta_fn(tn, slice(p0, p1))
+        inc = 0.5 * dt * torch.einsum("psnc,n->psc", b.reshape(p1 - p0, n_steps, 8, 3), glw)
+        x[p0:p1, 1:] = x0[p0:p1, None, :] + torch.cumsum(inc, dim=1)
+        del b, inc
+    return x
+
+
+def batch_problems_torch(n_problems: int = 64, seed: int = 4, scale: float = 1.0, device="cuda"):
+    """batch_problems(n_problems, seed, scale) with the trajectories generated by PyTorch in FP64 on
+    `device` (the full-scale set holds ~1e11 FP64 values): the same seeded draws in the same order
+    and the same formulas, positions by the same quadrature summed on the device, so values agree
+    with the numpy generator to rounding.  Returns a list of (kind, (x, u, q, t0, dt), Detector)."""
+    import torch
+    f64 = dict(dtype=torch.float64, device=device)
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_problems):
+        kind = ["undulator", "circular", "oscillator"][int(rng.integers(0, 3))]
+        n_p = max(1, int(round(math.exp(rng.uniform(math.log(100.0), math.log(5e4))) * scale)))
+        n_s = int(rng.integers(500, 8001))
+        side = [32, 64, 128][int(rng.integers(0, 3))]
+        n_b = 16 * side
+        sub = int(rng.integers(0, 2 ** 31 - 1))
+        if kind == "undulator":
+            gamma = float(rng.uniform(5.0, 30.0))
+            K = float(rng.uniform(0.3, 2.0))
+            n_periods, distance, sigma = 5.0, 1e3, 1e-3
+            r2 = np.random.default_rng(sub)
+            phi = torch.tensor(r2.uniform(0.0, 2.0 * math.pi, n_p), **f64)
+            off = r2.normal(0.0, sigma, (n_p, 2))
+            bz_bar, w_u = undulator_params(gamma, K, 1.0)
+            dt = n_periods / bz_bar / n_s
+            g2 = gamma * gamma
+
+            def beta_fn(t, sl, phi=phi, K=K, gamma=gamma, w_u=w_u, g2=g2):
+                by = (K / gamma) * torch.sin(w_u * t[None, :] + phi[sl, None])
+                bz = torch.sqrt(1.0 - 1.0 / g2 - by * by)
+                return torch.stack([torch.zeros_like(by), by, bz], dim=-1)
+            x0 = torch.zeros((n_p, 3), **f64)
+            x0[:, 0] = torch.tensor(off[:, 0], **f64)
+            x0[:, 1] = torch.tensor(off[:, 1], **f64)
+            x = _integrate_positions_torch(beta_fn, x0, dt, n_s)
+            t = dt * torch.arange(n_s + 1, **f64)
+            u = torch.cat([gamma * beta_fn(t, slice(p0, min(n_p, p0 + 512))) for p0 in range(0, n_p, 512)])
+            _, det = config_undulator(n_part=1, n_steps=n_s, n_side=side, n_bins=n_b, gamma=gamma, K=K,
+                                      n_periods=n_periods, distance=distance, seed=sub)
+            t0 = 0.0
+        elif kind == "circular":
+            gam = float(rng.uniform(2.0, 8.0))
+            r2 = np.random.default_rng(sub)
+            ph0 = torch.tensor(r2.uniform(0.0, 2.0 * math.pi, n_p), **f64)
+            beta = math.sqrt(1.0 - 1.0 / gam ** 2)
+            w0 = beta
+            dt = 4.0 * (2.0 * math.pi / w0) / n_s
+            ph = w0 * (dt * torch.arange(n_s + 1, **f64))[None, :] + ph0[:, None]
+            z = torch.zeros_like(ph)
+            x = torch.stack([torch.cos(ph), torch.sin(ph), z], dim=-1)
+            u = gam * beta * torch.stack([-torch.sin(ph), torch.cos(ph), z], dim=-1)
+            del ph, z
+            pos = spherical_cap(side, 1e3, 0.6, axis=2)
+            span = n_s * dt + 2.0
+            det = Detector(pos, None, 1e3 - 1.0 - 0.02 * span, 1.04 * span / n_b, n_b, RD_NEAR | RD_FAR, (side, side))
+            t0 = 0.0
+        else:
+            r2 = np.random.default_rng(sub)
+            a = torch.tensor(r2.uniform(0.1, 2.0, n_p), **f64)
+            phi = torch.tensor(r2.uniform(0.0, 2.0 * math.pi, n_p), **f64)
+            off = torch.tensor(r2.normal(0.0, 1e-2, (n_p, 3)), **f64)
+            dt = 6.0 * 2.0 * math.pi / n_s
+
+            def mom(t, sl, a=a, phi=phi):
+                ux = a[sl, None] * torch.sin(t[None, :] + phi[sl, None])
+                return torch.stack([ux, torch.zeros_like(ux), torch.zeros_like(ux)], dim=-1)
+
+            def beta_fn(t, sl, mom=mom):
+                uu = mom(t, sl)
+                return uu / torch.sqrt(1.0 + torch.sum(uu * uu, dim=-1, keepdim=True))
+            x = _integrate_positions_torch(beta_fn, off, dt, n_s)
+            t = dt * torch.arange(n_s + 1, **f64)
+            u = torch.cat([mom(t, slice(p0, min(n_p, p0 + 512))) for p0 in range(0, n_p, 512)])
+            pos = spherical_cap(side, 1e3, 0.6, axis=1)
+            reach = 3.0
+            span = n_s * dt + 2.0 * reach
+            det = Detector(pos, None, 1e3 - reach - 0.02 * span, 1.04 * span / n_b, n_b, RD_NEAR | RD_FAR, (side, side))
+            t0 = 0.0
+        out.append((kind, (x, u, torch.full((n_p,), -1.0, **f64), t0, dt), det))
+    return out
+
+
 def deposits(tr: Trajectories, det: Detector) -> int:
     """Number of (particle, interval, pixel) triples: the unit of the throughput metric."""
     return int(tr.n_part) * int(tr.n_steps) * int(det.n_pix)

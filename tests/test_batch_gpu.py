@@ -222,3 +222,41 @@ def test_batch_mixes_modes():
     res = run_batch(probs, torch.cuda.Stream())
     for (E, B), (Es, Bs) in zip(res[0], sep):
         assert parity_err(E, Es) <= 2e-6 and parity_err(B, Bs) <= 2e-6
+
+
+def test_uneven_64_problem_set_full_scale():
+    """The 64 uneven problems at their stated size (particle counts log-uniform in [100, 5e4], steps
+    500-8000, 32^2-128^2 cells x 16*side bins; ~1e13 deposits, ~1e11 FP64 trajectory values
+    generated on the device) in one rd_deposit_batch call (records in launch groups of at most
+    4 GiB); 16 random cells of every problem against the FP64 oracle at the mixed bar."""
+    import torch
+    probs = W.batch_problems_torch(64, seed=4, scale=1.0)
+    stream = torch.cuda.Stream()
+    dets = [rd.RadiationDetector.from_workload(det, "mixed") for _, _, det in probs]
+    trajs = [t for _, t, _ in probs]
+    with torch.cuda.stream(stream):
+        keep = rd.deposit_batch(dets, trajs, stream)
+        stream.synchronize()
+    del keep
+    rng = np.random.default_rng(44)
+    worst = 0.0
+    for i in range(len(probs)):
+        kind, (x, u, q, t0, dt), det = probs[i]
+        sel = np.sort(rng.choice(det.n_pix, 16, replace=False)).astype(np.int32)
+        E, B = dets[i].read("float32", "cuda", stream=stream)
+        stream.synchronize()
+        idx = torch.from_numpy(sel.astype(np.int64)).cuda()
+        Eb, Bb = E[idx].double().cpu().numpy(), B[idx].double().cpu().numpy()
+        st = dets[i].stats()
+        dets[i].close()
+        del E, B
+        tr = W.Trajectories(x.cpu().numpy(), u.cpu().numpy(), q.cpu().numpy(), t0, dt)
+        probs[i] = None
+        trajs[i] = None
+        del x, u, q
+        assert st.device_errors == 0, (i, kind)
+        Eo, Bo, _ = oracle.deposit(tr, det, sel)
+        err = max(parity_err(Eb, Eo), parity_err(Bb, Bo))
+        worst = max(worst, err)
+        assert err <= 1e-4, (i, kind, err)
+    print(f"64 problems at full scale: worst parity error {worst:.3e}")

@@ -461,3 +461,36 @@ def test_bounded_wait_runs_out_and_reports():
     tr = W.random_smooth(2, 60, 0.03, seed=31)
     det = W.Detector(W.spherical_cap(3, 12.0, 0.5), None, 9.0, 0.02, 300)
     check(tr, det, "mixed")
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_plasma_mirror_full_plane_and_steps(precision):
+    """The plasma-mirror configuration with its full detector (256x256 plane x 4096 bins of 5 dt,
+    per-cell time origins) and its full 10^4 steps, for the first 10^3 of its 10^5 electrons
+    (generated on the device by the generator a CPU test pins to the host one); 8 cells against the
+    FP64 oracle.  The mixed path deposits the whole plane (6.6e11 deposits); the FP64 path runs on a
+    detector of the 8 cells only (the whole plane in FP64 takes minutes)."""
+    import torch
+    n_steps = 10_000
+    x, u, q, (t0, dt) = W.plasma_mirror_surface_torch(slice(0, 1000), n_part=100_000, n_steps=n_steps)
+    det = W.plasma_mirror_detector(dt)
+    rng = np.random.default_rng(31)
+    sel = np.sort(rng.choice(det.n_pix, 8, replace=False)).astype(np.int32)
+    if precision == "mixed":
+        d = rd.RadiationDetector.from_workload(det, "mixed")
+        d.deposit(x, u, q, t0, dt)
+        E, B = d.read("float32", "cuda")
+        idx = torch.from_numpy(sel.astype(np.int64)).cuda()
+        E, B = E[idx].double().cpu().numpy(), B[idx].double().cpu().numpy()
+    else:
+        d = rd.RadiationDetector.from_workload(det.subset(sel), "fp64")
+        d.deposit(x, u, q, t0, dt)
+        E, B = d.read()
+    st = d.stats()
+    d.close()
+    assert st.device_errors == 0
+    tr = W.Trajectories(x.cpu().numpy(), u.cpu().numpy(), q.cpu().numpy(), t0, dt)
+    del x, u
+    Eo, Bo, _ = oracle.deposit(tr, det, sel)
+    assert np.abs(Eo).max() > 0
+    assert parity_err(E, Eo) <= TOL[precision] and parity_err(B, Bo) <= TOL[precision]

@@ -61,3 +61,24 @@ def test_boris_generator_rotation_closed_form():
     assert np.max(np.abs(np.abs(ang[:, -1]) - n * phi)) < 1e-10
     chord = np.linalg.norm(np.diff(tr.x, axis=1), axis=2) / dt
     assert chord.max() < 1.0
+
+
+def test_batch_problems_torch_matches_numpy_generator():
+    """The device generator of the 64-problem set (PyTorch FP64, run here on the CPU) reproduces the
+    numpy generator: same kinds, sizes, detectors and time axes, trajectories equal to rounding."""
+    torch = pytest.importorskip("torch")
+    ref = W.batch_problems(64, seed=4, scale=0.002)
+    dev = W.batch_problems_torch(64, seed=4, scale=0.002, device="cpu")
+    assert len(ref) == len(dev) == 64
+    kinds = set()
+    for (k1, tr, det), (k2, (x, u, q, t0, dt), det2) in zip(ref, dev):
+        kinds.add(k1)
+        assert k1 == k2 and x.shape == tr.x.shape and u.shape == tr.u.shape
+        assert dt == tr.dt and t0 == tr.t0
+        assert det.n_bins == det2.n_bins and det.t_min == det2.t_min and det.dt_det == det2.dt_det
+        assert np.array_equal(det.pix_pos, det2.pix_pos)
+        scale = max(1.0, float(np.max(np.abs(tr.x))))
+        assert np.max(np.abs(x.numpy() - tr.x)) <= 1e-12 * scale
+        assert np.max(np.abs(u.numpy() - tr.u)) <= 1e-13 * max(1.0, float(np.max(np.abs(tr.u))))
+        assert np.array_equal(q.numpy(), tr.q)
+    assert kinds == {"undulator", "circular", "oscillator"}
