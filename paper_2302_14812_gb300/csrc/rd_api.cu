@@ -261,7 +261,7 @@ int cell_group(int n_cell_blocks, int n_bins)
     return std::max(1, std::min(n_cell_blocks, RD_GROUP));
 #else
 #ifndef RD_GROUP_SLICE_MB
-#define RD_GROUP_SLICE_MB 140
+#define RD_GROUP_SLICE_MB 70
 #endif
     const double slice = (double)kMixedCellsPerCta * n_bins * 32.0;
     const int g = (int)((double)RD_GROUP_SLICE_MB * 1048576.0 / slice);

@@ -28,14 +28,6 @@ namespace rd {
 namespace {
 
 constexpr int NC = kMixedCells;
-constexpr int NP = NC / 2;          // packed pairs of cells per thread
-static_assert(NC % 2 == 0, "cells per thread come in packed pairs");
-
-// Lane j of the thread's per-cell values: cells 2q and 2q+1 share the float2 at index q, so that
-// the common step evaluates both with one packed FP32 instruction per operation (an lvalue).
-#define LN(a, j) ((j) & 1 ? (a)[(j) >> 1].y : (a)[(j) >> 1].x)
-// lane of one pair: cell j's value in the float2 of its pair
-#define LNV(v, j) ((j) & 1 ? (v).y : (v).x)
 // Bin indices of the walk are clamped to +-2^29 so that offsets (row * n_bins + bin, with
 // n_bins <= kMixedMaxBins) and differences of two of them stay inside int32.
 constexpr double kWalkClamp = 536870912.0;
@@ -44,12 +36,12 @@ __device__ __forceinline__ int walk_bin(double fb) { return (int)fmin(fmax(fb, -
 
 // Walk state of the thread's cells.
 struct Cells {
-    float2 px[NP], py[NP], pz[NP];  // cell positions
-    float2 f[NP];                   // time spent in the current bin, units of dt (0 <= f < W)
-    float2 rpd[NP];                 // R_{k-1} + dt (far-field limit: 1/R_c)
-    float2 ec[NP];                  // far-field limit: |n_c|^2 - 1 of the rounded direction
-    float2 acc[6][NP];              // E xyz, B xyz of the current bin so far (weights in bins)
-    float2 gp[6][NP];               // linear interpolation: scaled field of the previous sample
+    float px[NC], py[NC], pz[NC];   // cell positions
+    float f[NC];                    // time spent in the current bin, units of dt (0 <= f < W)
+    float rpd[NC];                  // R_{k-1} + dt (far-field limit: 1/R_c)
+    float ec[NC];                   // far-field limit: |n_c|^2 - 1 of the rounded direction
+    float acc[6][NC];               // E xyz, B xyz of the current bin so far (weights in bins)
+    float gp[6][NC];                // linear interpolation: scaled field of the previous sample
     int bo[NC];                     // row * n_bins + bin being filled (bin may lie outside the window)
     int rb[NC];                     // row * n_bins (row = the cell's index inside the CTA's block)
     bool live[NC];                  // some arrival of the chunk falls inside the window
@@ -97,9 +89,9 @@ template <bool FF>
 __device__ __forceinline__ void bin_b(const Cells& c, int j, const float* e, const float* carried, float* b)
 {
     if (FF) {
-        b[0] = fmaf(LN(c.py, j), e[2], -(LN(c.pz, j) * e[1]));
-        b[1] = fmaf(LN(c.pz, j), e[0], -(LN(c.px, j) * e[2]));
-        b[2] = fmaf(LN(c.px, j), e[1], -(LN(c.py, j) * e[0]));
+        b[0] = fmaf(c.py[j], e[2], -(c.pz[j] * e[1]));
+        b[1] = fmaf(c.pz[j], e[0], -(c.px[j] * e[2]));
+        b[2] = fmaf(c.px[j], e[1], -(c.py[j] * e[0]));
     } else {
         b[0] = carried[0];
         b[1] = carried[1];
@@ -111,8 +103,8 @@ __device__ __forceinline__ void bin_b(const Cells& c, int j, const float* e, con
 template <bool FF>
 __device__ __forceinline__ void flush_acc(const Consts& C, const Cells& c, int j, int b, int bo)
 {
-    const float e[3] = {LN(c.acc[0], j), LN(c.acc[1], j), LN(c.acc[2], j)};
-    const float cb[3] = {LN(c.acc[3], j), LN(c.acc[4], j), LN(c.acc[5], j)};
+    const float e[3] = {c.acc[0][j], c.acc[1][j], c.acc[2][j]};
+    const float cb[3] = {c.acc[3][j], c.acc[4][j], c.acc[5][j]};
     float bb[3];
     bin_b<FF>(c, j, e, cb, bb);
     flush(C, b, bo, e[0], e[1], e[2], bb[0], bb[1], bb[2]);
@@ -204,8 +196,8 @@ __device__ __forceinline__ void multi_edges(Cells& c, int j, const Field& o, con
         flush(C, b, c.rb[j] + b, o.E[0] * fs, o.E[1] * fs, o.E[2] * fs, o.B[0] * fb, o.B[1] * fb, o.B[2] * fb);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        LN(c.acc[i], j) = o.E[i] * fs;
-        if (!FF) LN(c.acc[3 + i], j) = o.B[i] * fb;
+        c.acc[i][j] = o.E[i] * fs;
+        if (!FF) c.acc[3 + i][j] = o.B[i] * fb;
     }
     c.bo[j] += m - 1;
     fn = fminf(fmaxf(fmaf(-(float)(m - 1), C.W, f), C.W), C.W * 1.99999988f);
@@ -241,7 +233,7 @@ __device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* G,
     constexpr int NF = FF ? 3 : 6;                                  // carried field components
     const float f = fn;
     if (!(f >= 2.f * C.W)) return;
-    const float f0 = LN(c.f, j);
+    const float f0 = c.f[j];
     const int b0 = c.bo[j] - c.rb[j];
     const int m = (int)fminf(floorf(f * C.invW), 16777216.f);      // edges passed, >= 2
     flush_acc<FF>(C, c, j, b0, c.bo[j]);
@@ -252,7 +244,7 @@ __device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* G,
         const float ramp = (s1 * s1 - s0 * s0) * inv2L;
         float v[6];
 #pragma unroll
-        for (int q = 0; q < NF; ++q) v[q] = fmaf(LN(c.gp[q], j), C.W - ramp, G[q] * ramp);
+        for (int q = 0; q < NF; ++q) v[q] = fmaf(c.gp[q][j], C.W - ramp, G[q] * ramp);
         bin_b<FF>(c, j, v, v + 3, v + 3);
         flush(C, b0 + i, c.bo[j] + i, v[0], v[1], v[2], v[3], v[4], v[5]);
     }
@@ -261,7 +253,7 @@ __device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* G,
     const float len = fmaf(-(float)m, C.W, f);
     const float ramp = (L * L - s0 * s0) * inv2L;
 #pragma unroll
-    for (int q = 0; q < NF; ++q) LN(c.acc[q], j) = fmaf(LN(c.gp[q], j), len - ramp, G[q] * ramp);
+    for (int q = 0; q < NF; ++q) c.acc[q][j] = fmaf(c.gp[q][j], len - ramp, G[q] * ramp);
     c.bo[j] += m;
     fn = fminf(fmaxf(len, 0.f), C.W * 0.99999994f);
     if (TRACK) {
@@ -295,33 +287,33 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         if (FF)
-            field_at_ff(r, LN(c.px, j), LN(c.py, j), LN(c.pz, j), LN(c.rpd, j), LN(c.ec, j), o[j]);
+            field_at_ff(r, c.px[j], c.py[j], c.pz[j], c.rpd[j], c.ec[j], o[j]);
         else
-            field_at(r, LN(c.px, j), LN(c.py, j), LN(c.pz, j), LN(c.rpd, j), C, o[j]);
+            field_at(r, c.px[j], c.py[j], c.pz[j], c.rpd[j], C, o[j]);
         float t;
         if (LAST) {
             t = fmaf((float)(bo_end[j] - c.bo[j]), C.W, f_end[j]);
-            if (MODE == kFast) t = LN(c.f, j) == -INFINITY ? -INFINITY : t;
+            if (MODE == kFast) t = c.f[j] == -INFINITY ? -INFINITY : t;
         } else {
-            t = fmaf(o[j].num, o[j].rden, LN(c.f, j));
+            t = fmaf(o[j].num, o[j].rden, c.f[j]);
         }
         if (LIN) {
             scaled_field(o[j], G[j]);
-            L[j] = t - LN(c.f, j);
+            L[j] = t - c.f[j];
             inv2L[j] = (0.5f * ramp) * fast_rcp(fmaxf(L[j], 1e-30f));
-            const float len1 = fminf(t, C.W) - LN(c.f, j);
+            const float len1 = fminf(t, C.W) - c.f[j];
             ramp1[j] = (len1 * len1) * inv2L[j];
             // G0 (s1 - s0) + (G - G0) ramp = G0 (s1 - s0 - ramp) + G ramp
             const float a1 = len1 - ramp1[j];
 #pragma unroll
-            for (int i = 0; i < NF; ++i) LN(c.acc[i], j) = fmaf(LN(c.gp[i], j), a1, fmaf(G[j][i], ramp1[j], LN(c.acc[i], j)));
+            for (int i = 0; i < NF; ++i) c.acc[i][j] = fmaf(c.gp[i][j], a1, fmaf(G[j][i], ramp1[j], c.acc[i][j]));
         } else {
-            const float ws = (fminf(t, C.W) - LN(c.f, j)) * o[j].S;
+            const float ws = (fminf(t, C.W) - c.f[j]) * o[j].S;
             const float wb = ws * o[j].rinv;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                LN(c.acc[i], j) = fmaf(o[j].E[i], ws, LN(c.acc[i], j));
-                if (!FF) LN(c.acc[3 + i], j) = fmaf(o[j].B[i], wb, LN(c.acc[3 + i], j));
+                c.acc[i][j] = fmaf(o[j].E[i], ws, c.acc[i][j]);
+                if (!FF) c.acc[3 + i][j] = fmaf(o[j].B[i], wb, c.acc[3 + i][j]);
             }
         }
         if (MODE == kFast)
@@ -346,8 +338,8 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
         if (MODE == kFast && !TRACK) {
             if (cr) {
                 float* a = bin_addr(C, c.bo[j]);
-                const float e[3] = {LN(c.acc[0], j), LN(c.acc[1], j), LN(c.acc[2], j)};
-                const float cb[3] = {LN(c.acc[3], j), LN(c.acc[4], j), LN(c.acc[5], j)};
+                const float e[3] = {c.acc[0][j], c.acc[1][j], c.acc[2][j]};
+                const float cb[3] = {c.acc[3][j], c.acc[4][j], c.acc[5][j]};
                 float bb[3];
                 bin_b<FF>(c, j, e, cb, bb);
                 red_add_v4(a, e[0], e[1], e[2], bb[0]);
@@ -356,28 +348,28 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
                 if (LIN) {
                     const float ramp2 = fmaf(0.5f * ramp, L[j], -ramp1[j]);
 #pragma unroll
-                    for (int i = 0; i < NF; ++i) LN(c.acc[i], j) = fmaf(LN(c.gp[i], j), rem - ramp2, G[j][i] * ramp2);
+                    for (int i = 0; i < NF; ++i) c.acc[i][j] = fmaf(c.gp[i][j], rem - ramp2, G[j][i] * ramp2);
                 } else {
                     const float rs = rem * o[j].S;
                     const float rbw = rs * o[j].rinv;
 #pragma unroll
                     for (int i = 0; i < 3; ++i) {
-                        LN(c.acc[i], j) = o[j].E[i] * rs;
-                        if (!FF) LN(c.acc[3 + i], j) = o[j].B[i] * rbw;
+                        c.acc[i][j] = o[j].E[i] * rs;
+                        if (!FF) c.acc[3 + i][j] = o[j].B[i] * rbw;
                     }
                 }
-                LN(c.f, j) = rem;
+                c.f[j] = rem;
                 c.bo[j] += 1;
             } else {
-                LN(c.f, j) = fn[j];
+                c.f[j] = fn[j];
             }
         } else {
             const int b = c.bo[j] - c.rb[j];
             const bool go = MODE == kFast || !ok[j];
             const bool pr = cr && go && (!TRACK || (unsigned)b < (unsigned)C.n_bins);
             float* a = bin_addr(C, c.bo[j]);
-            const float e[3] = {LN(c.acc[0], j), LN(c.acc[1], j), LN(c.acc[2], j)};
-            const float cb[3] = {LN(c.acc[3], j), LN(c.acc[4], j), LN(c.acc[5], j)};
+            const float e[3] = {c.acc[0][j], c.acc[1][j], c.acc[2][j]};
+            const float cb[3] = {c.acc[3][j], c.acc[4][j], c.acc[5][j]};
             float bb[3];
             bin_b<FF>(c, j, e, cb, bb);
             red_add_v4_if(pr, a, e[0], e[1], e[2], bb[0]);
@@ -387,19 +379,19 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
                 const float ramp2 = fmaf(0.5f * ramp, L[j], -ramp1[j]);
 #pragma unroll
                 for (int i = 0; i < NF; ++i) {
-                    const float v = fmaf(LN(c.gp[i], j), rem - ramp2, G[j][i] * ramp2);
-                    LN(c.acc[i], j) = cr ? v : LN(c.acc[i], j);
+                    const float v = fmaf(c.gp[i][j], rem - ramp2, G[j][i] * ramp2);
+                    c.acc[i][j] = cr ? v : c.acc[i][j];
                 }
             } else {
                 const float rs = rem * o[j].S;
                 const float rbw = rs * o[j].rinv;
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    LN(c.acc[i], j) = cr ? o[j].E[i] * rs : LN(c.acc[i], j);
-                    if (!FF) LN(c.acc[3 + i], j) = cr ? o[j].B[i] * rbw : LN(c.acc[3 + i], j);
+                    c.acc[i][j] = cr ? o[j].E[i] * rs : c.acc[i][j];
+                    if (!FF) c.acc[3 + i][j] = cr ? o[j].B[i] * rbw : c.acc[3 + i][j];
                 }
             }
-            LN(c.f, j) = cr ? rem : fn[j];
+            c.f[j] = cr ? rem : fn[j];
             if (TRACK) {
                 if (cr && b == -1) c.below[j] = k - k_begin + 1;
                 if (cr && b == C.n_bins - 1) c.above[j] = k_end - k + 1;
@@ -408,106 +400,10 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
         }
         if (LIN) {
 #pragma unroll
-            for (int i = 0; i < NF; ++i) LN(c.gp[i], j) = G[j][i];
+            for (int i = 0; i < NF; ++i) c.gp[i][j] = G[j][i];
         }
     }
 }
-
-// ---------------------------------------------------------------------------------------------
-// Packed form of the common step (fast walk, no clip tracking, held field, exact Eq. 1): each
-// pair of the thread's cells is evaluated with one packed FP32 instruction (fma/mul/add.rn.f32x2)
-// per operation of field_at / step, lane by lane the same operations in the same order as the
-// scalar code (every packed lane is one IEEE single-precision operation, rounded once), so the
-// packed fast walk and the scalar exact re-walk agree bit for bit.  Record values enter as a scalar
-// broadcast to both lanes.
-// ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-
-struct Field2 {
-    float2 E[3], B[3];
-    float2 S, rinv, num, rden;
-};
-
-__device__ __forceinline__ void field_at2(const RecS& r, float2 px, float2 py, float2 pz, float2& rpd, const Consts& C,
-                                          Field2& o)
-{
-    const float2 dx = add2(px, bc(r.nx)), dy = add2(py, bc(r.ny)), dz = add2(pz, bc(r.nz));
-    const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-    const float2 rinv = make_float2(fast_rsqrt(r2.x), fast_rsqrt(r2.y));
-    const float2 bx = fma2(dx, rinv, bc(r.nbx)), by = fma2(dy, rinv, bc(r.nby)), bz = fma2(dz, rinv, bc(r.nbz));
-    const float2 nb2 = fma2(bx, bx, fma2(by, by, mul2(bz, bz)));
-    const float2 gg = fma2(bx, bc(r.d2x), fma2(by, bc(r.d2y), fma2(bz, bc(r.d2z), add2(nb2, bc(r.gd)))));
-    o.num = fma2(bc(r.dtg), rinv, gg);
-    const float2 den = fma2(rpd, rinv, bc(1.f));
-    o.rden = make_float2(fast_rcp(den.x), fast_rcp(den.y));
-    rpd = fma2(r2, rinv, bc(C.DT));
-    const float2 kn = fma2(nb2, bc(-0.5f), bc(r.nhig2));
-    const float2 ikn = make_float2(fast_rcp(kn.x), fast_rcp(kn.y));
-    const float2 nrik = mul2(rinv, ikn);
-    o.S = mul2(nrik, ikn);
-    const float2 c1n = mul2(fma2(dx, bc(r.bdx), fma2(dy, bc(r.bdy), fma2(dz, bc(r.bdz), bc(r.ig2n)))), nrik);
-    o.E[0] = fma2(bx, c1n, bc(r.bdx));
-    o.E[1] = fma2(by, c1n, bc(r.bdy));
-    o.E[2] = fma2(bz, c1n, bc(r.bdz));
-    o.B[0] = fma2(dy, o.E[2], neg2(mul2(dz, o.E[1])));
-    o.B[1] = fma2(dz, o.E[0], neg2(mul2(dx, o.E[2])));
-    o.B[2] = fma2(dx, o.E[1], neg2(mul2(dy, o.E[0])));
-    o.rinv = rinv;
-}
-
-// step<kFast, false, false, false, false> in packed form
-__device__ __forceinline__ void step_packed(Cells& c, const RecS& r, const Consts& C)
-{
-    Field2 o[NP];
-    float2 fn[NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        field_at2(r, c.px[q], c.py[q], c.pz[q], c.rpd[q], C, o[q]);
-        float2 t = fma2(o[q].num, o[q].rden, c.f[q]);
-        const float2 tw = make_float2(fminf(t.x, C.W), fminf(t.y, C.W));
-        const float2 ws = mul2(add2(tw, neg2(c.f[q])), o[q].S);
-        const float2 wb = mul2(ws, o[q].rinv);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            c.acc[i][q] = fma2(o[q].E[i], ws, c.acc[i][q]);
-            c.acc[3 + i][q] = fma2(o[q].B[i], wb, c.acc[3 + i][q]);
-        }
-        t.x = t.x < 2.f * C.W ? t.x : -INFINITY;
-        t.y = t.y < 2.f * C.W ? t.y : -INFINITY;
-        fn[q] = t;
-    }
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        const Field2& oq = o[j >> 1];
-        const float fnj = LN(fn, j);
-        if (fnj >= C.W) {
-            // the arrival time passed the bin edge: add the bin, start the next one with the rest
-            float* a = bin_addr(C, c.bo[j]);
-            red_add_v4(a, LN(c.acc[0], j), LN(c.acc[1], j), LN(c.acc[2], j), LN(c.acc[3], j));
-            red_add_v2(a + 4, LN(c.acc[4], j), LN(c.acc[5], j));
-            const float rem = fnj - C.W;
-            const float rs = rem * LNV(oq.S, j);
-            const float rbw = rs * LNV(oq.rinv, j);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                LN(c.acc[i], j) = LNV(oq.E[i], j) * rs;
-                LN(c.acc[3 + i], j) = LNV(oq.B[i], j) * rbw;
-            }
-            LN(c.f, j) = rem;
-            c.bo[j] += 1;
-        } else {
-            LN(c.f, j) = fnj;
-        }
-    }
-}
-
-#ifndef RD_PACKED
-#define RD_PACKED 1
-#endif
 
 #ifndef RD_UNROLL
 #define RD_UNROLL 0
@@ -524,16 +420,16 @@ __device__ __forceinline__ void save_state(const Cells& c, float (*sv)[kMixedThr
     constexpr int NF = FF ? 3 : 6;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        sv[j * kSaveCell + 0][tid] = LN(c.f, j);
-        sv[j * kSaveCell + 1][tid] = LN(c.rpd, j);
+        sv[j * kSaveCell + 0][tid] = c.f[j];
+        sv[j * kSaveCell + 1][tid] = c.rpd[j];
         sv[j * kSaveCell + 2][tid] = __int_as_float(c.bo[j]);
         sv[j * kSaveCell + 3][tid] = __int_as_float(c.below[j]);
         sv[j * kSaveCell + 4][tid] = __int_as_float(c.above[j]);
 #pragma unroll
-        for (int i = 0; i < NF; ++i) sv[j * kSaveCell + 5 + i][tid] = LN(c.acc[i], j);
+        for (int i = 0; i < NF; ++i) sv[j * kSaveCell + 5 + i][tid] = c.acc[i][j];
         if (LIN) {
 #pragma unroll
-            for (int i = 0; i < NF; ++i) sv[j * kSaveCell + 11 + i][tid] = LN(c.gp[i], j);
+            for (int i = 0; i < NF; ++i) sv[j * kSaveCell + 11 + i][tid] = c.gp[i][j];
         }
     }
 }
@@ -544,16 +440,16 @@ __device__ __forceinline__ void restore_state(Cells& c, float (*sv)[kMixedThread
     constexpr int NF = FF ? 3 : 6;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        LN(c.f, j) = sv[j * kSaveCell + 0][tid];
-        LN(c.rpd, j) = sv[j * kSaveCell + 1][tid];
+        c.f[j] = sv[j * kSaveCell + 0][tid];
+        c.rpd[j] = sv[j * kSaveCell + 1][tid];
         c.bo[j] = __float_as_int(sv[j * kSaveCell + 2][tid]);
         c.below[j] = __float_as_int(sv[j * kSaveCell + 3][tid]);
         c.above[j] = __float_as_int(sv[j * kSaveCell + 4][tid]);
 #pragma unroll
-        for (int i = 0; i < NF; ++i) LN(c.acc[i], j) = sv[j * kSaveCell + 5 + i][tid];
+        for (int i = 0; i < NF; ++i) c.acc[i][j] = sv[j * kSaveCell + 5 + i][tid];
         if (LIN) {
 #pragma unroll
-            for (int i = 0; i < NF; ++i) LN(c.gp[i], j) = sv[j * kSaveCell + 11 + i][tid];
+            for (int i = 0; i < NF; ++i) c.gp[i][j] = sv[j * kSaveCell + 11 + i][tid];
         }
     }
 }
@@ -567,19 +463,14 @@ __device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, b
     const int n_regular = last_tile ? cnt - 1 : cnt;
     save_state<FF, LIN>(c, sv, tid);
     bool ok[NC];
-    if (RD_PACKED && !TRACK && !FF && !LIN) {
 #pragma unroll kUnroll
-        for (int i = 0; i < n_regular; ++i) step_packed(c, tile[i], C);
-    } else {
-#pragma unroll kUnroll
-        for (int i = 0; i < n_regular; ++i)
-            step<kFast, false, TRACK, FF, LIN>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok, ramp);
-    }
+    for (int i = 0; i < n_regular; ++i)
+        step<kFast, false, TRACK, FF, LIN>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok, ramp);
     if (last_tile)
         step<kFast, true, TRACK, FF, LIN>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok, ramp);
     bool stopped = false;
 #pragma unroll
-    for (int j = 0; j < NC; ++j) stopped = stopped || LN(c.f, j) == -INFINITY;
+    for (int j = 0; j < NC; ++j) stopped = stopped || c.f[j] == -INFINITY;
     if (__any_sync(0xffffffffu, stopped)) {
         // some interval of a cell of this warp passed two or more bin edges: walk the tile again
         restore_state<FF, LIN>(c, sv, tid);
@@ -647,15 +538,15 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
         c.bo[j] = c.rb[j];
         c.live[j] = false;
         c.below[j] = c.above[j] = 0;
-        LN(c.f, j) = -1e30f;
-        LN(c.rpd, j) = 1e6f;
-        LN(c.px, j) = 1e6f;
-        LN(c.py, j) = LN(c.pz, j) = 0.f;
-        LN(c.ec, j) = 0.f;
+        c.f[j] = -1e30f;
+        c.rpd[j] = 1e6f;
+        c.px[j] = 1e6f;
+        c.py[j] = c.pz[j] = 0.f;
+        c.ec[j] = 0.f;
         bo_end[j] = c.bo[j];
         f_end[j] = 0.f;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) LN(c.acc[i], j) = 0.f;
+        for (int i = 0; i < 6; ++i) c.acc[i][j] = 0.f;
         if (cell < P.n_pix) {
             const D4 cl = P.cells[cell];
             const double* xa = xp + 3 * (size_t)(k_begin - 1);
@@ -675,21 +566,21 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
             } else {
                 const double fla = floor(ua), fle = floor(ue);
                 c.bo[j] = c.rb[j] + walk_bin(fla);
-                LN(c.f, j) = (float)(ua - fla) * P.W;
+                c.f[j] = (float)(ua - fla) * P.W;
                 bo_end[j] = c.rb[j] + walk_bin(fle);
                 f_end[j] = (float)(ue - fle) * P.W;
                 if (FF) {
-                    LN(c.px, j) = (float)ncx;
-                    LN(c.py, j) = (float)ncy;
-                    LN(c.pz, j) = (float)ncz;
-                    LN(c.rpd, j) = (float)(1.0 / Rc);
-                    const double ex = LN(c.px, j), ey = LN(c.py, j), ez = LN(c.pz, j);
-                    LN(c.ec, j) = (float)(((ex * ex + ey * ey) + ez * ez) - 1.0);
+                    c.px[j] = (float)ncx;
+                    c.py[j] = (float)ncy;
+                    c.pz[j] = (float)ncz;
+                    c.rpd[j] = (float)(1.0 / Rc);
+                    const double ex = c.px[j], ey = c.py[j], ez = c.pz[j];
+                    c.ec[j] = (float)(((ex * ex + ey * ey) + ez * ez) - 1.0);
                 } else {
-                    LN(c.rpd, j) = (float)Ra + P.dt_f;
-                    LN(c.px, j) = (float)cl.x;
-                    LN(c.py, j) = (float)cl.y;
-                    LN(c.pz, j) = (float)cl.z;
+                    c.rpd[j] = (float)Ra + P.dt_f;
+                    c.px[j] = (float)cl.x;
+                    c.py[j] = (float)cl.y;
+                    c.pz[j] = (float)cl.z;
                 }
                 c.below[j] = (ua < 0.0) ? n_int : 0;
                 // unchecked bins need a margin of one bin to each window edge (the FP32 walk may
@@ -707,15 +598,15 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             Field o;
-            float rtmp = LN(c.rpd, j);
+            float rtmp = c.rpd[j];
             if (FF)
-                field_at_ff(r0, LN(c.px, j), LN(c.py, j), LN(c.pz, j), LN(c.rpd, j), LN(c.ec, j), o);
+                field_at_ff(r0, c.px[j], c.py[j], c.pz[j], c.rpd[j], c.ec[j], o);
             else
-                field_at(r0, LN(c.px, j), LN(c.py, j), LN(c.pz, j), rtmp, C, o);
+                field_at(r0, c.px[j], c.py[j], c.pz[j], rtmp, C, o);
             float G[6];
             scaled_field(o, G);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) LN(c.gp[i], j) = G[i];      // far field: only E is read
+            for (int i = 0; i < 6; ++i) c.gp[i][j] = G[i];      // far field: only E is read
         }
     }
     const bool track = __syncthreads_or(partial) != 0;
