@@ -87,6 +87,9 @@ def parse():
                     help="electrons of the adjoint workload (1e4 = the full configuration)")
     ap.add_argument("--adjoint-fp64-particles", type=int, default=100,
                     help="electrons of the adjoint workload given to the FP64 adjoint (0 = skip that leg)")
+    ap.add_argument("--shape", default=None,
+                    help="deposit shape of the mixed detector as CELLSxPER_THREAD[xCHUNKxGROUP] (default: the "
+                         "library's automatic shape)")
     ap.add_argument("--batch-scale", type=float, default=0.1,
                     help="particle-count scale of the 64-problem set (memory: every problem resident)")
     return ap.parse_args()
@@ -304,6 +307,7 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
+        "shape": mixed_shape,
         "config": {"workload": undulator_workload(tr.n_part), "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -573,6 +577,8 @@ def main():
 
     # ---------------- mixed path, inputs resident in HBM ----------------
     mixed = rd.RadiationDetector.from_workload(det, "mixed")
+    if args.shape:
+        mixed.set_shape(*[int(v) for v in args.shape.lower().split("x")])
     mixed.set_timing(True)
     for _ in range(args.warmup):
         mixed.zero()
@@ -596,6 +602,7 @@ def main():
     value = job_throughput(deposits, world, ms_step)
 
     E_mixed, B_mixed = mixed.read("float64", "cpu")
+    mixed_shape = mixed.shape()
 
     # ---------------- plain FP64 GPU path (speedup reference) ----------------
     fp64_info = None
@@ -824,6 +831,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "precision": "mixed: FP32 fields and accumulation, arrival times FP64-anchored at both ends of each step chunk (up to 4096 intervals)",
+        "shape": mixed_shape,
         "config": {"workload": undulator_workload(tr.n_part),
                    "deposits_per_step_per_gpu": deposits, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (x,u 192 MB; records 256 MB; fields 1.07 GB)"},

@@ -310,6 +310,51 @@ RD_API rd_status rd_set_chunk(rd_detector* det, int32_t chunk);
 RD_API rd_status rd_autotune(rd_detector* det, const rd_traj* traj, rd_stream stream, int32_t* chosen);
 
 /*
+ * Launch shape of an RD_MIXED detector's deposit (no counterpart in the paper: how the (particle,
+ * interval, cell) triples are split over the GPU).  A work item is one particle, one chunk of
+ * intervals between FP64 arrival anchors and one block of cells_per_cta cells (the pixel strip),
+ * walked by cells_per_cta / cells_per_thread threads; work items are ordered so that `group` cell
+ * blocks take each particle back to back (its records then come from DRAM once per group).
+ *   cells_per_cta    64, 128 or 256 (default 256)
+ *   cells_per_thread 1 or 2 (default 2)
+ *   chunk            intervals per work item, >= 0 (0: automatic, 4096 halved while the grid would
+ *                    leave the GPU idle)
+ *   group            cell blocks per group, >= 0 (0: automatic, as many as keep the group's slice of
+ *                    the detector, cells_per_cta x n_bins x 32 bytes each, within 70 MB of L2, at most 8)
+ * The far-field limit and the interpolation variants run the default cells per CTA and per thread
+ * (their chunk and group follow the shape).  rd_deposit_batch uses every detector's chunk and group
+ * and the default cells per CTA and per thread.  Results do not depend on the shape beyond the
+ * order of FP32 reductions and the placement of the FP64 anchors.
+ */
+typedef struct {
+    int32_t cells_per_cta;
+    int32_t cells_per_thread;
+    int32_t chunk;
+    int32_t group;
+} rd_shape;
+
+/* Set / read the shape (RD_ERR_ARG for an unsupported one; RD_ERR_STATE on an RD_FP64 detector for
+ * rd_set_shape).  rd_set_chunk(det, c) is rd_set_shape with only the chunk changed. */
+RD_API rd_status rd_set_shape(rd_detector* det, const rd_shape* shape);
+RD_API rd_status rd_get_shape(const rd_detector* det, rd_shape* shape);
+
+/*
+ * Shape autotuner: pick the fastest shape for depositing `traj` into this RD_MIXED detector and keep it
+ * (as rd_set_shape).  With cache_path (a JSON file; NULL: no cache) an entry for the same device and
+ * problem -- cells, bins, particles, intervals and flags -- is taken without timing (*from_cache = 1);
+ * otherwise the tuner times rd_deposit_trajectories of `traj` (each candidate once after a warm-up,
+ * CUDA events on `stream`) over every compiled cells-per-CTA x cells-per-thread shape at automatic
+ * chunk and group, then the chunks 512 ... 4096 at the best shape, then the groups 1, 2, 4, 8, and adds
+ * the winner to the cache file (read whole, rewritten whole through a temporary file).  The trial
+ * deposits go into this detector, whose fields are zeroed afterwards.  Synchronises the stream.
+ * chosen, from_cache and ms (the winner's time per deposit, or the cached one) may be NULL.
+ * Errors: as rd_deposit_trajectories; RD_ERR_STATE on an RD_FP64 detector; RD_ERR_ARG for a cache
+ * file that exists but cannot be read, parsed or written.
+ */
+RD_API rd_status rd_autotune_shape(rd_detector* det, const rd_traj* traj, const char* cache_path,
+                                   rd_stream stream, rd_shape* chosen, int32_t* from_cache, double* ms);
+
+/*
  * Allocation-free deposit.  The paper has no counterpart: this entry point exists for callers
  * that cannot call cudaMalloc -- a particle-in-cell code that reserves all device memory in its
  * own pool at start-up and allows no allocation inside its time-step loop, a host framework whose

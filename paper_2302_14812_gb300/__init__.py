@@ -25,7 +25,8 @@ __all__ = [
     "RD_MEM_HOST", "RD_MEM_HOST_ASYNC", "RD_F32", "RD_F64", "RDError", "rd_detector_desc", "rd_traj", "rd_stats",
     "load_library", "library_path", "rd_create_detector", "rd_destroy", "rd_zero_fields",
     "rd_deposit_trajectories", "rd_read_fields", "rd_synchronize", "rd_get_stats",
-    "rd_set_timing", "rd_adjoint_trajectories", "rd_set_adjoint_mode", "RD_ADJ_FP32", "RD_ADJ_COMPENSATED", "rd_deposit_batch", "rd_set_chunk", "rd_autotune",
+    "rd_set_timing", "rd_adjoint_trajectories", "rd_set_adjoint_mode", "RD_ADJ_FP32", "RD_ADJ_COMPENSATED", "rd_shape", "rd_set_shape", "rd_get_shape",
+    "rd_autotune_shape", "rd_deposit_batch", "rd_set_chunk", "rd_autotune",
     "rd_set_batch_budget", "rd_power_spectrum", "rd_deposit_stream", "rd_stream_reset",
     "rd_deposit_noalloc", "rd_measure_fma_peaks", "rd_check_bounded_wait", "rd_push_boris", "rd_last_error", "rd_version", "DepositFunction", "deposit_batch", "RadiationDetector", "build_library",
 ]
@@ -58,6 +59,14 @@ class rd_traj(ctypes.Structure):
     _fields_ = [("n_part", ctypes.c_int32), ("n_samples", ctypes.c_int32), ("x", ctypes.c_void_p),
                 ("u", ctypes.c_void_p), ("q", ctypes.c_void_p), ("mem", ctypes.c_int32),
                 ("t0", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
+class rd_shape(ctypes.Structure):
+    _fields_ = [("cells_per_cta", ctypes.c_int32), ("cells_per_thread", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("group", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class rd_stats(ctypes.Structure):
@@ -101,6 +110,10 @@ def load_library(build_if_missing: bool = True):
             "rd_deposit_batch": ([I, ctypes.POINTER(P), ctypes.POINTER(rd_traj), P], I),
             "rd_set_chunk": ([P, I], I),
             "rd_set_adjoint_mode": ([P, I], I),
+            "rd_set_shape": ([P, ctypes.POINTER(rd_shape)], I),
+            "rd_get_shape": ([P, ctypes.POINTER(rd_shape)], I),
+            "rd_autotune_shape": ([P, ctypes.POINTER(rd_traj), ctypes.c_char_p, P, ctypes.POINTER(rd_shape),
+                                   ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double)], I),
             "rd_set_batch_budget": ([P, ctypes.c_longlong], I),
             "rd_power_spectrum": ([P, I, P, P], I),
             "rd_deposit_stream": ([P, ctypes.POINTER(rd_traj), P], I),
@@ -198,6 +211,26 @@ def rd_deposit_batch(dets, trajs, stream=None) -> None:
 
 def rd_set_chunk(det: int, chunk: int) -> None:
     _check(load_library().rd_set_chunk(det, int(chunk)), "rd_set_chunk")
+
+
+def rd_set_shape(det: int, cells_per_cta: int = 256, cells_per_thread: int = 2, chunk: int = 0, group: int = 0) -> None:
+    sh = rd_shape(int(cells_per_cta), int(cells_per_thread), int(chunk), int(group))
+    _check(load_library().rd_set_shape(det, ctypes.byref(sh)), "rd_set_shape")
+
+
+def rd_get_shape(det: int) -> dict:
+    sh = rd_shape()
+    _check(load_library().rd_get_shape(det, ctypes.byref(sh)), "rd_get_shape")
+    return sh.as_dict()
+
+
+def rd_autotune_shape(det: int, traj: rd_traj, cache_path=None, stream=None):
+    """Tune the deposit shape for these trajectories; returns (shape dict, from_cache, ms)."""
+    sh, hit, ms = rd_shape(), ctypes.c_int32(0), ctypes.c_double(0.0)
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(load_library().rd_autotune_shape(det, ctypes.byref(traj), path, _stream_ptr(stream), ctypes.byref(sh),
+                                            ctypes.byref(hit), ctypes.byref(ms)), "rd_autotune_shape")
+    return sh.as_dict(), bool(hit.value), float(ms.value)
 
 
 def rd_set_adjoint_mode(det: int, mode: int) -> None:
@@ -431,6 +464,20 @@ class RadiationDetector:
 
     def set_chunk(self, chunk: int):
         rd_set_chunk(self._h, chunk)
+
+    def set_shape(self, cells_per_cta: int = 256, cells_per_thread: int = 2, chunk: int = 0, group: int = 0):
+        rd_set_shape(self._h, cells_per_cta, cells_per_thread, chunk, group)
+
+    def shape(self) -> dict:
+        return rd_get_shape(self._h)
+
+    def autotune_shape(self, x, u, q=None, t0: float = 0.0, dt: float = 1.0, cache_path=None, stream=None):
+        """Tune (or take from the JSON cache at cache_path) the deposit shape for these trajectories;
+        returns (shape dict, from_cache, ms).  Fields are zeroed afterwards."""
+        t, keep = self.traj_struct(x, u, q, t0, dt)
+        out = rd_autotune_shape(self._h, t, cache_path, stream)
+        del keep
+        return out
 
     def set_adjoint_mode(self, mode):
         """RD_ADJ_FP32 / "fp32" (default) or RD_ADJ_COMPENSATED / "compensated" (RD_MIXED only)."""

@@ -69,6 +69,9 @@ struct rd_detector {
     cudaGraphExec_t graph_exec = nullptr;
     long long n_deposits = 0;
     int chunk_override = 0;          // intervals per work item (0 = automatic)
+    int group_override = 0;          // cell blocks per work-order group (0 = automatic)
+    int cpc = kMixedCellsPerCta;     // RD_MIXED deposit shape: cells per CTA ...
+    int nc = kMixedCells;            // ... and cells per thread
     bool timing = false;             // record CUDA events around deposit launches
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
     long long timed_launches = 0;
@@ -215,7 +218,10 @@ void fill_mixed_params(DepositParams& P, const rd_detector* d, const rd_traj* t,
     P.lin = (d->flags & RD_LINEAR) ? 1 : (d->flags & RD_HOLD_PREV) ? 2 : 0;
     P.W = (float)(d->dt_det / t->dt);
     P.invW = (float)(t->dt / d->dt_det);
-    P.group = cell_group(P.n_cell_blocks, d->n_bins);
+    P.cpc = kMixedCellsPerCta;
+    P.nc = kMixedCells;
+    P.group = d->group_override > 0 ? std::min(d->group_override, P.n_cell_blocks)
+                                    : cell_group(P.n_cell_blocks, d->n_bins);
 }
 
 }  // namespace
@@ -255,7 +261,7 @@ int auto_chunk(long long n_cell_blocks, long long n_part, int S)
     return std::max(1, chunk);
 }
 
-int cell_group(int n_cell_blocks, int n_bins)
+int cell_group(int n_cell_blocks, int n_bins, int cells_per_cta)
 {
 #ifdef RD_GROUP
     return std::max(1, std::min(n_cell_blocks, RD_GROUP));
@@ -263,7 +269,7 @@ int cell_group(int n_cell_blocks, int n_bins)
 #ifndef RD_GROUP_SLICE_MB
 #define RD_GROUP_SLICE_MB 70
 #endif
-    const double slice = (double)kMixedCellsPerCta * n_bins * 32.0;
+    const double slice = (double)cells_per_cta * n_bins * 32.0;
     const int g = (int)((double)RD_GROUP_SLICE_MB * 1048576.0 / slice);
     return std::max(1, std::min(std::min(n_cell_blocks, 8), g));
 #endif
@@ -472,8 +478,11 @@ static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream
         st = ensure(&d->stage, &d->stage_bytes, per_part_in * pc + 256, s, "staging scratch");
         if (st != RD_OK) return st;
     }
-    const int n_cell_blocks = (d->n_pix + kDepositThreads - 1) / kDepositThreads;
+    // RD_MIXED: the detector's shape (the far-field and interpolation variants run the default one)
+    const bool def_shape = !mixed || (d->flags & (RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV));
+    const int cpc = def_shape ? kMixedCellsPerCta : d->cpc, nc = def_shape ? kMixedCells : d->nc;
     static_assert(kDepositThreads == kMixedCellsPerCta, "both deposit kernels cover 256 cells per CTA");
+    const int n_cell_blocks = (d->n_pix + (mixed ? cpc : kDepositThreads) - 1) / (mixed ? cpc : kDepositThreads);
     const int chunk = choose_chunk(d, std::min(pc, t->n_part), S - k_first + 1, n_cell_blocks);
 
     for (int p0 = 0; p0 < t->n_part; p0 += pc) {
@@ -517,7 +526,11 @@ static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream
         P.invW = (float)(t->dt / d->dt_det);
         P.ff = (d->flags & RD_FARFIELD) != 0;
         P.lin = (d->flags & RD_LINEAR) ? 1 : (d->flags & RD_HOLD_PREV) ? 2 : 0;
-        P.group = mixed ? cell_group(n_cell_blocks, d->n_bins) : 1;
+        P.cpc = cpc;
+        P.nc = nc;
+        P.group = !mixed ? 1
+                         : d->group_override > 0 ? std::min(d->group_override, n_cell_blocks)
+                                                 : cell_group(n_cell_blocks, d->n_bins, cpc);
         if (mixed) {
             RD_CUDA(launch_precompute_mixed(x, u, q, t->dt / d->dt_det, np, t->n_samples, t->dt, d->flags,
                                             static_cast<RecS*>(d->rec), d->counters, s),
@@ -752,6 +765,142 @@ rd_status rd_set_adjoint_mode(rd_detector* d, int32_t mode)
         return fail(RD_ERR_STATE, "RD_ADJ_COMPENSATED applies to RD_MIXED detectors");
     d->adjoint_mode = mode;
     return RD_OK;
+}
+
+static rd_status shape_error(const rd_shape* sh)
+{
+    if (!sh) return fail(RD_ERR_ARG, "shape is NULL");
+    if (!mixed_shape_supported(sh->cells_per_cta, sh->cells_per_thread))
+        return fail(RD_ERR_ARG, "unsupported shape: %d cells per CTA, %d per thread (64/128/256 and 1/2)",
+                    sh->cells_per_cta, sh->cells_per_thread);
+    if (sh->chunk < 0 || sh->group < 0) return fail(RD_ERR_ARG, "chunk and group must be >= 0");
+    return RD_OK;
+}
+
+rd_status rd_set_shape(rd_detector* d, const rd_shape* sh)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    rd_status st = shape_error(sh);
+    if (st != RD_OK) return st;
+    if (d->precision != RD_MIXED) return fail(RD_ERR_STATE, "shapes apply to RD_MIXED detectors");
+    d->cpc = sh->cells_per_cta;
+    d->nc = sh->cells_per_thread;
+    d->chunk_override = sh->chunk;
+    d->group_override = sh->group;
+    return RD_OK;
+}
+
+rd_status rd_get_shape(const rd_detector* d, rd_shape* sh)
+{
+    g_err.clear();
+    if (!d || !sh) return fail(RD_ERR_ARG, "detector/shape is NULL");
+    sh->cells_per_cta = d->cpc;
+    sh->cells_per_thread = d->nc;
+    sh->chunk = d->chunk_override;
+    sh->group = d->group_override;
+    return RD_OK;
+}
+
+// Tuning-cache key: the device (name, multiprocessor count) and the problem.
+static std::string shape_key(const rd_detector* d, const rd_traj* t)
+{
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, d->device) != cudaSuccess) prop.name[0] = 0;
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s|sm%d|pix%d|bins%d|part%d|int%d|flags%d", prop.name, prop.multiProcessorCount, d->n_pix,
+             d->n_bins, t->n_part, t->n_samples - 1, d->flags);
+    return buf;
+}
+
+rd_status rd_autotune_shape(rd_detector* d, const rd_traj* t, const char* cache_path, rd_stream stream,
+                            rd_shape* chosen, int32_t* from_cache, double* ms_out)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    rd_status st = check_traj(t);
+    if (st != RD_OK) return st;
+    if (d->precision != RD_MIXED) return fail(RD_ERR_STATE, "shape tuning applies to RD_MIXED detectors");
+    if (from_cache) *from_cache = 0;
+    if (ms_out) *ms_out = 0.0;
+    const int S = t->n_samples - 1;
+    const std::string key = shape_key(d, t);
+    if (cache_path) {
+        std::map<std::string, TuneEntry> cache;
+        std::string err;
+        if (!tune_cache_load(cache_path, cache, err)) return fail(RD_ERR_ARG, "%s", err.c_str());
+        const auto it = cache.find(key);
+        if (it != cache.end()) {
+            const rd_shape sh{it->second.cpc, it->second.nc, it->second.chunk, it->second.group};
+            if (shape_error(&sh) != RD_OK) return fail(RD_ERR_ARG, "tuning cache entry %s is invalid", key.c_str());
+            st = rd_set_shape(d, &sh);
+            if (st != RD_OK) return st;
+            if (from_cache) *from_cache = 1;
+            if (ms_out) *ms_out = it->second.ms;
+            if (chosen) *chosen = sh;
+            return RD_OK;
+        }
+    }
+    if (t->n_part == 0 || S < 1) return chosen ? rd_get_shape(d, chosen) : RD_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    RD_CUDA(cudaEventCreate(&e0), "autotune");
+    RD_CUDA(cudaEventCreate(&e1), "autotune");
+    rd_shape saved;
+    rd_get_shape(d, &saved);
+    const bool timing = d->timing;
+    d->timing = false;
+    rd_shape best = saved;
+    float best_ms = -1.f;
+    auto trial = [&](const rd_shape& sh) -> rd_status {
+        rd_status r = rd_set_shape(d, &sh);
+        if (r == RD_OK) r = rd_deposit_trajectories(d, t, stream);   // warm-up (also sizes the scratch)
+        if (r == RD_OK) {
+            cudaEventRecord(e0, s);
+            r = rd_deposit_trajectories(d, t, stream);
+            cudaEventRecord(e1, s);
+        }
+        if (r != RD_OK) return r;
+        if (cudaEventSynchronize(e1) != cudaSuccess) return cuda_fail(cudaGetLastError(), "autotune");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms < 0.f || ms < best_ms) {
+            best_ms = ms;
+            best = sh;
+        }
+        return RD_OK;
+    };
+    const bool variant = (d->flags & (RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV)) != 0;
+    // 1. cells per CTA x cells per thread, automatic chunk and group
+    for (int cpc : {256, 128, 64})
+        for (int nc : {2, 1}) {
+            if (variant && (cpc != kMixedCellsPerCta || nc != kMixedCells)) continue;
+            if (st == RD_OK) st = trial(rd_shape{cpc, nc, 0, 0});
+        }
+    // 2. step chunk at the best shape
+    const rd_shape b1 = best;
+    for (int c : {512, 1024, 2048, 4096})
+        if (st == RD_OK && c <= std::max(S, 512)) st = trial(rd_shape{b1.cells_per_cta, b1.cells_per_thread, std::min(c, S), 0});
+    // 3. work-order group at the best shape and chunk
+    const rd_shape b2 = best;
+    const int n_cb = (d->n_pix + b2.cells_per_cta - 1) / b2.cells_per_cta;
+    for (int g : {1, 2, 4, 8})
+        if (st == RD_OK && g <= n_cb) st = trial(rd_shape{b2.cells_per_cta, b2.cells_per_thread, b2.chunk, g});
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    d->timing = timing;
+    const rd_shape keep = st == RD_OK ? best : saved;
+    rd_set_shape(d, &keep);
+    const rd_status z = rd_zero_fields(d, stream);
+    if (st != RD_OK) return st;
+    if (cache_path) {
+        std::string err;
+        const TuneEntry e{best.cells_per_cta, best.cells_per_thread, best.chunk, best.group, (double)best_ms};
+        if (!tune_cache_store(cache_path, key, e, err)) return fail(RD_ERR_ARG, "%s", err.c_str());
+    }
+    if (chosen) *chosen = best;
+    if (ms_out) *ms_out = best_ms;
+    return z;
 }
 
 rd_status rd_set_chunk(rd_detector* d, int32_t chunk)

@@ -12,6 +12,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <string>
+
 #include "../../include/rd.h"
 
 namespace rd {
@@ -94,6 +97,8 @@ struct DepositParams {
     int lin;                    // 0: held field; 1: linear in arrival time (RD_LINEAR); 2: the previous
                                 // sample's field held (RD_HOLD_PREV); 1 and 2 carry the previous field
     int group = 1;              // mixed kernel work order: cell blocks per group (cell_group)
+    int cpc = 256;              // mixed kernel shape: cells per CTA (64, 128, 256) ...
+    int nc = 2;                 // ... and cells per thread (1, 2); n_cell_blocks counts blocks of cpc cells
 };
 
 #ifdef __CUDACC__
@@ -146,7 +151,14 @@ int grid_stride_blocks(long long n, int threads, int per_sm);
 int auto_chunk(long long n_cell_blocks, long long n_part, int S);
 // Cell blocks per group of the mixed kernels' work order (item_coords): as many as keep the group's
 // detector slice (256 cells x n_bins x 32 bytes per block) within RD_GROUP_SLICE_MB, at most 8.
-int cell_group(int n_cell_blocks, int n_bins);
+int cell_group(int n_cell_blocks, int n_bins, int cells_per_cta = 256);
+// Deposit-shape tuning cache (rd_tune.cu): entries keyed by device and problem, in a JSON file.
+struct TuneEntry {
+    int cpc, nc, chunk, group;
+    double ms;
+};
+bool tune_cache_load(const char* path, std::map<std::string, TuneEntry>& out, std::string& err);
+bool tune_cache_store(const char* path, const std::string& key, const TuneEntry& e, std::string& err);
 // Check of a detector's `flags` (include/rd.h): null if valid, else the reason.
 const char* flags_error(int flags);
 
@@ -159,6 +171,9 @@ cudaError_t launch_precompute_mixed(const double* x, const double* u, const doub
 cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part, int n_samples,
                                    double dt, RecD* rec, DevCounters* counters, cudaStream_t s);
 cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s);
+// shapes of the mixed kernel compiled into the library (held field, exact Eq. 1; the far-field and
+// interpolation variants and the batch kernel run the default shape, kMixedCellsPerCta x kMixedCells)
+bool mixed_shape_supported(int cells_per_cta, int cells_per_thread);
 cudaError_t launch_deposit_batch(const DepositParams* probs, const long long* item_off, int n_probs,
                                  unsigned long long* next_item, int grid, cudaStream_t s);
 int batch_grid();   // resident CTAs of the persistent batch kernel on the current device

@@ -27,14 +27,14 @@ namespace rd {
 
 namespace {
 
-constexpr int NC = kMixedCells;
 // Bin indices of the walk are clamped to +-2^29 so that offsets (row * n_bins + bin, with
 // n_bins <= kMixedMaxBins) and differences of two of them stay inside int32.
 constexpr double kWalkClamp = 536870912.0;
 
 __device__ __forceinline__ int walk_bin(double fb) { return (int)fmin(fmax(fb, -kWalkClamp), kWalkClamp); }
 
-// Walk state of the thread's cells.
+// Walk state of the thread's NC cells.
+template <int NC>
 struct Cells {
     float px[NC], py[NC], pz[NC];   // cell positions
     float f[NC];                    // time spent in the current bin, units of dt (0 <= f < W)
@@ -85,8 +85,8 @@ __device__ __forceinline__ void flush(const Consts& C, int b, int bo, float e0, 
 // B of a bin.  Far-field limit: every sample of a cell has the same n_c and scale (1/R_c folded
 // into S, 1/R = 1), so B = n_c x E holds for each sample's weighted field and hence for the bin
 // sums: the walk carries E only and forms B when the bin is written.  Otherwise B is carried.
-template <bool FF>
-__device__ __forceinline__ void bin_b(const Cells& c, int j, const float* e, const float* carried, float* b)
+template <int NC, bool FF>
+__device__ __forceinline__ void bin_b(const Cells<NC>& c, int j, const float* e, const float* carried, float* b)
 {
     if (FF) {
         b[0] = fmaf(c.py[j], e[2], -(c.pz[j] * e[1]));
@@ -100,13 +100,13 @@ __device__ __forceinline__ void bin_b(const Cells& c, int j, const float* e, con
 }
 
 // Add bin b of cell j from its accumulator.
-template <bool FF>
-__device__ __forceinline__ void flush_acc(const Consts& C, const Cells& c, int j, int b, int bo)
+template <int NC, bool FF>
+__device__ __forceinline__ void flush_acc(const Consts& C, const Cells<NC>& c, int j, int b, int bo)
 {
     const float e[3] = {c.acc[0][j], c.acc[1][j], c.acc[2][j]};
     const float cb[3] = {c.acc[3][j], c.acc[4][j], c.acc[5][j]};
     float bb[3];
-    bin_b<FF>(c, j, e, cb, bb);
+    bin_b<NC, FF>(c, j, e, cb, bb);
     flush(C, b, bo, e[0], e[1], e[2], bb[0], bb[1], bb[2]);
 }
 
@@ -180,15 +180,15 @@ __device__ __forceinline__ void field_at_ff(const RecS& r, float nx, float ny, f
 // Interval of cell j that passes two or more bin edges (rare): flush the bin being filled and the
 // whole bins inside the interval, leaving the state one edge short so that the common path below
 // finishes the step (it flushes the last whole bin and starts the next).
-template <bool TRACK, bool FF>
-__device__ __forceinline__ void multi_edges(Cells& c, int j, const Field& o, const Consts& C, float& fn, int k,
+template <int NC, bool TRACK, bool FF>
+__device__ __forceinline__ void multi_edges(Cells<NC>& c, int j, const Field& o, const Consts& C, float& fn, int k,
                                             int k_begin, int k_end)
 {
     const float f = fn;
     if (!(f >= 2.f * C.W)) return;
     const int b0 = c.bo[j] - c.rb[j];
     const int m = (int)fminf(floorf(f * C.invW), 16777216.f);      // edges passed, >= 2
-    flush_acc<FF>(C, c, j, b0, c.bo[j]);
+    flush_acc<NC, FF>(C, c, j, b0, c.bo[j]);
     const float fs = C.W * o.S, fb = fs * o.rinv;
     // whole bins b0+1 .. b0+m-2 now; bin b0+m-1 is left in the accumulator for the common path
     const int lo = max(b0 + 1, 0), hi = min(b0 + m - 2, C.n_bins - 1);
@@ -226,8 +226,8 @@ __device__ __forceinline__ void scaled_field(const Field& o, float* G)
 // edges (exact walk only): flush the bin being filled, every whole bin, and leave the last, partial
 // bin in the accumulator with the time already in it; fn comes back below W (no edge left for the
 // common path).
-template <bool TRACK, bool FF>
-__device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* G, float L, float inv2L,
+template <int NC, bool TRACK, bool FF>
+__device__ __forceinline__ void multi_edges_lin(Cells<NC>& c, int j, const float* G, float L, float inv2L,
                                                 const Consts& C, float& fn, int k, int k_begin, int k_end)
 {
     constexpr int NF = FF ? 3 : 6;                                  // carried field components
@@ -236,7 +236,7 @@ __device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* G,
     const float f0 = c.f[j];
     const int b0 = c.bo[j] - c.rb[j];
     const int m = (int)fminf(floorf(f * C.invW), 16777216.f);      // edges passed, >= 2
-    flush_acc<FF>(C, c, j, b0, c.bo[j]);
+    flush_acc<NC, FF>(C, c, j, b0, c.bo[j]);
     // whole bins b0+i, i = 1..m-1, cover [i W, (i+1) W] from the start of bin b0
     const int lo = max(1, -b0), hi = min(m - 1, C.n_bins - 1 - b0);
     for (int i = lo; i <= hi; ++i) {
@@ -245,7 +245,7 @@ __device__ __forceinline__ void multi_edges_lin(Cells& c, int j, const float* G,
         float v[6];
 #pragma unroll
         for (int q = 0; q < NF; ++q) v[q] = fmaf(c.gp[q][j], C.W - ramp, G[q] * ramp);
-        bin_b<FF>(c, j, v, v + 3, v + 3);
+        bin_b<NC, FF>(c, j, v, v + 3, v + 3);
         flush(C, b0 + i, c.bo[j] + i, v[0], v[1], v[2], v[3], v[4], v[5]);
     }
     // bin b0+m holds [m W, f]
@@ -276,8 +276,8 @@ enum { kFast = 0, kExact = 1 };
 // flushes the bin and starts the next one with the rest of the interval.  LAST: the interval ends
 // on the exact FP64 anchors.  TRACK: bins may lie outside the window (checked, clipped intervals
 // counted).  ok: kExact only, false from the interval that stopped the fast walk onwards.
-template <int MODE, bool LAST, bool TRACK, bool FF, bool LIN>
-__device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, const int* bo_end,
+template <int NC, int MODE, bool LAST, bool TRACK, bool FF, bool LIN>
+__device__ __forceinline__ void step(Cells<NC>& c, const RecS& r, const Consts& C, const int* bo_end,
                                      const float* f_end, int k, int k_begin, int k_end, bool* ok, float ramp)
 {
     constexpr int NF = FF ? 3 : 6;                  // carried field components (far field: E only)
@@ -326,9 +326,9 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             if (LIN)
-                multi_edges_lin<TRACK, FF>(c, j, G[j], L[j], inv2L[j], C, fn[j], k, k_begin, k_end);
+                multi_edges_lin<NC, TRACK, FF>(c, j, G[j], L[j], inv2L[j], C, fn[j], k, k_begin, k_end);
             else
-                multi_edges<TRACK, FF>(c, j, o[j], C, fn[j], k, k_begin, k_end);
+                multi_edges<NC, TRACK, FF>(c, j, o[j], C, fn[j], k, k_begin, k_end);
         }
     }
 #pragma unroll
@@ -341,7 +341,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
                 const float e[3] = {c.acc[0][j], c.acc[1][j], c.acc[2][j]};
                 const float cb[3] = {c.acc[3][j], c.acc[4][j], c.acc[5][j]};
                 float bb[3];
-                bin_b<FF>(c, j, e, cb, bb);
+                bin_b<NC, FF>(c, j, e, cb, bb);
                 red_add_v4(a, e[0], e[1], e[2], bb[0]);
                 red_add_v2(a + 4, bb[1], bb[2]);
                 const float rem = fn[j] - C.W;
@@ -371,7 +371,7 @@ __device__ __forceinline__ void step(Cells& c, const RecS& r, const Consts& C, c
             const float e[3] = {c.acc[0][j], c.acc[1][j], c.acc[2][j]};
             const float cb[3] = {c.acc[3][j], c.acc[4][j], c.acc[5][j]};
             float bb[3];
-            bin_b<FF>(c, j, e, cb, bb);
+            bin_b<NC, FF>(c, j, e, cb, bb);
             red_add_v4_if(pr, a, e[0], e[1], e[2], bb[0]);
             red_add_v2_if(pr, a + 4, bb[1], bb[2]);
             const float rem = fn[j] - C.W;
@@ -412,10 +412,9 @@ constexpr int kUnroll = RD_UNROLL > 0 ? RD_UNROLL : 1;   // samples per loop ite
 
 // Per-thread copy of the walk state at the start of a tile, in shared memory ([word][thread]).
 constexpr int kSaveCell = 17;               // f, rpd, bo, below, above, acc[6], gp[6]
-constexpr int kSaveWords = NC * kSaveCell;
 
-template <bool FF, bool LIN>
-__device__ __forceinline__ void save_state(const Cells& c, float (*sv)[kMixedThreads], int tid)
+template <int NC, int NT, bool FF, bool LIN>
+__device__ __forceinline__ void save_state(const Cells<NC>& c, float (*sv)[NT], int tid)
 {
     constexpr int NF = FF ? 3 : 6;
 #pragma unroll
@@ -434,8 +433,8 @@ __device__ __forceinline__ void save_state(const Cells& c, float (*sv)[kMixedThr
     }
 }
 
-template <bool FF, bool LIN>
-__device__ __forceinline__ void restore_state(Cells& c, float (*sv)[kMixedThreads], int tid)
+template <int NC, int NT, bool FF, bool LIN>
+__device__ __forceinline__ void restore_state(Cells<NC>& c, float (*sv)[NT], int tid)
 {
     constexpr int NF = FF ? 3 : 6;
 #pragma unroll
@@ -454,33 +453,33 @@ __device__ __forceinline__ void restore_state(Cells& c, float (*sv)[kMixedThread
     }
 }
 
-template <bool TRACK, bool FF, bool LIN>
-__device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, bool last_tile, const Consts& C,
+template <int NC, int NT, bool TRACK, bool FF, bool LIN>
+__device__ __forceinline__ void walk_tile(Cells<NC>& c, const RecS* tile, int cnt, bool last_tile, const Consts& C,
                                           float ramp, const int* bo_end, const float* f_end, int k0, int k_begin,
-                                          int k_end, float (*sv)[kMixedThreads])
+                                          int k_end, float (*sv)[NT])
 {
     const int tid = threadIdx.x;
     const int n_regular = last_tile ? cnt - 1 : cnt;
-    save_state<FF, LIN>(c, sv, tid);
+    save_state<NC, NT, FF, LIN>(c, sv, tid);
     bool ok[NC];
 #pragma unroll kUnroll
     for (int i = 0; i < n_regular; ++i)
-        step<kFast, false, TRACK, FF, LIN>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok, ramp);
+        step<NC, kFast, false, TRACK, FF, LIN>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok, ramp);
     if (last_tile)
-        step<kFast, true, TRACK, FF, LIN>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok, ramp);
+        step<NC, kFast, true, TRACK, FF, LIN>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok, ramp);
     bool stopped = false;
 #pragma unroll
     for (int j = 0; j < NC; ++j) stopped = stopped || c.f[j] == -INFINITY;
     if (__any_sync(0xffffffffu, stopped)) {
         // some interval of a cell of this warp passed two or more bin edges: walk the tile again
-        restore_state<FF, LIN>(c, sv, tid);
+        restore_state<NC, NT, FF, LIN>(c, sv, tid);
 #pragma unroll
         for (int j = 0; j < NC; ++j) ok[j] = true;
 #pragma unroll 1
         for (int i = 0; i < n_regular; ++i)
-            step<kExact, false, TRACK, FF, LIN>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok, ramp);
+            step<NC, kExact, false, TRACK, FF, LIN>(c, tile[i], C, bo_end, f_end, k0 + i, k_begin, k_end, ok, ramp);
         if (last_tile)
-            step<kExact, true, TRACK, FF, LIN>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok, ramp);
+            step<NC, kExact, true, TRACK, FF, LIN>(c, tile[cnt - 1], C, bo_end, f_end, k_end, k_begin, k_end, ok, ramp);
     }
 }
 
@@ -490,11 +489,12 @@ __device__ __forceinline__ void walk_tile(Cells& c, const RecS* tile, int cnt, b
 // CTA.  tile / bar: the CTA's shared staging buffers; g_base counts the tiles the CTA staged
 // before this item (it selects buffer and mbarrier phase, so the buffers carry over between items).
 // Returns false if a bounded wait ran out (the error is recorded; the CTA must stop).
-template <bool FF, bool LIN>
+template <bool FF, bool LIN, int NC, int CPC>
 __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int cb, int ch,
-                                             RecS (*tile)[kTileSteps], uint64_t* bar, float (*sv)[kMixedThreads],
+                                             RecS (*tile)[kTileSteps], uint64_t* bar, float (*sv)[CPC / NC],
                                              unsigned& g_base)
 {
+    constexpr int NT = CPC / NC;                // threads of the CTA
     const int S = P.n_samples - 1;
     const int k_begin = P.k_first + ch * P.chunk;
     const int k_end = min(S, k_begin + P.chunk - 1);
@@ -519,10 +519,10 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
     C.invW = P.invW;
     C.DT = P.dt_f;
     C.n_bins = P.n_bins;
-    C.base = static_cast<float*>(P.fields) + (size_t)cb * kMixedCellsPerCta * P.n_bins * 8;
+    C.base = static_cast<float*>(P.fields) + (size_t)cb * CPC * P.n_bins * 8;
 
     // anchors: exact FP64 arrival (bins) at both ends of the chunk, per cell
-    Cells c;
+    Cells<NC> c;
     int bo_end[NC];
     float f_end[NC];
     bool partial = false;
@@ -530,8 +530,8 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
     const double* xp = P.x + (size_t)p * P.n_samples * 3;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        const int row = j * kMixedThreads + tid;
-        const int cell = cb * kMixedCellsPerCta + row;
+        const int row = j * NT + tid;
+        const int cell = cb * CPC + row;
         // a cell without arrivals in the window still walks (no per-cell branch in the step) but
         // from a time that never reaches a bin edge: nothing is flushed
         c.rb[j] = row * P.n_bins;
@@ -629,10 +629,10 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
         const int cnt = min(kTileSteps, k_end - k0 + 1);
         const bool last_tile = (t == n_tiles - 1);
         if (track)
-            walk_tile<true, FF, LIN>(c, tile[buf], cnt, last_tile, C, P.lin == 1 ? 1.f : 0.f, bo_end, f_end, k0,
+            walk_tile<NC, NT, true, FF, LIN>(c, tile[buf], cnt, last_tile, C, P.lin == 1 ? 1.f : 0.f, bo_end, f_end, k0,
                                      k_begin, k_end, sv);
         else
-            walk_tile<false, FF, LIN>(c, tile[buf], cnt, last_tile, C, P.lin == 1 ? 1.f : 0.f, bo_end, f_end, k0,
+            walk_tile<NC, NT, false, FF, LIN>(c, tile[buf], cnt, last_tile, C, P.lin == 1 ? 1.f : 0.f, bo_end, f_end, k0,
                                       k_begin, k_end, sv);
         __syncthreads();
         if (tid == 0 && t + 2 < n_tiles) {
@@ -648,7 +648,7 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         if (c.live[j]) {
-            flush_acc<FF>(C, c, j, c.bo[j] - c.rb[j], c.bo[j]);
+            flush_acc<NC, FF>(C, c, j, c.bo[j] - c.rb[j], c.bo[j]);
             clip += (unsigned long long)min(n_int, c.below[j] + c.above[j]);
         }
     }
@@ -670,17 +670,22 @@ __device__ __forceinline__ void init_staging(uint64_t* bar)
     __syncthreads();
 }
 
-template <bool FF, bool LIN>
-__global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS) k_deposit_mixed(const DepositParams P)
+// Resident CTAs per SM the register allotment must allow: about 640 threads, as for the default
+// shape (2 cells per thread, 256 cells per CTA: 128 threads, 5 CTAs).
+constexpr int mixed_min_blocks(int nt) { return nt >= 128 ? (nt == 128 ? RD_MIXED_MINBLOCKS : 640 / nt) : 640 / nt; }
+
+template <bool FF, bool LIN, int NC, int CPC>
+__global__ void __launch_bounds__(CPC / NC, mixed_min_blocks(CPC / NC)) k_deposit_mixed(const DepositParams P)
 {
+    constexpr int NT = CPC / NC;
     __shared__ __align__(128) RecS tile[2][kTileSteps];
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ float sv[kSaveWords][kMixedThreads];
+    __shared__ float sv[NC * kSaveCell][NT];
     init_staging(bar);
     int p, cb, ch;
     item_coords(blockIdx.x, P, p, cb, ch);
     unsigned g = 0;
-    (void)deposit_item<FF, LIN>(P, p, cb, ch, tile, bar, sv, g);
+    (void)deposit_item<FF, LIN, NC, CPC>(P, p, cb, ch, tile, bar, sv, g);
 }
 
 // Persistent form: the resident CTAs draw work items of all problems from one counter.
@@ -693,7 +698,7 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS)
     __shared__ __align__(128) RecS tile[2][kTileSteps];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ long long s_item;
-    __shared__ float sv[kSaveWords][kMixedThreads];
+    __shared__ float sv[kMixedCells * kSaveCell][kMixedThreads];
     init_staging(bar);
     const long long total = item_off[n_probs];
     unsigned g = 0;
@@ -713,11 +718,11 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS)
         item_coords((unsigned)(item - item_off[lo]), P, p, cb, ch);
         bool ok;
         if (P.lin)
-            ok = P.ff ? deposit_item<true, true>(P, p, cb, ch, tile, bar, sv, g)
-                      : deposit_item<false, true>(P, p, cb, ch, tile, bar, sv, g);
+            ok = P.ff ? deposit_item<true, true, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g)
+                      : deposit_item<false, true, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g);
         else
-            ok = P.ff ? deposit_item<true, false>(P, p, cb, ch, tile, bar, sv, g)
-                      : deposit_item<false, false>(P, p, cb, ch, tile, bar, sv, g);
+            ok = P.ff ? deposit_item<true, false, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g)
+                      : deposit_item<false, false, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g);
         if (!ok) break;
     }
 }
@@ -738,19 +743,54 @@ int batch_grid()
     return std::max(1, sms) * std::max(1, per_sm);
 }
 
+#ifndef RD_CARVEOUT
+#define RD_CARVEOUT 0
+#endif
+
+template <bool FF, bool LIN, int NC, int CPC>
+static void launch_mixed(const DepositParams& p, unsigned blocks, cudaStream_t s)
+{
+    if (RD_CARVEOUT) {
+        // the largest shared-memory carveout, so that shared memory does not cap the resident CTAs
+        static bool done = false;
+        if (!done) {
+            cudaFuncSetAttribute(k_deposit_mixed<FF, LIN, NC, CPC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+            done = true;
+        }
+    }
+    k_deposit_mixed<FF, LIN, NC, CPC><<<blocks, CPC / NC, 0, s>>>(p);
+}
+
+bool mixed_shape_supported(int cells_per_cta, int cells_per_thread)
+{
+    return (cells_per_cta == 64 || cells_per_cta == 128 || cells_per_cta == 256) &&
+           (cells_per_thread == 1 || cells_per_thread == 2);
+}
+
 cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s)
 {
     const long long blocks = (long long)p.n_cell_blocks * p.n_part * p.n_chunks;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if (p.ff && p.lin)
-        k_deposit_mixed<true, true><<<(unsigned)blocks, kMixedThreads, 0, s>>>(p);
-    else if (p.ff)
-        k_deposit_mixed<true, false><<<(unsigned)blocks, kMixedThreads, 0, s>>>(p);
-    else if (p.lin)
-        k_deposit_mixed<false, true><<<(unsigned)blocks, kMixedThreads, 0, s>>>(p);
-    else
-        k_deposit_mixed<false, false><<<(unsigned)blocks, kMixedThreads, 0, s>>>(p);
+    const unsigned b = (unsigned)blocks;
+    if (p.ff || p.lin) {
+        // the far-field and interpolation variants run in the default shape only
+        if (p.cpc != kMixedCellsPerCta || p.nc != kMixedCells) return cudaErrorInvalidValue;
+        if (p.ff && p.lin) launch_mixed<true, true, kMixedCells, kMixedCellsPerCta>(p, b, s);
+        else if (p.ff) launch_mixed<true, false, kMixedCells, kMixedCellsPerCta>(p, b, s);
+        else launch_mixed<false, true, kMixedCells, kMixedCellsPerCta>(p, b, s);
+        return cudaGetLastError();
+    }
+    switch (p.cpc * 8 + p.nc) {
+    case 256 * 8 + 2: launch_mixed<false, false, 2, 256>(p, b, s); break;
+    case 128 * 8 + 2: launch_mixed<false, false, 2, 128>(p, b, s); break;
+    case 64 * 8 + 2: launch_mixed<false, false, 2, 64>(p, b, s); break;
+    case 256 * 8 + 1: launch_mixed<false, false, 1, 256>(p, b, s); break;
+    case 128 * 8 + 1: launch_mixed<false, false, 1, 128>(p, b, s); break;
+    case 64 * 8 + 1: launch_mixed<false, false, 1, 64>(p, b, s); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

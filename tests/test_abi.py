@@ -126,3 +126,12 @@ def test_argument_errors_without_gpu():
                                       ctypes.byref(t), 16, None, None) == rd.RD_ERR_ARG, flags
     assert "Eq. 1" in (lib.rd_deposit_noalloc(ctypes.cast(cells, ctypes.c_void_p), None, 1, 0.0, 0.1, 8,
                                               rd.RD_LINEAR, ctypes.byref(t), 16, None, None) and rd.rd_last_error())
+
+
+def test_shape_entry_points_refuse_bad_arguments():
+    lib = rd.load_library()
+    sh = rd.rd_shape(256, 2, 0, 0)
+    assert lib.rd_set_shape(None, ctypes.byref(sh)) == rd.RD_ERR_ARG
+    assert lib.rd_get_shape(None, ctypes.byref(sh)) == rd.RD_ERR_ARG
+    assert lib.rd_autotune_shape(None, None, None, None, None, None, None) == rd.RD_ERR_ARG
+    assert lib.rd_set_adjoint_mode(None, 1) == rd.RD_ERR_ARG
