@@ -5,7 +5,8 @@ are the only users.  The product path (the CUDA library and its binding) never i
 package, and the two share no code.
 
 Parity of each function:
-  field, beta, arrival_time, bin_coord, deposit_interval, deposit  -- pinned by tests/test_oracle_*.py
+  field, beta, arrival_time, bin_coord, deposit_interval, deposit_interval_lin, deposit_interval_quad,
+  deposit (all flag variants)                                       -- pinned by tests/test_oracle_*.py
   deposit_dir (complex-step derivative)                            -- pinned by central finite differences
   deposit_ext (long double evaluation of deposit)                   -- pinned against deposit where FP64 rounding
                                                                       is negligible, and against the rounding
@@ -64,6 +65,11 @@ def _load():
             lib.rdo_bin_coord.restype = ctypes.c_double
             lib.rdo_deposit_interval.argtypes = [ctypes.c_double, ctypes.c_double, D, ctypes.c_int32, D]
             lib.rdo_deposit_interval.restype = ctypes.c_int32
+            lib.rdo_deposit_interval_lin.argtypes = [ctypes.c_double, ctypes.c_double, D, D, ctypes.c_int32, D]
+            lib.rdo_deposit_interval_lin.restype = ctypes.c_int32
+            lib.rdo_deposit_interval_quad.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, D, D, D,
+                                                      ctypes.c_int32, D]
+            lib.rdo_deposit_interval_quad.restype = ctypes.c_int32
             lib.rdo_beta.argtypes = [D, D]
             lib.rdo_beta.restype = None
             lib.rdo_deposit.argtypes = [ctypes.POINTER(_Problem), ctypes.c_void_p, ctypes.c_int32, D, D,
@@ -133,6 +139,25 @@ def deposit_interval(a, c, F, n_bins, row=None):
         row = np.zeros((n_bins, 6))
     Fs = _vec(F)
     clipped = lib.rdo_deposit_interval(float(a), float(c), _dp(Fs), int(n_bins), _dp(row))
+    return row, int(clipped)
+
+
+def deposit_interval_lin(a, c, F0, F1, n_bins, row=None):
+    """Deposit the field going linearly from F0 at a to F1 at c (bin units) into row[n_bins][6]."""
+    lib = _load()
+    if row is None:
+        row = np.zeros((n_bins, 6))
+    clipped = lib.rdo_deposit_interval_lin(float(a), float(c), _dp(_vec(F0)), _dp(_vec(F1)), int(n_bins), _dp(row))
+    return row, int(clipped)
+
+
+def deposit_interval_quad(p, a, c, Fp, Fa, Fc, n_bins, row=None):
+    """Deposit over [a, c] the quadratic through (p, Fp), (a, Fa), (c, Fc) (bin units) into row[n_bins][6]."""
+    lib = _load()
+    if row is None:
+        row = np.zeros((n_bins, 6))
+    clipped = lib.rdo_deposit_interval_quad(float(p), float(a), float(c), _dp(_vec(Fp)), _dp(_vec(Fa)),
+                                            _dp(_vec(Fc)), int(n_bins), _dp(row))
     return row, int(clipped)
 
 

@@ -118,6 +118,19 @@ int32_t rdo_deposit_interval(double a, double c, const double F[6], int32_t n_bi
     return deposit_interval_r(a, c, F, n_bins, row);
 }
 
+/* The linear-in-time interval (flags bit 8) and the quadratic one (flags bit 32), for the pins. */
+int32_t rdo_deposit_interval_lin(double a, double c, const double F0[6], const double F1[6], int32_t n_bins,
+                                 double* row)
+{
+    return deposit_interval_lin_r(a, c, F0, F1, n_bins, row);
+}
+
+int32_t rdo_deposit_interval_quad(double p, double a, double c, const double Fp[6], const double Fa[6],
+                                  const double Fc[6], int32_t n_bins, double* row)
+{
+    return deposit_interval_quad_r(p, a, c, Fp, Fa, Fc, n_bins, row);
+}
+
 void rdo_beta(const double u[3], double beta[3]) { beta_of_r(u, beta); }
 
 /* ------------------------------------------------------------------------------------------ */

@@ -173,6 +173,44 @@ static int FN(deposit_interval_lin)(SCALAR a, SCALAR c, const SCALAR F0[6], cons
 }
 
 /*
+ * Quadratic-in-time variant (flags bit 32; the next order after the linear one): over the arrival
+ * interval [a, c] of sample k the field is the quadratic through (p, F_{k-2}), (a, F_{k-1}),
+ * (c, F_k), p = t_det,k-2 < a, written in Newton form about a with s = tau - a, L = c - a, h = a - p:
+ *     F(s) = Fa + D1 s + D2 s (s - L),   D1 = (Fc - Fa) / L,   D0 = (Fa - Fp) / h,
+ *     D2 = (D1 - D0) / (L + h)   (the second divided difference),
+ * and bin b receives its integral over the overlap [s0, s1] of [a, c] with [b, b+1):
+ *     Fa (s1 - s0) + D1 (s1^2 - s0^2) / 2 + D2 ((s1^3 - s0^3) / 3 - L (s1^2 - s0^2) / 2).
+ */
+static int FN(deposit_interval_quad)(SCALAR p, SCALAR a, SCALAR c, const SCALAR Fp[6], const SCALAR Fa[6],
+                                     const SCALAR Fc[6], int n_bins, SCALAR* row)
+{
+    double ra = RE(a), rc = RE(c);
+    int clipped = (ra < 0.0) || (rc > (double)n_bins);
+    if (rc <= 0.0 || ra >= (double)n_bins) return 1;
+    SCALAR L = c - a, h = a - p;
+    SCALAR D1[6], D2[6];
+    for (int i = 0; i < 6; ++i) {
+        SCALAR D0 = (Fa[i] - Fp[i]) / h;
+        D1[i] = (Fc[i] - Fa[i]) / L;
+        D2[i] = (D1[i] - D0) / (L + h);
+    }
+    long long first = floor(ra) < 0.0 ? 0 : (long long)floor(ra);
+    long long last = floor(rc) > (double)(n_bins - 1) ? (long long)(n_bins - 1) : (long long)floor(rc);
+    for (long long b = first; b <= last; ++b) {
+        SCALAR u0 = (ra > (double)b) ? a : (SCALAR)(double)b;
+        SCALAR u1 = (rc < (double)(b + 1)) ? c : (SCALAR)(double)(b + 1);
+        SCALAR len = u1 - u0;
+        if (RE(len) > 0.0) {
+            SCALAR s0 = u0 - a, s1 = u1 - a;
+            SCALAR sq = (s1 * s1 - s0 * s0) / 2.0;
+            SCALAR cu = (s1 * s1 * s1 - s0 * s0 * s0) / 3.0 - L * sq;
+            for (int i = 0; i < 6; ++i) row[6 * b + i] += Fa[i] * len + D1[i] * sq + D2[i] * cu;
+        }
+    }
+    return clipped;
+}
+
+/*
  * One (cell, particle) pair: Algorithm 1 inner body for every interval k = 1..S.
  *   beta_k from u_k; betadot_k = (beta_k - beta_{k-1}) / dt (backward difference);
  *   the field of sample k is held over [t_det,k-1, t_det,k] (the algorithm passes the current
@@ -182,6 +220,9 @@ static int FN(deposit_interval_lin)(SCALAR a, SCALAR c, const SCALAR F0[6], cons
  * flags bit 16: from interval 2 on, the interval holds the field of its first sample, F_{k-1}
  * (the other reading of which field the interpolation holds: the worked example of Section 3.2
  * writes, for the interval ending at t'_4, the field at t'_3); interval 1 holds F_1.
+ * flags bit 32: from interval 3 on, the quadratic through the fields of samples k-2, k-1, k at
+ * their arrival times (deposit_interval_quad); interval 2 is linear (F_1 to F_2), interval 1 holds
+ * F_1 (sample 0 has no field, so the first two intervals have fewer than three fields behind them).
  * x, u point at this particle's samples [n_samples][3]; row is [n_bins][6] (E xyz, B xyz).
  * Returns the number of intervals that had a part outside the window.
  */
@@ -189,10 +230,11 @@ static long long FN(pixel_particle)(const SCALAR* x, const SCALAR* u, int n_samp
                                     double t0, double dt, const double P[3], double T0,
                                     double inv_dt_det, int n_bins, int flags, SCALAR* row)
 {
-    SCALAR beta_prev[3], beta[3], bdot[3], E[3], B[3], F[6], Fprev[6];
+    SCALAR beta_prev[3], beta[3], bdot[3], E[3], B[3], F[6], Fprev[6], Fpp[6];
     long long clipped = 0;
     FN(beta_of)(u, beta_prev);
     SCALAR a = FN(bin_coord)(t0, 0, dt, x, P, T0, inv_dt_det, flags);
+    SCALAR ap = a;                                   /* arrival of sample k-2 */
     for (int k = 1; k < n_samples; ++k) {
         const SCALAR* xk = x + 3 * (size_t)k;
         FN(beta_of)(u + 3 * (size_t)k, beta);
@@ -203,13 +245,19 @@ static long long FN(pixel_particle)(const SCALAR* x, const SCALAR* u, int n_samp
             FN(lw_field)(xk, beta, bdot, P, q, flags, E, B);
         for (int i = 0; i < 3; ++i) { F[i] = E[i]; F[3 + i] = B[i]; }
         SCALAR c = FN(bin_coord)(t0, k, dt, xk, P, T0, inv_dt_det, flags);
-        if ((flags & 8) && k > 1)
+        if ((flags & 32) && k > 2)
+            clipped += FN(deposit_interval_quad)(ap, a, c, Fpp, Fprev, F, n_bins, row);
+        else if ((flags & (8 | 32)) && k > 1)
             clipped += FN(deposit_interval_lin)(a, c, Fprev, F, n_bins, row);
         else if ((flags & 16) && k > 1)
             clipped += FN(deposit_interval)(a, c, Fprev, n_bins, row);
         else
             clipped += FN(deposit_interval)(a, c, F, n_bins, row);
-        for (int i = 0; i < 6; ++i) Fprev[i] = F[i];
+        for (int i = 0; i < 6; ++i) {
+            Fpp[i] = Fprev[i];
+            Fprev[i] = F[i];
+        }
+        ap = a;
         a = c;
         for (int i = 0; i < 3; ++i) beta_prev[i] = beta[i];
     }

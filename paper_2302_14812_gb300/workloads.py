@@ -31,6 +31,7 @@ RD_FAR = 2
 RD_FARFIELD = 4
 RD_LINEAR = 8
 RD_HOLD_PREV = 16
+RD_QUADRATIC = 32
 
 
 @dataclasses.dataclass

@@ -44,6 +44,11 @@ MUTATIONS = {
                             "SCALAR ramp = ((u1 - a) * (u1 - a) - (u0 - a) * (u0 - a)) / (c - a);"),
     "linear_ends_exchanged": ("row[6 * b + i] += F0[i] * len + (F1[i] - F0[i]) * ramp;",
                               "row[6 * b + i] += F1[i] * len + (F0[i] - F1[i]) * ramp;"),
+    # quadratic-in-time interpolation: the curvature term's sign; the second divided difference over
+    # the interval alone instead of the span of the three points
+    "quadratic_curvature_sign": ("row[6 * b + i] += Fa[i] * len + D1[i] * sq + D2[i] * cu;",
+                                 "row[6 * b + i] += Fa[i] * len + D1[i] * sq - D2[i] * cu;"),
+    "quadratic_divided_difference": ("D2[i] = (D1[i] - D0) / (L + h);", "D2[i] = (D1[i] - D0) / L;"),
     # held-previous field: the current sample's field held instead
     "hold_previous_uses_current": ("clipped += FN(deposit_interval)(a, c, Fprev, n_bins, row);",
                                    "clipped += FN(deposit_interval)(a, c, F, n_bins, row);"),

@@ -828,3 +828,115 @@ def test_extended_precision_sum_rule(oracle_lib, gamma):
         assert err_64 > 100.0 * err_ext, (err_64, err_ext)
     else:
         assert err_64 < 1e-6, err_64
+
+
+# --------------------------------------------------------------------------------------------
+# Quadratic-in-time interpolation (flags bit 32)
+# --------------------------------------------------------------------------------------------
+def _quad_integral(p, a, c, Fp, Fa, Fc, s0, s1):
+    """Integral over [s0, s1] of the quadratic through (p, Fp), (a, Fa), (c, Fc), component by
+    component, from numpy's polynomial fit through the three points (abscissae taken from a, which
+    keeps the fit well conditioned) and its antiderivative."""
+    out = np.zeros(6)
+    for i in range(6):
+        coef = np.polyfit([p - a, 0.0, c - a], [Fp[i], Fa[i], Fc[i]], 2)
+        prim = np.polyint(coef)
+        out[i] = np.polyval(prim, s1 - a) - np.polyval(prim, s0 - a)
+    return out
+
+
+def test_quadratic_interval_exact_and_reductions(oracle_lib):
+    """The quadratic interval deposit integrates the quadratic through its three points exactly over
+    every bin it touches (numpy fit and antiderivative), reduces to the linear deposit when the three
+    fields lie on a line, to the held deposit when they are equal, and clips at the window edges."""
+    rng = np.random.default_rng(8)
+    for _ in range(20):
+        p = rng.uniform(0.5, 2.0)
+        a = p + rng.uniform(0.3, 1.7)
+        c = a + rng.uniform(0.2, 2.6)
+        Fp, Fa, Fc = rng.normal(size=(3, 6))
+        row, clipped = oracle.deposit_interval_quad(p, a, c, Fp, Fa, Fc, 8)
+        assert clipped == 0
+        for b in range(8):
+            s0, s1 = max(a, b), min(c, b + 1)
+            want = _quad_integral(p, a, c, Fp, Fa, Fc, s0, s1) if s1 > s0 else np.zeros(6)
+            np.testing.assert_allclose(row[b], want, rtol=1e-10, atol=1e-12)
+        # fields on a line in arrival time: the linear deposit; equal fields: the held one
+        slope = rng.normal(size=6)
+        lin_row, _ = oracle.deposit_interval_lin(a, c, Fa, Fa + slope * (c - a), 8)
+        q_row, _ = oracle.deposit_interval_quad(p, a, c, Fa - slope * (a - p), Fa, Fa + slope * (c - a), 8)
+        np.testing.assert_allclose(q_row, lin_row, rtol=1e-12, atol=1e-13)
+        held, _ = oracle.deposit_interval(a, c, Fa, 8)
+        q_row, _ = oracle.deposit_interval_quad(p, a, c, Fa, Fa, Fa, 8)
+        np.testing.assert_allclose(q_row, held, rtol=1e-13, atol=1e-14)
+    row, clipped = oracle.deposit_interval_quad(-2.0, -1.0, 1.5, np.ones(6), np.ones(6), np.ones(6), 1)
+    assert clipped == 1 and np.allclose(row[0], 1.0)
+
+
+def test_quadratic_interpolation_sum_rule(oracle_lib):
+    """With every arrival inside the window, the bins of a cell add up to the integrals of the
+    interpolant over the arrival intervals: F_1 held on the first, the line F_1 -> F_2 on the second,
+    and from the third on the quadratic through samples k-2, k-1, k (numpy fit and antiderivative)."""
+    tr = W.random_smooth(2, 60, 0.02, max_u=2.0, seed=13)
+    P = np.array([[-7.0, 11.0, 2.0]])
+    det = W.Detector(P, None, 0.0, 0.05, 2000, flags=W.RD_NEAR | W.RD_FAR | W.RD_QUADRATIC)
+    E, B, clipped = oracle.deposit(tr, det)
+    assert clipped == 0
+    want = np.zeros(6)
+    for p in range(tr.n_part):
+        F, u = _sample_fields(tr, p, P[0], W.RD_NEAR | W.RD_FAR)
+        want += F[1] * (u[1] - u[0]) + 0.5 * (F[1] + F[2]) * (u[2] - u[1])
+        for k in range(3, tr.n_samples):
+            want += _quad_integral(u[k - 2], u[k - 1], u[k], F[k - 2], F[k - 1], F[k], u[k - 1], u[k])
+    got = np.concatenate([E[0].sum(axis=0), B[0].sum(axis=0)])
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-11 * np.abs(want).max())
+
+
+def test_quadratic_interpolation_brute_force(oracle_lib):
+    """One particle, 12 samples, bins about as long as the intervals: each bin equals a fine
+    midpoint-rule integral of the piecewise-quadratic emission."""
+    tr = W.random_smooth(1, 11, 0.05, max_u=1.5, seed=19)
+    P = np.array([[2.0, -3.0, 1.5]])
+    F, u = _sample_fields(tr, 0, P[0], W.RD_NEAR | W.RD_FAR)
+    lo = int(np.floor(u[0])) - 1
+    det = W.Detector(P, None, lo * 0.05, 0.05, int(np.ceil(u[-1])) - lo + 2,
+                     flags=W.RD_NEAR | W.RD_FAR | W.RD_QUADRATIC)
+    E, B, clipped = oracle.deposit(tr, det)
+    assert clipped == 0
+    uu = u - lo
+    got = np.concatenate([E[0], B[0]], axis=1)
+    n_sub = 20000
+    for b in range(det.n_bins):
+        s = b + (np.arange(n_sub) + 0.5) / n_sub
+        val = np.zeros((n_sub, 6))
+        val[(s >= uu[0]) & (s < uu[1])] = F[1]
+        m = (s >= uu[1]) & (s < uu[2])
+        if np.any(m):
+            w = ((s[m] - uu[1]) / (uu[2] - uu[1]))[:, None]
+            val[m] = (1.0 - w) * F[1] + w * F[2]
+        for k in range(3, tr.n_samples):
+            m = (s >= uu[k - 1]) & (s < uu[k])
+            if np.any(m):
+                for i in range(6):
+                    coef = np.polyfit([uu[k - 2] - uu[k - 1], 0.0, uu[k] - uu[k - 1]],
+                                      [F[k - 2][i], F[k - 1][i], F[k][i]], 2)
+                    val[m, i] = np.polyval(coef, s[m] - uu[k - 1])
+        # the bins holding the emission's start and end see a step from or to zero, which the midpoint
+        # samples resolve to ~1/n_sub of the field; every other bin agrees to rounding
+        edge = b == int(np.floor(uu[0])) or b == int(np.floor(uu[-1]))
+        np.testing.assert_allclose(got[b], val.mean(axis=0), rtol=1e-9,
+                                   atol=(1e-4 if edge else 1e-11) * np.abs(got).max())
+
+
+def test_quadratic_interpolation_is_third_order(oracle_lib):
+    """The circular-orbit velocity field of the second-order test: halving dt cuts the change of the
+    deposit eightfold with the quadratic interpolation (fourfold linear, twofold held)."""
+    P = np.array([[6.0, 2.0, 1.0]])
+    period = 2.0 * math.pi / math.sqrt(0.75)
+    Ds = []
+    for m in (1, 2, 4):
+        tr = W.circular_orbit(gamma=2.0, radius=1.0, n_steps=200 * m, dt_frac=0.01 / m)
+        det = W.Detector(P, None, 7.0, period / 50.0, 80, flags=W.RD_NEAR | W.RD_QUADRATIC)
+        Ds.append(oracle.deposit(tr, det)[0][0])
+    ratio = np.linalg.norm(Ds[0] - Ds[1]) / np.linalg.norm(Ds[1] - Ds[2])
+    assert 7.0 < ratio < 9.0, ratio
