@@ -72,10 +72,13 @@ enum { RD_FP64 = 0, RD_MIXED = 1 };
  * trajectory still holds the field of sample 1).  RD_HOLD_PREV (instead of RD_LINEAR) holds the
  * field of sample k-1 over interval k (the reading of Section 3.2's worked example, which writes
  * the field at the interval's start; first order like the default, which holds the field of
- * sample k as Algorithm 2 passes it); interval 1 holds the field of sample 1.  Neither is
- * supported by rd_adjoint_trajectories.
+ * sample k as Algorithm 2 passes it); interval 1 holds the field of sample 1.  RD_QUADRATIC (instead
+ * of the two) makes the field over interval k the quadratic in arrival time through the fields of
+ * samples k-2, k-1 and k at their arrival times, integrated exactly over each bin overlap (third
+ * order in dt); interval 2 is linear and interval 1 holds the field of sample 1 (the first samples
+ * have fewer fields behind them).  None of the three is supported by rd_adjoint_trajectories.
  */
-enum { RD_NEAR = 1, RD_FAR = 2, RD_FARFIELD = 4, RD_LINEAR = 8, RD_HOLD_PREV = 16 };
+enum { RD_NEAR = 1, RD_FAR = 2, RD_FARFIELD = 4, RD_LINEAR = 8, RD_HOLD_PREV = 16, RD_QUADRATIC = 32 };
 /* where a caller buffer lives; RD_MEM_HOST_ASYNC: pinned host memory written asynchronously
  * (rd_read_fields only) */
 enum { RD_MEM_DEVICE = 0, RD_MEM_HOST = 1, RD_MEM_HOST_ASYNC = 2 };
@@ -103,7 +106,7 @@ typedef struct {
     int32_t n_bins;            /* >= 1; <= 4194304 (2^22) for RD_MIXED                          */
     int32_t precision;         /* RD_MIXED or RD_FP64                                           */
     int32_t flags;             /* RD_NEAR | RD_FAR (0 = both), or RD_FAR | RD_FARFIELD;
-                                  | RD_LINEAR or | RD_HOLD_PREV                                   */
+                                  | RD_LINEAR, | RD_HOLD_PREV or | RD_QUADRATIC                   */
 } rd_detector_desc;
 
 /*

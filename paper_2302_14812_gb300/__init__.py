@@ -33,7 +33,7 @@ __all__ = [
 
 RD_OK, RD_ERR_ARG, RD_ERR_CUDA, RD_ERR_OOM, RD_ERR_STATE, RD_ERR_TIMEOUT, RD_ERR_BOUNDS, RD_ERR_INPUT = range(8)
 RD_FP64, RD_MIXED = 0, 1
-RD_NEAR, RD_FAR, RD_FARFIELD, RD_LINEAR, RD_HOLD_PREV = 1, 2, 4, 8, 16
+RD_NEAR, RD_FAR, RD_FARFIELD, RD_LINEAR, RD_HOLD_PREV, RD_QUADRATIC = 1, 2, 4, 8, 16, 32
 RD_MEM_DEVICE, RD_MEM_HOST, RD_MEM_HOST_ASYNC = 0, 1, 2
 RD_F32, RD_F64 = 0, 1
 RD_SPEC_E, RD_SPEC_B = 0, 1

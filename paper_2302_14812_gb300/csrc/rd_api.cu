@@ -57,12 +57,14 @@ struct rd_detector {
     int spec_n = 0;
     std::vector<float2> spec_tw_host;
     // streamed deposits: the last sample (x, u) of every particle from the previous call
-    void* strm_last = nullptr;       // x then u, each [n_part][2][3] doubles (last samples)
+    void* strm_last = nullptr;       // x then u, each [n_part][3][3] doubles (last samples)
     size_t strm_last_bytes = 0;
     void* strm_stage = nullptr;      // this call's samples with the stored one in front, and q
     size_t strm_stage_bytes = 0;
     int strm_n_part = -1;            // -1: no stream in progress
-    int strm_have = 0;               // samples kept per particle (1, or 2 with RD_LINEAR / RD_HOLD_PREV)
+    int strm_have = 0;               // samples kept per particle (1; 2 with RD_LINEAR / RD_HOLD_PREV; 3 with
+                                     // RD_QUADRATIC)
+    long long strm_count = 0;        // samples of the stream handed over so far
     double strm_t_last = 0.0;
     double strm_dt = 0.0;
     std::vector<unsigned long long> graph_key;
@@ -215,7 +217,7 @@ void fill_mixed_params(DepositParams& P, const rd_detector* d, const rd_traj* t,
     P.dt_f = (float)t->dt;
     P.du_scale = (float)(t->dt / d->dt_det);
     P.ff = (d->flags & RD_FARFIELD) != 0;
-    P.lin = (d->flags & RD_LINEAR) ? 1 : (d->flags & RD_HOLD_PREV) ? 2 : 0;
+    P.lin = (d->flags & RD_LINEAR) ? 1 : (d->flags & RD_HOLD_PREV) ? 2 : (d->flags & RD_QUADRATIC) ? 3 : 0;
     P.W = (float)(d->dt_det / t->dt);
     P.invW = (float)(t->dt / d->dt_det);
     P.cpc = kMixedCellsPerCta;
@@ -277,8 +279,9 @@ int cell_group(int n_cell_blocks, int n_bins, int cells_per_cta)
 
 const char* flags_error(int flags)
 {
-    if (flags & ~(RD_NEAR | RD_FAR | RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV)) return "unknown flag bits";
-    if ((flags & RD_LINEAR) && (flags & RD_HOLD_PREV)) return "RD_LINEAR and RD_HOLD_PREV are alternatives";
+    if (flags & ~(RD_NEAR | RD_FAR | RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV | RD_QUADRATIC)) return "unknown flag bits";
+    const int interp = flags & (RD_LINEAR | RD_HOLD_PREV | RD_QUADRATIC);
+    if (interp & (interp - 1)) return "RD_LINEAR, RD_HOLD_PREV and RD_QUADRATIC are alternatives";
     if ((flags & (RD_NEAR | RD_FAR)) == 0 && flags != 0)
         return "flags select no term of Eq. 1 (RD_NEAR and/or RD_FAR)";
     if ((flags & RD_FARFIELD) && (flags & RD_NEAR))
@@ -455,7 +458,7 @@ rd_status rd_zero_fields(rd_detector* d, rd_stream stream)
 
 // Deposit intervals k_first..S of t (k_first > 1: the earlier samples only provide the
 // previous quantities, used by streamed calls).
-static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream, int k_first)
+static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream, int k_first, int k_real0 = 0)
 {
     g_err.clear();
     if (!d) return fail(RD_ERR_ARG, "detector is NULL");
@@ -479,7 +482,7 @@ static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream
         if (st != RD_OK) return st;
     }
     // RD_MIXED: the detector's shape (the far-field and interpolation variants run the default one)
-    const bool def_shape = !mixed || (d->flags & (RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV));
+    const bool def_shape = !mixed || (d->flags & (RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV | RD_QUADRATIC));
     const int cpc = def_shape ? kMixedCellsPerCta : d->cpc, nc = def_shape ? kMixedCells : d->nc;
     static_assert(kDepositThreads == kMixedCellsPerCta, "both deposit kernels cover 256 cells per CTA");
     const int n_cell_blocks = (d->n_pix + (mixed ? cpc : kDepositThreads) - 1) / (mixed ? cpc : kDepositThreads);
@@ -515,6 +518,7 @@ static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream
         P.n_part = np;
         P.chunk = chunk;
         P.k_first = k_first;
+        P.k_real0 = k_real0;
         P.n_chunks = (S - k_first + chunk) / chunk;
         P.n_cell_blocks = n_cell_blocks;
         P.t0 = t->t0;
@@ -525,7 +529,7 @@ static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream
         P.W = (float)(d->dt_det / t->dt);
         P.invW = (float)(t->dt / d->dt_det);
         P.ff = (d->flags & RD_FARFIELD) != 0;
-        P.lin = (d->flags & RD_LINEAR) ? 1 : (d->flags & RD_HOLD_PREV) ? 2 : 0;
+        P.lin = (d->flags & RD_LINEAR) ? 1 : (d->flags & RD_HOLD_PREV) ? 2 : (d->flags & RD_QUADRATIC) ? 3 : 0;
         P.cpc = cpc;
         P.nc = nc;
         P.group = !mixed ? 1
@@ -676,7 +680,7 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
     if (!d) return fail(RD_ERR_ARG, "detector is NULL");
     rd_status st = check_traj(t);
     if (st != RD_OK) return st;
-    if (d->flags & (RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV))
+    if (d->flags & (RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV | RD_QUADRATIC))
         return fail(RD_ERR_STATE, "the adjoint covers the exact fields with the held interpolation only");
     if (t->mem != RD_MEM_DEVICE) return fail(RD_ERR_ARG, "the adjoint needs device trajectories");
     if (!gE && !gB) return fail(RD_ERR_ARG, "gE and gB are both NULL");
@@ -870,7 +874,7 @@ rd_status rd_autotune_shape(rd_detector* d, const rd_traj* t, const char* cache_
         }
         return RD_OK;
     };
-    const bool variant = (d->flags & (RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV)) != 0;
+    const bool variant = (d->flags & (RD_FARFIELD | RD_LINEAR | RD_HOLD_PREV | RD_QUADRATIC)) != 0;
     // 1. cells per CTA x cells per thread, automatic chunk and group
     for (int cpc : {256, 128, 64})
         for (int nc : {2, 1}) {
@@ -1175,9 +1179,10 @@ rd_status rd_deposit_stream(rd_detector* d, const rd_traj* t, rd_stream stream)
             return fail(RD_ERR_STATE, "streamed call starts at t0 = %.17g, the stream continues at %.17g", t->t0,
                         expect);
     }
-    // samples kept between calls: the last one (its interval to the first new sample), and with
-    // RD_LINEAR / RD_HOLD_PREV the one before it too (the field of the last sample needs its betadot)
-    const int keep = (d->flags & (RD_LINEAR | RD_HOLD_PREV)) ? 2 : 1;
+    // samples kept between calls: the last one (its interval to the first new sample), with RD_LINEAR /
+    // RD_HOLD_PREV the one before it too (the field of the last sample needs its betadot), and with
+    // RD_QUADRATIC one more (the field two samples back)
+    const int keep = (d->flags & RD_QUADRATIC) ? 3 : (d->flags & (RD_LINEAR | RD_HOLD_PREV)) ? 2 : 1;
     const int have = cont ? d->strm_have : 0;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int np = t->n_part, m = t->n_samples, ns = m + have;
@@ -1186,14 +1191,14 @@ rd_status rd_deposit_stream(rd_detector* d, const rd_traj* t, rd_stream stream)
     st = ensure(&d->strm_stage, &d->strm_stage_bytes, 2 * row * np + sizeof(double) * np, s, "stream staging");
     if (st != RD_OK) return st;
     if (!cont) {
-        st = ensure(&d->strm_last, &d->strm_last_bytes, 2 * one * 2 * np, s, "stream state");
+        st = ensure(&d->strm_last, &d->strm_last_bytes, 2 * one * 3 * np, s, "stream state");
         if (st != RD_OK) return st;
     }
     double* xs = static_cast<double*>(d->strm_stage);
     double* us = xs + (size_t)np * ns * 3;
     double* qs = us + (size_t)np * ns * 3;
-    double* lx = static_cast<double*>(d->strm_last);        // [np][have][3]
-    double* lu = lx + (size_t)np * 2 * 3;
+    double* lx = static_cast<double*>(d->strm_last);        // [np][have][3], have <= 3
+    double* lu = lx + (size_t)np * 3 * 3;
     const cudaMemcpyKind kind = t->mem == RD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     RD_CUDA(cudaMemcpy2DAsync(xs + 3 * have, row, t->x, mrow, mrow, np, kind, s), "stream x");
     RD_CUDA(cudaMemcpy2DAsync(us + 3 * have, row, t->u, mrow, mrow, np, kind, s), "stream u");
@@ -1209,8 +1214,10 @@ rd_status rd_deposit_stream(rd_detector* d, const rd_traj* t, rd_stream stream)
     staged.q = t->q ? qs : nullptr;
     staged.mem = RD_MEM_DEVICE;
     staged.t0 = t->t0 - have * t->dt;
-    // intervals already deposited by earlier calls are not deposited again
-    st = deposit_from(d, &staged, stream, have > 1 ? 2 : 1);
+    // intervals already deposited by earlier calls are not deposited again; the staged sample 0 is
+    // sample strm_count - have of the whole trajectory
+    const long long count0 = cont ? d->strm_count : 0;
+    st = deposit_from(d, &staged, stream, std::max(1, have), (int)std::min<long long>(count0 - have, 1 << 30));
     if (st != RD_OK) return st;
     const int kept = std::min(keep, ns);
     RD_CUDA(cudaMemcpy2DAsync(lx, one * kept, xs + 3 * (size_t)(ns - kept), row, one * kept, np,
@@ -1221,6 +1228,7 @@ rd_status rd_deposit_stream(rd_detector* d, const rd_traj* t, rd_stream stream)
             "stream state");
     d->strm_n_part = np;
     d->strm_have = kept;
+    d->strm_count = count0 + m;
     d->strm_t_last = t->t0 + (double)(m - 1) * t->dt;
     d->strm_dt = t->dt;
     return RD_OK;

@@ -129,7 +129,9 @@ struct D64State {
     int b;
     double a;       // arrival (bins) of the previous sample
     double acc[6];
-    double Fp[6];   // RD_LINEAR: field of the previous sample
+    double Fp[6];   // RD_LINEAR / RD_QUADRATIC: field of the previous sample
+    double Fpp[6];  // RD_QUADRATIC: field two samples back ...
+    double ap;      // ... and its arrival (bins)
     int n_below;
     int n_above;
 };
@@ -267,6 +269,64 @@ __device__ __forceinline__ void fp64_deposit_lin(D64State& st, const double* F0,
     st.a = c;
 }
 
+// RD_QUADRATIC: over [a, c] the quadratic through (p, Fpp), (a, Fa), (c, Fc) in arrival time, in Newton
+// form about a (s = tau - a, L = c - a, h = a - p): F(s) = Fa + D1 s + D2 s (s - L), D1 = (Fc - Fa) / L,
+// D2 = (D1 - (Fa - Fpp) / h) / (L + h); the overlap [u0, u1] receives
+// Fa (s1 - s0) + D1 (s1^2 - s0^2) / 2 + D2 ((s1^3 - s0^3) / 3 - L (s1^2 - s0^2) / 2).
+__device__ __forceinline__ void fp64_quad_part(const double* Fa, const double* D1, const double* D2, double a,
+                                               double L, double u0, double u1, double* out, bool add)
+{
+    const double s0 = u0 - a, s1 = u1 - a;
+    const double sq = (s1 * s1 - s0 * s0) / 2.0;
+    const double cu = (s1 * s1 * s1 - s0 * s0 * s0) / 3.0 - L * sq;
+    const double len = u1 - u0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double v = Fa[i] * len + D1[i] * sq + D2[i] * cu;
+        out[i] = add ? out[i] + v : v;
+    }
+}
+
+__device__ __forceinline__ void fp64_deposit_quad(D64State& st, const double* Fc, double c, double* row, int n_bins,
+                                                  int k, int k_begin, int k_end)
+{
+    const double a = st.a;
+    const double fc = floor(c);
+    const int bc = clamp_bin(fc);
+    if (!(c > a)) {
+        st.a = c;
+        return;
+    }
+    const double L = c - a, h = a - st.ap;
+    double D1[6], D2[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double D0 = (st.Fp[i] - st.Fpp[i]) / h;
+        D1[i] = (Fc[i] - st.Fp[i]) / L;
+        D2[i] = (D1[i] - D0) / (L + h);
+    }
+    if (bc <= st.b) {
+        fp64_quad_part(st.Fp, D1, D2, a, L, a, c, st.acc, true);
+        st.a = c;
+        return;
+    }
+    fp64_quad_part(st.Fp, D1, D2, a, L, a, (double)(st.b + 1), st.acc, true);
+    flush_f64(row, n_bins, st.b, st.acc);
+    const int lo = max(st.b + 1, 0), hi = min(bc - 1, n_bins - 1);
+    for (int j = lo; j <= hi; ++j) {
+        double v[6];
+        fp64_quad_part(st.Fp, D1, D2, a, L, (double)j, (double)(j + 1), v, false);
+        flush_f64(row, n_bins, j, v);
+    }
+    fp64_quad_part(st.Fp, D1, D2, a, L, fc, c, st.acc, false);
+    if (st.b < 0 && bc >= 0) st.n_below = k - k_begin + 1;
+    if (st.b < n_bins && bc >= n_bins) st.n_above = k_end - k + 1;
+    st.b = bc;
+    st.a = c;
+}
+
+// LM: interpolation family, 0 held field (default), 1 linear or held-previous (P.lin 1, 2), 2 quadratic
+template <int LM>
 __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const DepositParams P,
                                                                        int flags)
 {
@@ -335,7 +395,7 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
         if (!live) atomicAdd(&P.counters->clipped, (unsigned long long)n_int);
     }
     const double q = P.q ? P.q[p] : 1.0;
-    if (P.lin && live) {
+    if (LM && live) {
         // field of the sample before the chunk; a trajectory's first interval holds F_1
         const RecD r0 = rec[k_begin > 1 ? k_begin - 1 : 1];
         if (ff) {
@@ -344,6 +404,23 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
             double R0;
             (void)arrival_bins(r0.xa.x, r0.xa.y, r0.xa.z, cl, P.t0, 0, P.dt, P.inv_dt_det, R0);
             fp64_field(r0, cl, R0, q, flags, st.Fp);
+        }
+        // RD_QUADRATIC: the field and arrival of the sample two before the chunk (used from the
+        // trajectory's third interval on)
+        st.ap = st.a - 1.0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) st.Fpp[i] = st.Fp[i];
+        if (LM == 2 && k_begin >= 3) {
+            const RecD r1 = rec[k_begin - 2];
+            if (ff) {
+                fp64_field_ff(r1, ncx, ncy, ncz, Rc, q, flags, st.Fpp);
+                st.ap = arrival_bins_ff(r1.xa.x, r1.xa.y, r1.xa.z, ncx, ncy, ncz, Rc, cl.w, P.t0, k_begin - 2, P.dt,
+                                        P.inv_dt_det);
+            } else {
+                double R1;
+                st.ap = arrival_bins(r1.xa.x, r1.xa.y, r1.xa.z, cl, P.t0, k_begin - 2, P.dt, P.inv_dt_det, R1);
+                fp64_field(r1, cl, R1, q, flags, st.Fpp);
+            }
         }
     }
 
@@ -375,11 +452,18 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
                     cbin = arrival_bins(r.xa.x, r.xa.y, r.xa.z, cl, P.t0, k, P.dt, P.inv_dt_det, R);
                     fp64_field(r, cl, R, q, flags, F);
                 }
-                if (P.lin) {
-                    // RD_HOLD_PREV (lin 2): the previous field at both ends, i.e. held
-                    fp64_deposit_lin(st, st.Fp, P.lin == 1 ? F : st.Fp, cbin, row, P.n_bins, k, k_begin, k_end);
+                if (LM) {
+                    const double a_prev = st.a;
+                    if (LM == 2 && k + P.k_real0 >= 3)
+                        fp64_deposit_quad(st, F, cbin, row, P.n_bins, k, k_begin, k_end);
+                    else    // RD_HOLD_PREV (lin 2): the previous field at both ends, i.e. held
+                        fp64_deposit_lin(st, st.Fp, P.lin == 2 ? st.Fp : F, cbin, row, P.n_bins, k, k_begin, k_end);
 #pragma unroll
-                    for (int j = 0; j < 6; ++j) st.Fp[j] = F[j];
+                    for (int j = 0; j < 6; ++j) {
+                        if (LM == 2) st.Fpp[j] = st.Fp[j];
+                        st.Fp[j] = F[j];
+                    }
+                    if (LM == 2) st.ap = a_prev;
                 } else {
                     fp64_deposit(st, F, cbin, row, P.n_bins, k, k_begin, k_end);
                 }
@@ -452,7 +536,12 @@ cudaError_t launch_deposit_fp64(const DepositParams& p, int flags, cudaStream_t 
     const long long blocks = (long long)p.n_cell_blocks * p.n_part * p.n_chunks;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    k_deposit_fp64<<<(unsigned)blocks, kDepositThreads, 0, s>>>(p, flags);
+    if (p.lin == 3)
+        k_deposit_fp64<2><<<(unsigned)blocks, kDepositThreads, 0, s>>>(p, flags);
+    else if (p.lin)
+        k_deposit_fp64<1><<<(unsigned)blocks, kDepositThreads, 0, s>>>(p, flags);
+    else
+        k_deposit_fp64<0><<<(unsigned)blocks, kDepositThreads, 0, s>>>(p, flags);
     return cudaGetLastError();
 }
 

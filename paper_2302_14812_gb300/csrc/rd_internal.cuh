@@ -95,7 +95,9 @@ struct DepositParams {
     float du_scale;             // dt / dt_det
     int ff;                     // far-field limit (RD_FARFIELD): Eq. 3, radiation term at (n_c, R_c)
     int lin;                    // 0: held field; 1: linear in arrival time (RD_LINEAR); 2: the previous
-                                // sample's field held (RD_HOLD_PREV); 1 and 2 carry the previous field
+                                // sample's field held (RD_HOLD_PREV); 3: quadratic in arrival time
+                                // (RD_QUADRATIC); 1-3 carry the previous field, 3 the one before too
+    int k_real0 = 0;            // index in the whole trajectory of this call's sample 0 (streamed calls)
     int group = 1;              // mixed kernel work order: cell blocks per group (cell_group)
     int cpc = 256;              // mixed kernel shape: cells per CTA (64, 128, 256) ...
     int nc = 2;                 // ... and cells per thread (1, 2); n_cell_blocks counts blocks of cpc cells

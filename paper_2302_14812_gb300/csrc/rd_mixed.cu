@@ -41,7 +41,9 @@ struct Cells {
     float rpd[NC];                  // R_{k-1} + dt (far-field limit: 1/R_c)
     float ec[NC];                   // far-field limit: |n_c|^2 - 1 of the rounded direction
     float acc[6][NC];               // E xyz, B xyz of the current bin so far (weights in bins)
-    float gp[6][NC];                // linear interpolation: scaled field of the previous sample
+    float gp[6][NC];                // linear / quadratic interpolation: scaled field of the previous sample
+    float gpp[6][NC];               // quadratic interpolation: scaled field two samples back ...
+    float hp[NC];                   // ... and the previous interval's length (units of dt)
     int bo[NC];                     // row * n_bins + bin being filled (bin may lie outside the window)
     int rb[NC];                     // row * n_bins (row = the cell's index inside the CTA's block)
     bool live[NC];                  // some arrival of the chunk falls inside the window
@@ -55,6 +57,8 @@ struct Consts {
     float DT;
     int n_bins;
     float* base;                    // field row 0 of the CTA's cell block
+    int kq;                         // quadratic interpolation: first interval (this call's index) with
+                                    // three fields behind it (the trajectory's third interval)
 };
 
 // Field of one sample at one cell, scaled to the bin weights (E = S E', B = (S/R) d x E').
@@ -222,13 +226,18 @@ __device__ __forceinline__ void scaled_field(const Field& o, float* G)
 // held over the interval, RD_HOLD_PREV): over the interval the field goes linearly from G0 = gp (previous
 // sample) to G (this sample); the part [s0, s1] of the interval (dt units from its start, length L)
 // weighs G0 (s1 - s0) + (G - G0) (s1^2 - s0^2) / (2 L) = G0 (s1 - s0 - ramp) + G ramp with
-// ramp = (s1^2 - s0^2) / (2 L).  Interval of cell j passing two or more bin
+// ramp = (s1^2 - s0^2) / (2 L).  Quadratic interpolation (RD_QUADRATIC) adds D2 cu, D2 the second
+// divided difference of the scaled fields of samples k-2, k-1, k over their arrival times and
+// cu = int_{s0}^{s1} s (s - L) ds (qcube below).  Interval of cell j passing two or more bin
 // edges (exact walk only): flush the bin being filled, every whole bin, and leave the last, partial
 // bin in the accumulator with the time already in it; fn comes back below W (no edge left for the
 // common path).
-template <int NC, bool TRACK, bool FF>
-__device__ __forceinline__ void multi_edges_lin(Cells<NC>& c, int j, const float* G, float L, float inv2L,
-                                                const Consts& C, float& fn, int k, int k_begin, int k_end)
+// s^2 (s/3 - L/2): int_0^s t (t - L) dt
+__device__ __forceinline__ float qcube(float s, float L) { return (s * s) * fmaf(s, 1.f / 3.f, -0.5f * L); }
+
+template <int NC, bool TRACK, bool FF, bool QUAD>
+__device__ __forceinline__ void multi_edges_lin(Cells<NC>& c, int j, const float* G, const float* D2, float L,
+                                                float inv2L, const Consts& C, float& fn, int k, int k_begin, int k_end)
 {
     constexpr int NF = FF ? 3 : 6;                                  // carried field components
     const float f = fn;
@@ -245,6 +254,11 @@ __device__ __forceinline__ void multi_edges_lin(Cells<NC>& c, int j, const float
         float v[6];
 #pragma unroll
         for (int q = 0; q < NF; ++q) v[q] = fmaf(c.gp[q][j], C.W - ramp, G[q] * ramp);
+        if (QUAD) {
+            const float cu = qcube(s1, L) - qcube(s0, L);
+#pragma unroll
+            for (int q = 0; q < NF; ++q) v[q] = fmaf(D2[q], cu, v[q]);
+        }
         bin_b<NC, FF>(c, j, v, v + 3, v + 3);
         flush(C, b0 + i, c.bo[j] + i, v[0], v[1], v[2], v[3], v[4], v[5]);
     }
@@ -254,6 +268,11 @@ __device__ __forceinline__ void multi_edges_lin(Cells<NC>& c, int j, const float
     const float ramp = (L * L - s0 * s0) * inv2L;
 #pragma unroll
     for (int q = 0; q < NF; ++q) c.acc[q][j] = fmaf(c.gp[q][j], len - ramp, G[q] * ramp);
+    if (QUAD) {
+        const float cu = qcube(L, L) - qcube(s0, L);
+#pragma unroll
+        for (int q = 0; q < NF; ++q) c.acc[q][j] = fmaf(D2[q], cu, c.acc[q][j]);
+    }
     c.bo[j] += m;
     fn = fminf(fmaxf(len, 0.f), C.W * 0.99999994f);
     if (TRACK) {
@@ -276,14 +295,18 @@ enum { kFast = 0, kExact = 1 };
 // flushes the bin and starts the next one with the rest of the interval.  LAST: the interval ends
 // on the exact FP64 anchors.  TRACK: bins may lie outside the window (checked, clipped intervals
 // counted).  ok: kExact only, false from the interval that stopped the fast walk onwards.
-template <int NC, int MODE, bool LAST, bool TRACK, bool FF, bool LIN>
+template <int NC, int MODE, bool LAST, bool TRACK, bool FF, int LIN>
 __device__ __forceinline__ void step(Cells<NC>& c, const RecS& r, const Consts& C, const int* bo_end,
                                      const float* f_end, int k, int k_begin, int k_end, bool* ok, float ramp)
 {
     constexpr int NF = FF ? 3 : 6;                  // carried field components (far field: E only)
+    constexpr bool QUAD = LIN == 2;                 // quadratic interpolation (RD_QUADRATIC)
     Field o[NC];
     float fn[NC];
-    float G[NC][6], L[NC], inv2L[NC], ramp1[NC];               // linear interpolation only
+    float G[NC][6], L[NC], inv2L[NC], ramp1[NC];               // linear / quadratic interpolation only
+    float D2[NC][6], cu1[NC];                                  // quadratic interpolation only
+    // the trajectory's first two intervals have fewer than three fields behind them: no curvature
+    const float qon = (QUAD && k >= C.kq) ? 1.f : 0.f;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         if (FF)
@@ -307,6 +330,19 @@ __device__ __forceinline__ void step(Cells<NC>& c, const RecS& r, const Consts& 
             const float a1 = len1 - ramp1[j];
 #pragma unroll
             for (int i = 0; i < NF; ++i) c.acc[i][j] = fmaf(c.gp[i][j], a1, fmaf(G[j][i], ramp1[j], c.acc[i][j]));
+            if (QUAD) {
+                // D2 = ((G - G0) / L - (G0 - Gpp) / h) / (L + h), h the previous interval (ramp = 1 here,
+                // so 2 inv2L = 1/L); the part [0, len1] adds D2 int_0^len1 s (s - L) ds
+                const float iL = 2.f * inv2L[j];
+                const float ih = fast_rcp(c.hp[j]);
+                const float iLh = qon * fast_rcp(L[j] + c.hp[j]);
+                cu1[j] = qcube(len1, L[j]);
+#pragma unroll
+                for (int i = 0; i < NF; ++i) {
+                    D2[j][i] = fmaf(G[j][i] - c.gp[i][j], iL, -((c.gp[i][j] - c.gpp[i][j]) * ih)) * iLh;
+                    c.acc[i][j] = fmaf(D2[j][i], cu1[j], c.acc[i][j]);
+                }
+            }
         } else {
             const float ws = (fminf(t, C.W) - c.f[j]) * o[j].S;
             const float wb = ws * o[j].rinv;
@@ -326,7 +362,7 @@ __device__ __forceinline__ void step(Cells<NC>& c, const RecS& r, const Consts& 
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             if (LIN)
-                multi_edges_lin<NC, TRACK, FF>(c, j, G[j], L[j], inv2L[j], C, fn[j], k, k_begin, k_end);
+                multi_edges_lin<NC, TRACK, FF, QUAD>(c, j, G[j], D2[j], L[j], inv2L[j], C, fn[j], k, k_begin, k_end);
             else
                 multi_edges<NC, TRACK, FF>(c, j, o[j], C, fn[j], k, k_begin, k_end);
         }
@@ -349,6 +385,11 @@ __device__ __forceinline__ void step(Cells<NC>& c, const RecS& r, const Consts& 
                     const float ramp2 = fmaf(0.5f * ramp, L[j], -ramp1[j]);
 #pragma unroll
                     for (int i = 0; i < NF; ++i) c.acc[i][j] = fmaf(c.gp[i][j], rem - ramp2, G[j][i] * ramp2);
+                    if (QUAD) {
+                        const float cu2 = qcube(L[j], L[j]) - cu1[j];       // the part [len1, L]
+#pragma unroll
+                        for (int i = 0; i < NF; ++i) c.acc[i][j] = fmaf(D2[j][i], cu2, c.acc[i][j]);
+                    }
                 } else {
                     const float rs = rem * o[j].S;
                     const float rbw = rs * o[j].rinv;
@@ -377,9 +418,11 @@ __device__ __forceinline__ void step(Cells<NC>& c, const RecS& r, const Consts& 
             const float rem = fn[j] - C.W;
             if (LIN) {
                 const float ramp2 = fmaf(0.5f * ramp, L[j], -ramp1[j]);
+                const float cu2 = QUAD ? qcube(L[j], L[j]) - cu1[j] : 0.f;
 #pragma unroll
                 for (int i = 0; i < NF; ++i) {
-                    const float v = fmaf(c.gp[i][j], rem - ramp2, G[j][i] * ramp2);
+                    float v = fmaf(c.gp[i][j], rem - ramp2, G[j][i] * ramp2);
+                    if (QUAD) v = fmaf(D2[j][i], cu2, v);
                     c.acc[i][j] = cr ? v : c.acc[i][j];
                 }
             } else {
@@ -400,7 +443,11 @@ __device__ __forceinline__ void step(Cells<NC>& c, const RecS& r, const Consts& 
         }
         if (LIN) {
 #pragma unroll
-            for (int i = 0; i < NF; ++i) c.gp[i][j] = G[j][i];
+            for (int i = 0; i < NF; ++i) {
+                if (QUAD) c.gpp[i][j] = c.gp[i][j];
+                c.gp[i][j] = G[j][i];
+            }
+            if (QUAD) c.hp[j] = L[j];
         }
     }
 }
@@ -410,13 +457,15 @@ __device__ __forceinline__ void step(Cells<NC>& c, const RecS& r, const Consts& 
 #endif
 constexpr int kUnroll = RD_UNROLL > 0 ? RD_UNROLL : 1;   // samples per loop iteration
 
-// Per-thread copy of the walk state at the start of a tile, in shared memory ([word][thread]).
-constexpr int kSaveCell = 17;               // f, rpd, bo, below, above, acc[6], gp[6]
+// Per-thread copy of the walk state at the start of a tile, in shared memory ([word][thread]):
+// f, rpd, bo, below, above, acc[6], gp[6], and for the quadratic interpolation gpp[6], hp.
+constexpr int save_cell(int lin) { return lin == 2 ? 24 : 17; }
 
-template <int NC, int NT, bool FF, bool LIN>
+template <int NC, int NT, bool FF, int LIN>
 __device__ __forceinline__ void save_state(const Cells<NC>& c, float (*sv)[NT], int tid)
 {
     constexpr int NF = FF ? 3 : 6;
+    constexpr int kSaveCell = save_cell(LIN);
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         sv[j * kSaveCell + 0][tid] = c.f[j];
@@ -430,13 +479,19 @@ __device__ __forceinline__ void save_state(const Cells<NC>& c, float (*sv)[NT], 
 #pragma unroll
             for (int i = 0; i < NF; ++i) sv[j * kSaveCell + 11 + i][tid] = c.gp[i][j];
         }
+        if (LIN == 2) {
+#pragma unroll
+            for (int i = 0; i < NF; ++i) sv[j * kSaveCell + 17 + i][tid] = c.gpp[i][j];
+            sv[j * kSaveCell + 23][tid] = c.hp[j];
+        }
     }
 }
 
-template <int NC, int NT, bool FF, bool LIN>
+template <int NC, int NT, bool FF, int LIN>
 __device__ __forceinline__ void restore_state(Cells<NC>& c, float (*sv)[NT], int tid)
 {
     constexpr int NF = FF ? 3 : 6;
+    constexpr int kSaveCell = save_cell(LIN);
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         c.f[j] = sv[j * kSaveCell + 0][tid];
@@ -450,10 +505,15 @@ __device__ __forceinline__ void restore_state(Cells<NC>& c, float (*sv)[NT], int
 #pragma unroll
             for (int i = 0; i < NF; ++i) c.gp[i][j] = sv[j * kSaveCell + 11 + i][tid];
         }
+        if (LIN == 2) {
+#pragma unroll
+            for (int i = 0; i < NF; ++i) c.gpp[i][j] = sv[j * kSaveCell + 17 + i][tid];
+            c.hp[j] = sv[j * kSaveCell + 23][tid];
+        }
     }
 }
 
-template <int NC, int NT, bool TRACK, bool FF, bool LIN>
+template <int NC, int NT, bool TRACK, bool FF, int LIN>
 __device__ __forceinline__ void walk_tile(Cells<NC>& c, const RecS* tile, int cnt, bool last_tile, const Consts& C,
                                           float ramp, const int* bo_end, const float* f_end, int k0, int k_begin,
                                           int k_end, float (*sv)[NT])
@@ -489,7 +549,7 @@ __device__ __forceinline__ void walk_tile(Cells<NC>& c, const RecS* tile, int cn
 // CTA.  tile / bar: the CTA's shared staging buffers; g_base counts the tiles the CTA staged
 // before this item (it selects buffer and mbarrier phase, so the buffers carry over between items).
 // Returns false if a bounded wait ran out (the error is recorded; the CTA must stop).
-template <bool FF, bool LIN, int NC, int CPC>
+template <bool FF, int LIN, int NC, int CPC>
 __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int cb, int ch,
                                              RecS (*tile)[kTileSteps], uint64_t* bar, float (*sv)[CPC / NC],
                                              unsigned& g_base)
@@ -520,11 +580,15 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
     C.DT = P.dt_f;
     C.n_bins = P.n_bins;
     C.base = static_cast<float*>(P.fields) + (size_t)cb * CPC * P.n_bins * 8;
+    C.kq = 3 - P.k_real0;
+    constexpr bool QUAD = LIN == 2;
+    const bool q_prev = QUAD && k_begin >= 3;     // the chunk starts with three fields behind it
 
     // anchors: exact FP64 arrival (bins) at both ends of the chunk, per cell
     Cells<NC> c;
     int bo_end[NC];
     float f_end[NC];
+    float hp0[NC];                              // quadratic: length of interval k_begin - 1 (dt units)
     bool partial = false;
     unsigned long long clip = 0, crossed = 0;
     const double* xp = P.x + (size_t)p * P.n_samples * 3;
@@ -561,6 +625,16 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
                 ue = arrival_bins(xe[0], xe[1], xe[2], cl, P.t0, k_end, P.dt, P.inv_dt_det, Re);
             }
             c.live[j] = (ue > 0.0) && (ua < (double)P.n_bins);
+            hp0[j] = 1.f;
+            if (q_prev && c.live[j]) {
+                const double* xq = xp + 3 * (size_t)(k_begin - 2);
+                double Rq;
+                const double uq =
+                    FF ? arrival_bins_ff(xq[0], xq[1], xq[2], ncx, ncy, ncz, Rc, cl.w, P.t0, k_begin - 2, P.dt,
+                                         P.inv_dt_det)
+                       : arrival_bins(xq[0], xq[1], xq[2], cl, P.t0, k_begin - 2, P.dt, P.inv_dt_det, Rq);
+                hp0[j] = (float)((ua - uq) * P.W);
+            }
             if (!c.live[j]) {
                 clip += (unsigned long long)n_int;
             } else {
@@ -607,6 +681,22 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
             scaled_field(o, G);
 #pragma unroll
             for (int i = 0; i < 6; ++i) c.gp[i][j] = G[i];      // far field: only E is read
+            if (QUAD) {
+                // the field two samples before the chunk and the interval before it (used from the
+                // trajectory's third interval on)
+                c.hp[j] = hp0[j];
+                if (q_prev) {
+                    const RecS r1 = rec[k_begin - 2];
+                    float rtmp1 = c.rpd[j];
+                    if (FF)
+                        field_at_ff(r1, c.px[j], c.py[j], c.pz[j], c.rpd[j], c.ec[j], o);
+                    else
+                        field_at(r1, c.px[j], c.py[j], c.pz[j], rtmp1, C, o);
+                    scaled_field(o, G);
+                }
+#pragma unroll
+                for (int i = 0; i < 6; ++i) c.gpp[i][j] = G[i];
+            }
         }
     }
     const bool track = __syncthreads_or(partial) != 0;
@@ -629,10 +719,10 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
         const int cnt = min(kTileSteps, k_end - k0 + 1);
         const bool last_tile = (t == n_tiles - 1);
         if (track)
-            walk_tile<NC, NT, true, FF, LIN>(c, tile[buf], cnt, last_tile, C, P.lin == 1 ? 1.f : 0.f, bo_end, f_end, k0,
+            walk_tile<NC, NT, true, FF, LIN>(c, tile[buf], cnt, last_tile, C, P.lin == 2 ? 0.f : 1.f, bo_end, f_end, k0,
                                      k_begin, k_end, sv);
         else
-            walk_tile<NC, NT, false, FF, LIN>(c, tile[buf], cnt, last_tile, C, P.lin == 1 ? 1.f : 0.f, bo_end, f_end, k0,
+            walk_tile<NC, NT, false, FF, LIN>(c, tile[buf], cnt, last_tile, C, P.lin == 2 ? 0.f : 1.f, bo_end, f_end, k0,
                                       k_begin, k_end, sv);
         __syncthreads();
         if (tid == 0 && t + 2 < n_tiles) {
@@ -674,13 +764,13 @@ __device__ __forceinline__ void init_staging(uint64_t* bar)
 // shape (2 cells per thread, 256 cells per CTA: 128 threads, 5 CTAs).
 constexpr int mixed_min_blocks(int nt) { return nt >= 128 ? (nt == 128 ? RD_MIXED_MINBLOCKS : 640 / nt) : 640 / nt; }
 
-template <bool FF, bool LIN, int NC, int CPC>
+template <bool FF, int LIN, int NC, int CPC>
 __global__ void __launch_bounds__(CPC / NC, mixed_min_blocks(CPC / NC)) k_deposit_mixed(const DepositParams P)
 {
     constexpr int NT = CPC / NC;
     __shared__ __align__(128) RecS tile[2][kTileSteps];
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ float sv[NC * kSaveCell][NT];
+    __shared__ float sv[NC * save_cell(LIN)][NT];
     init_staging(bar);
     int p, cb, ch;
     item_coords(blockIdx.x, P, p, cb, ch);
@@ -698,7 +788,7 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS)
     __shared__ __align__(128) RecS tile[2][kTileSteps];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ long long s_item;
-    __shared__ float sv[kMixedCells * kSaveCell][kMixedThreads];
+    __shared__ float sv[kMixedCells * save_cell(2)][kMixedThreads];
     init_staging(bar);
     const long long total = item_off[n_probs];
     unsigned g = 0;
@@ -717,12 +807,15 @@ __global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS)
         int p, cb, ch;
         item_coords((unsigned)(item - item_off[lo]), P, p, cb, ch);
         bool ok;
-        if (P.lin)
-            ok = P.ff ? deposit_item<true, true, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g)
-                      : deposit_item<false, true, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g);
+        if (P.lin == 3)
+            ok = P.ff ? deposit_item<true, 2, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g)
+                      : deposit_item<false, 2, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g);
+        else if (P.lin)
+            ok = P.ff ? deposit_item<true, 1, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g)
+                      : deposit_item<false, 1, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g);
         else
-            ok = P.ff ? deposit_item<true, false, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g)
-                      : deposit_item<false, false, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g);
+            ok = P.ff ? deposit_item<true, 0, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g)
+                      : deposit_item<false, 0, kMixedCells, kMixedCellsPerCta>(P, p, cb, ch, tile, bar, sv, g);
         if (!ok) break;
     }
 }
@@ -747,7 +840,7 @@ int batch_grid()
 #define RD_CARVEOUT 0
 #endif
 
-template <bool FF, bool LIN, int NC, int CPC>
+template <bool FF, int LIN, int NC, int CPC>
 static void launch_mixed(const DepositParams& p, unsigned blocks, cudaStream_t s)
 {
     if (RD_CARVEOUT) {
@@ -777,18 +870,24 @@ cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s)
     if (p.ff || p.lin) {
         // the far-field and interpolation variants run in the default shape only
         if (p.cpc != kMixedCellsPerCta || p.nc != kMixedCells) return cudaErrorInvalidValue;
-        if (p.ff && p.lin) launch_mixed<true, true, kMixedCells, kMixedCellsPerCta>(p, b, s);
-        else if (p.ff) launch_mixed<true, false, kMixedCells, kMixedCellsPerCta>(p, b, s);
-        else launch_mixed<false, true, kMixedCells, kMixedCellsPerCta>(p, b, s);
+        const int lm = p.lin == 3 ? 2 : p.lin ? 1 : 0;       // walk: held, linear family, quadratic
+        if (p.ff) {
+            if (lm == 2) launch_mixed<true, 2, kMixedCells, kMixedCellsPerCta>(p, b, s);
+            else if (lm == 1) launch_mixed<true, 1, kMixedCells, kMixedCellsPerCta>(p, b, s);
+            else launch_mixed<true, 0, kMixedCells, kMixedCellsPerCta>(p, b, s);
+        } else {
+            if (lm == 2) launch_mixed<false, 2, kMixedCells, kMixedCellsPerCta>(p, b, s);
+            else launch_mixed<false, 1, kMixedCells, kMixedCellsPerCta>(p, b, s);
+        }
         return cudaGetLastError();
     }
     switch (p.cpc * 8 + p.nc) {
-    case 256 * 8 + 2: launch_mixed<false, false, 2, 256>(p, b, s); break;
-    case 128 * 8 + 2: launch_mixed<false, false, 2, 128>(p, b, s); break;
-    case 64 * 8 + 2: launch_mixed<false, false, 2, 64>(p, b, s); break;
-    case 256 * 8 + 1: launch_mixed<false, false, 1, 256>(p, b, s); break;
-    case 128 * 8 + 1: launch_mixed<false, false, 1, 128>(p, b, s); break;
-    case 64 * 8 + 1: launch_mixed<false, false, 1, 64>(p, b, s); break;
+    case 256 * 8 + 2: launch_mixed<false, 0, 2, 256>(p, b, s); break;
+    case 128 * 8 + 2: launch_mixed<false, 0, 2, 128>(p, b, s); break;
+    case 64 * 8 + 2: launch_mixed<false, 0, 2, 64>(p, b, s); break;
+    case 256 * 8 + 1: launch_mixed<false, 0, 1, 256>(p, b, s); break;
+    case 128 * 8 + 1: launch_mixed<false, 0, 1, 128>(p, b, s); break;
+    case 64 * 8 + 1: launch_mixed<false, 0, 1, 64>(p, b, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -145,7 +145,7 @@ extern "C" rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix
             P.W = (float)(dt_det / t->dt);
             P.invW = (float)(t->dt / dt_det);
             P.ff = (fl & RD_FARFIELD) != 0;
-            P.lin = (fl & RD_LINEAR) ? 1 : (fl & RD_HOLD_PREV) ? 2 : 0;
+            P.lin = (fl & RD_LINEAR) ? 1 : (fl & RD_HOLD_PREV) ? 2 : (fl & RD_QUADRATIC) ? 3 : 0;
             P.group = cell_group(n_cell_blocks, n_bins);
             e = launch_deposit_mixed(P, s);
         }

@@ -81,8 +81,12 @@ def test_argument_errors_without_gpu():
     d.flags = rd.RD_NEAR | rd.RD_FAR | rd.RD_LINEAR | rd.RD_HOLD_PREV
     assert lib.rd_create_detector(ctypes.byref(d), None, ctypes.byref(h)) == rd.RD_ERR_ARG
     assert "alternatives" in rd.rd_last_error()
-    d.flags = rd.RD_NEAR | 32
+    d.flags = rd.RD_NEAR | 64
     assert lib.rd_create_detector(ctypes.byref(d), None, ctypes.byref(h)) == rd.RD_ERR_ARG
+    for both in (rd.RD_LINEAR | rd.RD_QUADRATIC, rd.RD_HOLD_PREV | rd.RD_QUADRATIC):
+        d.flags = rd.RD_NEAR | rd.RD_FAR | both
+        assert lib.rd_create_detector(ctypes.byref(d), None, ctypes.byref(h)) == rd.RD_ERR_ARG
+        assert "alternatives" in rd.rd_last_error()
     assert lib.rd_set_batch_budget(None, 0) == rd.RD_ERR_ARG
     assert lib.rd_deposit_stream(None, None, None) == rd.RD_ERR_ARG
     assert lib.rd_stream_reset(None) == rd.RD_ERR_ARG
@@ -120,7 +124,7 @@ def test_argument_errors_without_gpu():
     # Eq. 1 (the far-field limit or an interpolation variant alone) is refused before any CUDA call
     t.mem = rd.RD_MEM_DEVICE
     t.n_samples = 10
-    for flags in (rd.RD_FARFIELD, rd.RD_LINEAR, rd.RD_HOLD_PREV, rd.RD_NEAR | rd.RD_FARFIELD, rd.RD_NEAR | 32,
+    for flags in (rd.RD_FARFIELD, rd.RD_LINEAR, rd.RD_HOLD_PREV, rd.RD_QUADRATIC, rd.RD_NEAR | rd.RD_FARFIELD, rd.RD_NEAR | 64,
                   rd.RD_NEAR | rd.RD_LINEAR | rd.RD_HOLD_PREV):
         assert lib.rd_deposit_noalloc(ctypes.cast(cells, ctypes.c_void_p), None, 1, 0.0, 0.1, 8, flags,
                                       ctypes.byref(t), 16, None, None) == rd.RD_ERR_ARG, flags

@@ -440,6 +440,77 @@ def test_linear_interpolation_chunks_and_particle_splits():
         assert parity_err(E, Ef) <= 2e-6 and parity_err(B, Bf) <= 2e-6
 
 
+# --------------------------------------------------------------------------------------------
+# quadratic-in-time interpolation (RD_QUADRATIC)
+# --------------------------------------------------------------------------------------------
+def _quadratic_cases():
+    out = []
+    for tr, det in _linear_cases():
+        det.flags = (det.flags & ~W.RD_LINEAR) | W.RD_QUADRATIC
+        out.append((tr, det))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", [0, 1, 2, 3])
+def test_quadratic_interpolation(precision, case):
+    """RD_QUADRATIC (the quadratic through the fields of samples k-2, k-1, k) on the four cases of the
+    linear interpolation -- window cuts and per-cell origins, the undulator ensemble, intervals
+    spanning several bins in tracked and untracked blocks, the far-field limit: every cell against the
+    oracle (clipped counts exact in FP64)."""
+    tr, det = _quadratic_cases()[case]
+    check(tr, det, precision)
+
+
+def test_quadratic_chunks_streams_and_batch():
+    """RD_QUADRATIC does not depend on how the work is split: step chunks of 64 and 100 intervals
+    (every chunk starts from the fields of the two samples before it), two calls over particle
+    halves, the stream in stretches of 1, 1, 7, 64 and the rest (the detector keeps three samples and
+    the trajectory's interval count), and one batched launch beside a held problem -- each equals
+    the plain call (2e-6), and the plain call the oracle."""
+    import torch
+    tr, det = _quadratic_cases()[0]
+    xd, ud, qd = (torch.from_numpy(a).cuda() for a in (tr.x, tr.u, tr.q))
+    ref = rd.RadiationDetector.from_workload(det, "mixed")
+    ref.deposit(xd, ud, qd, tr.t0, tr.dt)
+    Er, Br = ref.read()
+    Eo, Bo, _ = oracle.deposit(tr, det)
+    assert parity_err(Er, Eo) <= TOL["mixed"] and parity_err(Br, Bo) <= TOL["mixed"]
+    for chunk in (64, 100):
+        d = rd.RadiationDetector.from_workload(det, "mixed")
+        d.set_chunk(chunk)
+        for sl in (slice(0, 2), slice(2, tr.n_part)):
+            one = tr.subset(range(tr.n_part)[sl])
+            d.deposit(torch.from_numpy(one.x).cuda(), torch.from_numpy(one.u).cuda(),
+                      torch.from_numpy(one.q).cuda(), one.t0, one.dt)
+        E, B = d.read()
+        d.close()
+        assert parity_err(E, Er) <= 2e-6 and parity_err(B, Br) <= 2e-6, chunk
+    for precision in ("mixed", "fp64"):
+        d = rd.RadiationDetector.from_workload(det, precision)
+        k = 0
+        for m in (1, 1, 7, 64, tr.n_samples):
+            b = min(tr.n_samples, k + m)
+            d.deposit_stream(xd[:, k:b].contiguous(), ud[:, k:b].contiguous(), qd, tr.t0 + k * tr.dt, tr.dt)
+            k = b
+            if k >= tr.n_samples:
+                break
+        E, B = d.read()
+        d.close()
+        tol = 2e-6 if precision == "mixed" else 1e-10
+        want = (Er, Br) if precision == "mixed" else (Eo, Bo)
+        assert parity_err(E, want[0]) <= tol and parity_err(B, want[1]) <= tol, precision
+    det_held = W.Detector(det.pix_pos, det.pix_t0, det.t_min, det.dt_det, det.n_bins, W.RD_NEAR | W.RD_FAR)
+    dets = [rd.RadiationDetector.from_workload(det, "mixed"), rd.RadiationDetector.from_workload(det_held, "mixed")]
+    keep = rd.deposit_batch(dets, [(xd, ud, qd, tr.t0, tr.dt)] * 2)
+    E0, B0 = dets[0].read()
+    assert parity_err(E0, Er) <= 2e-6 and parity_err(B0, Br) <= 2e-6
+    for dd in dets:
+        dd.close()
+    ref.close()
+    del keep
+
+
 def test_measure_fma_peaks_plausible():
     """The FMA microbenchmark (roofline denominator): FP32 within the 152-SM part's range
     (at most 152 x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s; a run far below that would be a
