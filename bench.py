@@ -43,9 +43,10 @@ UNIT = "deposits/s"
 FLOPS_PER_DEPOSIT_MIXED = 75
 FLOPS_PER_CROSSING_MIXED = 9
 # FP64 operations of the plain kernel per deposit, counted from its source the same way (square
-# root, division and floor count 1 each): arrival time (Eq. 2) 14, Eq. 1 with B = n x E 56,
-# accumulation into the running bin 14.
-FLOPS_PER_DEPOSIT_FP64 = 84
+# root, reciprocal and floor count 1 each): arrival time (Eq. 2, t_k from the record) 12, Eq. 1
+# multiplied out over the one reciprocal 1/(kappa R) with B = n x E 45, accumulation into the
+# running bin 14.
+FLOPS_PER_DEPOSIT_FP64 = 71
 # FP32 lanes per multiprocessor of this architecture (sm_103a: 4 sub-partitions x 32).
 FP32_LANES_PER_SM = 128
 WORKLOAD_UNDULATOR = ("undulator ensemble: 1000 e- (gamma 20, K 1, 10 periods) x 4000 steps, "

@@ -542,8 +542,8 @@ static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream
             LaunchTimer timer(d, s);
             RD_CUDA(launch_deposit_mixed(P, s), "deposit (mixed)");
         } else {
-            RD_CUDA(launch_precompute_fp64(x, u, np, t->n_samples, t->dt, static_cast<RecD*>(d->rec),
-                                           d->counters, s),
+            RD_CUDA(launch_precompute_fp64(x, u, np, t->n_samples, t->t0, t->dt, d->flags,
+                                           static_cast<RecD*>(d->rec), d->counters, s),
                     "precompute");
             LaunchTimer timer(d, s);
             RD_CUDA(launch_deposit_fp64(P, d->flags, s), "deposit (fp64)");
@@ -713,8 +713,8 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
         const size_t off = (size_t)p0 * t->n_samples * 3;
         RD_CUDA(cudaMemsetAsync(d->gbeta, 0, per_part_gb * np, s), "clear gradient scratch");
         if (fp64)
-            RD_CUDA(launch_precompute_fp64(t->x + off, t->u + off, np, t->n_samples, t->dt, static_cast<RecD*>(d->rec),
-                                           d->counters, s),
+            RD_CUDA(launch_precompute_fp64(t->x + off, t->u + off, np, t->n_samples, t->t0, t->dt,
+                                           RD_NEAR | RD_FAR, static_cast<RecD*>(d->rec), d->counters, s),
                     "precompute");
         else
             RD_CUDA(launch_precompute_mixed(t->x + off, t->u + off, nullptr, 0.0, np, t->n_samples, t->dt, d->flags,

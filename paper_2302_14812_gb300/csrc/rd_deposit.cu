@@ -91,9 +91,10 @@ __global__ void k_precompute_mixed(const double* __restrict__ x, const double* _
 }
 
 __global__ void k_precompute_fp64(const double* __restrict__ x, const double* __restrict__ u,
-                                  int n_part, int n_samples, double dt, RecD* __restrict__ rec,
-                                  DevCounters* counters)
+                                  int n_part, int n_samples, double t0, double dt, int flags,
+                                  RecD* __restrict__ rec, DevCounters* counters)
 {
+    const double near = (flags & RD_NEAR) ? 1.0 : 0.0, far = (flags & RD_FAR) ? 1.0 : 0.0;
     const long long total = (long long)n_part * n_samples;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -115,9 +116,9 @@ __global__ void k_precompute_fp64(const double* __restrict__ x, const double* __
         }
         if (bad) atomicOr(&counters->errors, ERRBIT_INPUT);
         RecD r;
-        r.xa = D4{xk[0], xk[1], xk[2], 0.0};
-        r.bb = D4{bx, by, bz, ig2};
-        r.bd = D4{ax, ay, az, 0.0};
+        r.xa = D4{xk[0], xk[1], xk[2], __dadd_rn(t0, __dmul_rn((double)k, dt))};
+        r.bb = D4{bx, by, bz, near * ig2};
+        r.bd = D4{far * ax, far * ay, far * az, 0.0};
         rec[i] = r;
     }
 }
@@ -145,34 +146,54 @@ __device__ __forceinline__ void flush_f64(double* row, int n_bins, int b, const 
     }
 }
 
-// Eq. 1 at one cell; R = |x_cell - x_k| as computed for the arrival time (Eq. 2).  With |n| = 1,
-// n x ((n - beta) x betadot) = (n - beta)(n.betadot) - kappa betadot, so both terms share one form:
-//   E = q / (kappa^3 R) [(n - beta)(gamma^-2 / R + n.betadot) - kappa betadot],   B = n x E
-// (gamma^-2 / R: velocity term, RD_NEAR; the rest: acceleration term, RD_FAR).
-__device__ __forceinline__ void fp64_field(const RecD& r, const D4& cl, double R, double q, int flags,
+// 1/d by Newton-Raphson iteration from the hardware's approximate reciprocal: each step
+// y <- y + y (1 - d y) squares the relative error, so two steps take the approximation to FP64
+// rounding.  For the positive, normal arguments the field passes (kappa R >= R / (2 gamma^2)).
+__device__ __forceinline__ double rcp_newton(double d)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+    double e = fma(-d, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-d, y, 1.0);
+    return fma(y, e, y);
+}
+
+// Eq. 1 at one cell, with d = x_cell - x_k and R = |d| as computed for the arrival time (Eq. 2).
+// Writing n = d / R and kappa R = R - beta.d, Eq. 1 multiplies out to
+//   E = q / (kappa R)^3 [a d - R v],   B = n x E = q / (kappa R)^3 v x d,
+//   a = gamma^-2 + d.betadot,   v = a beta + (kappa R) betadot,
+// so the only reciprocal is 1/(kappa R).  The record holds gamma^-2 = 0 without the velocity term
+// (RD_NEAR) and betadot = 0 without the acceleration term (RD_FAR).
+__device__ __forceinline__ void fp64_field(const RecD& r, double dx, double dy, double dz, double R, double q,
                                            double* F)
 {
-    const double near = (flags & RD_NEAR) ? 1.0 : 0.0, far = (flags & RD_FAR) ? 1.0 : 0.0;
-    const double dx = cl.x - r.xa.x, dy = cl.y - r.xa.y, dz = cl.z - r.xa.z;
-    // kappa R = R - beta.d; one division gives both 1/R and 1/kappa = R / (kappa R)
-    const double kR = R - (r.bb.x * dx + r.bb.y * dy + r.bb.z * dz);
-    const double inv = 1.0 / (R * kR);
-    const double rinv = kR * inv;
-    const double ik = (R * R) * inv;
-    const double nx = dx * rinv, ny = dy * rinv, nz = dz * rinv;
-    const double bx = nx - r.bb.x, by = ny - r.bb.y, bz = nz - r.bb.z;
-    const double c1 = near * (r.bb.w * rinv) + far * (nx * r.bd.x + ny * r.bd.y + nz * r.bd.z);
-    const double kb = far * (kR * rinv);
-    const double s = q * (ik * ik * ik) * rinv;
-    const double Ex = s * (bx * c1 - kb * r.bd.x);
-    const double Ey = s * (by * c1 - kb * r.bd.y);
-    const double Ez = s * (bz * c1 - kb * r.bd.z);
-    F[0] = Ex;
-    F[1] = Ey;
-    F[2] = Ez;
-    F[3] = ny * Ez - nz * Ey;
-    F[4] = nz * Ex - nx * Ez;
-    F[5] = nx * Ey - ny * Ex;
+    const double kR = fma(-r.bb.z, dz, fma(-r.bb.y, dy, fma(-r.bb.x, dx, R)));
+    const double a = fma(r.bd.z, dz, fma(r.bd.y, dy, fma(r.bd.x, dx, r.bb.w)));
+    const double w = rcp_newton(kR);
+    const double Q = (q * w) * (w * w);
+    const double Qa = Q * a, Qk = Q * kR;
+    const double vx = fma(Qa, r.bb.x, Qk * r.bd.x);     // Q v
+    const double vy = fma(Qa, r.bb.y, Qk * r.bd.y);
+    const double vz = fma(Qa, r.bb.z, Qk * r.bd.z);
+    F[0] = fma(Qa, dx, -R * vx);
+    F[1] = fma(Qa, dy, -R * vy);
+    F[2] = fma(Qa, dz, -R * vz);
+    F[3] = fma(vy, dz, -vz * dy);
+    F[4] = fma(vz, dx, -vx * dz);
+    F[5] = fma(vx, dy, -vy * dx);
+}
+
+// Eq. 2 for a record: the cell offset d, R = |d| and the arrival time in bins, with the same
+// separately rounded operations as arrival_bins (t_k from the record).
+__device__ __forceinline__ double fp64_arrival(const RecD& r, const D4& cl, double inv_dt_det, double& dx,
+                                               double& dy, double& dz, double& R)
+{
+    dx = __dsub_rn(cl.x, r.xa.x);
+    dy = __dsub_rn(cl.y, r.xa.y);
+    dz = __dsub_rn(cl.z, r.xa.z);
+    R = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+    return __dmul_rn(__dsub_rn(__dadd_rn(r.xa.w, R), cl.w), inv_dt_det);
 }
 
 // Far-field limit of the radiation term: E = q n_c x ((n_c - beta) x betadot) / (kappa^3 R_c),
@@ -199,14 +220,13 @@ __device__ __forceinline__ void fp64_field_ff(const RecD& r, double nx, double n
 __device__ __forceinline__ void fp64_deposit(D64State& st, const double* F, double c, double* row,
                                              int n_bins, int k, int k_begin, int k_end)
 {
-    const double fc = floor(c);
-    const int bc = clamp_bin(fc);
+    // floor by conversion (saturating), clamped like clamp_bin; past the clamp the bin is outside
+    // the window and its partial sums are never added
+    const int bc = min(max(__double2int_rd(c), -(1 << 30)), 1 << 30);
     if (bc <= st.b) {
         const double w = c - st.a;
-        if (w > 0.0) {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) st.acc[i] = fma(F[i], w, st.acc[i]);
-        }
+        for (int i = 0; i < 6; ++i) st.acc[i] = fma(F[i], w, st.acc[i]);
         st.a = c;
         return;
     }
@@ -216,7 +236,7 @@ __device__ __forceinline__ void fp64_deposit(D64State& st, const double* F, doub
     flush_f64(row, n_bins, st.b, st.acc);
     const int lo = max(st.b + 1, 0), hi = min(bc - 1, n_bins - 1);
     for (int j = lo; j <= hi; ++j) flush_f64(row, n_bins, j, F);
-    const double wl = c - fc;
+    const double wl = c - (double)bc;
 #pragma unroll
     for (int i = 0; i < 6; ++i) st.acc[i] = F[i] * wl;
     if (st.b < 0 && bc >= 0) st.n_below = k - k_begin + 1;
@@ -325,9 +345,13 @@ __device__ __forceinline__ void fp64_deposit_quad(D64State& st, const double* Fc
     st.a = c;
 }
 
+#ifndef RD_FP64_MINBLOCKS
+#define RD_FP64_MINBLOCKS 2      // CTAs of 256 threads per SM the held-field FP64 kernel is compiled for
+#endif
+
 // LM: interpolation family, 0 held field (default), 1 linear or held-previous (P.lin 1, 2), 2 quadratic
 template <int LM>
-__global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const DepositParams P,
+__global__ void __launch_bounds__(kDepositThreads, LM == 0 ? RD_FP64_MINBLOCKS : 2) k_deposit_fp64(const DepositParams P,
                                                                        int flags)
 {
     __shared__ __align__(128) RecD tile[2][kTileSteps];
@@ -401,9 +425,9 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
         if (ff) {
             fp64_field_ff(r0, ncx, ncy, ncz, Rc, q, flags, st.Fp);
         } else {
-            double R0;
-            (void)arrival_bins(r0.xa.x, r0.xa.y, r0.xa.z, cl, P.t0, 0, P.dt, P.inv_dt_det, R0);
-            fp64_field(r0, cl, R0, q, flags, st.Fp);
+            double dx, dy, dz, R0;
+            (void)fp64_arrival(r0, cl, P.inv_dt_det, dx, dy, dz, R0);
+            fp64_field(r0, dx, dy, dz, R0, q, st.Fp);
         }
         // RD_QUADRATIC: the field and arrival of the sample two before the chunk (used from the
         // trajectory's third interval on)
@@ -417,9 +441,9 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
                 st.ap = arrival_bins_ff(r1.xa.x, r1.xa.y, r1.xa.z, ncx, ncy, ncz, Rc, cl.w, P.t0, k_begin - 2, P.dt,
                                         P.inv_dt_det);
             } else {
-                double R1;
-                st.ap = arrival_bins(r1.xa.x, r1.xa.y, r1.xa.z, cl, P.t0, k_begin - 2, P.dt, P.inv_dt_det, R1);
-                fp64_field(r1, cl, R1, q, flags, st.Fpp);
+                double dx, dy, dz, R1;
+                st.ap = fp64_arrival(r1, cl, P.inv_dt_det, dx, dy, dz, R1);
+                fp64_field(r1, dx, dy, dz, R1, q, st.Fpp);
             }
         }
     }
@@ -448,9 +472,9 @@ __global__ void __launch_bounds__(kDepositThreads, 2) k_deposit_fp64(const Depos
                     fp64_field_ff(r, ncx, ncy, ncz, Rc, q, flags, F);
                     cbin = arrival_bins_ff(r.xa.x, r.xa.y, r.xa.z, ncx, ncy, ncz, Rc, cl.w, P.t0, k, P.dt, P.inv_dt_det);
                 } else {
-                    double R;
-                    cbin = arrival_bins(r.xa.x, r.xa.y, r.xa.z, cl, P.t0, k, P.dt, P.inv_dt_det, R);
-                    fp64_field(r, cl, R, q, flags, F);
+                    double dx, dy, dz, R;
+                    cbin = fp64_arrival(r, cl, P.inv_dt_det, dx, dy, dz, R);
+                    fp64_field(r, dx, dy, dz, R, q, F);
                 }
                 if (LM) {
                     const double a_prev = st.a;
@@ -523,11 +547,11 @@ cudaError_t launch_precompute_mixed(const double* x, const double* u, const doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part, int n_samples,
-                                   double dt, RecD* rec, DevCounters* counters, cudaStream_t s)
+cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part, int n_samples, double t0,
+                                   double dt, int flags, RecD* rec, DevCounters* counters, cudaStream_t s)
 {
     const long long n = (long long)n_part * n_samples;
-    k_precompute_fp64<<<grid_for(n, 256), 256, 0, s>>>(x, u, n_part, n_samples, dt, rec, counters);
+    k_precompute_fp64<<<grid_for(n, 256), 256, 0, s>>>(x, u, n_part, n_samples, t0, dt, flags, rec, counters);
     return cudaGetLastError();
 }
 

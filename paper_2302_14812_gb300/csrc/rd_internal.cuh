@@ -59,7 +59,9 @@ struct __align__(32) D4 {
     double x, y, z, w;
 };
 
-// FP64 path, 96 bytes: (x_k, 0), (beta_k, gamma_k^-2), (betadot_k, 0).
+// FP64 path, 96 bytes: (x_k, t_k), (beta_k, gamma_k^-2), (betadot_k, 0), with t_k = t0 + k dt rounded as
+// Eq. 2's arrival time takes it; gamma^-2 is stored as zero without the velocity term (RD_NEAR) and betadot
+// as zero without the acceleration term (RD_FAR).
 struct __align__(32) RecD {
     D4 xa;
     D4 bb;
@@ -170,8 +172,8 @@ const char* flags_error(int flags);
 cudaError_t launch_precompute_mixed(const double* x, const double* u, const double* q, double qscale, int n_part,
                                     int n_samples, double dt, int flags, RecS* rec, DevCounters* counters,
                                     cudaStream_t s);
-cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part, int n_samples,
-                                   double dt, RecD* rec, DevCounters* counters, cudaStream_t s);
+cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part, int n_samples, double t0,
+                                   double dt, int flags, RecD* rec, DevCounters* counters, cudaStream_t s);
 cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s);
 // shapes of the mixed kernel compiled into the library (held field, exact Eq. 1; the far-field and
 // interpolation variants and the batch kernel run the default shape, kMixedCellsPerCta x kMixedCells)
