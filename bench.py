@@ -43,10 +43,10 @@ UNIT = "deposits/s"
 FLOPS_PER_DEPOSIT_MIXED = 75
 FLOPS_PER_CROSSING_MIXED = 9
 # FP64 operations of the plain kernel per deposit, counted from its source the same way (square
-# root, reciprocal and floor count 1 each): arrival time (Eq. 2, t_k from the record) 12, Eq. 1
-# multiplied out over the one reciprocal 1/(kappa R) with B = n x E 45, accumulation into the
-# running bin 14.
-FLOPS_PER_DEPOSIT_FP64 = 71
+# root, reciprocal and the bin-edge compare count 1 each): arrival time (Eq. 2, t_k from the record)
+# 12, Eq. 1 multiplied out over the one reciprocal 1/(kappa R) with B = n x E (charge folded into
+# the record) 44, accumulation into the running bin 14.
+FLOPS_PER_DEPOSIT_FP64 = 70
 # FP32 lanes per multiprocessor of this architecture (sm_103a: 4 sub-partitions x 32).
 FP32_LANES_PER_SM = 128
 WORKLOAD_UNDULATOR = ("undulator ensemble: 1000 e- (gamma 20, K 1, 10 periods) x 4000 steps, "
@@ -383,8 +383,20 @@ def run_adjoint_workload(args):
     q = torch.from_numpy(tr.q).cuda()
     d = rd.RadiationDetector.from_workload(det, "mixed")
     d.set_timing(True)
+    # loss 1/2 sum |E - E_target|^2 over E: the target is the deposit of the same electrons with
+    # seeded perturbations of 1e-4 (a position offset and a momentum scale per electron), and the
+    # adjoint's input is the misfit E - E_target
     rng = np.random.default_rng(5)
-    gE = torch.from_numpy(rng.normal(size=(det.n_pix, det.n_bins, 3)).astype(np.float32)).cuda()
+    x_off = torch.from_numpy(1e-4 * rng.normal(size=(tr.n_part, 1, 3))).cuda()
+    u_scl = torch.from_numpy(1.0 + 1e-4 * rng.normal(size=(tr.n_part, 1, 1))).cuda()
+    d.deposit(x + x_off, u * u_scl, q, tr.t0, tr.dt)
+    E_tgt, _ = d.read("float32", "cuda")
+    d.zero()
+    d.deposit(x, u, q, tr.t0, tr.dt)
+    gE, _ = d.read("float32", "cuda")
+    gE -= E_tgt
+    misfit_rel = float(torch.linalg.norm(gE) / torch.linalg.norm(E_tgt))
+    del E_tgt, x_off, u_scl
     dc = rd.RadiationDetector.from_workload(det, "mixed")
     dc.set_timing(True)
     dc.set_adjoint_mode("compensated")
@@ -449,7 +461,9 @@ def run_adjoint_workload(args):
             "warmup": args.warmup, "ms_per_step": res["adjoint"]["ms_per_step"], "higher_is_better": True,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{tr.n_part} undulator e- (gamma 10, K 1) x 2000 steps, 64x64 cap x 1024 "
-                                   "bins, anchors recomputed every 250 samples", "deposits_per_step": deposits},
+                                   "bins, anchors recomputed every 250 samples; loss 1/2 |E - E_target|^2, target "
+                                   "from trajectories perturbed by 1e-4", "deposits_per_step": deposits,
+                       "misfit_rel_l2": misfit_rel},
             "forward": res["forward"], "adjoint": res["adjoint"],
             "adjoint_compensated": res["adjoint_compensated"], "fp64_adjoint": fp64,
             "adjoint_over_forward_time": res["adjoint"]["ms_per_step"] / res["forward"]["ms_per_step"]}

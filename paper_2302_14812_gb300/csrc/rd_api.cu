@@ -542,7 +542,7 @@ static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream
             LaunchTimer timer(d, s);
             RD_CUDA(launch_deposit_mixed(P, s), "deposit (mixed)");
         } else {
-            RD_CUDA(launch_precompute_fp64(x, u, np, t->n_samples, t->t0, t->dt, d->flags,
+            RD_CUDA(launch_precompute_fp64(x, u, q, np, t->n_samples, t->t0, t->dt, d->flags,
                                            static_cast<RecD*>(d->rec), d->counters, s),
                     "precompute");
             LaunchTimer timer(d, s);
@@ -713,7 +713,7 @@ rd_status rd_adjoint_trajectories(rd_detector* d, const rd_traj* t, const void* 
         const size_t off = (size_t)p0 * t->n_samples * 3;
         RD_CUDA(cudaMemsetAsync(d->gbeta, 0, per_part_gb * np, s), "clear gradient scratch");
         if (fp64)
-            RD_CUDA(launch_precompute_fp64(t->x + off, t->u + off, np, t->n_samples, t->t0, t->dt,
+            RD_CUDA(launch_precompute_fp64(t->x + off, t->u + off, nullptr, np, t->n_samples, t->t0, t->dt,
                                            RD_NEAR | RD_FAR, static_cast<RecD*>(d->rec), d->counters, s),
                     "precompute");
         else
@@ -990,17 +990,26 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
     std::vector<int> group_first{0};          // group g = segs[group_first[g], group_first[g + 1])
     std::vector<long long> item_off{0};       // per segment, restarting at 0 in every group
     size_t used = 0, rec_need = 256;
-    // Step chunks: the persistent launch fills the GPU from all problems at once, so a small problem
-    // keeps full-length chunks (fewer FP64 anchors) unless the whole batch is too small to fill it.
-    long long items_full = 0;
-    for (int i = 0; i < n; ++i) {
-        const int S = trajs[i].n_samples - 1;
-        if (trajs[i].n_part == 0 || S < 1) continue;
-        const int ncb = (dets[i]->n_pix + kMixedCellsPerCta - 1) / kMixedCellsPerCta;
-        const int ck = dets[i]->chunk_override > 0 ? std::min(dets[i]->chunk_override, S) : std::min(kDefaultChunk, S);
-        items_full += (long long)ncb * trajs[i].n_part * ((S + ck - 1) / ck);
-    }
-    const bool full_chunks = items_full >= 8LL * sm_count();
+    // Step chunks: the persistent launch fills the GPU from all problems at once, so every problem
+    // without a chunk of its own takes one batch-wide length: the default, halved (down to 512) while
+    // the batch has fewer than kBatchItemsPerSm items per multiprocessor, since the items still
+    // running at the end of the launch then leave much of the GPU idle (64 problems of 1-50
+    // electrons: 53.3 ms at 4096-step chunks, 47.0 at 1024, 46.3 at 512).  A batch too small to
+    // fill the GPU even so takes each problem's own choice.
+    auto items_at = [&](int cap) {
+        long long items = 0;
+        for (int i = 0; i < n; ++i) {
+            const int S = trajs[i].n_samples - 1;
+            if (trajs[i].n_part == 0 || S < 1) continue;
+            const int ncb = (dets[i]->n_pix + kMixedCellsPerCta - 1) / kMixedCellsPerCta;
+            const int ck = dets[i]->chunk_override > 0 ? std::min(dets[i]->chunk_override, S) : std::min(cap, S);
+            items += (long long)ncb * trajs[i].n_part * ((S + ck - 1) / ck);
+        }
+        return items;
+    };
+    int cap = kDefaultChunk;
+    while (cap > 512 && items_at(cap) < (long long)kBatchItemsPerSm * sm_count()) cap /= 2;
+    const bool full_chunks = items_at(cap) >= 8LL * sm_count();
     for (int i = 0; i < n; ++i) {
         const rd_traj& t = trajs[i];
         const int S = t.n_samples - 1;
@@ -1009,7 +1018,7 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
         const size_t budget = std::max(d0->batch_budget, per_part);
         const int ncb = (dets[i]->n_pix + kMixedCellsPerCta - 1) / kMixedCellsPerCta;
         const int chunk = full_chunks ? (dets[i]->chunk_override > 0 ? std::min(dets[i]->chunk_override, S)
-                                                                      : std::min(kDefaultChunk, S))
+                                                                      : std::min(cap, S))
                                       : choose_chunk(dets[i], t.n_part, S, ncb);
         for (int p0 = 0; p0 < t.n_part;) {
             if (budget - std::min(used, budget) < per_part) {      // close the group

@@ -91,8 +91,8 @@ __global__ void k_precompute_mixed(const double* __restrict__ x, const double* _
 }
 
 __global__ void k_precompute_fp64(const double* __restrict__ x, const double* __restrict__ u,
-                                  int n_part, int n_samples, double t0, double dt, int flags,
-                                  RecD* __restrict__ rec, DevCounters* counters)
+                                  const double* __restrict__ q, int n_part, int n_samples, double t0,
+                                  double dt, int flags, RecD* __restrict__ rec, DevCounters* counters)
 {
     const double near = (flags & RD_NEAR) ? 1.0 : 0.0, far = (flags & RD_FAR) ? 1.0 : 0.0;
     const long long total = (long long)n_part * n_samples;
@@ -116,9 +116,10 @@ __global__ void k_precompute_fp64(const double* __restrict__ x, const double* __
         }
         if (bad) atomicOr(&counters->errors, ERRBIT_INPUT);
         RecD r;
+        const double qp = q ? q[i / n_samples] : 1.0;
         r.xa = D4{xk[0], xk[1], xk[2], __dadd_rn(t0, __dmul_rn((double)k, dt))};
-        r.bb = D4{bx, by, bz, near * ig2};
-        r.bd = D4{far * ax, far * ay, far * az, 0.0};
+        r.bb = D4{bx, by, bz, (near * qp) * ig2};
+        r.bd = D4{(far * qp) * ax, (far * qp) * ay, (far * qp) * az, 0.0};
         rec[i] = r;
     }
 }
@@ -133,6 +134,7 @@ struct D64State {
     double Fp[6];   // RD_LINEAR / RD_QUADRATIC: field of the previous sample
     double Fpp[6];  // RD_QUADRATIC: field two samples back ...
     double ap;      // ... and its arrival (bins)
+    double e;       // held field: upper edge of bin b (b + 1)
     int n_below;
     int n_above;
 };
@@ -163,15 +165,15 @@ __device__ __forceinline__ double rcp_newton(double d)
 // Writing n = d / R and kappa R = R - beta.d, Eq. 1 multiplies out to
 //   E = q / (kappa R)^3 [a d - R v],   B = n x E = q / (kappa R)^3 v x d,
 //   a = gamma^-2 + d.betadot,   v = a beta + (kappa R) betadot,
-// so the only reciprocal is 1/(kappa R).  The record holds gamma^-2 = 0 without the velocity term
-// (RD_NEAR) and betadot = 0 without the acceleration term (RD_FAR).
-__device__ __forceinline__ void fp64_field(const RecD& r, double dx, double dy, double dz, double R, double q,
-                                           double* F)
+// so the only reciprocal is 1/(kappa R).  The record holds q gamma^-2 and q betadot, with gamma^-2 = 0
+// without the velocity term (RD_NEAR) and betadot = 0 without the acceleration term (RD_FAR), so that
+// a and v carry the charge.
+__device__ __forceinline__ void fp64_field(const RecD& r, double dx, double dy, double dz, double R, double* F)
 {
     const double kR = fma(-r.bb.z, dz, fma(-r.bb.y, dy, fma(-r.bb.x, dx, R)));
     const double a = fma(r.bd.z, dz, fma(r.bd.y, dy, fma(r.bd.x, dx, r.bb.w)));
     const double w = rcp_newton(kR);
-    const double Q = (q * w) * (w * w);
+    const double Q = w * (w * w);
     const double Qa = Q * a, Qk = Q * kR;
     const double vx = fma(Qa, r.bb.x, Qk * r.bd.x);     // Q v
     const double vy = fma(Qa, r.bb.y, Qk * r.bd.y);
@@ -197,13 +199,13 @@ __device__ __forceinline__ double fp64_arrival(const RecD& r, const D4& cl, doub
 }
 
 // Far-field limit of the radiation term: E = q n_c x ((n_c - beta) x betadot) / (kappa^3 R_c),
-// kappa = 1 - beta.n_c, B = n_c x E.
-__device__ __forceinline__ void fp64_field_ff(const RecD& r, double nx, double ny, double nz, double Rc, double q,
-                                              int flags, double* F)
+// kappa = 1 - beta.n_c, B = n_c x E (the record's betadot carries q, and is zero without RD_FAR).
+__device__ __forceinline__ void fp64_field_ff(const RecD& r, double nx, double ny, double nz, double Rc,
+                                              double* F)
 {
     const double mx = nx - r.bb.x, my = ny - r.bb.y, mz = nz - r.bb.z;
     const double kap = 1.0 - (r.bb.x * nx + r.bb.y * ny + r.bb.z * nz);
-    const double s = (flags & RD_FAR) ? q / (kap * kap * kap * Rc) : 0.0;
+    const double s = 1.0 / (kap * kap * kap * Rc);
     const double wx = my * r.bd.z - mz * r.bd.y;
     const double wy = mz * r.bd.x - mx * r.bd.z;
     const double wz = mx * r.bd.y - my * r.bd.x;
@@ -216,32 +218,36 @@ __device__ __forceinline__ void fp64_field_ff(const RecD& r, double nx, double n
     F[5] = nx * Ey - ny * Ex;
 }
 
-// Deposit [st.a, c] with the bin-overlap arithmetic of the integrator detector.
+// Deposit [st.a, c] with the bin-overlap arithmetic of the integrator detector.  The part inside the
+// filling bin (up to its upper edge st.e = st.b + 1) is added on every step; only an interval that
+// passes the edge flushes the bin and starts the next one with the rest, so the operations that
+// every lane of a warp runs stay few (nearly every warp has a lane that crosses on each step).
 __device__ __forceinline__ void fp64_deposit(D64State& st, const double* F, double c, double* row,
                                              int n_bins, int k, int k_begin, int k_end)
 {
-    // floor by conversion (saturating), clamped like clamp_bin; past the clamp the bin is outside
-    // the window and its partial sums are never added
-    const int bc = min(max(__double2int_rd(c), -(1 << 30)), 1 << 30);
-    if (bc <= st.b) {
-        const double w = c - st.a;
+    const bool cr = c >= st.e;
+    const double wi = (cr ? st.e : c) - st.a;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) st.acc[i] = fma(F[i], w, st.acc[i]);
-        st.a = c;
-        return;
+    for (int i = 0; i < 6; ++i) st.acc[i] = fma(F[i], wi, st.acc[i]);
+    if (cr) {
+        flush_f64(row, n_bins, st.b, st.acc);
+        int b = st.b + 1;
+        double e = st.e;                       // lower edge of bin b
+        if (c >= e + 1.0) {                    // more than one edge: whole bins in between
+            const int bc = clamp_bin(floor(c));
+            const int lo = max(b, 0), hi = min(bc - 1, n_bins - 1);
+            for (int j = lo; j <= hi; ++j) flush_f64(row, n_bins, j, F);
+            b = bc;
+            e = (double)bc;
+        }
+        const double wl = c - e;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) st.acc[i] = F[i] * wl;
+        if (st.b < 0 && b >= 0) st.n_below = k - k_begin + 1;
+        if (st.b < n_bins && b >= n_bins) st.n_above = k_end - k + 1;
+        st.b = b;
+        st.e = e + 1.0;
     }
-    const double w1 = (double)(st.b + 1) - st.a;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) st.acc[i] = fma(F[i], w1, st.acc[i]);
-    flush_f64(row, n_bins, st.b, st.acc);
-    const int lo = max(st.b + 1, 0), hi = min(bc - 1, n_bins - 1);
-    for (int j = lo; j <= hi; ++j) flush_f64(row, n_bins, j, F);
-    const double wl = c - (double)bc;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) st.acc[i] = F[i] * wl;
-    if (st.b < 0 && bc >= 0) st.n_below = k - k_begin + 1;
-    if (st.b < n_bins && bc >= n_bins) st.n_above = k_end - k + 1;
-    st.b = bc;
     st.a = c;
 }
 
@@ -411,6 +417,7 @@ __global__ void __launch_bounds__(kDepositThreads, LM == 0 ? RD_FP64_MINBLOCKS :
         live = (ue > 0.0) && (ua < (double)P.n_bins);
         st.a = ua;
         st.b = clamp_bin(floor(ua));
+        st.e = LM == 0 ? (double)st.b + 1.0 : 0.0;
         st.n_below = (ua < 0.0) ? n_int : 0;
         st.n_above = 0;
 #pragma unroll
@@ -418,16 +425,15 @@ __global__ void __launch_bounds__(kDepositThreads, LM == 0 ? RD_FP64_MINBLOCKS :
         row = static_cast<double*>(P.fields) + (size_t)cell * P.n_bins * 6;
         if (!live) atomicAdd(&P.counters->clipped, (unsigned long long)n_int);
     }
-    const double q = P.q ? P.q[p] : 1.0;
     if (LM && live) {
         // field of the sample before the chunk; a trajectory's first interval holds F_1
         const RecD r0 = rec[k_begin > 1 ? k_begin - 1 : 1];
         if (ff) {
-            fp64_field_ff(r0, ncx, ncy, ncz, Rc, q, flags, st.Fp);
+            fp64_field_ff(r0, ncx, ncy, ncz, Rc, st.Fp);
         } else {
             double dx, dy, dz, R0;
             (void)fp64_arrival(r0, cl, P.inv_dt_det, dx, dy, dz, R0);
-            fp64_field(r0, dx, dy, dz, R0, q, st.Fp);
+            fp64_field(r0, dx, dy, dz, R0, st.Fp);
         }
         // RD_QUADRATIC: the field and arrival of the sample two before the chunk (used from the
         // trajectory's third interval on)
@@ -437,13 +443,13 @@ __global__ void __launch_bounds__(kDepositThreads, LM == 0 ? RD_FP64_MINBLOCKS :
         if (LM == 2 && k_begin >= 3) {
             const RecD r1 = rec[k_begin - 2];
             if (ff) {
-                fp64_field_ff(r1, ncx, ncy, ncz, Rc, q, flags, st.Fpp);
+                fp64_field_ff(r1, ncx, ncy, ncz, Rc, st.Fpp);
                 st.ap = arrival_bins_ff(r1.xa.x, r1.xa.y, r1.xa.z, ncx, ncy, ncz, Rc, cl.w, P.t0, k_begin - 2, P.dt,
                                         P.inv_dt_det);
             } else {
                 double dx, dy, dz, R1;
                 st.ap = fp64_arrival(r1, cl, P.inv_dt_det, dx, dy, dz, R1);
-                fp64_field(r1, dx, dy, dz, R1, q, st.Fpp);
+                fp64_field(r1, dx, dy, dz, R1, st.Fpp);
             }
         }
     }
@@ -469,12 +475,12 @@ __global__ void __launch_bounds__(kDepositThreads, LM == 0 ? RD_FP64_MINBLOCKS :
                 const int k = k0 + i;
                 double cbin;
                 if (ff) {
-                    fp64_field_ff(r, ncx, ncy, ncz, Rc, q, flags, F);
+                    fp64_field_ff(r, ncx, ncy, ncz, Rc, F);
                     cbin = arrival_bins_ff(r.xa.x, r.xa.y, r.xa.z, ncx, ncy, ncz, Rc, cl.w, P.t0, k, P.dt, P.inv_dt_det);
                 } else {
                     double dx, dy, dz, R;
                     cbin = fp64_arrival(r, cl, P.inv_dt_det, dx, dy, dz, R);
-                    fp64_field(r, dx, dy, dz, R, q, F);
+                    fp64_field(r, dx, dy, dz, R, F);
                 }
                 if (LM) {
                     const double a_prev = st.a;
@@ -547,11 +553,11 @@ cudaError_t launch_precompute_mixed(const double* x, const double* u, const doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part, int n_samples, double t0,
-                                   double dt, int flags, RecD* rec, DevCounters* counters, cudaStream_t s)
+cudaError_t launch_precompute_fp64(const double* x, const double* u, const double* q, int n_part, int n_samples,
+                                   double t0, double dt, int flags, RecD* rec, DevCounters* counters, cudaStream_t s)
 {
     const long long n = (long long)n_part * n_samples;
-    k_precompute_fp64<<<grid_for(n, 256), 256, 0, s>>>(x, u, n_part, n_samples, t0, dt, flags, rec, counters);
+    k_precompute_fp64<<<grid_for(n, 256), 256, 0, s>>>(x, u, q, n_part, n_samples, t0, dt, flags, rec, counters);
     return cudaGetLastError();
 }
 

@@ -59,9 +59,10 @@ struct __align__(32) D4 {
     double x, y, z, w;
 };
 
-// FP64 path, 96 bytes: (x_k, t_k), (beta_k, gamma_k^-2), (betadot_k, 0), with t_k = t0 + k dt rounded as
-// Eq. 2's arrival time takes it; gamma^-2 is stored as zero without the velocity term (RD_NEAR) and betadot
-// as zero without the acceleration term (RD_FAR).
+// FP64 path, 96 bytes: (x_k, t_k), (beta_k, q gamma_k^-2), (q betadot_k, 0), with t_k = t0 + k dt rounded
+// as Eq. 2's arrival time takes it and q the particle's charge; gamma^-2 is stored as zero without the
+// velocity term (RD_NEAR) and betadot as zero without the acceleration term (RD_FAR).  The FP64 adjoint
+// takes the records with q = 1 and both terms.
 struct __align__(32) RecD {
     D4 xa;
     D4 bb;
@@ -110,7 +111,9 @@ struct DepositParams {
 // chunks slowest; inside a chunk, groups of P.group cell blocks; inside a group the cell block
 // fastest, then the particle.  Consecutive CTAs so take one particle to the group's cell blocks
 // back to back (its staged records are read from DRAM once per group, then from L2) while the
-// resident CTAs reduce into the group's detector slice.  group = 1 is particle-fastest order.
+// resident CTAs reduce into the group's detector slice.  Odd groups take the particles in reverse
+// order, so that a group starts on the records the previous one read last (still in L2).
+// group = 1 is particle-fastest order.
 __device__ __forceinline__ void item_coords(unsigned idx, const DepositParams& P, int& p, int& cb, int& ch)
 {
     // 32-bit arithmetic: a launch (or a batch segment) holds fewer than 2^31 items (host-checked)
@@ -124,6 +127,7 @@ __device__ __forceinline__ void item_coords(unsigned idx, const DepositParams& P
     const unsigned Gg = min(G, (unsigned)P.n_cell_blocks - g * G);
     cb = (int)(g * G + r % Gg);
     p = (int)(r / Gg);
+    if (g & 1u) p = P.n_part - 1 - p;
 }
 #endif
 
@@ -143,6 +147,7 @@ constexpr int kMixedMaxBins = 1 << 22;         // bins per cell of an RD_MIXED d
 #endif
 constexpr int kTileSteps = RD_TILE_STEPS;   // intervals per shared-memory tile
 constexpr int kDefaultChunk = 4096;    // intervals per work item (one FP64 anchor at each end)
+constexpr int kBatchItemsPerSm = 512;  // work items per multiprocessor the batched deposit aims for
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // give up a wait after 2 s
 
 // host helpers (rd_api.cu)
@@ -172,8 +177,8 @@ const char* flags_error(int flags);
 cudaError_t launch_precompute_mixed(const double* x, const double* u, const double* q, double qscale, int n_part,
                                     int n_samples, double dt, int flags, RecS* rec, DevCounters* counters,
                                     cudaStream_t s);
-cudaError_t launch_precompute_fp64(const double* x, const double* u, int n_part, int n_samples, double t0,
-                                   double dt, int flags, RecD* rec, DevCounters* counters, cudaStream_t s);
+cudaError_t launch_precompute_fp64(const double* x, const double* u, const double* q, int n_part, int n_samples,
+                                   double t0, double dt, int flags, RecD* rec, DevCounters* counters, cudaStream_t s);
 cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s);
 // shapes of the mixed kernel compiled into the library (held field, exact Eq. 1; the far-field and
 // interpolation variants and the batch kernel run the default shape, kMixedCellsPerCta x kMixedCells)

@@ -146,10 +146,10 @@ def test_uneven_64_problem_set_reduced_particles():
     """The 64 uneven problems (undulator / circular / oscillator, steps 500-8000, 32^2-128^2 cells,
     16*side bins) with particle counts scaled by 0.004: one batched launch vs separate launches
     (compared on the device, problem by problem), and the oracle on one cell of every eighth
-    problem.  The batched launch keeps full-length step chunks while a separate launch of a small
-    problem halves its chunk to fill the GPU, so the two FP32 walks re-anchor at different steps
-    and agree to the mixed path's rounding (bar 1e-5, ten times below the oracle bar), not bit
-    for bit."""
+    problem.  The batched launch takes one batch-wide step chunk (halved while the batch is short of
+    work items) while a separate launch of a small problem halves its chunk to fill the GPU, so the
+    two FP32 walks re-anchor at different steps and agree to the mixed path's rounding (bar 1e-5,
+    ten times below the oracle bar), not bit for bit."""
     import torch
     probs = [(tr, det) for _, tr, det in W.batch_problems(64, seed=4, scale=0.004)]
     stream = torch.cuda.Stream()
