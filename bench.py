@@ -844,7 +844,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "precision": "mixed: FP32 fields and accumulation, arrival times FP64-anchored at both ends of each step chunk (up to 4096 intervals)",
+        "precision": "mixed: FP32 fields and accumulation, arrival times FP64-anchored at both ends of each step chunk (up to 2048 intervals)",
         "shape": mixed_shape,
         "config": {"workload": undulator_workload(tr.n_part),
                    "deposits_per_step_per_gpu": deposits, "parallelism": f"replicas x{world}",

@@ -300,7 +300,7 @@ RD_API rd_status rd_set_batch_budget(rd_detector* det, long long bytes);
 
 /*
  * Steps per work item (the step chunk between exact FP64 arrival anchors) for this detector's
- * deposits; 0 = automatic (4096, halved while the grid would be too small to fill the GPU).
+ * deposits; 0 = automatic (2048, halved while the grid would be too small to fill the GPU).
  */
 RD_API rd_status rd_set_chunk(rd_detector* det, int32_t chunk);
 
@@ -320,10 +320,12 @@ RD_API rd_status rd_autotune(rd_detector* det, const rd_traj* traj, rd_stream st
  * blocks take each particle back to back (its records then come from DRAM once per group).
  *   cells_per_cta    64, 128 or 256 (default 256)
  *   cells_per_thread 1 or 2 (default 2)
- *   chunk            intervals per work item, >= 0 (0: automatic, 4096 halved while the grid would
+ *   chunk            intervals per work item, >= 0 (0: automatic, 2048 halved while the grid would
  *                    leave the GPU idle)
- *   group            cell blocks per group, >= 0 (0: automatic, as many as keep the group's slice of
- *                    the detector, cells_per_cta x n_bins x 32 bytes each, within 70 MB of L2, at most 8)
+ *   group            cell blocks per group, >= 0 (0: automatic, as many as keep the group's active slice
+ *                    of the detector -- cells_per_cta x 32 bytes x the bins one chunk's arrivals span,
+ *                    taken as 1.25 x its share of the trajectory's bins, each -- within 70 MB of L2,
+ *                    at most 8)
  * The far-field limit and the interpolation variants run the default cells per CTA and per thread
  * (their chunk and group follow the shape).  rd_deposit_batch uses every detector's chunk and group
  * and the default cells per CTA and per thread.  Results do not depend on the shape beyond the

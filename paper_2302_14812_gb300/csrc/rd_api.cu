@@ -223,7 +223,7 @@ void fill_mixed_params(DepositParams& P, const rd_detector* d, const rd_traj* t,
     P.cpc = kMixedCellsPerCta;
     P.nc = kMixedCells;
     P.group = d->group_override > 0 ? std::min(d->group_override, P.n_cell_blocks)
-                                    : cell_group(P.n_cell_blocks, d->n_bins);
+                                    : cell_group(P.n_cell_blocks, d->n_bins, kMixedCellsPerCta, chunk, S);
 }
 
 }  // namespace
@@ -263,7 +263,7 @@ int auto_chunk(long long n_cell_blocks, long long n_part, int S)
     return std::max(1, chunk);
 }
 
-int cell_group(int n_cell_blocks, int n_bins, int cells_per_cta)
+int cell_group(int n_cell_blocks, int n_bins, int cells_per_cta, int chunk, int n_intervals)
 {
 #ifdef RD_GROUP
     return std::max(1, std::min(n_cell_blocks, RD_GROUP));
@@ -271,7 +271,10 @@ int cell_group(int n_cell_blocks, int n_bins, int cells_per_cta)
 #ifndef RD_GROUP_SLICE_MB
 #define RD_GROUP_SLICE_MB 70
 #endif
-    const double slice = (double)cells_per_cta * n_bins * 32.0;
+    // a chunk's arrivals span about its share of the trajectory's bins (the window holds every
+    // arrival), and the resident CTAs, at different points of their chunks, a quarter more
+    const double span = std::min(1.0, 1.25 * (double)chunk / (double)std::max(1, n_intervals));
+    const double slice = (double)cells_per_cta * n_bins * 32.0 * span;
     const int g = (int)((double)RD_GROUP_SLICE_MB * 1048576.0 / slice);
     return std::max(1, std::min(std::min(n_cell_blocks, 8), g));
 #endif
@@ -534,7 +537,7 @@ static rd_status deposit_from(rd_detector* d, const rd_traj* t, rd_stream stream
         P.nc = nc;
         P.group = !mixed ? 1
                          : d->group_override > 0 ? std::min(d->group_override, n_cell_blocks)
-                                                 : cell_group(n_cell_blocks, d->n_bins, cpc);
+                                                 : cell_group(n_cell_blocks, d->n_bins, cpc, chunk, S - k_first + 1);
         if (mixed) {
             RD_CUDA(launch_precompute_mixed(x, u, q, t->dt / d->dt_det, np, t->n_samples, t->dt, d->flags,
                                             static_cast<RecS*>(d->rec), d->counters, s),
@@ -1010,10 +1013,25 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
     int cap = kDefaultChunk;
     while (cap > 512 && items_at(cap) < (long long)kBatchItemsPerSm * sm_count()) cap /= 2;
     const bool full_chunks = items_at(cap) >= 8LL * sm_count();
-    for (int i = 0; i < n; ++i) {
+    // problems of one walk family form consecutive groups: each group is one launch of its
+    // family's persistent kernel
+    auto family_of = [&](int i) {
+        const int f = dets[i]->flags;
+        return ((f & RD_FARFIELD) ? 4 : 0) + ((f & RD_QUADRATIC) ? 2 : (f & (RD_LINEAR | RD_HOLD_PREV)) ? 1 : 0);
+    };
+    std::vector<int> order;
+    for (int fam : {0, 1, 2, 4, 5, 6})
+        for (int i = 0; i < n; ++i)
+            if (family_of(i) == fam) order.push_back(i);
+    for (int i : order) {
         const rd_traj& t = trajs[i];
         const int S = t.n_samples - 1;
         if (t.n_part == 0 || S < 1) continue;
+        if (!segs.empty() && family_of(segs.back().prob) != family_of(i) && group_first.back() != (int)segs.size()) {
+            group_first.push_back((int)segs.size());            // a new family starts a new group
+            item_off.push_back(0);
+            used = 0;
+        }
         const size_t per_part = sizeof(RecS) * (size_t)t.n_samples;
         const size_t budget = std::max(d0->batch_budget, per_part);
         const int ncb = (dets[i]->n_pix + kMixedCellsPerCta - 1) / kMixedCellsPerCta;
@@ -1021,8 +1039,8 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
                                                                       : std::min(cap, S))
                                       : choose_chunk(dets[i], t.n_part, S, ncb);
         for (int p0 = 0; p0 < t.n_part;) {
-            if (budget - std::min(used, budget) < per_part) {      // close the group
-                group_first.push_back((int)segs.size());
+            if (budget - std::min(used, budget) < per_part && group_first.back() != (int)segs.size()) {
+                group_first.push_back((int)segs.size());           // close the group
                 item_off.push_back(0);
                 used = 0;
             }
@@ -1105,7 +1123,7 @@ rd_status rd_deposit_batch(int32_t n, rd_detector* const* dets, const rd_traj* t
             }
             // segment k's items are d_off[k + gi], relative to the group's first item
             if (e == cudaSuccess)
-                e = launch_deposit_batch(d_probs + a, d_off + a + gi, b - a, d_counter + gi, batch_grid(), s);
+                e = launch_deposit_batch(family_of(segs[a].prob), d_probs + a, d_off + a + gi, b - a, d_counter + gi, s);
         }
         return e;
     };

@@ -146,7 +146,7 @@ constexpr int kMixedMaxBins = 1 << 22;         // bins per cell of an RD_MIXED d
 #define RD_TILE_STEPS 64
 #endif
 constexpr int kTileSteps = RD_TILE_STEPS;   // intervals per shared-memory tile
-constexpr int kDefaultChunk = 4096;    // intervals per work item (one FP64 anchor at each end)
+constexpr int kDefaultChunk = 2048;    // intervals per work item (one FP64 anchor at each end)
 constexpr int kBatchItemsPerSm = 512;  // work items per multiprocessor the batched deposit aims for
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // give up a wait after 2 s
 
@@ -159,8 +159,9 @@ int grid_stride_blocks(long long n, int threads, int per_sm);
 // the grid (cell blocks x particles x chunks) would hold fewer than 8 CTAs per multiprocessor.
 int auto_chunk(long long n_cell_blocks, long long n_part, int S);
 // Cell blocks per group of the mixed kernels' work order (item_coords): as many as keep the group's
-// detector slice (256 cells x n_bins x 32 bytes per block) within RD_GROUP_SLICE_MB, at most 8.
-int cell_group(int n_cell_blocks, int n_bins, int cells_per_cta = 256);
+// active detector slice (cells_per_cta x 32 bytes x the bins a step chunk of `chunk` of the
+// trajectory's n_intervals spans, per block) within RD_GROUP_SLICE_MB, at most 8.
+int cell_group(int n_cell_blocks, int n_bins, int cells_per_cta, int chunk, int n_intervals);
 // Deposit-shape tuning cache (rd_tune.cu): entries keyed by device and problem, in a JSON file.
 struct TuneEntry {
     int cpc, nc, chunk, group;
@@ -183,9 +184,12 @@ cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s);
 // shapes of the mixed kernel compiled into the library (held field, exact Eq. 1; the far-field and
 // interpolation variants and the batch kernel run the default shape, kMixedCellsPerCta x kMixedCells)
 bool mixed_shape_supported(int cells_per_cta, int cells_per_thread);
-cudaError_t launch_deposit_batch(const DepositParams* probs, const long long* item_off, int n_probs,
-                                 unsigned long long* next_item, int grid, cudaStream_t s);
-int batch_grid();   // resident CTAs of the persistent batch kernel on the current device
+cudaError_t launch_deposit_batch(int family, const DepositParams* probs, const long long* item_off, int n_probs,
+                                 unsigned long long* next_item, cudaStream_t s);
+// walk family of a problem (batch_family: 4 x far field + 0 held / 1 linear family / 2 quadratic),
+// and the resident CTAs of its persistent batch kernel on the current device
+int batch_family(const DepositParams& p);
+int batch_grid(int family);
 cudaError_t launch_deposit_fp64(const DepositParams& p, int flags, cudaStream_t s);
 // adjoint (rd_adjoint.cu)
 struct AdjointParams {

@@ -146,7 +146,7 @@ extern "C" rd_status rd_deposit_noalloc(const double* pix_pos, const double* pix
             P.invW = (float)(t->dt / dt_det);
             P.ff = (fl & RD_FARFIELD) != 0;
             P.lin = (fl & RD_LINEAR) ? 1 : (fl & RD_HOLD_PREV) ? 2 : (fl & RD_QUADRATIC) ? 3 : 0;
-            P.group = cell_group(n_cell_blocks, n_bins);
+            P.group = cell_group(n_cell_blocks, n_bins, kMixedCellsPerCta, chunk, S);
             e = launch_deposit_mixed(P, s);
         }
     }

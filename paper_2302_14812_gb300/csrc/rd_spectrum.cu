@@ -107,96 +107,219 @@ struct Load3<double, 6> {
     }
 };
 
-// Shared-memory index of element i of a transform: one float2 of padding after every 32, so that
-// the bit-reversed stores of the load phase (consecutive bins -> elements N/32 apart) spread over
-// the banks.
-__device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
-
-__device__ __forceinline__ void butterfly(float2* z, int i0, int i1, float2 w)
-{
-    const float2 a = z[pad(i0)], b = cmul(z[pad(i1)], w);
-    z[pad(i0)] = make_float2(a.x + b.x, a.y + b.y);
-    z[pad(i1)] = make_float2(a.x - b.x, a.y - b.y);
-}
+// Shared-memory index of element i of a transform: one float2 of padding after every 16, so that
+// the strided reads and writes of every radix-16 pass (and of the shorter last pass) fall on
+// distinct banks.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
-// Two stages at once on the four elements i0 + {0, h, 2h, 3h} (i0 = 4 G h + p, p < h): span h
-// pairs (0, 1) and (2, 3) with twiddle w1 = exp(-2 pi i p / (2h)), then span 2h pairs (0, 2) with
-// w2a = exp(-2 pi i p / (4h)) and (1, 3) with w2b = exp(-2 pi i (p + h) / (4h)).
-__device__ __forceinline__ void butterfly2x2(float2* z, int i0, int h, float2 w1, float2 w2a, float2 w2b)
+// exp(-2 pi i j / 16), j = 0..7: the roots the in-register transforms of length <= 16 multiply by
+__device__ __forceinline__ float2 root16(int j)
 {
-    const float2 a0 = z[pad(i0)], a1 = cmul(z[pad(i0 + h)], w1);
-    const float2 a2 = z[pad(i0 + 2 * h)], a3 = cmul(z[pad(i0 + 3 * h)], w1);
-    const float2 b0 = cadd(a0, a1), b1 = csub(a0, a1), b2 = cmul(cadd(a2, a3), w2a), b3 = cmul(csub(a2, a3), w2b);
-    z[pad(i0)] = cadd(b0, b2);
-    z[pad(i0 + 2 * h)] = csub(b0, b2);
-    z[pad(i0 + h)] = cadd(b1, b3);
-    z[pad(i0 + 3 * h)] = csub(b1, b3);
+    constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
+    const float re[8] = {1.f, c1, h, s1, 0.f, -s1, -h, -c1};
+    const float im[8] = {0.f, -s1, -h, -c1, -1.f, -c1, -h, -s1};
+    return make_float2(re[j], im[j]);
 }
 
-// One CTA per cell at a time (persistent over cells).  Shared memory: Z1 and Z2 (N elements each,
-// padded) and the twiddles of every stage, stage h (span h) holding exp(-2 pi i p / (2h)), p < h,
-// at h - 1 + p (contiguous in p, so a warp's lanes read consecutive entries).  The bins are loaded
-// in bit-reversed order, so in-place decimation-in-time butterflies leave the transforms in
-// natural order.
-template <typename T, int STRIDE>
-__global__ void __launch_bounds__(256) k_spectrum_fused(const T* __restrict__ fields, int n_pix, int N, int logN,
-                                                        int c0, const float2* __restrict__ tw_g, float scale,
-                                                        float* __restrict__ P)
+// a * exp(-2 pi i j / 16) with the trivial roots (1, -i) taken without a multiply; j is a
+// compile-time constant after unrolling
+__device__ __forceinline__ float2 mul_root16(float2 a, int j)
+{
+    if (j == 0) return a;
+    if (j == 4) return make_float2(a.y, -a.x);
+    return cmul(a, root16(j));
+}
+
+// In-register DFT of length R (2, 4, 8, 16): X[k] = sum_r a[r] exp(-2 pi i r k / R), by radix-2
+// decimation in frequency; the result is left in bit-reversed order (a[bitrev(k)] = X[k]).
+template <int R>
+constexpr int log2_of() { return R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1; }
+
+template <int R>
+__device__ __forceinline__ void dft_bitrev(float2 (&a)[R])
+{
+    constexpr int L = log2_of<R>();
+#pragma unroll
+    for (int st = 0; st < L; ++st) {
+        const int h = R >> (st + 1);                            // span of this stage
+#pragma unroll
+        for (int g = 0; g < (1 << st); ++g) {
+#pragma unroll
+            for (int i = 0; i < R / (2 << st); ++i) {
+                const int j = g * (R >> st);
+                const float2 u = a[j + i], v = a[j + i + h];
+                a[j + i] = cadd(u, v);
+                a[j + i + h] = mul_root16(csub(u, v), i * (8 / h));     // exp(-2 pi i i / (2h))
+            }
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ constexpr int bitrev(int k)
+{
+    constexpr int L = log2_of<R>();
+    int r = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) r |= ((k >> i) & 1) << (L - 1 - i);
+    return r;
+}
+
+// exp(-2 pi i j / N) for 0 <= j < N from the half-circle table tw[j] (j < N/2, in shared memory)
+__device__ __forceinline__ float2 twiddle(const float2* tw, int j, int half_n)
+{
+    if (j < half_n) return tw[j];
+    const float2 w = tw[j - half_n];
+    return make_float2(-w.x, -w.y);
+}
+
+// One Stockham pass of radix R on both transforms of a cell (in place in shared memory, or reading
+// the cell's bins from global memory when s = 1 and G): with n = N / s and m = n / R, butterfly
+// (p, q), p < m, q < s, takes a_r = x[q + s (p + r m)], r < R, forms b_k = DFT_R(a)[k] and writes
+// y[q + s (R p + k)] = b_k exp(-2 pi i p k / n).  After the passes of radices R1 R2 ... = N the
+// transform is in natural order.  Each thread holds 16 elements of each transform (16 / R
+// butterflies); all reads of a pass finish before its writes.
+template <int R, bool G, typename T, int STRIDE>
+__device__ __forceinline__ void spec_pass(float2* z1, float2* z2, const T* row, int c0, int N, int s,
+                                          const float2* tw, int tid)
+{
+    constexpr int NB = 16 / R;                  // butterflies per thread
+    const int n = N / s, m = n / R;
+    const int nb = N / R;                       // butterflies per transform
+    float2 a1[NB][R], a2[NB][R];
+    int bq[NB], bp[NB];
+    bool on[NB];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        const int t = tid + u * blockDim.x;
+        on[u] = t < nb;
+        bq[u] = t % s;
+        bp[u] = t / s;
+        if (on[u]) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = bq[u] + s * (bp[u] + r * m);
+                if (G) {
+                    const float3 v = Load3<T, STRIDE>::get(row, i, c0);
+                    a1[u][r] = make_float2(v.x, v.y);
+                    a2[u][r] = make_float2(v.z, 0.f);
+                } else {
+                    a1[u][r] = z1[pad(i)];
+                    a2[u][r] = z2[pad(i)];
+                }
+            }
+        }
+    }
+    __syncthreads();    // every read of the pass is done (first pass: the twiddle table is filled)
+    const int half_n = N >> 1;
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        if (!on[u]) continue;
+        dft_bitrev<R>(a1[u]);
+        dft_bitrev<R>(a2[u]);
+        const int o = bq[u] + s * R * bp[u];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            float2 b1 = a1[u][bitrev<R>(k)], b2 = a2[u][bitrev<R>(k)];
+            if (k > 0) {
+                const float2 w = twiddle(tw, bp[u] * k * s, half_n);      // exp(-2 pi i p k / n)
+                b1 = cmul(b1, w);
+                b2 = cmul(b2, w);
+            }
+            z1[pad(o + s * k)] = b1;
+            z2[pad(o + s * k)] = b2;
+        }
+    }
+    __syncthreads();
+}
+
+// The passes after the first, at stride S, of a length-N transform: radix 16 while 16 elements
+// remain per butterfly, then the remaining radix (a compile-time sequence, so that every pass's
+// registers are allocated on their own).
+template <int N, int S, typename T, int STRIDE>
+__device__ __forceinline__ void spec_passes(float2* z1, float2* z2, const float2* tw, int tid)
+{
+    if constexpr (S < N) {
+        constexpr int R = N / S >= 16 ? 16 : N / S;
+        spec_pass<R, false, T, STRIDE>(z1, z2, nullptr, 0, N, S, tw, tid);
+        spec_passes<N, S * R, T, STRIDE>(z1, z2, tw, tid);
+    }
+}
+
+constexpr int spec_threads(int N) { return N / 16 > 128 ? N / 16 : 128; }
+// resident CTAs per SM the kernel is compiled for: 512 threads per SM (128 registers a thread)
+constexpr int spec_min_blocks(int N) { return 512 / spec_threads(N); }
+
+// One CTA per cell, spec_threads(N) threads.  Shared memory: Z1 and Z2 (N elements each, padded)
+// and the N/2 twiddles.  The first pass reads the cell's bins from global memory (consecutive
+// threads, consecutive bins); the power of frequency k needs Z1 at k and N - k, so it is formed
+// from shared memory after the last pass.  (A CTA looping over cells keeps every pass's state
+// live across the loop and spills; a fresh CTA per cell fits the registers, and reloading the
+// twiddles from L2 costs N/2 x 8 bytes per cell.)
+template <int N, typename T, int STRIDE>
+__global__ void __launch_bounds__(spec_threads(N), spec_min_blocks(N)) k_spectrum_fused(const T* __restrict__ fields,
+                                                                                        int c0,
+                                                                                        const float2* __restrict__ tw_g,
+                                                                                        float scale, float* __restrict__ P)
 {
     extern __shared__ float2 sm[];
-    const int zlen = pad(N - 1) + 1;
+    constexpr int zlen = N + N / 16;
+    constexpr int R1 = N >= 16 ? 16 : N;
     float2* z1 = sm;
     float2* z2 = sm + zlen;
     float2* tw = sm + 2 * zlen;
-    const int half_n = N >> 1;
-    for (int h = 1; h < N; h <<= 1) {
-        const int step = half_n / h;
-        for (int p = threadIdx.x; p < h; p += blockDim.x) tw[h - 1 + p] = tw_g[p * step];
+    const int tid = threadIdx.x;
+    const size_t cell = blockIdx.x;
+    const T* row = fields + cell * N * STRIDE;
+    // filled before the first pass's barrier, read after it
+    for (int j = tid; j < N / 2; j += blockDim.x) tw[j] = tw_g[j];
+    spec_pass<R1, true, T, STRIDE>(z1, z2, row, c0, N, 1, tw, tid);
+    spec_passes<N, R1, T, STRIDE>(z1, z2, tw, tid);
+    constexpr int nk = N / 2 + 1;
+    float* out = P + cell * nk;
+    for (int k = tid; k < nk; k += blockDim.x) {
+        const int km = (N - k) & (N - 1);
+        const float2 a = z1[pad(k)], am = z1[pad(km)], c = z2[pad(k)];
+        const float pxy = 0.5f * (a.x * a.x + a.y * a.y + am.x * am.x + am.y * am.y);
+        out[k] = scale * (pxy + (c.x * c.x + c.y * c.y));
     }
-    const int nk = half_n + 1;
-    for (int cell = blockIdx.x; cell < n_pix; cell += gridDim.x) {
-        const T* row = fields + (size_t)cell * N * STRIDE;
-#pragma unroll 4
-        for (int b = threadIdx.x; b < N; b += blockDim.x) {
-            const int r = pad((int)(__brev((unsigned)b) >> (32 - logN)));
-            const float3 v = Load3<T, STRIDE>::get(row, b, c0);
-            z1[r] = make_float2(v.x, v.y);
-            z2[r] = make_float2(v.z, 0.f);
-        }
-        __syncthreads();
-        int h = 1;
-        for (; 4 * h <= N; h <<= 2) {                 // stages of span h and 2h in one pass
-            const float2* wa = tw + (h - 1);
-            const float2* wb = tw + (2 * h - 1);
-            for (int t = threadIdx.x; t < (N >> 2); t += blockDim.x) {
-                const int G = t / h, p = t - G * h;
-                const int i0 = 4 * G * h + p;
-                const float2 w1 = wa[p], w2a = wb[p], w2b = wb[p + h];
-                butterfly2x2(z1, i0, h, w1, w2a, w2b);
-                butterfly2x2(z2, i0, h, w1, w2a, w2b);
-            }
-            __syncthreads();
-        }
-        if (h < N) {                                  // odd number of stages: the last, span N/2
-            const float2* wh = tw + (h - 1);
-            for (int t = threadIdx.x; t < half_n; t += blockDim.x) {
-                const float2 w = wh[t];
-                butterfly(z1, t, t + h, w);
-                butterfly(z2, t, t + h, w);
-            }
-            __syncthreads();
-        }
-        float* out = P + (size_t)cell * nk;
-        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-            const int km = (N - k) & (N - 1);
-            const float2 a = z1[pad(k)], am = z1[pad(km)], c = z2[pad(k)];
-            const float pxy = 0.5f * (a.x * a.x + a.y * a.y + am.x * am.x + am.y * am.y);
-            out[k] = scale * (pxy + (c.x * c.x + c.y * c.y));
-        }
-        __syncthreads();
+}
+
+template <int N, typename T, int STRIDE>
+cudaError_t launch_fused_n(const T* fields, int n_pix, int c0, const float2* tw, float scale, float* P,
+                           cudaStream_t s)
+{
+    constexpr int threads = spec_threads(N);
+    const size_t smem = sizeof(float2) * (2 * (size_t)(N + N / 16) + N / 2);
+    auto k = k_spectrum_fused<N, T, STRIDE>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<n_pix, threads, smem, s>>>(fields, c0, tw, scale, P);
+    return cudaGetLastError();
+}
+
+template <typename T, int STRIDE>
+cudaError_t launch_fused(const T* fields, int n_pix, int N, int c0, const float2* tw, float scale, float* P,
+                         cudaStream_t s)
+{
+    switch (N) {
+    case 2: return launch_fused_n<2, T, STRIDE>(fields, n_pix, c0, tw, scale, P, s);
+    case 4: return launch_fused_n<4, T, STRIDE>(fields, n_pix, c0, tw, scale, P, s);
+    case 8: return launch_fused_n<8, T, STRIDE>(fields, n_pix, c0, tw, scale, P, s);
+    case 16: return launch_fused_n<16, T, STRIDE>(fields, n_pix, c0, tw, scale, P, s);
+    case 32: return launch_fused_n<32, T, STRIDE>(fields, n_pix, c0, tw, scale, P, s);
+    case 64: return launch_fused_n<64, T, STRIDE>(fields, n_pix, c0, tw, scale, P, s);
+    case 128: return launch_fused_n<128, T, STRIDE>(fields, n_pix, c0, tw, scale, P, s);
+    case 256: return launch_fused_n<256, T, STRIDE>(fields, n_pix, c0, tw, scale, P, s);
+    case 512: return launch_fused_n<512, T, STRIDE>(fields, n_pix, c0, tw, scale, P, s);
+    case 1024: return launch_fused_n<1024, T, STRIDE>(fields, n_pix, c0, tw, scale, P, s);
+    case 2048: return launch_fused_n<2048, T, STRIDE>(fields, n_pix, c0, tw, scale, P, s);
+    case 4096: return launch_fused_n<4096, T, STRIDE>(fields, n_pix, c0, tw, scale, P, s);
+    case 8192: return launch_fused_n<8192, T, STRIDE>(fields, n_pix, c0, tw, scale, P, s);
+    default: return cudaErrorInvalidValue;
     }
 }
 
@@ -220,29 +343,9 @@ cudaError_t launch_power_spectrum(const void* fields, int precision, int n_pix, 
                                   float2* y, const float2* tw, float scale, float* P, cudaStream_t s)
 {
     if (spectrum_fused(N)) {
-        int logN = 0;
-        while ((1 << logN) < N) ++logN;
-        const size_t smem = sizeof(float2) * (2 * (size_t)(N + N / 32) + N);
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaError_t e;
-        if (precision == RD_MIXED) {
-            auto k = k_spectrum_fused<float, 8>;
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem);
-            if (e != cudaSuccess) return e;
-            const int grid = (int)std::min<long long>(n_pix, (long long)sms * std::max(1, per_sm));
-            k<<<grid, 256, smem, s>>>(static_cast<const float*>(fields), n_pix, N, logN, c0, tw, scale, P);
-        } else {
-            auto k = k_spectrum_fused<double, 6>;
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem);
-            if (e != cudaSuccess) return e;
-            const int grid = (int)std::min<long long>(n_pix, (long long)sms * std::max(1, per_sm));
-            k<<<grid, 256, smem, s>>>(static_cast<const double*>(fields), n_pix, N, logN, c0, tw, scale, P);
-        }
-        return cudaGetLastError();
+        if (precision == RD_MIXED)
+            return launch_fused<float, 8>(static_cast<const float*>(fields), n_pix, N, c0, tw, scale, P, s);
+        return launch_fused<double, 6>(static_cast<const double*>(fields), n_pix, N, c0, tw, scale, P, s);
     }
     const long long n = (long long)n_pix * N;
     if (precision == RD_MIXED)

@@ -182,6 +182,53 @@ def test_high_gamma_against_extended_precision(gamma):
         assert parity_err(E, E64) <= TOL["fp64"] and parity_err(B, B64) <= TOL["fp64"]
 
 
+def _config_sample(name):
+    """(trajectories, detector, cell sample) of one workload configuration, at its full detector
+    geometry and step count with few particles."""
+    rng = np.random.default_rng(41)
+    if name == "circular":                       # synchrotron arc, all 64 cells
+        tr, det = W.config_circular()
+        return tr, det, np.arange(det.n_pix, dtype=np.int32)
+    if name == "undulator":                      # the headline geometry, 16 electrons
+        tr, det = W.config_undulator(n_part=16)
+    elif name == "plasma_mirror":                # full plane and steps, 40 of the electrons
+        tr, det = W.config_plasma_mirror(n_part=100_000, particles=slice(0, 40))
+    elif name == "batch":                        # one problem of each kind from the 64-problem set
+        probs = W.batch_problems(64, seed=4, scale=0.002)
+        kind, tr, det = next(p for p in probs if p[0] == "oscillator")
+    else:                                        # the adjoint workload's geometry
+        tr, det = W.config_undulator(n_part=16, n_steps=2000, n_side=64, n_bins=1024, gamma=10.0, K=1.0,
+                                     n_periods=10.0, distance=1e4, seed=5)
+    sel = np.sort(rng.choice(det.n_pix, 6, replace=False)).astype(np.int32)
+    return tr, det, sel
+
+
+@pytest.mark.parametrize("name", ["circular", "undulator", "plasma_mirror", "batch", "adjoint"])
+def test_every_config_against_extended_precision(name):
+    """Each workload configuration on a cell sample against the oracle evaluated in long double,
+    which does not share the FP64 rounding of Eq. 2 that the FP64 kernel and the FP64 oracle both
+    fix (reading A17): the FP64 form within 1e-7 (the spread FP64 rounding of t + R leaves at these
+    distances is ~1e-9), the mixed form within its 1e-4 bar."""
+    tr, det, sel = _config_sample(name)
+    Ee, Be, _ = oracle.deposit_ext(tr, det, sel)
+    assert np.abs(Ee).max() > 0
+    sub = det.subset(sel)
+    for precision, bar in (("fp64", 1e-7), ("mixed", 1e-4)):
+        E, B, st = gpu_run(tr, sub, precision)
+        assert st.device_errors == 0
+        eE, eB = parity_err(E, Ee), parity_err(B, Be)
+        print(f"{name} {precision} vs long double: E {eE:.2e} B {eB:.2e}")
+        assert eE <= bar and eB <= bar, (name, precision, eE, eB)
+    if name == "batch":
+        probs = [p for p in W.batch_problems(64, seed=4, scale=0.002) if p[0] != "oscillator"]
+        for kind in ("undulator", "circular"):
+            _, tr, det = next(p for p in probs if p[0] == kind)
+            sel = np.array([0, det.n_pix // 2, det.n_pix - 1], dtype=np.int32)
+            Ee, Be, _ = oracle.deposit_ext(tr, det, sel)
+            E, B, _ = gpu_run(tr, det.subset(sel), "fp64")
+            assert parity_err(E, Ee) <= 1e-7 and parity_err(B, Be) <= 1e-7, kind
+
+
 # --------------------------------------------------------------------------------------------
 # edge cases and API behaviour
 # --------------------------------------------------------------------------------------------
