@@ -212,8 +212,8 @@ def test_batch_record_budget_splits_into_groups():
 
 
 def test_batch_mixes_modes():
-    """One batch with a linear-interpolation problem, a far-field problem and a plain one (each
-    work item follows its own problem's mode) equals the separate deposits."""
+    """One batch with a linear-interpolation problem, a far-field problem and a plain one (three walk
+    families, so three persistent launches in the batch's graph) equals the separate deposits."""
     import torch
     probs = small_problems()[:3]
     probs[0][1].flags = W.RD_NEAR | W.RD_FAR | W.RD_LINEAR
