@@ -186,9 +186,8 @@ cudaError_t launch_deposit_mixed(const DepositParams& p, cudaStream_t s);
 bool mixed_shape_supported(int cells_per_cta, int cells_per_thread);
 cudaError_t launch_deposit_batch(int family, const DepositParams* probs, const long long* item_off, int n_probs,
                                  unsigned long long* next_item, cudaStream_t s);
-// walk family of a problem (batch_family: 4 x far field + 0 held / 1 linear family / 2 quadratic),
-// and the resident CTAs of its persistent batch kernel on the current device
-int batch_family(const DepositParams& p);
+// resident CTAs of the persistent batch kernel of a walk family (4 x far field + 0 held / 1 linear
+// family / 2 quadratic) on the current device
 int batch_grid(int family);
 cudaError_t launch_deposit_fp64(const DepositParams& p, int flags, cudaStream_t s);
 // adjoint (rd_adjoint.cu)

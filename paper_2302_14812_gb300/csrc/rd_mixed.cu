@@ -831,11 +831,6 @@ cudaError_t launch_deposit_batch(int family, const DepositParams* probs, const l
     return cudaGetLastError();
 }
 
-int batch_family(const DepositParams& p)
-{
-    return (p.ff ? 4 : 0) + (p.lin == 3 ? 2 : p.lin ? 1 : 0);
-}
-
 template <bool FF, int LIN>
 static int resident_batch_ctas()
 {
