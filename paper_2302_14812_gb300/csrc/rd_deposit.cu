@@ -134,10 +134,37 @@ struct D64State {
     double Fp[6];   // RD_LINEAR / RD_QUADRATIC: field of the previous sample
     double Fpp[6];  // RD_QUADRATIC: field two samples back ...
     double ap;      // ... and its arrival (bins)
-    double e;       // held field: upper edge of bin b (b + 1)
+    double e;       // held field: upper edge of bin b (b + 1) ...
+    long long ke;   // ... and its order key (dkey)
     int n_below;
     int n_above;
 };
+
+// An integer that orders like the double x (finite x): the bit pattern for x >= 0, the magnitude bits
+// flipped for x < 0, so that bin-edge tests run on the integer pipe.
+__device__ __forceinline__ long long dkey(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+__device__ __forceinline__ void set_edge(D64State& st, double e)
+{
+    st.e = e;
+    st.ke = dkey(e);
+}
+
+// The double n (|n| < 2^31) assembled from its integer on the integer pipe: sign, exponent
+// 1023 + floor(log2 |n|), and the bits of |n| below its leading one as the mantissa's top bits.
+__device__ __forceinline__ double int_to_double_bits(int n)
+{
+    const unsigned m = (unsigned)(n < 0 ? -n : n);
+    const int hb = 31 - __clz((int)m);
+    const long long bits = ((long long)(n < 0) << 63) | ((long long)(1023 + hb) << 52) |
+                           ((long long)(m ^ (1u << hb)) << (52 - hb));
+    return __longlong_as_double(n == 0 ? 0LL : bits);
+}
+
 
 __device__ __forceinline__ void flush_f64(double* row, int n_bins, int b, const double* v)
 {
@@ -246,9 +273,70 @@ __device__ __forceinline__ void fp64_deposit(D64State& st, const double* F, doub
         if (st.b < 0 && b >= 0) st.n_below = k - k_begin + 1;
         if (st.b < n_bins && b >= n_bins) st.n_above = k_end - k + 1;
         st.b = b;
-        st.e = e + 1.0;
+        set_edge(st, e + 1.0);
     }
     st.a = c;
+}
+
+// fp64_deposit for a warp whose 32 lanes all walk a cell (`warp` converged on every call).  The
+// lanes whose arrival passed their bin's upper edge (about one in five) start their next bin with
+// the rest of the interval, F times (c - e): instead of each lane's six multiplies taking six
+// warp-wide FP64 instructions, the warp's crossing lanes' products are spread over all 32 lanes by
+// shuffles (one or two FP64 instructions); the edge tests are integer compares and the next edge is
+// assembled on the integer pipe, so that the FP64 pipe does the arithmetic of Eq. 1 and 2.
+__device__ __forceinline__ void fp64_deposit_warp(D64State& st, const double* F, double c, double* row,
+                                                  int n_bins, int k, int k_begin, int k_end)
+{
+    constexpr unsigned warp = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long kc = dkey(c);
+    const bool cr = kc >= st.ke;
+    const double wi = (cr ? st.e : c) - st.a;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) st.acc[i] = fma(F[i], wi, st.acc[i]);
+    st.a = c;
+    const unsigned m = __ballot_sync(warp, cr);
+    if (m == 0u) return;
+    double wl = 0.0;
+    if (cr) {
+        flush_f64(row, n_bins, st.b, st.acc);
+        int b = st.b + 1;
+        wl = c - st.e;                         // st.e: lower edge of bin b
+        // c - e >= 1 (compared on the bits: both are >= 0): more than one edge, whole bins in between
+        if (__double_as_longlong(wl) >= 0x3FF0000000000000LL) {
+            const int bc = clamp_bin(floor(c));
+            const int lo = max(b, 0), hi = min(bc - 1, n_bins - 1);
+            for (int j = lo; j <= hi; ++j) flush_f64(row, n_bins, j, F);
+            b = bc;
+            wl = c - (double)bc;
+        }
+        if (st.b < 0 && b >= 0) st.n_below = k - k_begin + 1;
+        if (st.b < n_bins && b >= n_bins) st.n_above = k_end - k + 1;
+        st.b = b;
+        set_edge(st, int_to_double_bits(b + 1));
+    }
+    // product p = 6 r + q (r: rank of a crossing lane, q: component) is formed by lane p % 32 in
+    // round p / 32 and handed back to its crossing lane
+    const int n = __popc(m);
+    const int rank = __popc(m & ((1u << lane) - 1u));
+    for (int base = 0; base < 6 * n; base += 32) {
+        const int pi = base + lane;
+        const int r = pi / 6, q = pi - 6 * (pi / 6);
+        const int src = pi < 6 * n ? (int)__fns(m, 0u, r + 1) : lane;
+        double f = 0.0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const double v = __shfl_sync(warp, F[i], src);
+            f = (q == i) ? v : f;
+        }
+        const double prod = f * __shfl_sync(warp, wl, src);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const int idx = 6 * rank + i;
+            const double v = __shfl_sync(warp, prod, idx & 31);
+            if (cr && idx >= base && idx < base + 32) st.acc[i] = v;
+        }
+    }
 }
 
 // RD_LINEAR: the field goes linearly from F0 at st.a to F1 at c; the overlap [u0, u1] of the interval
@@ -417,7 +505,7 @@ __global__ void __launch_bounds__(kDepositThreads, LM == 0 ? RD_FP64_MINBLOCKS :
         live = (ue > 0.0) && (ua < (double)P.n_bins);
         st.a = ua;
         st.b = clamp_bin(floor(ua));
-        st.e = LM == 0 ? (double)st.b + 1.0 : 0.0;
+        if (LM == 0) set_edge(st, (double)st.b + 1.0);
         st.n_below = (ua < 0.0) ? n_int : 0;
         st.n_above = 0;
 #pragma unroll
@@ -425,6 +513,8 @@ __global__ void __launch_bounds__(kDepositThreads, LM == 0 ? RD_FP64_MINBLOCKS :
         row = static_cast<double*>(P.fields) + (size_t)cell * P.n_bins * 6;
         if (!live) atomicAdd(&P.counters->clipped, (unsigned long long)n_int);
     }
+    // held field: warps whose every lane walks a cell share their bin-start work (fp64_deposit_warp)
+    const bool full_warp = LM == 0 && __ballot_sync(0xffffffffu, live) == 0xffffffffu;
     if (LM && live) {
         // field of the sample before the chunk; a trajectory's first interval holds F_1
         const RecD r0 = rec[k_begin > 1 ? k_begin - 1 : 1];
@@ -495,7 +585,10 @@ __global__ void __launch_bounds__(kDepositThreads, LM == 0 ? RD_FP64_MINBLOCKS :
                     }
                     if (LM == 2) st.ap = a_prev;
                 } else {
-                    fp64_deposit(st, F, cbin, row, P.n_bins, k, k_begin, k_end);
+                    if (full_warp)
+                        fp64_deposit_warp(st, F, cbin, row, P.n_bins, k, k_begin, k_end);
+                    else
+                        fp64_deposit(st, F, cbin, row, P.n_bins, k, k_begin, k_end);
                 }
             }
             if (t == n_tiles - 1) {
