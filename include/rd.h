@@ -182,6 +182,24 @@ RD_API rd_status rd_read_fields(rd_detector* det, void* E, void* B, int32_t dtyp
                          rd_stream stream);
 
 /*
+ * Set the detector's accumulated fields to E[n_pix][n_bins][3] and B[n_pix][n_bins][3] (the layout
+ * rd_read_fields writes; dtype RD_F32 or RD_F64, converted to the detector's precision; either may
+ * be NULL, which sets that part to zero).  Deposits add (the detector holds the superposition of
+ * everything deposited, Section 3.2), so a run checkpointed with rd_read_fields resumes in a new
+ * detector (or process) by rd_write_fields followed by the remaining deposits: particle subsets
+ * and step chunks that share their boundary sample, as the run-time mode of Section 3.1 hands
+ * them over (exact for the held field; an interpolated field restarts its first interval).
+ * Counters and the state of streamed deposits are not part of the fields and are left alone.
+ *   mem: RD_MEM_DEVICE (device pointers, asynchronous), RD_MEM_HOST (any host memory; the call
+ *        returns after the copy), RD_MEM_HOST_ASYNC (pinned host memory the caller keeps until the
+ *        stream has passed the call).
+ * Errors: RD_ERR_ARG (NULL detector, bad dtype or mem), RD_ERR_OOM (staging for host input),
+ * RD_ERR_CUDA.
+ */
+RD_API rd_status rd_write_fields(rd_detector* det, const void* E, const void* B, int32_t dtype, int32_t mem,
+                                 rd_stream stream);
+
+/*
  * Streamed deposit (Section 3: run-time use inside a particle code, which hands over each new
  * stretch of the trajectories as it computes them).  traj holds the NEW samples only, at
  * t0 + k*dt, k < n_samples; the detector keeps every particle's last sample from the previous

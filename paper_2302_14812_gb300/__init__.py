@@ -103,6 +103,7 @@ def load_library(build_if_missing: bool = True):
             "rd_zero_fields": ([P, P], I),
             "rd_deposit_trajectories": ([P, ctypes.POINTER(rd_traj), P], I),
             "rd_read_fields": ([P, P, P, I, I, P], I),
+            "rd_write_fields": ([P, P, P, I, I, P], I),
             "rd_synchronize": ([P, P], I),
             "rd_get_stats": ([P, P, ctypes.POINTER(rd_stats)], I),
             "rd_set_timing": ([P, I], I),
@@ -181,6 +182,11 @@ def rd_deposit_trajectories(det: int, traj: rd_traj, stream=None) -> None:
 def rd_read_fields(det: int, E_ptr, B_ptr, dtype: int, mem: int, stream=None) -> None:
     _check(load_library().rd_read_fields(det, E_ptr, B_ptr, dtype, mem, _stream_ptr(stream)),
            "rd_read_fields")
+
+
+def rd_write_fields(det: int, E_ptr, B_ptr, dtype: int, mem: int, stream=None) -> None:
+    _check(load_library().rd_write_fields(det, E_ptr, B_ptr, dtype, mem, _stream_ptr(stream)),
+           "rd_write_fields")
 
 
 def rd_synchronize(det: int, stream=None) -> None:
@@ -421,6 +427,31 @@ class RadiationDetector:
         B = torch.empty_like(E)
         rd_read_fields(self._h, E.data_ptr(), B.data_ptr(), code, RD_MEM_DEVICE, stream)
         return E, B
+
+    def write(self, E, B, stream=None):
+        """Set the fields to E, B ([n_pix][n_bins][3] each, float32 or float64; numpy arrays or CUDA
+        tensors; None sets that part to zero): resumes a run checkpointed with read()."""
+        arrs = [a for a in (E, B) if a is not None]
+        if not arrs:
+            rd_write_fields(self._h, None, None, RD_F64, RD_MEM_DEVICE, stream)
+            return
+        shape = (self.n_pix, self.n_bins, 3)
+        if isinstance(arrs[0], np.ndarray):
+            dt = np.float32 if arrs[0].dtype == np.float32 else np.float64
+            E = None if E is None else np.ascontiguousarray(E, dtype=dt).reshape(shape)
+            B = None if B is None else np.ascontiguousarray(B, dtype=dt).reshape(shape)
+            code = RD_F32 if dt == np.float32 else RD_F64
+            rd_write_fields(self._h, None if E is None else E.ctypes.data, None if B is None else B.ctypes.data,
+                            code, RD_MEM_HOST, stream)
+            return
+        import torch
+        tdt = torch.float32 if arrs[0].dtype == torch.float32 else torch.float64
+        E = None if E is None else E.to(dtype=tdt).contiguous().reshape(shape)
+        B = None if B is None else B.to(dtype=tdt).contiguous().reshape(shape)
+        code = RD_F32 if tdt == torch.float32 else RD_F64
+        rd_write_fields(self._h, None if E is None else E.data_ptr(), None if B is None else B.data_ptr(), code,
+                        RD_MEM_DEVICE, stream)
+        self._keep = (E, B)            # kept until the next call: the copy is asynchronous
 
     def deposit_stream(self, x, u, q=None, t0: float = 0.0, dt: float = 1.0, stream=None):
         """Deposit the next stretch of a streamed trajectory (new samples only, at t0 + k dt)."""

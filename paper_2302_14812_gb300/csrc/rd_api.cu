@@ -591,6 +591,30 @@ rd_status rd_read_fields(rd_detector* d, void* E, void* B, int32_t dtype, int32_
     return latched(*d->host_counters);
 }
 
+rd_status rd_write_fields(rd_detector* d, const void* E, const void* B, int32_t dtype, int32_t mem, rd_stream stream)
+{
+    g_err.clear();
+    if (!d) return fail(RD_ERR_ARG, "detector is NULL");
+    if (dtype != RD_F32 && dtype != RD_F64) return fail(RD_ERR_ARG, "bad dtype %d", dtype);
+    if (mem != RD_MEM_DEVICE && mem != RD_MEM_HOST && mem != RD_MEM_HOST_ASYNC) return fail(RD_ERR_ARG, "bad mem %d", mem);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (mem == RD_MEM_DEVICE) {
+        RD_CUDA(launch_write_fields(d->fields, d->precision, d->n_pix, d->n_bins, E, B, dtype, s), "rd_write_fields");
+        return RD_OK;
+    }
+    const size_t elem = dtype == RD_F32 ? sizeof(float) : sizeof(double);
+    const size_t one = (size_t)d->n_pix * d->n_bins * 3 * elem;
+    rd_status st = ensure(&d->readback, &d->readback_bytes, 2 * one, s, "field staging");
+    if (st != RD_OK) return st;
+    char* dE = E ? static_cast<char*>(d->readback) : nullptr;
+    char* dB = B ? static_cast<char*>(d->readback) + one : nullptr;
+    if (E) RD_CUDA(cudaMemcpyAsync(dE, E, one, cudaMemcpyHostToDevice, s), "copy E to the device");
+    if (B) RD_CUDA(cudaMemcpyAsync(dB, B, one, cudaMemcpyHostToDevice, s), "copy B to the device");
+    RD_CUDA(launch_write_fields(d->fields, d->precision, d->n_pix, d->n_bins, dE, dB, dtype, s), "rd_write_fields");
+    if (mem == RD_MEM_HOST) RD_CUDA(cudaStreamSynchronize(s), "rd_write_fields");
+    return RD_OK;
+}
+
 rd_status rd_synchronize(rd_detector* d, rd_stream stream)
 {
     g_err.clear();

@@ -631,6 +631,24 @@ __global__ void k_read(const Tin* __restrict__ fields, long long n, Tout* __rest
     }
 }
 
+// E[n_pix][n_bins][3], B[...] -> internal layout (the inverse of k_read); a NULL E or B sets that
+// part to zero, and the padding of the mixed layout is cleared
+template <typename Tin, int STRIDE, typename Tf>
+__global__ void k_write(Tf* __restrict__ fields, long long n, const Tin* __restrict__ E, const Tin* __restrict__ B)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        Tf* v = fields + i * STRIDE;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            v[c] = E ? (Tf)E[3 * i + c] : (Tf)0;
+            v[3 + c] = B ? (Tf)B[3 * i + c] : (Tf)0;
+        }
+#pragma unroll
+        for (int c = 6; c < STRIDE; ++c) v[c] = (Tf)0;
+    }
+}
+
 // =============================================================================================
 // launchers
 // =============================================================================================
@@ -687,6 +705,29 @@ cudaError_t launch_read_fields(const void* fields, int precision, int n_pix, int
         else
             k_read<double, 6, double><<<g, 256, 0, s>>>(static_cast<const double*>(fields), n,
                                                         static_cast<double*>(E), static_cast<double*>(B));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_write_fields(void* fields, int precision, int n_pix, int n_bins, const void* E, const void* B,
+                                int dtype, cudaStream_t s)
+{
+    const long long n = (long long)n_pix * n_bins;
+    const int g = grid_for(n, 256);
+    if (precision == RD_MIXED) {
+        if (dtype == RD_F32)
+            k_write<float, 8, float><<<g, 256, 0, s>>>(static_cast<float*>(fields), n, static_cast<const float*>(E),
+                                                       static_cast<const float*>(B));
+        else
+            k_write<double, 8, float><<<g, 256, 0, s>>>(static_cast<float*>(fields), n, static_cast<const double*>(E),
+                                                        static_cast<const double*>(B));
+    } else {
+        if (dtype == RD_F32)
+            k_write<float, 6, double><<<g, 256, 0, s>>>(static_cast<double*>(fields), n, static_cast<const float*>(E),
+                                                        static_cast<const float*>(B));
+        else
+            k_write<double, 6, double><<<g, 256, 0, s>>>(static_cast<double*>(fields), n,
+                                                         static_cast<const double*>(E), static_cast<const double*>(B));
     }
     return cudaGetLastError();
 }

@@ -255,6 +255,8 @@ cudaError_t launch_wait_probe(unsigned long long limit_ns, unsigned* errors, cud
 
 cudaError_t launch_read_fields(const void* fields, int precision, int n_pix, int n_bins, void* E,
                                void* B, int dtype, cudaStream_t s);
+cudaError_t launch_write_fields(void* fields, int precision, int n_pix, int n_bins, const void* E, const void* B,
+                                int dtype, cudaStream_t s);
 // power spectra (rd_spectrum.cu): twiddles exp(-2 pi i j / N), j < N/2, computed on the host
 void fill_twiddles(float2* host, int N);
 constexpr int kFusedMaxN = 8192;   // longest series transformed in shared memory (24.5 N bytes per CTA)

@@ -51,6 +51,10 @@ struct Cells {
     int above[NC];                  // intervals whose end lies after the window (clip tracking only)
 };
 
+#ifndef RD_CHECK
+#define RD_CHECK 0   // 1: the walk's unguarded reductions check their bin (a checked build, for tests)
+#endif
+
 struct Consts {
     float W;                        // bin width / dt
     float invW;
@@ -59,7 +63,25 @@ struct Consts {
     float* base;                    // field row 0 of the CTA's cell block
     int kq;                         // quadratic interpolation: first interval (this call's index) with
                                     // three fields behind it (the trajectory's third interval)
+#if RD_CHECK
+    unsigned* errors;               // the detector's latched error bits
+#endif
 };
+
+// Checked build: a reduction the window margin should keep inside the detector row is verified,
+// and one that would leave it latches RD_ERR_BOUNDS and is dropped.
+__device__ __forceinline__ bool bin_ok(const Consts& C, int b)
+{
+#if RD_CHECK
+    if ((unsigned)b < (unsigned)C.n_bins) return true;
+    atomicOr(C.errors, ERRBIT_BOUNDS);
+    return false;
+#else
+    (void)C;
+    (void)b;
+    return true;
+#endif
+}
 
 // Field of one sample at one cell, scaled to the bin weights (E = S E', B = (S/R) d x E').
 struct Field {
@@ -378,8 +400,10 @@ __device__ __forceinline__ void step(Cells<NC>& c, const RecS& r, const Consts& 
                 const float cb[3] = {c.acc[3][j], c.acc[4][j], c.acc[5][j]};
                 float bb[3];
                 bin_b<NC, FF>(c, j, e, cb, bb);
-                red_add_v4(a, e[0], e[1], e[2], bb[0]);
-                red_add_v2(a + 4, bb[1], bb[2]);
+                if (bin_ok(C, c.bo[j] - c.rb[j])) {
+                    red_add_v4(a, e[0], e[1], e[2], bb[0]);
+                    red_add_v2(a + 4, bb[1], bb[2]);
+                }
                 const float rem = fn[j] - C.W;
                 if (LIN) {
                     const float ramp2 = fmaf(0.5f * ramp, L[j], -ramp1[j]);
@@ -407,7 +431,7 @@ __device__ __forceinline__ void step(Cells<NC>& c, const RecS& r, const Consts& 
         } else {
             const int b = c.bo[j] - c.rb[j];
             const bool go = MODE == kFast || !ok[j];
-            const bool pr = cr && go && (!TRACK || (unsigned)b < (unsigned)C.n_bins);
+            const bool pr = cr && go && (TRACK ? (unsigned)b < (unsigned)C.n_bins : (!RD_CHECK || bin_ok(C, b)));
             float* a = bin_addr(C, c.bo[j]);
             const float e[3] = {c.acc[0][j], c.acc[1][j], c.acc[2][j]};
             const float cb[3] = {c.acc[3][j], c.acc[4][j], c.acc[5][j]};
@@ -581,6 +605,9 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
     C.n_bins = P.n_bins;
     C.base = static_cast<float*>(P.fields) + (size_t)cb * CPC * P.n_bins * 8;
     C.kq = 3 - P.k_real0;
+#if RD_CHECK
+    C.errors = &P.counters->errors;
+#endif
     constexpr bool QUAD = LIN == 2;
     const bool q_prev = QUAD && k_begin >= 3;     // the chunk starts with three fields behind it
 

@@ -52,6 +52,7 @@ def test_argument_errors_without_gpu():
     assert lib.rd_zero_fields(None, None) == rd.RD_ERR_ARG
     assert lib.rd_deposit_trajectories(None, None, None) == rd.RD_ERR_ARG
     assert lib.rd_read_fields(None, None, None, 0, 0, None) == rd.RD_ERR_ARG
+    assert lib.rd_write_fields(None, None, None, rd.RD_F32, rd.RD_MEM_HOST, None) == rd.RD_ERR_ARG
     assert lib.rd_destroy(None) == rd.RD_OK
     d = rd.rd_detector_desc()
     d.n_pix = 0
