@@ -192,7 +192,8 @@ RD_API rd_status rd_read_fields(rd_detector* det, void* E, void* B, int32_t dtyp
  * Counters and the state of streamed deposits are not part of the fields and are left alone.
  *   mem: RD_MEM_DEVICE (device pointers, asynchronous), RD_MEM_HOST (any host memory; the call
  *        returns after the copy), RD_MEM_HOST_ASYNC (pinned host memory the caller keeps until the
- *        stream has passed the call).
+ *        stream has passed the call).  Host input is staged in the detector's readback buffer, so
+ *        it must not overlap a host readback of the same detector enqueued on another stream.
  * Errors: RD_ERR_ARG (NULL detector, bad dtype or mem), RD_ERR_OOM (staging for host input),
  * RD_ERR_CUDA.
  */
