@@ -710,6 +710,19 @@ def main():
                                  "vs_held": ms_step / ms_prev,
                                  "mode": "RD_HOLD_PREV: interval k holds the field of sample k-1"}
 
+        det_quad = W.Detector(det.pix_pos, det.pix_t0, det.t_min, det.dt_det, det.n_bins,
+                              W.RD_NEAR | W.RD_FAR | W.RD_QUADRATIC)
+        qdd = rd.RadiationDetector.from_workload(det_quad, "mixed")
+
+        def quad_step():
+            qdd.zero()
+            qdd.deposit(xd, ud, qd, tr.t0, tr.dt)
+        ms_quad = timed(quad_step, 2)
+        qdd.close()
+        variants["quadratic"] = {"value": deposits * world / (ms_quad / 1e3), "ms_per_step": ms_quad,
+                                 "vs_held": ms_step / ms_quad,
+                                 "mode": "RD_QUADRATIC: field quadratic in arrival time through samples k-2, k-1, k"}
+
         n_str = 8
         bounds = np.linspace(0, tr.n_samples, n_str + 1).astype(int)
         pieces = [(xd[:, a:b].contiguous(), ud[:, a:b].contiguous(), tr.t0 + a * tr.dt)

@@ -789,10 +789,16 @@ __device__ __forceinline__ void init_staging(uint64_t* bar)
 
 // Resident CTAs per SM the register allotment must allow: about 640 threads, as for the default
 // shape (2 cells per thread, 256 cells per CTA: 128 threads, 5 CTAs).
-constexpr int mixed_min_blocks(int nt) { return nt >= 128 ? (nt == 128 ? RD_MIXED_MINBLOCKS : 640 / nt) : 640 / nt; }
+#ifndef RD_QUAD_MINBLOCKS
+#define RD_QUAD_MINBLOCKS 4      // the quadratic walk's CTAs per SM (its state needs more than 96 registers)
+#endif
+constexpr int mixed_min_blocks(int nt, int lin = 0)
+{
+    return nt >= 128 ? (nt == 128 ? (lin == 2 ? RD_QUAD_MINBLOCKS : RD_MIXED_MINBLOCKS) : 640 / nt) : 640 / nt;
+}
 
 template <bool FF, int LIN, int NC, int CPC>
-__global__ void __launch_bounds__(CPC / NC, mixed_min_blocks(CPC / NC)) k_deposit_mixed(const DepositParams P)
+__global__ void __launch_bounds__(CPC / NC, mixed_min_blocks(CPC / NC, LIN)) k_deposit_mixed(const DepositParams P)
 {
     constexpr int NT = CPC / NC;
     __shared__ __align__(128) RecS tile[2][kTileSteps];
@@ -813,7 +819,7 @@ __global__ void __launch_bounds__(CPC / NC, mixed_min_blocks(CPC / NC)) k_deposi
 // state.  (Drawing the next item while walking the current one measured 8 % slower: the drawing
 // thread then waits on the atomic before it issues the current item's record copies.)
 template <bool FF, int LIN>
-__global__ void __launch_bounds__(kMixedThreads, RD_MIXED_MINBLOCKS)
+__global__ void __launch_bounds__(kMixedThreads, mixed_min_blocks(kMixedThreads, LIN))
     k_deposit_batch(const DepositParams* __restrict__ probs, const long long* __restrict__ item_off, int n_probs,
                     unsigned long long* next_item)
 {
