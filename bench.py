@@ -766,24 +766,26 @@ def main():
         h2d = (xh.numel() + uh.numel() + qh.numel()) * 8
         d2h = (Eh.numel() + Bh.numel()) * 4
 
-        # Two detectors on two CUDA streams.  Step i is enqueued as upload + deposit + readback
-        # (asynchronous, into pinned host memory) on stream i % 2; the host then waits for step i-1
-        # and checks its errors.  So step i+1's upload runs on a copy engine during step i's
-        # kernel, step i's readback conversion runs before step i+1's kernel, and its copy to the
-        # host during that kernel.  Every step uploads its trajectories from pinned host memory
-        # and reads its fields back to the host.
+        # Three detectors on three CUDA streams.  Step i is enqueued as upload + deposit + readback
+        # (asynchronous, into pinned host memory) on stream i % 3; the host then waits for step i-2
+        # and checks its errors.  So the next steps' uploads run on a copy engine during step i's
+        # kernel, step i's readback conversion runs before the next kernel, and its copy to the host
+        # during that kernel; with two steps queued ahead, a late host wake-up does not leave the GPU
+        # without work.  Every step uploads its trajectories from pinned host memory and reads its
+        # fields back to the host.
         # The readback runs on a high-priority stream (after the deposit's event), so that its layout
         # conversion is dispatched ahead of the CTAs of the next step's kernel, which is already
-        # queued on the other stream.
-        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        # queued on another stream.
+        depth = 3
+        streams = [torch.cuda.Stream() for _ in range(depth)]
         top = torch.cuda.Stream.priority_range()[1] if hasattr(torch.cuda.Stream, "priority_range") else -1
-        rstreams = [torch.cuda.Stream(priority=top), torch.cuda.Stream(priority=top)]
-        pair = [mixed, rd.RadiationDetector.from_workload(det, "mixed")]
-        Ehs = [Eh, torch.empty_like(Eh).pin_memory()]
-        Bhs = [Bh, torch.empty_like(Bh).pin_memory()]
+        rstreams = [torch.cuda.Stream(priority=top) for _ in range(depth)]
+        pair = [mixed] + [rd.RadiationDetector.from_workload(det, "mixed") for _ in range(depth - 1)]
+        Ehs = [Eh] + [torch.empty_like(Eh).pin_memory() for _ in range(depth - 1)]
+        Bhs = [Bh] + [torch.empty_like(Bh).pin_memory() for _ in range(depth - 1)]
 
         def enqueue(i):
-            j = i % 2
+            j = i % depth
             pair[j].zero(streams[j])
             pair[j].deposit(xh, uh, qh, tr.t0, tr.dt, stream=streams[j])   # H2D inside the call
             ev = torch.cuda.Event()
@@ -793,20 +795,21 @@ def main():
                               rd.RD_MEM_HOST_ASYNC, rstreams[j])
 
         def finish(i):     # step i's fields are on the host once its readback stream is done
-            pair[i % 2].synchronize(rstreams[i % 2])
+            pair[i % depth].synchronize(rstreams[i % depth])
 
         def run(n, t0):      # returns the host time at which each step's fields had arrived
             done = []
             for i in range(n):
                 enqueue(i)
-                if i > 0:
-                    finish(i - 1)
+                if i >= depth - 1:
+                    finish(i - depth + 1)
                     done.append(time.perf_counter() - t0)
-            finish(n - 1)
-            done.append(time.perf_counter() - t0)
+            for i in range(max(0, n - depth + 1), n):
+                finish(i)
+                done.append(time.perf_counter() - t0)
             return done
         mixed.set_timing(False)
-        run(max(2, args.warmup), time.perf_counter())
+        run(max(depth, args.warmup), time.perf_counter())
         torch.cuda.synchronize()
         barrier()
         gc.collect()
@@ -818,14 +821,15 @@ def main():
             barrier()
             secs = slowest(time.perf_counter() - t)
         gc.enable()
-        pair[1].close()
+        for dd in pair[1:]:
+            dd.close()
         e2e = {"value": deposits * world * args.steps / secs, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * secs / args.steps,
                "step_done_ms": [round(1e3 * v, 2) for v in done],
                "clocks": e2e_clk.summary(),
-               "pipeline": "2 detectors on 2 CUDA streams, readbacks on high-priority streams: copies of one step "
-                           "overlap the next step's deposit",
+               "pipeline": f"{depth} detectors on {depth} CUDA streams, readbacks on high-priority streams: "
+                           "copies of one step overlap the next step's deposit",
                "host_link": host_link_gbs(Ehs[0], xh)}
     mixed.close()
 
