@@ -1,5 +1,5 @@
-// Per-sample precompute (both precisions), the plain FP64 deposit and the field readout (the
-// mixed-precision deposit is in rd_mixed.cu).
+// Per-sample precompute (both precisions), the plain FP64 deposit and the field readout and
+// write-in (the mixed-precision deposit is in rd_mixed.cu).
 //
 // Work decomposition of the FP64 deposit: one CTA = 256 detector cells (one per thread) x one
 // particle x one chunk of consecutive intervals.  The chunk's per-sample records are streamed
@@ -7,7 +7,9 @@
 // mbarrier completion); every thread reads each record as a broadcast.  Each thread evaluates its
 // cell's arrival time from Eq. 2 for every sample (they increase for sub-luminal chords), keeps
 // the bin it is filling in registers and adds the bin to global memory only when its arrival time
-// leaves the bin.
+// leaves the bin.  The FP64 pipe is the bound (on GB300 it runs at 1.6 % of the FP32 rate), so in a
+// warp whose lanes all walk a cell, the FP64 work of the few lanes that start a new bin is spread
+// over the warp by shuffles and the bin-edge tests run on the integer pipe (fp64_deposit_warp).
 #include <math.h>
 
 #include "rd_internal.cuh"

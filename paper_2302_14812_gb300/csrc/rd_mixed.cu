@@ -1,12 +1,13 @@
 // Mixed-precision deposit: FP32 Lienard-Wiechert field (Eq. 1) and FP32 accumulation, with the
 // arrival time (Eq. 2) kept FP64-accurate.
 //
-// Work item = (step chunk, block of 256 cells, particle), ordered by item_coords: consecutive CTAs
-// take one particle to a small group of cell blocks, then the next particle, so the CTAs resident
-// at one time reduce into the group's slice of the detector, which stays in L2, and each
-// particle's staged records come from DRAM once per group.
+// Work item = (step chunk, block of CPC cells, particle) with CPC = 64, 128 or 256 (the launch
+// shape; 256 by default), ordered by item_coords: consecutive CTAs take one particle to a small
+// group of cell blocks, then the next particle (odd groups in reverse particle order), so the CTAs
+// resident at one time reduce into the group's slice of the detector, which stays in L2, and each
+// particle's staged records come from DRAM about once per group.
 //
-// Each thread walks kMixedCells cells through the chunk; the per-sample constants (RecS) are read
+// Each thread walks NC cells (1 or 2) through the chunk; the per-sample constants (RecS) are read
 // once per sample from shared memory and serve all of them.  Per cell the walk carries the bin it
 // is filling (as an offset from the CTA's first field row) and the time f already spent in that
 // bin, in units of dt; a step adds the arrival-time increment
