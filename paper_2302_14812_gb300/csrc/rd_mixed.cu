@@ -40,7 +40,7 @@ struct Cells {
     float px[NC], py[NC], pz[NC];   // cell positions
     float f[NC];                    // time spent in the current bin, units of dt (0 <= f < W)
     float rpd[NC];                  // R_{k-1} + dt (far-field limit: 1/R_c)
-    float ec[NC];                   // far-field limit: |n_c|^2 - 1 of the rounded direction
+    float nlx[NC], nly[NC], nlz[NC];  // far-field limit: n_c - (its FP32 rounding in px, py, pz)
     float acc[6][NC];               // E xyz, B xyz of the current bin so far (weights in bins)
     float gp[6][NC];                // linear / quadratic interpolation: scaled field of the previous sample
     float gpp[6][NC];               // quadratic interpolation: scaled field two samples back ...
@@ -179,16 +179,18 @@ __device__ __forceinline__ void field_at(const RecS& r, float px, float py, floa
 
 // Far-field limit (RD_FARFIELD) at one cell, seen from the origin along n_c at R_c (n_c and
 // 1/R_c fixed per cell):
-//   t'_k - t'_{k-1} = dt (1 - n_c.vbar) = dt [g + |n_c - vbar|^2 - (|n_c|^2 - 1)] / 2   (Eq. 3)
+//   t'_k - t'_{k-1} = dt (1 - n_c.vbar) = dt [g + |n_c - vbar|^2] / 2   (Eq. 3, |n_c| = 1)
 //   E = S E',  S = 1/(kappa^2 R_c),  E' = Q [(n_c - beta)(-n_c.betadot/kappa) + betadot],  B = S n_c x E'
-// with kappa = 1 - beta.n_c = (gamma^-2 + |n_c - beta|^2 - (|n_c|^2 - 1))/2: the rounded direction is
-// not exactly of unit length, and its error ec = |n_c|^2 - 1 (~1e-7, fixed per cell) is taken out
-// of |n_c - beta|^2 so that kappa carries no per-cell bias.
-__device__ __forceinline__ void field_at_ff(const RecS& r, float nx, float ny, float nz, float invR, float ec,
-                                            Field& o)
+// with kappa = 1 - beta.n_c = (gamma^-2 + |n_c - beta|^2)/2.  n_c is held as its FP32 rounding
+// (nx, ny, nz) plus the rest (lx, ly, lz): the rounding is fixed per cell, and along the beam, where
+// n_c - beta is ~1e-3, it would bias kappa by ~5e-5 (the field by ~1.5e-4, as kappa^-3) on every
+// sample of the cell.  nx - beta_x is exact there (the two are within a factor of two), and adding
+// the rest restores n_c - beta to FP32 precision.
+__device__ __forceinline__ void field_at_ff(const RecS& r, float nx, float ny, float nz, float invR, float lx,
+                                            float ly, float lz, Field& o)
 {
-    const float bx = nx + r.nbx, by = ny + r.nby, bz = nz + r.nbz;      // n_c - beta
-    const float nb2 = fmaf(bx, bx, fmaf(by, by, fmaf(bz, bz, -ec)));
+    const float bx = (nx + r.nbx) + lx, by = (ny + r.nby) + ly, bz = (nz + r.nbz) + lz;   // n_c - beta
+    const float nb2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
     o.num = fmaf(bx, r.d2x, fmaf(by, r.d2y, fmaf(bz, r.d2z, nb2 + r.gd)));
     o.rden = 0.5f;
     const float kn = fmaf(nb2, -0.5f, r.nhig2);                         // -kappa
@@ -333,7 +335,7 @@ __device__ __forceinline__ void step(Cells<NC>& c, const RecS& r, const Consts& 
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         if (FF)
-            field_at_ff(r, c.px[j], c.py[j], c.pz[j], c.rpd[j], c.ec[j], o[j]);
+            field_at_ff(r, c.px[j], c.py[j], c.pz[j], c.rpd[j], c.nlx[j], c.nly[j], c.nlz[j], o[j]);
         else
             field_at(r, c.px[j], c.py[j], c.pz[j], c.rpd[j], C, o[j]);
         float t;
@@ -634,7 +636,7 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
         c.rpd[j] = 1e6f;
         c.px[j] = 1e6f;
         c.py[j] = c.pz[j] = 0.f;
-        c.ec[j] = 0.f;
+        c.nlx[j] = c.nly[j] = c.nlz[j] = 0.f;
         bo_end[j] = c.bo[j];
         f_end[j] = 0.f;
 #pragma unroll
@@ -676,8 +678,9 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
                     c.py[j] = (float)ncy;
                     c.pz[j] = (float)ncz;
                     c.rpd[j] = (float)(1.0 / Rc);
-                    const double ex = c.px[j], ey = c.py[j], ez = c.pz[j];
-                    c.ec[j] = (float)(((ex * ex + ey * ey) + ez * ez) - 1.0);
+                    c.nlx[j] = (float)(ncx - (double)c.px[j]);
+                    c.nly[j] = (float)(ncy - (double)c.py[j]);
+                    c.nlz[j] = (float)(ncz - (double)c.pz[j]);
                 } else {
                     c.rpd[j] = (float)Ra + P.dt_f;
                     c.px[j] = (float)cl.x;
@@ -702,7 +705,7 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
             Field o;
             float rtmp = c.rpd[j];
             if (FF)
-                field_at_ff(r0, c.px[j], c.py[j], c.pz[j], c.rpd[j], c.ec[j], o);
+                field_at_ff(r0, c.px[j], c.py[j], c.pz[j], c.rpd[j], c.nlx[j], c.nly[j], c.nlz[j], o);
             else
                 field_at(r0, c.px[j], c.py[j], c.pz[j], rtmp, C, o);
             float G[6];
@@ -717,7 +720,7 @@ __device__ __forceinline__ bool deposit_item(const DepositParams& P, int p, int 
                     const RecS r1 = rec[k_begin - 2];
                     float rtmp1 = c.rpd[j];
                     if (FF)
-                        field_at_ff(r1, c.px[j], c.py[j], c.pz[j], c.rpd[j], c.ec[j], o);
+                        field_at_ff(r1, c.px[j], c.py[j], c.pz[j], c.rpd[j], c.nlx[j], c.nly[j], c.nlz[j], o);
                     else
                         field_at(r1, c.px[j], c.py[j], c.pz[j], rtmp1, C, o);
                     scaled_field(o, G);

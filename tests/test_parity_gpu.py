@@ -140,6 +140,37 @@ def test_undulator_full_size_sampled_cells(precision):
     check(tr, det, precision, sel=sel)
 
 
+@pytest.mark.parametrize("mode", ["linear", "hold_prev", "quadratic", "farfield"])
+def test_variants_full_size_sampled_cells(mode):
+    """The interpolation variants and the far-field limit on the benchmark workload at full size:
+    the mixed path deposits the whole 128x128 x 2048 detector as the benchmark launches it, the
+    FP64 path a detector of the 6 sampled cells; both against the oracle on those cells."""
+    import torch
+    tr, det = W.config_undulator()
+    det.flags = {"linear": W.RD_NEAR | W.RD_FAR | W.RD_LINEAR,
+                 "hold_prev": W.RD_NEAR | W.RD_FAR | W.RD_HOLD_PREV,
+                 "quadratic": W.RD_NEAR | W.RD_FAR | W.RD_QUADRATIC,
+                 "farfield": W.RD_FAR | W.RD_FARFIELD}[mode]
+    sel = np.array([0, 127, 64 * 128 + 64, 5000, 128 * 127, 128 * 128 - 1], dtype=np.int32)
+    Eo, Bo, _ = oracle.deposit(tr, det, sel)
+    assert np.abs(Eo).max() > 0
+    x, u, q = (torch.from_numpy(a).cuda() for a in (tr.x, tr.u, tr.q))
+    d = rd.RadiationDetector.from_workload(det, "mixed")
+    d.deposit(x, u, q, tr.t0, tr.dt)
+    E, B = d.read("float32", "cuda")
+    st = d.stats()
+    d.close()
+    idx = torch.from_numpy(sel.astype(np.int64)).cuda()
+    E, B = E[idx].double().cpu().numpy(), B[idx].double().cpu().numpy()
+    assert st.device_errors == 0
+    assert parity_err(E, Eo) <= TOL["mixed"] and parity_err(B, Bo) <= TOL["mixed"], mode
+    d64 = rd.RadiationDetector.from_workload(det.subset(sel), "fp64")
+    d64.deposit(x, u, q, tr.t0, tr.dt)
+    E64, B64 = d64.read()
+    d64.close()
+    assert parity_err(E64, Eo) <= TOL["fp64"] and parity_err(B64, Bo) <= TOL["fp64"], mode
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_plasma_mirror_reduced(precision):
     """Plasma-mirror-like surface (a0 5, 20 harmonics, 10000 steps), 300 electrons, 48x48 plane
