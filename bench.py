@@ -144,6 +144,17 @@ class ClockSampler:
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        # the timed region starts once the sampler has written its first sample: its start-up
+        # (attaching to the driver) then does not fall inside the region
+        t_end = time.perf_counter() + 5.0
+        while time.perf_counter() < t_end and self.proc.poll() is None:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    break
+            except OSError:
+                pass
+            time.sleep(0.02)
         return self
 
     def __exit__(self, *exc):
